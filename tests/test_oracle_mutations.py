@@ -1,0 +1,84 @@
+"""Mutation checks: plant a plausible mistake in the oracle (on the CPU, by monkeypatching)
+and confirm that one of the pins fails.  This shows that the pins discriminate, i.e. that
+a dropped term, a wrong sign or a transposed operand in the oracle would not go unseen."""
+import numpy as np
+import pytest
+
+from oracle import hubbard as o
+import test_oracle_fd as tfd
+import test_oracle_hamiltonian as th
+import test_oracle_chefsi as tc
+
+
+def test_wrong_laplacian_weight_is_caught(monkeypatch):
+    good = o.fd_laplacian_weights
+
+    def bad(n0):
+        c0, c = good(n0)
+        c = c.copy()
+        c[1] = -c[1]                     # wrong sign of the p = 2 weight
+        return c0, c
+    monkeypatch.setattr(o, "fd_laplacian_weights", bad)
+    with pytest.raises(AssertionError):
+        tfd.test_weights_match_published_table()
+    with pytest.raises(AssertionError):
+        tfd.test_second_derivative_exact_on_polynomials(6)
+
+
+def test_wrong_bloch_phase_is_caught(monkeypatch):
+    good = o.bloch_shift
+
+    def bad(F, grid, axis, p):
+        grid2 = o.Grid(grid.n, grid.L, -grid.kpt, grid.n0)    # conjugated Bloch factor
+        return good(F, grid2, axis, p)
+    monkeypatch.setattr(o, "bloch_shift", bad)
+    with pytest.raises(AssertionError):
+        tfd.test_fourier_symbol_plane_and_bloch_waves((0.13, -0.27, 0.41))
+
+
+def test_transposed_hubbard_coefficients_are_caught(monkeypatch):
+    def bad_hubbard(self, X):
+        Y = np.zeros(X.shape, dtype=np.result_type(X, self.hub[0][1]))
+        for I, (idx, vals, U) in enumerate(self.hub):
+            M = self.hubbard_coefficients(I)
+            C = self.grid.dV * (vals.conj().T @ X[idx])
+            Y[idx] += vals @ (M.T @ C)        # literal D_mm' slot: transposed coefficients
+        return Y
+    monkeypatch.setattr(o.Hamiltonian, "hubbard", bad_hubbard)
+    fd, an = th.check_hubbard_derivative((0.3, -0.2, 0.25))
+    assert abs(fd - an) > 1e-6 * max(1.0, abs(an))
+
+
+def test_dropped_factor_two_in_hubbard_coefficients_is_caught(monkeypatch):
+    def bad_coef(self, I):
+        return 0.5 * self.hub[I][2] * (np.eye(5) - self.D[I])     # (delta - D), not (delta - 2D)
+    monkeypatch.setattr(o.Hamiltonian, "hubbard_coefficients", bad_coef)
+    fd, an = th.check_hubbard_derivative((0.0, 0.0, 0.0))
+    assert abs(fd - an) > 1e-6 * max(1.0, abs(an))
+
+
+def test_missing_volume_element_in_occupation_is_caught(monkeypatch):
+    good = o.occupation_matrices
+
+    def bad(ham, X, f, kweight=1.0):
+        return good(ham, X, f, kweight) / ham.grid.dV
+    monkeypatch.setattr(o, "occupation_matrices", bad)
+    with pytest.raises(AssertionError):
+        tc_kpt = (0.0, 0.0, 0.0)
+        th.test_occupation_identities_for_orbital_built_states(tc_kpt)
+
+
+def test_wrong_filter_recurrence_is_caught(monkeypatch):
+    def bad_filter(ham, X, m, a, b, a_low):
+        e, c = 0.5 * (b - a), 0.5 * (b + a)
+        sigma = e / (a_low - c)
+        tau = 2.0 / sigma
+        Y = (sigma / e) * (ham.apply(X) - c * X)
+        for _ in range(2, m + 1):
+            sigma_new = 1.0 / (tau - sigma)
+            Ynew = (2.0 * sigma_new / e) * (ham.apply(Y) - c * Y) - sigma_new * X   # dropped sigma
+            X, Y, sigma = Y, Ynew, sigma_new
+        return Y
+    monkeypatch.setattr(o, "chebyshev_filter", bad_filter)
+    with pytest.raises(AssertionError):
+        tc.test_filter_equals_chebyshev_polynomial_of_dense_H((0.0, 0.0, 0.0))
