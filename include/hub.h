@@ -1,0 +1,205 @@
+/*
+ * hub.h -- C ABI of the GB300 (sm_103a) library for real-space DFT+U
+ * Chebyshev-filtered subspace iteration (CheFSI).
+ *
+ * Paper: "Real-space Hubbard-corrected density functional theory" (arXiv 2507.23612).
+ *   Sec. II.A.1  Dudarev energy E_U (Eq. E_U), occupation matrix D (Eq. orbital_occup_ext),
+ *                Bloch-periodically mapped atomic orbitals.
+ *   Sec. II.A.2  Hubbard potential V_U (Eq. DerED and the V_U equation).
+ *   Sec. II.B    uniform grid, 2*n0-th order centred finite differences, Bloch-periodic
+ *                index wrap, trapezoidal quadrature, atom-by-atom projector integrals
+ *                "computed simultaneously", CheFSI with Pulay mixing of D.
+ *
+ * Conventions shared by every call
+ *   - Grid: orthogonal cell L_a = n_a h_a; node (i1,i2,i3) at (i1 h1, i2 h2, i3 h3);
+ *     grid functions are flattened x-fastest: g = i1 + n1*(i2 + n2*i3); Nd = n1 n2 n3.
+ *   - A block of ncol orbitals is column-major: element (g, j) at X[g + j*ld], ld >= Nd.
+ *   - Element type of X/Y/work is fixed by the handle: HUB_F64 -> double, HUB_F32 and
+ *     HUB_MIXED_BF16 -> float; with ncomplex = 1 it is the interleaved complex of that type
+ *     (re, im).  Occupation matrices, eigenvalues and energies are always double.
+ *   - Inner products carry the quadrature weight dV = h1 h2 h3: <u|v> = dV sum_g u_g^* v_g,
+ *     so Rayleigh-Ritz returns orbitals with dV X^H X = I.
+ *   - Ownership: array arguments marked "device" are caller-owned device memory (e.g.
+ *     torch tensors); "host" arrays are caller-owned host memory.  The handle owns only its
+ *     grid metadata, projector tables, occupation matrices and internal workspaces, all
+ *     released by hub_destroy.
+ *   - Streams: every call is ordered on the CUDA stream given at creation.  Calls that
+ *     return host values (eigenvalues, D, bounds, SCF results) synchronise that stream;
+ *     the others are asynchronous.
+ *   - Errors: every function returns 0 (HUB_OK) or a negative hub_status; hub_last_error
+ *     returns a message for the last failure on that handle.  Device-side checks (a
+ *     non-SPD Gram matrix, a non-finite value, a bounded wait that ran out) surface at the
+ *     next call that synchronises.
+ */
+#ifndef HUB_H
+#define HUB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hub_ctx* hub_t;
+
+typedef enum {
+    HUB_OK = 0,
+    HUB_EINVAL = -1,      /* bad argument: size, pointer, alignment, state order */
+    HUB_ENOMEM = -2,      /* device or host allocation failed */
+    HUB_ECUDA = -3,       /* a CUDA runtime call failed */
+    HUB_ENOTSPD = -4,     /* Cholesky of the Gram matrix broke down */
+    HUB_ENONFINITE = -5,  /* a NaN or Inf appeared in a result */
+    HUB_ENOCONV = -6,     /* SCF or eigensolver did not converge within its limit */
+    HUB_ETIMEOUT = -7     /* a bounded device wait ran out (the kernel returned early) */
+} hub_status;
+
+typedef enum {
+    HUB_F64 = 0,          /* every step in double */
+    HUB_F32 = 1,          /* filter and Rayleigh-Ritz products in float; dense steps double */
+    HUB_MIXED_BF16 = 2    /* float filter, BF16 tensor-core X^T H X and X Q with float
+                             accumulation; Gram, Cholesky, eigensolve, D and E_U double */
+} hub_prec;
+
+/* Create a handle for one grid, one Bloch wavevector and one precision.
+ *   n1,n2,n3      grid points per axis (each >= 1)
+ *   L1,L2,L3      cell side lengths in bohr (h_a = L_a / n_a)
+ *   fd_half_order n0 of the 2*n0-th order centred Laplacian (Sec. II.B); 1 <= n0 <= 8
+ *   ncomplex      0: real orbitals (Gamma point, kpt ignored); 1: complex Bloch orbitals
+ *   kpt           Bloch wavevector (bohr^-1, Cartesian), host [3]; NULL means Gamma.
+ *                 Wrap convention: psi(x + L_a e_a) = exp(i k_a L_a) psi(x).
+ *   prec          hub_prec
+ *   cuda_stream   cudaStream_t to order all work on (NULL = legacy default stream)
+ * Errors: HUB_EINVAL (sizes), HUB_ENOMEM, HUB_ECUDA. */
+int hub_create_grid(hub_t* out, int n1, int n2, int n3, double L1, double L2, double L3,
+                    int fd_half_order, int ncomplex, const double* kpt, int prec,
+                    void* cuda_stream);
+
+/* Release every resource of the handle (synchronises its stream).  NULL is accepted. */
+int hub_destroy(hub_t h);
+
+/* Message of the last error on this handle (static string owned by the handle). */
+const char* hub_last_error(hub_t h);
+
+/* Local effective potential V_eff (Ha) on the grid, device double [Nd]; copied into the
+ * handle (and rounded to float for HUB_F32 / HUB_MIXED_BF16). */
+int hub_set_veff(hub_t h, const double* veff_dev);
+
+/* Atoms and their localized functions (Sec. II.A.1 Bloch-mapped orbitals; Sec. II.B: the
+ * Hubbard orbitals are handled like nonlocal pseudopotential projectors).  All host arrays.
+ *   natoms           number of atoms
+ *   pos              [natoms*3] Cartesian positions (bohr); any value, images are summed
+ *   kb_nchan         [natoms] KB channels per atom (0 allowed)
+ *   kb_l, kb_rs, kb_gamma   [sum kb_nchan] per channel: angular momentum l (0..2), Gaussian
+ *                    width rs (bohr) of R(r) = N r^l exp(-r^2/(2 rs^2)), energy gamma (Ha)
+ *   kb_rc            [natoms] KB cutoff radius (bohr)
+ *   hub_l            [natoms] -1 = no Hubbard shell, else l (only 2 is supported)
+ *   hub_rs, hub_rc, hub_U  [natoms] Hubbard radial width (bohr), cutoff (bohr), U (Ha)
+ * Every localized function is radial(|x - R - T|) * real Y_lm (orthonormal, m = -l..l, no
+ * Condon-Shortley sign) summed over lattice images T within the cutoff, with Bloch phase
+ * exp(i k.T).  The tables are built on the device.  Resets the occupation matrices to 0.
+ * Errors: HUB_EINVAL (l out of range, rc <= 0, NULL pointers with nonzero counts). */
+int hub_set_atoms_projectors(hub_t h, int natoms, const double* pos,
+                             const int* kb_nchan, const int* kb_l, const double* kb_rs,
+                             const double* kb_gamma, const double* kb_rc,
+                             const int* hub_l, const double* hub_rs, const double* hub_rc,
+                             const double* hub_U);
+
+/* Number of atoms that carry a Hubbard shell (the leading dimension of D arrays). */
+int hub_num_hubbard_atoms(hub_t h, int* nhub);
+
+/* Occupation matrices D^I of one spin channel (spin 0 or 1), host double
+ * [nhub*5*5] row-major per atom (D_re; D_im is NULL at Gamma or a host array of the same
+ * shape).  Sets the Hubbard coefficients M_I = (U_I/2)(I - 2 D_I) used by hub_apply_H for
+ * that spin (Eq. DerED; coefficient of phi_m' is sum_m M_m'm <phi_m|psi>). */
+int hub_set_occupation_matrix(hub_t h, int spin, const double* D_re, const double* D_im);
+
+/* Y = H X for ncol columns (device, column-major, leading dimension ld):
+ *   H = -1/2 Lap_h + V_eff + sum_I sum_p gamma_Ip |chi_Ip><chi_Ip|
+ *       + sum_I sum_mm' (U_I/2)(delta_mm' - 2 D_m'm) |phi_Im'><phi_Im|
+ * X and Y must not overlap.  Errors: HUB_EINVAL (ncol < 0, ld < Nd, state not set). */
+int hub_apply_H(hub_t h, int spin, const void* X, void* Y, int ncol, int ld);
+
+/* Chebyshev filter in place: X <- p_m(H) X with
+ *   p_m(t) = T_m((t - c)/e) / T_m((a_low - c)/e),  e = (b - a)/2,  c = (b + a)/2,
+ * evaluated by the scaled three-term recurrence (CheFSI, Sec. II.B).  Requires
+ * a_low < a < b.  work: device scratch of >= ld*ncol elements, or NULL to use a buffer
+ * owned by the handle (allocated on first use).  Errors: HUB_EINVAL. */
+int hub_chefsi_filter(hub_t h, int spin, void* X, int ncol, int ld, int degree,
+                      double a, double b, double a_low, void* work);
+
+/* Cholesky Rayleigh-Ritz in place (CheFSI, Sec. II.B):
+ *   S = <X|X> = L L^H;  H^ = L^-1 <X|H|X> L^-H;  H^ = V diag(eig) V^H;  X <- X L^-H V.
+ * eig_host: host double [ncol], ascending.  work: device scratch >= ld*ncol elements or
+ * NULL (handle-owned).  Real orbitals only (ncomplex = 0).
+ * Errors: HUB_ENOTSPD (X rank-deficient), HUB_ENOCONV (Jacobi sweep limit),
+ * HUB_ETIMEOUT, HUB_EINVAL. */
+int hub_rayleigh_ritz(hub_t h, int spin, void* X, int ncol, int ld, double* eig_host,
+                      void* work);
+
+/* Occupation matrices and Hubbard energy of one (spin, k) block (Eq. orbital_occup_ext,
+ * Eq. E_U):  D^I_mm' = kweight sum_n f_n <psi_n|phi_m'><phi_m|psi_n>,
+ *            EU = sum_I (U_I/2) Tr(D^I - D^I D^I)   (of this D alone).
+ * f_host: host double [ncol].  D_re_out: host double [nhub*25] (overwritten); D_im_out:
+ * NULL or host [nhub*25] (zeros at Gamma); EU_out: NULL or host double.  Synchronises. */
+int hub_occupation(hub_t h, int spin, const void* X, int ncol, int ld, const double* f_host,
+                   double kweight, double* D_re_out, double* D_im_out, double* EU_out);
+
+/* k-step Lanczos from the device vector v0 [Nd] (handle element type): returns the
+ * smallest Ritz value and the largest Ritz value plus |beta_k| (the CheFSI bound
+ * estimate).  1 <= steps <= 64.  Synchronises. */
+int hub_lanczos_bound(hub_t h, int spin, int steps, const void* v0, double* lo_out,
+                      double* up_out);
+
+/* ---------------------------------------------------------------------------------
+ * SCF driver with a fixed local potential (the Hamiltonian depends on the orbitals only
+ * through D; D is updated every iteration and Pulay-mixed, Sec. II.B last paragraph).
+ * Per iteration and spin: filter (bounds from the previous Rayleigh-Ritz; Lanczos and
+ * first_passes filter+RR passes in the first iteration), Rayleigh-Ritz; then Fermi-Dirac
+ * occupations with one chemical potential; D_out; energy
+ *   E = sum f eig - sum_I Tr(M_in D_out) + E_U(D_out) - kT S;
+ * then Pulay mixing of D.  Converged when |dE|/natoms < tol_e_atom in two consecutive
+ * iterations and max|D_out - D_in| < tol_D.
+ * --------------------------------------------------------------------------------- */
+typedef struct {
+    int nspin;            /* 1 (every state holds 2 electrons) or 2 (one each) */
+    int ncol;             /* orbitals per spin */
+    int ld;               /* leading dimension of the X blocks */
+    int degree;           /* Chebyshev degree */
+    int max_iter;
+    int first_passes;     /* filter+RR passes in the first iteration */
+    int lanczos_steps;
+    int pulay_history;
+    int natoms;           /* for the per-atom energy tolerance */
+    double pulay_beta;
+    double kT;            /* Ha; 0 = step occupations */
+    double n_elec;
+    double tol_e_atom;    /* Ha/atom */
+    double tol_D;
+} hub_scf_params;
+
+typedef struct {
+    int iter;             /* iterations done */
+    int converged;        /* 1 once the criterion above holds */
+    double E, E_band, E_U, dE, dD, mu;
+} hub_scf_result;
+
+/* Start an SCF: X[nspin] device blocks (ld*ncol each; updated in place every iteration),
+ * v0[nspin] device Lanczos start vectors [Nd], D0 host [nspin*nhub*25] starting D. */
+int hub_scf_begin(hub_t h, const hub_scf_params* p, void* const* X, const void* const* v0,
+                  const double* D0);
+/* One SCF iteration; fills *res.  Synchronises.  Returns HUB_OK also when not converged. */
+int hub_scf_iterate(hub_t h, hub_scf_result* res);
+/* Run iterations until converged or max_iter; HUB_ENOCONV if max_iter was reached. */
+int hub_scf_run(hub_t h, hub_scf_result* res);
+/* Results of the last iteration: eig/occ host [nspin*ncol] (may be NULL),
+ * D_out host [nspin*nhub*25] (may be NULL). */
+int hub_scf_get(hub_t h, double* eig, double* occ, double* D_out);
+
+/* Library build information: writes a short string (arch, version) into buf. */
+int hub_version(char* buf, int len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HUB_H */

@@ -1,0 +1,247 @@
+"""ctypes binding of the hub C ABI (include/hub.h): argument marshalling only."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HUB_F64, HUB_F32, HUB_MIXED_BF16 = 0, 1, 2
+STATUS_NAMES = {0: "HUB_OK", -1: "HUB_EINVAL", -2: "HUB_ENOMEM", -3: "HUB_ECUDA",
+                -4: "HUB_ENOTSPD", -5: "HUB_ENONFINITE", -6: "HUB_ENOCONV", -7: "HUB_ETIMEOUT"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "libhub.so")
+
+
+class HubError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class scf_params(C.Structure):
+    _fields_ = [("nspin", C.c_int), ("ncol", C.c_int), ("ld", C.c_int), ("degree", C.c_int),
+                ("max_iter", C.c_int), ("first_passes", C.c_int), ("lanczos_steps", C.c_int),
+                ("pulay_history", C.c_int), ("natoms", C.c_int), ("pulay_beta", C.c_double),
+                ("kT", C.c_double), ("n_elec", C.c_double), ("tol_e_atom", C.c_double),
+                ("tol_D", C.c_double)]
+
+
+class scf_result(C.Structure):
+    _fields_ = [("iter", C.c_int), ("converged", C.c_int), ("E", C.c_double),
+                ("E_band", C.c_double), ("E_U", C.c_double), ("dE", C.c_double),
+                ("dD", C.c_double), ("mu", C.c_double)]
+
+
+_P, _I, _D = C.c_void_p, C.c_int, C.c_double
+_PD, _PI = C.POINTER(C.c_double), C.POINTER(C.c_int)
+_SIGS = {
+    "hub_create_grid": [C.POINTER(C.c_void_p), _I, _I, _I, _D, _D, _D, _I, _I, _PD, _I, _P],
+    "hub_destroy": [_P],
+    "hub_last_error": [_P],
+    "hub_set_veff": [_P, _P],
+    "hub_set_atoms_projectors": [_P, _I, _PD, _PI, _PI, _PD, _PD, _PD, _PI, _PD, _PD, _PD],
+    "hub_num_hubbard_atoms": [_P, _PI],
+    "hub_set_occupation_matrix": [_P, _I, _PD, _PD],
+    "hub_apply_H": [_P, _I, _P, _P, _I, _I],
+    "hub_chefsi_filter": [_P, _I, _P, _I, _I, _I, _D, _D, _D, _P],
+    "hub_rayleigh_ritz": [_P, _I, _P, _I, _I, _PD, _P],
+    "hub_occupation": [_P, _I, _P, _I, _I, _PD, _D, _PD, _PD, _PD],
+    "hub_lanczos_bound": [_P, _I, _I, _P, _PD, _PD],
+    "hub_scf_begin": [_P, C.POINTER(scf_params), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), _PD],
+    "hub_scf_iterate": [_P, C.POINTER(scf_result)],
+    "hub_scf_run": [_P, C.POINTER(scf_result)],
+    "hub_scf_get": [_P, _PD, _PD, _PD],
+    "hub_version": [C.c_char_p, _I],
+}
+
+
+def load_library(path: str | None = None) -> C.CDLL:
+    """Load libhub.so (raises OSError if it is missing: there is no fallback)."""
+    global _LIB
+    if _LIB is not None and path is None:
+        return _LIB
+    p = path or library_path()
+    if not os.path.exists(p):
+        raise OSError(f"libhub.so not found at {p}; build it with "
+                      "`python -m paper_2507_23612_gb300.build`")
+    lib = C.CDLL(p)
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_char_p if name == "hub_last_error" else C.c_int
+    if path is None:
+        _LIB = lib
+    return lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_PD)
+
+
+def _iptr(a: np.ndarray):
+    return a.ctypes.data_as(_PI)
+
+
+def _tptr(t):
+    """Device pointer of a torch CUDA tensor (must be contiguous)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Hub:
+    """One grid / k-point / precision handle (hub_create_grid ... hub_destroy)."""
+
+    def __init__(self, n, L, fd_half_order: int = 6, kpt=None, complex_: bool = False,
+                 prec: int = HUB_F64, stream=None):
+        import torch
+        self.lib = load_library()
+        self.n = tuple(int(v) for v in n)
+        self.Nd = self.n[0] * self.n[1] * self.n[2]
+        self.prec = prec
+        self.complex = bool(complex_)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        k = np.ascontiguousarray(kpt if kpt is not None else [0.0, 0.0, 0.0], dtype=np.float64)
+        rc = self.lib.hub_create_grid(C.byref(h), *self.n, *[float(x) for x in L], int(fd_half_order),
+                                      int(self.complex), _dptr(k), int(prec),
+                                      C.c_void_p(stream.cuda_stream))
+        if rc != 0:
+            raise HubError(rc, "hub_create_grid failed")
+        self.h = h
+        self.nhub = 0
+
+    # ------------------------------------------------------------------ helpers
+    def _check(self, rc, what):
+        if rc != 0:
+            msg = self.lib.hub_last_error(self.h)
+            raise HubError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    @property
+    def dtype(self):
+        import torch
+        if self.complex:
+            return torch.complex128 if self.prec == HUB_F64 else torch.complex64
+        return torch.float64 if self.prec == HUB_F64 else torch.float32
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hub_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ setup
+    def set_veff(self, veff):
+        self._check(self.lib.hub_set_veff(self.h, _tptr(veff)), "hub_set_veff")
+
+    def set_atoms(self, atoms):
+        """atoms: objects with pos, kb_l, kb_rs, kb_gamma, kb_rc, hub_l, hub_rs, hub_rc, hub_U."""
+        nat = len(atoms)
+        pos = np.ascontiguousarray([a.pos for a in atoms], dtype=np.float64).reshape(-1)
+        nch = np.ascontiguousarray([len(a.kb_l) for a in atoms], dtype=np.int32)
+        kb_l = np.ascontiguousarray([l for a in atoms for l in a.kb_l] or [0], dtype=np.int32)
+        kb_rs = np.ascontiguousarray([r for a in atoms for r in a.kb_rs] or [1.0], dtype=np.float64)
+        kb_g = np.ascontiguousarray([g for a in atoms for g in a.kb_gamma] or [0.0], dtype=np.float64)
+        kb_rc = np.ascontiguousarray([a.kb_rc for a in atoms], dtype=np.float64)
+        hl = np.ascontiguousarray([a.hub_l for a in atoms], dtype=np.int32)
+        hrs = np.ascontiguousarray([a.hub_rs for a in atoms], dtype=np.float64)
+        hrc = np.ascontiguousarray([a.hub_rc for a in atoms], dtype=np.float64)
+        hU = np.ascontiguousarray([a.hub_U for a in atoms], dtype=np.float64)
+        self._check(self.lib.hub_set_atoms_projectors(
+            self.h, nat, _dptr(pos), _iptr(nch), _iptr(kb_l), _dptr(kb_rs), _dptr(kb_g),
+            _dptr(kb_rc), _iptr(hl), _dptr(hrs), _dptr(hrc), _dptr(hU)), "hub_set_atoms_projectors")
+        n = C.c_int()
+        self._check(self.lib.hub_num_hubbard_atoms(self.h, C.byref(n)), "hub_num_hubbard_atoms")
+        self.nhub = n.value
+
+    def set_occupation_matrix(self, spin: int, D, D_im=None):
+        Dr = np.ascontiguousarray(np.real(D), dtype=np.float64).reshape(-1)
+        Di = None if D_im is None else np.ascontiguousarray(D_im, dtype=np.float64).reshape(-1)
+        if D_im is None and np.iscomplexobj(D):
+            Di = np.ascontiguousarray(np.imag(D), dtype=np.float64).reshape(-1)
+        self._check(self.lib.hub_set_occupation_matrix(self.h, spin, _dptr(Dr),
+                                                       None if Di is None else _dptr(Di)),
+                    "hub_set_occupation_matrix")
+
+    # ------------------------------------------------------------------ hot path
+    def apply_H(self, spin: int, X, Y):
+        ncol, ld = X.shape
+        self._check(self.lib.hub_apply_H(self.h, spin, _tptr(X), _tptr(Y), ncol, ld), "hub_apply_H")
+
+    def chefsi_filter(self, spin: int, X, degree: int, a: float, b: float, a_low: float, work=None):
+        ncol, ld = X.shape
+        self._check(self.lib.hub_chefsi_filter(self.h, spin, _tptr(X), ncol, ld, degree, a, b, a_low,
+                                               _tptr(work)), "hub_chefsi_filter")
+
+    def rayleigh_ritz(self, spin: int, X, work=None) -> np.ndarray:
+        ncol, ld = X.shape
+        eig = np.zeros(ncol)
+        self._check(self.lib.hub_rayleigh_ritz(self.h, spin, _tptr(X), ncol, ld, _dptr(eig),
+                                               _tptr(work)), "hub_rayleigh_ritz")
+        return eig
+
+    def occupation(self, spin: int, X, f, kweight: float = 1.0):
+        ncol, ld = X.shape
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        Dr = np.zeros((max(self.nhub, 1), 5, 5))
+        Di = np.zeros_like(Dr)
+        eu = C.c_double()
+        self._check(self.lib.hub_occupation(self.h, spin, _tptr(X), ncol, ld, _dptr(f), kweight,
+                                            _dptr(Dr), _dptr(Di), C.byref(eu)), "hub_occupation")
+        return Dr[:self.nhub], Di[:self.nhub], eu.value
+
+    def lanczos_bound(self, spin: int, steps: int, v0):
+        lo, up = C.c_double(), C.c_double()
+        self._check(self.lib.hub_lanczos_bound(self.h, spin, steps, _tptr(v0), C.byref(lo), C.byref(up)),
+                    "hub_lanczos_bound")
+        return lo.value, up.value
+
+    # ------------------------------------------------------------------ SCF driver
+    def scf_begin(self, params: scf_params, Xs, v0s, D0):
+        self._scf_keep = (list(Xs), list(v0s))
+        xa = (C.c_void_p * len(Xs))(*[t.data_ptr() for t in Xs])
+        va = (C.c_void_p * len(v0s))(*[t.data_ptr() for t in v0s])
+        D0 = np.ascontiguousarray(D0, dtype=np.float64).reshape(-1)
+        self._scf_D0 = D0
+        self._check(self.lib.hub_scf_begin(self.h, C.byref(params), xa, va, _dptr(D0)), "hub_scf_begin")
+        self._scf_params = params
+
+    def scf_iterate(self) -> dict:
+        r = scf_result()
+        self._check(self.lib.hub_scf_iterate(self.h, C.byref(r)), "hub_scf_iterate")
+        return {k: getattr(r, k) for k, _ in scf_result._fields_}
+
+    def scf_run(self) -> dict:
+        r = scf_result()
+        rc = self.lib.hub_scf_run(self.h, C.byref(r))
+        out = {k: getattr(r, k) for k, _ in scf_result._fields_}
+        if rc not in (0, -6):
+            self._check(rc, "hub_scf_run")
+        out["status"] = rc
+        return out
+
+    def scf_get(self):
+        p = self._scf_params
+        eig = np.zeros(p.nspin * p.ncol)
+        occ = np.zeros_like(eig)
+        D = np.zeros(p.nspin * max(self.nhub, 1) * 25)
+        self._check(self.lib.hub_scf_get(self.h, _dptr(eig), _dptr(occ), _dptr(D)), "hub_scf_get")
+        return (eig.reshape(p.nspin, p.ncol), occ.reshape(p.nspin, p.ncol),
+                D[:p.nspin * self.nhub * 25].reshape(p.nspin, self.nhub, 5, 5))

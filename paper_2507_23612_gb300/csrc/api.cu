@@ -1,0 +1,614 @@
+// C ABI of the hub library (declared in include/hub.h): handle lifecycle, H application,
+// Chebyshev filter, Rayleigh-Ritz, occupation matrices, Lanczos bounds and the SCF driver.
+// Host code here only orchestrates: every step on grid-sized data runs in this library's
+// kernels.  The SCF driver's scalar work (Fermi level bisection over the eigenvalues, Pulay
+// mixing of the 25-entry D matrices) runs on the host.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "hub_internal.cuh"
+
+namespace hub {
+
+int fail(hub_t h, int code, const std::string& msg) {
+    if (h) h->last_error = msg;
+    return code;
+}
+
+int ensure(hub_t h, void** p, size_t* have, size_t need) {
+    if (*have >= need && *p) return HUB_OK;
+    if (*p) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(*p);
+        *p = nullptr;
+        *have = 0;
+    }
+    if (need == 0) return HUB_OK;
+    cudaError_t e = cudaMalloc(p, need);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(h, HUB_ENOMEM, std::string("cudaMalloc of workspace failed: ") + cudaGetErrorString(e));
+    }
+    *have = need;
+    return HUB_OK;
+}
+
+int check_flags(hub_t h) {
+    int f[8];
+    HUB_CUDA_TRY(h, cudaMemcpyAsync(f, h->d_flags, sizeof(f), cudaMemcpyDeviceToHost, h->stream));
+    HUB_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    bool any = false;
+    for (int i = 0; i < 8; ++i) any |= f[i] != 0;
+    if (!any) return HUB_OK;
+    HUB_CUDA_TRY(h, cudaMemsetAsync(h->d_flags, 0, 8 * sizeof(int), h->stream));
+    HUB_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (f[FLAG_TIMEOUT]) return fail(h, HUB_ETIMEOUT, "a bounded device wait ran out");
+    if (f[FLAG_NOTSPD]) return fail(h, HUB_ENOTSPD, "Gram matrix is not positive definite");
+    if (f[FLAG_NONFINITE]) return fail(h, HUB_ENONFINITE, "non-finite value");
+    if (f[FLAG_NOCONV]) return fail(h, HUB_ENOCONV, "Jacobi eigensolver hit its sweep limit");
+    return HUB_OK;
+}
+
+static void fd_weights(int n0, double* c0, double* c) {
+    // centred second-derivative weights of order 2 n0:
+    // c_p = 2 (-1)^{p+1} (n0!)^2 / (p^2 (n0-p)! (n0+p)!),  c_0 = -2 sum 1/p^2
+    auto fact = [](int k) { double r = 1.0; for (int i = 2; i <= k; ++i) r *= i; return r; };
+    double s = 0.0;
+    for (int p = 1; p <= n0; ++p) {
+        c[p - 1] = 2.0 * ((p % 2) ? 1.0 : -1.0) * fact(n0) * fact(n0) / ((double)p * p * fact(n0 - p) * fact(n0 + p));
+        s += 1.0 / ((double)p * p);
+    }
+    *c0 = -2.0 * s;
+}
+
+int apply_H_internal(hub_t h, int spin, const void* X, int ld, void* Y, int ncol, double alpha,
+                     double shift, const void* Yprev, double beta) {
+    int rc;
+    if (h->proj.nsites > 0)
+        if ((rc = launch_gather(h, X, ncol, ld, spin, true))) return rc;
+    StencilArgs a{};
+    a.Y = X;
+    a.Yprev = Yprev;
+    a.Yout = Y;
+    a.V = h->d_veff;
+    a.n1 = h->n1; a.n2 = h->n2; a.n3 = h->n3; a.ld = ld; a.ncol = ncol;
+    a.n0 = h->n0;
+    double c0, c[kMaxHalf];
+    fd_weights(h->n0, &c0, c);
+    double inv2 = 0.0;
+    for (int ax = 0; ax < 3; ++ax) {
+        const double ih2 = 1.0 / (h->h[ax] * h->h[ax]);
+        inv2 += ih2;
+        for (int p = 0; p < h->n0; ++p) a.w[ax][p] = alpha * (-0.5) * c[p] * ih2;
+        a.phase[ax][0] = std::cos(h->kpt[ax] * h->L[ax]);
+        a.phase[ax][1] = std::sin(h->kpt[ax] * h->L[ax]);
+    }
+    a.center = alpha * (-0.5 * c0 * inv2 - shift);
+    a.alpha = alpha;
+    a.beta = beta;
+    if ((rc = launch_stencil(h, a))) return rc;
+    if (h->proj.nsites > 0)
+        if ((rc = launch_scatter(h, Y, ncol, ld, alpha))) return rc;
+    return HUB_OK;
+}
+
+static size_t elem_bytes(hub_t h) { return (size_t)h->esize * (h->cplx ? 2 : 1); }
+
+static int check_block(hub_t h, int spin, const void* X, int ncol, int ld) {
+    if (!h) return HUB_EINVAL;
+    if (spin < 0 || spin > 1) return fail(h, HUB_EINVAL, "spin must be 0 or 1");
+    if (ncol < 0) return fail(h, HUB_EINVAL, "ncol must be >= 0");
+    if (ncol > 0 && !X) return fail(h, HUB_EINVAL, "NULL block");
+    if ((long)ld < h->Nd) return fail(h, HUB_EINVAL, "ld must be >= n1*n2*n3");
+    if (!h->veff_set) return fail(h, HUB_EINVAL, "hub_set_veff has not been called");
+    if (!h->atoms_set) return fail(h, HUB_EINVAL, "hub_set_atoms_projectors has not been called");
+    return HUB_OK;
+}
+
+// ---------------------------------------------------------------------------- SCF state
+struct ScfState {
+    hub_scf_params p{};
+    std::vector<void*> X;
+    std::vector<const void*> v0;
+    std::vector<double> D_in, D_out, eig, occ;
+    std::vector<std::vector<double>> hx, hr;   // Pulay history of inputs and residuals
+    double bounds[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    bool have_bounds[2] = {false, false};
+    int iter = 0;
+    int small = 0;
+    bool have_prev = false;
+    double E_prev = 0.0;
+    hub_scf_result last{};
+};
+
+}  // namespace hub
+
+using namespace hub;
+
+extern "C" {
+
+int hub_version(char* buf, int len) {
+    const char* s = "hub 0.1 (sm_103a; real-space DFT+U CheFSI)";
+    if (!buf || len <= 0) return HUB_EINVAL;
+    std::strncpy(buf, s, (size_t)len - 1);
+    buf[len - 1] = 0;
+    return HUB_OK;
+}
+
+int hub_create_grid(hub_t* out, int n1, int n2, int n3, double L1, double L2, double L3,
+                    int fd_half_order, int ncomplex, const double* kpt, int prec, void* cuda_stream) {
+    if (!out) return HUB_EINVAL;
+    *out = nullptr;
+    if (n1 < 1 || n2 < 1 || n3 < 1 || !(L1 > 0) || !(L2 > 0) || !(L3 > 0)) return HUB_EINVAL;
+    if (fd_half_order < 1 || fd_half_order > 6) return HUB_EINVAL;
+    if (prec < HUB_F64 || prec > HUB_MIXED_BF16) return HUB_EINVAL;
+    if ((long)n1 * n2 * n3 > 2000000000L) return HUB_EINVAL;
+    hub_t h = new (std::nothrow) hub_ctx();
+    if (!h) return HUB_ENOMEM;
+    h->n1 = n1; h->n2 = n2; h->n3 = n3;
+    h->Nd = (int64_t)n1 * n2 * n3;
+    h->L[0] = L1; h->L[1] = L2; h->L[2] = L3;
+    h->h[0] = L1 / n1; h->h[1] = L2 / n2; h->h[2] = L3 / n3;
+    h->dV = h->h[0] * h->h[1] * h->h[2];
+    h->n0 = fd_half_order;
+    h->cplx = ncomplex ? 1 : 0;
+    if (kpt && h->cplx) { h->kpt[0] = kpt[0]; h->kpt[1] = kpt[1]; h->kpt[2] = kpt[2]; }
+    h->prec = prec;
+    h->esize = prec == HUB_F64 ? 8 : 4;
+    h->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_flags, 8 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_bar, 4 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_scal, 4096 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_veff, (size_t)h->Nd * h->esize);
+    if (e == cudaSuccess) e = cudaMemset(h->d_flags, 0, 8 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->d_scal, 0, 4096 * sizeof(double));
+    if (e != cudaSuccess) {
+        hub_destroy(h);
+        return e == cudaErrorMemoryAllocation ? HUB_ENOMEM : HUB_ECUDA;
+    }
+    *out = h;
+    return HUB_OK;
+}
+
+int hub_destroy(hub_t h) {
+    if (!h) return HUB_OK;
+    cudaStreamSynchronize(h->stream);
+    free_table(h->proj);
+    void* ptrs[] = {h->d_veff, h->d_work, h->d_work2, h->d_part, h->d_C, h->d_W, h->d_small,
+                    h->d_gpart, h->d_bf16, h->d_aux, h->d_flags, h->d_bar, h->d_scal};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete h->scf;
+    delete h;
+    return HUB_OK;
+}
+
+const char* hub_last_error(hub_t h) {
+    if (!h) return "NULL handle";
+    return h->last_error.c_str();
+}
+
+int hub_set_veff(hub_t h, const double* veff_dev) {
+    if (!h) return HUB_EINVAL;
+    if (!veff_dev) return fail(h, HUB_EINVAL, "NULL potential");
+    int rc = launch_copy_convert_veff(h, veff_dev, h->d_veff);
+    if (rc) return rc;
+    h->veff_set = true;
+    return HUB_OK;
+}
+
+int hub_set_atoms_projectors(hub_t h, int natoms, const double* pos, const int* kb_nchan,
+                             const int* kb_l, const double* kb_rs, const double* kb_gamma,
+                             const double* kb_rc, const int* hub_l, const double* hub_rs,
+                             const double* hub_rc, const double* hub_U) {
+    if (!h) return HUB_EINVAL;
+    if (natoms < 0) return fail(h, HUB_EINVAL, "natoms < 0");
+    if (natoms > 0 && (!pos || !kb_nchan || !kb_rc || !hub_l || !hub_rs || !hub_rc || !hub_U))
+        return fail(h, HUB_EINVAL, "NULL per-atom array");
+    int nch = 0;
+    for (int a = 0; a < natoms; ++a) nch += kb_nchan[a];
+    if (nch > 0 && (!kb_l || !kb_rs || !kb_gamma)) return fail(h, HUB_EINVAL, "NULL KB channel array");
+    int rc = build_tables(h, natoms, pos, kb_nchan, kb_l, kb_rs, kb_gamma, kb_rc, hub_l, hub_rs,
+                          hub_rc, hub_U);
+    if (rc) return rc;
+    h->atoms_set = true;
+    h->D_set[0] = h->D_set[1] = false;
+    return HUB_OK;
+}
+
+int hub_num_hubbard_atoms(hub_t h, int* nhub) {
+    if (!h || !nhub) return HUB_EINVAL;
+    *nhub = h->proj.nhub;
+    return HUB_OK;
+}
+
+int hub_set_occupation_matrix(hub_t h, int spin, const double* D_re, const double* D_im) {
+    if (!h) return HUB_EINVAL;
+    if (spin < 0 || spin > 1) return fail(h, HUB_EINVAL, "spin must be 0 or 1");
+    if (!h->atoms_set) return fail(h, HUB_EINVAL, "hub_set_atoms_projectors has not been called");
+    const int nh = h->proj.nhub;
+    if (nh == 0) return HUB_OK;
+    if (!D_re) return fail(h, HUB_EINVAL, "NULL D");
+    const int cw = h->cplx ? 2 : 1;
+    std::vector<double>& M = h->proj.h_M[spin];
+    M.assign((size_t)nh * 25 * cw, 0.0);
+    for (int i = 0; i < nh; ++i) {
+        const double U = h->proj.h_U[i];
+        for (int p = 0; p < 5; ++p)
+            for (int m = 0; m < 5; ++m) {
+                // M_pm = (U/2)(delta_pm - 2 D_pm); the transform applies W_p = sum_m M_pm C_m
+                const size_t q = (size_t)i * 25 + p * 5 + m;
+                M[q * cw] = 0.5 * U * ((p == m ? 1.0 : 0.0) - 2.0 * D_re[q]);
+                if (cw == 2) M[q * cw + 1] = 0.5 * U * (-2.0 * (D_im ? D_im[q] : 0.0));
+            }
+    }
+    HUB_CUDA_TRY(h, cudaMemcpyAsync(h->proj.d_M[spin], M.data(), M.size() * sizeof(double),
+                                    cudaMemcpyHostToDevice, h->stream));
+    HUB_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->D_set[spin] = true;
+    return HUB_OK;
+}
+
+int hub_apply_H(hub_t h, int spin, const void* X, void* Y, int ncol, int ld) {
+    int rc = check_block(h, spin, X, ncol, ld);
+    if (rc) return rc;
+    if (ncol > 0 && !Y) return fail(h, HUB_EINVAL, "NULL output");
+    if (ncol == 0) return HUB_OK;
+    return apply_H_internal(h, spin, X, ld, Y, ncol, 1.0, 0.0, nullptr, 0.0);
+}
+
+int hub_chefsi_filter(hub_t h, int spin, void* X, int ncol, int ld, int degree, double a, double b,
+                      double a_low, void* work) {
+    int rc = check_block(h, spin, X, ncol, ld);
+    if (rc) return rc;
+    if (degree < 1) return fail(h, HUB_EINVAL, "degree must be >= 1");
+    if (!(a_low < a && a < b)) return fail(h, HUB_EINVAL, "filter bounds need a_low < a < b");
+    if (ncol == 0) return HUB_OK;
+    void* B1 = work;
+    if (!B1) {
+        if ((rc = ensure(h, &h->d_work, &h->work_bytes, (size_t)ld * ncol * elem_bytes(h)))) return rc;
+        B1 = h->d_work;
+    }
+    const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+    double sigma = e / (a_low - c);
+    const double tau = 2.0 / sigma;
+    if ((rc = apply_H_internal(h, spin, X, ld, B1, ncol, sigma / e, c, nullptr, 0.0))) return rc;
+    void* cur = B1;
+    void* prev = X;
+    for (int i = 2; i <= degree; ++i) {
+        const double sn = 1.0 / (tau - sigma);
+        if ((rc = apply_H_internal(h, spin, cur, ld, prev, ncol, 2.0 * sn / e, c, prev, -sigma * sn))) return rc;
+        std::swap(cur, prev);
+        sigma = sn;
+    }
+    if (cur != X)
+        if ((rc = launch_copy_block(h, cur, ld, X, ld, ncol))) return rc;
+    return HUB_OK;
+}
+
+int hub_rayleigh_ritz(hub_t h, int spin, void* X, int ncol, int ld, double* eig_host, void* work) {
+    int rc = check_block(h, spin, X, ncol, ld);
+    if (rc) return rc;
+    if (h->cplx) return fail(h, HUB_EINVAL, "Rayleigh-Ritz supports real orbitals only");
+    if (ncol > 0 && !eig_host) return fail(h, HUB_EINVAL, "NULL eigenvalue output");
+    if (ncol == 0) return HUB_OK;
+    const int n = ncol;
+    void* HX = work;
+    if (!HX) {
+        if ((rc = ensure(h, &h->d_work, &h->work_bytes, (size_t)ld * ncol * elem_bytes(h)))) return rc;
+        HX = h->d_work;
+    }
+    const size_t nn = (size_t)n * n;
+    if ((rc = ensure(h, &h->d_small, &h->small_bytes, (6 * nn + n) * sizeof(double)))) return rc;
+    double* S = (double*)h->d_small;
+    double* Hs = S + nn;
+    double* Linv = Hs + nn;
+    double* T = Linv + nn;
+    double* Vs = T + nn;
+    double* Q = Vs + nn;
+    double* eig = Q + nn;
+    if ((rc = apply_H_internal(h, spin, X, ld, HX, ncol, 1.0, 0.0, nullptr, 0.0))) return rc;
+    if (h->prec == HUB_MIXED_BF16) {
+        if ((rc = launch_gram(h, X, ld, X, ld, n, n, h->dV, true, S))) return rc;
+        if ((rc = launch_gram_bf16(h, X, ld, HX, ld, n, n, h->dV, true, Hs))) return rc;
+    } else {
+        if ((rc = launch_gram(h, X, ld, X, ld, n, n, h->dV, true, S))) return rc;
+        if ((rc = launch_gram(h, X, ld, HX, ld, n, n, h->dV, true, Hs))) return rc;
+    }
+    if ((rc = dense_cholesky(h, S, n))) return rc;
+    if ((rc = check_flags(h))) return rc;
+    if ((rc = dense_tri_inverse(h, S, Linv, n))) return rc;
+    if ((rc = dense_gemm(h, false, false, n, n, n, 1.0, Linv, n, Hs, n, 0.0, T, n))) return rc;
+    if ((rc = dense_gemm(h, false, true, n, n, n, 1.0, T, n, Linv, n, 0.0, Hs, n))) return rc;
+    if ((rc = dense_symmetrize(h, Hs, n))) return rc;
+    if ((rc = dense_jacobi_eigh(h, Hs, Vs, eig, n))) return rc;
+    if ((rc = dense_gemm(h, true, false, n, n, n, 1.0, Linv, n, Vs, n, 0.0, Q, n))) return rc;
+    if (h->prec == HUB_MIXED_BF16) {
+        if ((rc = launch_rotate_bf16(h, X, ld, Q, n, n, HX, ld))) return rc;
+    } else {
+        if ((rc = launch_rotate(h, X, ld, Q, n, n, HX, ld))) return rc;
+    }
+    if ((rc = launch_copy_block(h, HX, ld, X, ld, ncol))) return rc;
+    HUB_CUDA_TRY(h, cudaMemcpyAsync(eig_host, eig, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if ((rc = check_flags(h))) return rc;
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(eig_host[i])) return fail(h, HUB_ENONFINITE, "non-finite Ritz value");
+    return HUB_OK;
+}
+
+int hub_occupation(hub_t h, int spin, const void* X, int ncol, int ld, const double* f_host,
+                   double kweight, double* D_re_out, double* D_im_out, double* EU_out) {
+    int rc = check_block(h, spin, X, ncol, ld);
+    if (rc) return rc;
+    const int nh = h->proj.nhub;
+    if (nh > 0 && !D_re_out) return fail(h, HUB_EINVAL, "NULL D output");
+    if (ncol > 0 && !f_host) return fail(h, HUB_EINVAL, "NULL occupations");
+    if (nh == 0 || ncol == 0) {
+        if (D_re_out) std::fill(D_re_out, D_re_out + (size_t)nh * 25, 0.0);
+        if (D_im_out) std::fill(D_im_out, D_im_out + (size_t)nh * 25, 0.0);
+        if (EU_out) *EU_out = 0.0;
+        return HUB_OK;
+    }
+    if ((rc = launch_gather(h, X, ncol, ld, spin, false))) return rc;
+    const size_t need = (size_t)ncol * sizeof(double) + (size_t)nh * 50 * sizeof(double);
+    if ((rc = ensure(h, &h->d_aux, &h->aux_bytes, std::max(need, h->aux_bytes)))) return rc;
+    double* f_dev = (double*)h->d_aux;
+    double* D_dev = f_dev + ncol;
+    HUB_CUDA_TRY(h, cudaMemcpyAsync(f_dev, f_host, ncol * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if ((rc = launch_occupation(h, ncol, f_dev, kweight, D_dev))) return rc;
+    std::vector<double> D((size_t)nh * 50);
+    double eu = 0.0;
+    HUB_CUDA_TRY(h, cudaMemcpyAsync(D.data(), D_dev, D.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    HUB_CUDA_TRY(h, cudaMemcpyAsync(&eu, h->d_scal, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if ((rc = check_flags(h))) return rc;
+    for (size_t q = 0; q < (size_t)nh * 25; ++q) {
+        D_re_out[q] = D[2 * q];
+        if (D_im_out) D_im_out[q] = D[2 * q + 1];
+    }
+    if (EU_out) *EU_out = eu;
+    return HUB_OK;
+}
+
+int hub_lanczos_bound(hub_t h, int spin, int steps, const void* v0, double* lo_out, double* up_out) {
+    int rc = check_block(h, spin, v0, 1, (int)h->Nd);
+    if (rc) return rc;
+    if (steps < 1 || steps > 64) return fail(h, HUB_EINVAL, "1 <= steps <= 64");
+    if (!lo_out || !up_out) return fail(h, HUB_EINVAL, "NULL output");
+    if ((rc = launch_lanczos(h, spin, steps, v0, lo_out, up_out))) return rc;
+    return check_flags(h);
+}
+
+// ---------------------------------------------------------------------------- SCF driver
+
+static void fermi_dirac(const std::vector<double>& e, double kT, double nel, double deg,
+                        std::vector<double>& f, double& mu) {
+    const size_t n = e.size();
+    f.assign(n, 0.0);
+    if (kT <= 0.0) {
+        std::vector<size_t> ord(n);
+        std::iota(ord.begin(), ord.end(), 0);
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return e[a] < e[b]; });
+        const long nfill = std::lround(nel / deg);
+        for (long i = 0; i < nfill && i < (long)n; ++i) f[ord[i]] = 1.0;
+        mu = nfill > 0 ? e[ord[std::min<long>(nfill, n) - 1]] : e[ord[0]];
+        return;
+    }
+    auto count = [&](double m) {
+        double s = 0.0;
+        for (size_t i = 0; i < n; ++i) s += deg * 0.5 * (1.0 - std::tanh((e[i] - m) / (2.0 * kT)));
+        return s;
+    };
+    double lo = *std::min_element(e.begin(), e.end()) - 50 * kT;
+    double hi = *std::max_element(e.begin(), e.end()) + 50 * kT;
+    for (int it = 0; it < 200; ++it) {
+        const double m = 0.5 * (lo + hi);
+        if (count(m) < nel) lo = m; else hi = m;
+        if (hi - lo < 1e-15) break;
+    }
+    mu = 0.5 * (lo + hi);
+    for (size_t i = 0; i < n; ++i) f[i] = 0.5 * (1.0 - std::tanh((e[i] - mu) / (2.0 * kT)));
+}
+
+static double fd_entropy(const std::vector<double>& f) {
+    double s = 0.0;
+    for (double x : f) {
+        const double a = std::min(std::max(x, 1e-300), 1.0 - 1e-16);
+        const double b = std::max(1.0 - a, 1e-300);
+        s -= a * std::log(a) + b * std::log(b);
+    }
+    return s;
+}
+
+// Pulay / DIIS: minimise |sum c_i r_i| with sum c_i = 1, then x = sum c_i (x_i + beta r_i)
+static std::vector<double> pulay_mix(ScfState& st, const std::vector<double>& xin,
+                                     const std::vector<double>& xout) {
+    const size_t n = xin.size();
+    std::vector<double> r(n);
+    for (size_t i = 0; i < n; ++i) r[i] = xout[i] - xin[i];
+    st.hx.push_back(xin);
+    st.hr.push_back(r);
+    const int hist = std::max(1, st.p.pulay_history);
+    while ((int)st.hx.size() > hist) { st.hx.erase(st.hx.begin()); st.hr.erase(st.hr.begin()); }
+    const int k = (int)st.hr.size();
+    const double beta = st.p.pulay_beta;
+    std::vector<double> out(n);
+    std::vector<double> coef(k, 0.0);
+    bool ok = k > 1;
+    if (ok) {
+        const int m = k + 1;
+        std::vector<double> A((size_t)m * m, 0.0), b(m, 0.0);
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j) {
+                double s = 0.0;
+                for (size_t q = 0; q < n; ++q) s += st.hr[i][q] * st.hr[j][q];
+                A[(size_t)i * m + j] = s;
+            }
+        for (int i = 0; i < k; ++i) { A[(size_t)i * m + k] = 1.0; A[(size_t)k * m + i] = 1.0; }
+        b[k] = 1.0;
+        // Gaussian elimination with partial pivoting
+        double scale = 0.0;
+        for (double v : A) scale = std::max(scale, std::fabs(v));
+        for (int c = 0; c < m && ok; ++c) {
+            int piv = c;
+            for (int r2 = c + 1; r2 < m; ++r2)
+                if (std::fabs(A[(size_t)r2 * m + c]) > std::fabs(A[(size_t)piv * m + c])) piv = r2;
+            if (std::fabs(A[(size_t)piv * m + c]) <= 1e-14 * scale) { ok = false; break; }
+            if (piv != c) {
+                for (int q = 0; q < m; ++q) std::swap(A[(size_t)c * m + q], A[(size_t)piv * m + q]);
+                std::swap(b[c], b[piv]);
+            }
+            for (int r2 = c + 1; r2 < m; ++r2) {
+                const double fct = A[(size_t)r2 * m + c] / A[(size_t)c * m + c];
+                for (int q = c; q < m; ++q) A[(size_t)r2 * m + q] -= fct * A[(size_t)c * m + q];
+                b[r2] -= fct * b[c];
+            }
+        }
+        if (ok) {
+            std::vector<double> x(m);
+            for (int c = m - 1; c >= 0; --c) {
+                double s = b[c];
+                for (int q = c + 1; q < m; ++q) s -= A[(size_t)c * m + q] * x[q];
+                x[c] = s / A[(size_t)c * m + c];
+            }
+            for (int i = 0; i < k; ++i) coef[i] = x[i];
+        }
+    }
+    if (!ok) {
+        for (size_t q = 0; q < n; ++q) out[q] = xin[q] + beta * r[q];
+        return out;
+    }
+    for (size_t q = 0; q < n; ++q) {
+        double xs = 0.0, rs = 0.0;
+        for (int i = 0; i < k; ++i) { xs += coef[i] * st.hx[i][q]; rs += coef[i] * st.hr[i][q]; }
+        out[q] = xs + beta * rs;
+    }
+    return out;
+}
+
+int hub_scf_begin(hub_t h, const hub_scf_params* p, void* const* X, const void* const* v0,
+                  const double* D0) {
+    if (!h || !p || !X || !v0) return HUB_EINVAL;
+    if (p->nspin < 1 || p->nspin > 2) return fail(h, HUB_EINVAL, "nspin must be 1 or 2");
+    if (p->ncol < 1 || p->degree < 1 || p->max_iter < 1 || p->lanczos_steps < 1 || p->lanczos_steps > 64)
+        return fail(h, HUB_EINVAL, "bad SCF parameters");
+    if (h->cplx) return fail(h, HUB_EINVAL, "the SCF driver runs real (Gamma-point) orbitals");
+    for (int s = 0; s < p->nspin; ++s) {
+        int rc = check_block(h, s, X[s], p->ncol, p->ld);
+        if (rc) return rc;
+        if (!v0[s]) return fail(h, HUB_EINVAL, "NULL Lanczos start vector");
+    }
+    const int nh = h->proj.nhub;
+    if (nh > 0 && !D0) return fail(h, HUB_EINVAL, "NULL starting D");
+    delete h->scf;
+    h->scf = new ScfState();
+    ScfState& st = *h->scf;
+    st.p = *p;
+    st.X.assign(X, X + p->nspin);
+    st.v0.assign(v0, v0 + p->nspin);
+    st.D_in.assign(D0 ? D0 : nullptr, D0 ? D0 + (size_t)p->nspin * nh * 25 : nullptr);
+    st.D_in.resize((size_t)p->nspin * nh * 25, 0.0);
+    st.D_out.assign(st.D_in.size(), 0.0);
+    st.eig.assign((size_t)p->nspin * p->ncol, 0.0);
+    st.occ.assign(st.eig.size(), 0.0);
+    return HUB_OK;
+}
+
+int hub_scf_iterate(hub_t h, hub_scf_result* res) {
+    if (!h || !h->scf) return fail(h, HUB_EINVAL, "hub_scf_begin has not been called");
+    ScfState& st = *h->scf;
+    const hub_scf_params& p = st.p;
+    const int nh = h->proj.nhub;
+    const int ns = p.nspin;
+    const double deg = ns == 1 ? 2.0 : 1.0;
+    int rc;
+    for (int s = 0; s < ns; ++s) {
+        if ((rc = hub_set_occupation_matrix(h, s, st.D_in.data() + (size_t)s * nh * 25, nullptr))) return rc;
+        const int passes = st.iter == 0 ? std::max(1, p.first_passes) : 1;
+        for (int pass = 0; pass < passes; ++pass) {
+            if (!st.have_bounds[s]) {
+                double lo, up;
+                if ((rc = hub_lanczos_bound(h, s, p.lanczos_steps, st.v0[s], &lo, &up))) return rc;
+                st.bounds[s][0] = lo;
+                st.bounds[s][1] = lo + 0.1 * (up - lo);
+                st.bounds[s][2] = up;
+                st.have_bounds[s] = true;
+            }
+            if ((rc = hub_chefsi_filter(h, s, st.X[s], p.ncol, p.ld, p.degree, st.bounds[s][1],
+                                        st.bounds[s][2], st.bounds[s][0], nullptr))) return rc;
+            double* eg = st.eig.data() + (size_t)s * p.ncol;
+            if ((rc = hub_rayleigh_ritz(h, s, st.X[s], p.ncol, p.ld, eg, nullptr))) return rc;
+            st.bounds[s][0] = eg[0];
+            st.bounds[s][1] = eg[p.ncol - 1];
+        }
+    }
+    double mu = 0.0;
+    fermi_dirac(st.eig, p.kT, p.n_elec, deg, st.occ, mu);
+    double e_band = 0.0, e_dc = 0.0, e_u = 0.0, ent = 0.0;
+    for (int s = 0; s < ns; ++s) {
+        double eu_s = 0.0;
+        const double* f = st.occ.data() + (size_t)s * p.ncol;
+        if ((rc = hub_occupation(h, s, st.X[s], p.ncol, p.ld, f, 1.0,
+                                 st.D_out.data() + (size_t)s * nh * 25, nullptr, &eu_s))) return rc;
+        e_u += deg * eu_s;
+        for (int n = 0; n < p.ncol; ++n) e_band += deg * f[n] * st.eig[(size_t)s * p.ncol + n];
+        for (int i = 0; i < nh; ++i) {
+            const double U = h->proj.h_U[i];
+            for (int a = 0; a < 5; ++a)
+                for (int b = 0; b < 5; ++b) {
+                    const size_t q = ((size_t)s * nh + i) * 25 + a * 5 + b;
+                    const double M = 0.5 * U * ((a == b ? 1.0 : 0.0) - 2.0 * st.D_in[q]);
+                    e_dc += deg * M * st.D_out[q];
+                }
+        }
+    }
+    if (p.kT > 0) {
+        for (int s = 0; s < ns; ++s) {
+            std::vector<double> f(st.occ.begin() + (size_t)s * p.ncol, st.occ.begin() + (size_t)(s + 1) * p.ncol);
+            ent += deg * fd_entropy(f);
+        }
+    }
+    const double E = e_band - e_dc + e_u - p.kT * ent;
+    double dD = 0.0;
+    for (size_t q = 0; q < st.D_in.size(); ++q) dD = std::max(dD, std::fabs(st.D_out[q] - st.D_in[q]));
+    const double dE = st.have_prev ? E - st.E_prev : 0.0;
+    if (st.have_prev && std::fabs(dE) / std::max(1, p.natoms) < p.tol_e_atom) st.small++;
+    else st.small = 0;
+    st.have_prev = true;
+    st.E_prev = E;
+    st.iter++;
+    hub_scf_result r{};
+    r.iter = st.iter;
+    r.converged = (st.small >= 2 && dD < p.tol_D) ? 1 : 0;
+    r.E = E; r.E_band = e_band; r.E_U = e_u; r.dE = dE; r.dD = dD; r.mu = mu;
+    st.last = r;
+    if (!r.converged) st.D_in = pulay_mix(st, st.D_in, st.D_out);
+    if (res) *res = r;
+    return HUB_OK;
+}
+
+int hub_scf_run(hub_t h, hub_scf_result* res) {
+    if (!h || !h->scf) return fail(h, HUB_EINVAL, "hub_scf_begin has not been called");
+    hub_scf_result r{};
+    while (h->scf->iter < h->scf->p.max_iter) {
+        int rc = hub_scf_iterate(h, &r);
+        if (rc) return rc;
+        if (r.converged) break;
+    }
+    if (res) *res = r;
+    return r.converged ? HUB_OK : fail(h, HUB_ENOCONV, "SCF reached max_iter");
+}
+
+int hub_scf_get(hub_t h, double* eig, double* occ, double* D_out) {
+    if (!h || !h->scf) return fail(h, HUB_EINVAL, "hub_scf_begin has not been called");
+    ScfState& st = *h->scf;
+    if (eig) std::copy(st.eig.begin(), st.eig.end(), eig);
+    if (occ) std::copy(st.occ.begin(), st.occ.end(), occ);
+    if (D_out) std::copy(st.D_out.begin(), st.D_out.end(), D_out);
+    return HUB_OK;
+}
+
+}  // extern "C"

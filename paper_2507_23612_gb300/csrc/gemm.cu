@@ -1,0 +1,174 @@
+// Rayleigh-Ritz block products (CheFSI, Sec. II.B) on CUDA cores:
+//   Gram / projected Hamiltonian  G = alpha * A^T B   (A, B tall: Nd x m, Nd x n)
+//   rotation                      Y = X Q             (X tall: Nd x k, Q small k x n)
+// The tall dimension is split over CTAs (split-K); every CTA writes a double partial tile
+// and a second kernel sums the partials in a fixed order (deterministic).
+#include "hub_internal.cuh"
+#include "cplx.cuh"
+
+namespace hub {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+// partial[z][i][j] = sum_{k in chunk z} A[k, i] B[k, j]; tile (bi, bj) from a tile list
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_gram_partial(const T* __restrict__ A, int lda, const T* __restrict__ B, int ldb, long K, int m,
+               int n, long chunk, int tn, int sym, double* __restrict__ part) {
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BN + 1];
+    const int bi = blockIdx.x / tn, bj = blockIdx.x % tn;
+    if (sym && bi > bj) return;          // mirrored by the reduction
+    const int i0 = bi * BM, j0 = bj * BN;
+    const long k0 = (long)blockIdx.y * chunk;
+    const long k1 = min(K, k0 + chunk);
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+    for (long kb = k0; kb < k1; kb += BK) {
+        // 64 columns x 16 rows of each operand; k is the contiguous index
+        for (int e = threadIdx.x; e < BK * BM; e += 256) {
+            const int kk = e % BK, ii = e / BK;
+            const long k = kb + kk;
+            const int i = i0 + ii, j = j0 + ii;
+            As[kk][ii] = (k < k1 && i < m) ? A[(size_t)i * lda + k] : (T)0;
+            Bs[kk][ii] = (k < k1 && j < n) ? B[(size_t)j * ldb + k] : (T)0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) { a[r] = As[kk][ty + 16 * r]; b[r] = Bs[kk][tx + 16 * r]; }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+    double* P = part + (size_t)blockIdx.y * m * n;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int i = i0 + ty + 16 * r, j = j0 + tx + 16 * c;
+            if (i < m && j < n) P[(size_t)i * n + j] = (double)acc[r][c];
+        }
+}
+
+__global__ void k_gram_reduce(const double* __restrict__ part, int splits, int m, int n, double alpha,
+                              int sym, double* __restrict__ G) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)m * n) return;
+    int i = (int)(t / n), j = (int)(t % n);
+    if (sym && (i / BM) > (j / BN)) {   // lower blocks were not computed: mirror
+        const int tmp = i; i = j; j = tmp;
+    }
+    double s = 0.0;
+    for (int z = 0; z < splits; ++z) s += part[(size_t)z * m * n + (size_t)i * n + j];
+    G[t] = alpha * s;
+}
+
+// Y[r, j] = sum_kk X[r, kk] Q[kk, j]; Q row-major double [k x n]
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_rotate(const T* __restrict__ X, int ldx, const double* __restrict__ Q, int k, int n, long K,
+         T* __restrict__ Y, int ldy) {
+    __shared__ T Xs[BK][BM + 1];
+    __shared__ T Qs[BK][BN + 1];
+    const long r0 = (long)blockIdx.x * BM;
+    const int j0 = blockIdx.y * BN;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+    for (int kb = 0; kb < k; kb += BK) {
+        for (int e = threadIdx.x; e < BK * BM; e += 256) {
+            const int rr = e % BM, kk = e / BM;
+            const long r = r0 + rr;
+            Xs[kk][rr] = (r < K && kb + kk < k) ? X[(size_t)(kb + kk) * ldx + r] : (T)0;
+            const int jj = e % BN, kq = e / BN;
+            Qs[kq][jj] = (kb + kq < k && j0 + jj < n) ? (T)Q[(size_t)(kb + kq) * n + j0 + jj] : (T)0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) { a[r] = Xs[kk][tx + 16 * r]; b[r] = Qs[kk][ty + 16 * r]; }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int j = j0 + ty + 16 * c;
+        if (j >= n) continue;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const long row = r0 + tx + 16 * r;
+            if (row < K) Y[(size_t)j * ldy + row] = acc[r][c];
+        }
+    }
+}
+
+template <typename T>
+int gram_t(hub_t h, const void* A, int lda, const void* B, int ldb, int m, int n, double alpha,
+           bool sym, double* G) {
+    const int tm = (m + BM - 1) / BM, tn = (n + BN - 1) / BN;
+    const long ntiles = sym ? (long)tm * (tm + 1) / 2 : (long)tm * tn;
+    const long K = h->Nd;
+    int splits = (int)((4L * h->num_sms + ntiles - 1) / ntiles);
+    long chunk = (K + splits - 1) / splits;
+    chunk = ((chunk + BK - 1) / BK) * BK;
+    if (chunk < 4 * BK) chunk = 4 * BK;
+    splits = (int)((K + chunk - 1) / chunk);
+    int rc;
+    if ((rc = ensure(h, &h->d_gpart, &h->gpart_bytes, (size_t)splits * m * n * sizeof(double))))
+        return rc;
+    double* part = (double*)h->d_gpart;
+    dim3 grid((unsigned)(tm * tn), splits);
+    k_gram_partial<T><<<grid, 256, 0, h->stream>>>((const T*)A, lda, (const T*)B, ldb, K, m, n, chunk,
+                                                   tn, sym ? 1 : 0, part);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    const long tot = (long)m * n;
+    k_gram_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(part, splits, m, n, alpha,
+                                                                        sym ? 1 : 0, G);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    return HUB_OK;
+}
+
+}  // namespace
+
+int launch_gram(hub_t h, const void* A, int lda, const void* B, int ldb, int m, int n,
+                double alpha, bool sym, double* G) {
+    if (h->cplx) return fail(h, HUB_EINVAL, "Rayleigh-Ritz supports real orbitals only");
+    if (m == 0 || n == 0) return HUB_OK;
+    if (h->esize == 8) return gram_t<double>(h, A, lda, B, ldb, m, n, alpha, sym, G);
+    return gram_t<float>(h, A, lda, B, ldb, m, n, alpha, sym, G);
+}
+
+int launch_rotate(hub_t h, const void* X, int ldx, const double* Q, int k, int n, void* Y, int ldy) {
+    if (h->cplx) return fail(h, HUB_EINVAL, "Rayleigh-Ritz supports real orbitals only");
+    if (n == 0) return HUB_OK;
+    dim3 grid((unsigned)((h->Nd + BM - 1) / BM), (n + BN - 1) / BN);
+    if (h->esize == 8)
+        k_rotate<double><<<grid, 256, 0, h->stream>>>((const double*)X, ldx, Q, k, n, h->Nd, (double*)Y, ldy);
+    else
+        k_rotate<float><<<grid, 256, 0, h->stream>>>((const float*)X, ldx, Q, k, n, h->Nd, (float*)Y, ldy);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    return HUB_OK;
+}
+
+}  // namespace hub

@@ -1,0 +1,194 @@
+// Internal declarations of the hub library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/hub.h"
+
+namespace hub {
+
+constexpr int kMaxHalf = 8;      // largest supported n0
+constexpr int kMaxProj = 9;      // most projectors one atom carries in one table (s+p+d)
+
+// ---------------------------------------------------------------------------- errors
+struct Error {
+    int code;
+    std::string msg;
+};
+
+#define HUB_CUDA_TRY(h, expr)                                                         \
+    do {                                                                              \
+        cudaError_t _e = (expr);                                                      \
+        if (_e != cudaSuccess) {                                                      \
+            return hub::fail((h), HUB_ECUDA, std::string(#expr) + ": " +              \
+                                                  cudaGetErrorString(_e));            \
+        }                                                                             \
+    } while (0)
+
+// ---------------------------------------------------------------------------- tables
+// A "site" is one (atom, kind) pair: kind 0 = KB-type nonlocal projectors, kind 1 = a
+// Hubbard shell.  Its points are table rows [pt_off, pt_off + npts) (grid index in idx);
+// its values are point-major at vals[val_off + (row - pt_off) * nproj + p] (complex: pairs);
+// its projector rows in C / W are [proj_off, proj_off + nproj).
+struct SiteDev {
+    double R[3];
+    double rc;
+    int tlo[3], thi[3];   // lattice translations whose sphere meets the cell
+    int nch;
+    int l[3];
+    double rs[3];
+    double N[3];
+    int pt_off, npts, nproj, val_off, proj_off;
+    int kind;
+    int hub_index;        // Hubbard sites: index among Hubbard atoms, else -1
+};
+
+struct Table {
+    int nsites = 0, nproj = 0, npts = 0, nvals = 0, nhub = 0, nitems = 0;
+    std::vector<SiteDev> h_sites;
+    std::vector<int> h_hub_sites;     // site index of each Hubbard atom
+    std::vector<double> h_U;          // U per Hubbard atom (Ha)
+    std::vector<int> h_item_first;    // first gather item of each site, size nsites + 1
+    SiteDev* d_sites = nullptr;
+    int* d_items = nullptr;           // [nitems*3]: site, first absolute row, count
+    int* d_item_first = nullptr;
+    int* d_idx = nullptr;             // [npts] grid index of each row
+    void* d_vals = nullptr;           // working type, [nvals] (x2 complex)
+    int* d_csr_off = nullptr;         // [Nd+1] entries per grid point
+    int* d_csr_val = nullptr;         // value index of the entry's first projector
+    int* d_csr_w = nullptr;           // projector row of the entry's site
+    int* d_csr_np = nullptr;          // projectors of the entry's site
+    double* d_gamma = nullptr;        // [nproj] KB energy per projector row (0 for Hubbard)
+    int* d_hub_sites = nullptr;
+    double* d_U = nullptr;
+    double* d_M[2] = {nullptr, nullptr};  // per spin [nhub*25] (x2 complex), row p, col m
+    std::vector<double> h_M[2];
+};
+
+// ---------------------------------------------------------------------------- handle
+struct ScfState;
+void free_table(Table& t);
+
+}  // namespace hub
+
+struct hub_ctx {
+    int n1 = 0, n2 = 0, n3 = 0;
+    int64_t Nd = 0;
+    double L[3] = {0, 0, 0};
+    double h[3] = {0, 0, 0};
+    double dV = 0;
+    int n0 = 6;
+    int cplx = 0;
+    double kpt[3] = {0, 0, 0};
+    int prec = HUB_F64;
+    int esize = 8;                // bytes per real component of the working type
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+
+    void* d_veff = nullptr;       // working type [Nd]
+    bool veff_set = false;
+
+    hub::Table proj;
+    bool atoms_set = false;
+    bool D_set[2] = {false, false};
+
+    // workspaces (grown on demand)
+    void* d_work = nullptr;       size_t work_bytes = 0;    // one X-sized block
+    void* d_work2 = nullptr;      size_t work2_bytes = 0;   // second X-sized block
+    void* d_part = nullptr;       size_t part_bytes = 0;    // gather partial sums
+    void* d_C = nullptr;          size_t C_bytes = 0;       // projector coefficients
+    void* d_W = nullptr;          size_t W_bytes = 0;
+    void* d_small = nullptr;      size_t small_bytes = 0;   // n x n matrices (double)
+    void* d_gpart = nullptr;      size_t gpart_bytes = 0;   // split-K GEMM partials
+    void* d_bf16 = nullptr;       size_t bf16_bytes = 0;    // bf16 operand copies
+    void* d_aux = nullptr;        size_t aux_bytes = 0;     // occupations and D output
+    int* d_flags = nullptr;       // [8] device error flags
+    unsigned int* d_bar = nullptr;  // [4] grid-barrier state
+    double* d_scal = nullptr;     // [256] device scalars (Lanczos, reductions)
+
+    hub::ScfState* scf = nullptr;
+
+    std::string last_error;
+};
+
+namespace hub {
+
+int fail(hub_t h, int code, const std::string& msg);
+int ensure(hub_t h, void** p, size_t* have, size_t need);
+
+// flags
+enum { FLAG_NOTSPD = 0, FLAG_NONFINITE = 1, FLAG_TIMEOUT = 2, FLAG_NOCONV = 3 };
+int check_flags(hub_t h);   // syncs stream, reads and clears flags, maps to a status
+
+// ---------------------------------------------------------------------------- launchers
+// stencil.cu
+struct StencilArgs {
+    const void* Y;       // current block
+    const void* Yprev;   // previous block or nullptr (beta ignored)
+    void* Yout;
+    const void* V;       // working type [Nd]
+    int n1, n2, n3, ld, ncol;
+    double w[3][kMaxHalf];  // alpha * (-1/2) c_p / h_a^2
+    double center;          // alpha * ((-1/2) c0 sum_a h_a^-2 - shift)
+    double alpha;           // multiplies V
+    double beta;
+    int n0;
+    double phase[3][2];     // exp(i k_a L_a) (re, im), complex only
+};
+int launch_stencil(hub_t h, const StencilArgs& a);
+
+// projectors.cu
+int build_tables(hub_t h, int natoms, const double* pos, const int* kb_nchan, const int* kb_l,
+                 const double* kb_rs, const double* kb_gamma, const double* kb_rc,
+                 const int* hub_l, const double* hub_rs, const double* hub_rc,
+                 const double* hub_U);
+void free_table(Table& t);
+// C[P x ncol] (double, x2 complex) = dV * <proj_p|x_n>; with want_W also W = transform(C)
+// in the working type (gamma .* C for KB rows, M_spin C for Hubbard rows).
+int launch_gather(hub_t h, const void* X, int ncol, int ld, int spin, bool want_W);
+// Y[g, n] += alpha * sum_e vals_e . W[rows_e, n]   (W from the last launch_gather)
+int launch_scatter(hub_t h, void* Y, int ncol, int ld, double alpha);
+// D per Hubbard atom (double, [nhub*50] re/im pairs) and E_U into d_scal[0] from the C of
+// the last launch_gather; f_dev [ncol] double.
+int launch_occupation(hub_t h, int ncol, const double* f_dev, double kweight, double* D_dev);
+
+// gemm.cu
+// G[m x n] = alpha * A^H B, A: [K x m] (lda), B: [K x n] (ldb); K = Nd. Out double, row-major
+// G[i*n + j].  sym: only blocks i <= j are computed and mirrored.
+int launch_gram(hub_t h, const void* A, int lda, const void* B, int ldb, int m, int n,
+                double alpha, bool sym, double* G);
+// Y[K x n] = X[K x k] Q[k x n]; Q double column-major [k x n] (ldq = k)
+int launch_rotate(hub_t h, const void* X, int ldx, const double* Q, int k, int n, void* Y,
+                  int ldy);
+// mixed-precision variants (tcgen05 bf16 path)
+int launch_gram_bf16(hub_t h, const void* A, int lda, const void* B, int ldb, int m, int n,
+                     double alpha, bool sym, double* G);
+int launch_rotate_bf16(hub_t h, const void* X, int ldx, const double* Q, int k, int n,
+                       void* Y, int ldy);
+
+// dense.cu (double, n x n, row-major)
+int dense_cholesky(hub_t h, double* A, int n);                 // lower L in place
+int dense_tri_inverse(hub_t h, const double* L, double* Linv, int n);
+// C = alpha op(A) op(B) + beta C ; row-major n x n style small matrices
+int dense_gemm(hub_t h, bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
+               int lda, const double* B, int ldb, double beta, double* C, int ldc);
+int dense_jacobi_eigh(hub_t h, double* A, double* V, double* eig, int n);  // ascending
+int dense_symmetrize(hub_t h, double* A, int n);
+
+// misc.cu
+int launch_copy_convert_veff(hub_t h, const double* src, void* dst);
+int launch_axpby_vec(hub_t h, int op, void* w, const void* v, const void* vprev, int step);
+int launch_lanczos(hub_t h, int spin, int steps, const void* v0, double* lo, double* up);
+int launch_copy_block(hub_t h, const void* src, int lds, void* dst, int ldd, int ncol);
+
+// api: apply_H with explicit buffers (used by filter / RR / Lanczos)
+// Y = alpha (H X - shift X) + beta Yprev  (Yprev may alias Y; X, Y, Yprev share ld)
+int apply_H_internal(hub_t h, int spin, const void* X, int ld, void* Y, int ncol, double alpha,
+                     double shift, const void* Yprev, double beta);
+
+}  // namespace hub

@@ -1,0 +1,201 @@
+// Small device helpers: potential conversion, block copies, deterministic dot products and
+// the Lanczos bound estimator used to place the Chebyshev filter interval (CheFSI, Sec. II.B).
+#include <algorithm>
+#include <cmath>
+
+#include "hub_internal.cuh"
+#include "cplx.cuh"
+
+namespace hub {
+
+namespace {
+
+template <typename R>
+__global__ void k_convert(const double* __restrict__ src, R* __restrict__ dst, long n) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) dst[t] = (R)src[t];
+}
+
+template <typename T>
+__global__ void k_copy_block(const T* __restrict__ src, int lds, T* __restrict__ dst, int ldd, long Nd) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < Nd) dst[(size_t)blockIdx.y * ldd + t] = src[(size_t)blockIdx.y * lds + t];
+}
+
+constexpr int RBLK = 512;     // blocks of the first reduction stage
+
+// partial[b] = sum over a grid-stride slice of conj(x) y (double accumulation)
+template <typename R, bool CPLX>
+__global__ void k_dot_partial(const typename VT<R, CPLX>::T* __restrict__ x,
+                              const typename VT<R, CPLX>::T* __restrict__ y, long n,
+                              double* __restrict__ part) {
+    double acc = 0.0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        if constexpr (CPLX) acc += (double)x[i].x * (double)y[i].x + (double)x[i].y * (double)y[i].y;
+        else acc += (double)x[i] * (double)y[i];
+    }
+    __shared__ double s[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// out = sum(part[0..n)) [op]: 0 plain, 1 sqrt
+__global__ void k_dot_final(const double* __restrict__ part, int n, double* out, int op) {
+    __shared__ double s[RBLK];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = op == 1 ? sqrt(s[0]) : s[0];
+}
+
+// Lanczos vector updates with scalars read from device memory (no host round trip)
+//   mode 0: v = x / scal[ia]
+//   mode 1: w = w - scal[ia] * v - scal[ib] * vprev     (ib < 0: no vprev term)
+template <typename R, bool CPLX>
+__global__ void k_lanczos_axpy(int mode, typename VT<R, CPLX>::T* __restrict__ out,
+                               const typename VT<R, CPLX>::T* __restrict__ v,
+                               const typename VT<R, CPLX>::T* __restrict__ vprev, long n,
+                               const double* __restrict__ scal, int ia, int ib) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (mode == 0) {
+        const double inv = 1.0 / scal[ia];
+        out[i] = mulr((R)inv, v[i]);
+    } else {
+        auto w = out[i];
+        w = fmar((R)(-scal[ia]), v[i], w);
+        if (ib >= 0) w = fmar((R)(-scal[ib]), vprev[i], w);
+        out[i] = w;
+    }
+}
+
+// eigenvalues of the k x k symmetric tridiagonal (alpha, beta) by cyclic Jacobi, one thread;
+// out[0] = min, out[1] = max + |beta_k|
+__global__ void k_tridiag_bounds(const double* __restrict__ alpha, const double* __restrict__ beta, int k,
+                                 double* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double A[64][64];
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) A[i][j] = 0.0;
+    for (int i = 0; i < k; ++i) {
+        A[i][i] = alpha[i];
+        if (i + 1 < k) { A[i][i + 1] = beta[i]; A[i + 1][i] = beta[i]; }
+    }
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < k; ++p)
+            for (int q = p + 1; q < k; ++q) off = fmax(off, fabs(A[p][q]));
+        if (off < 1e-300) break;
+        for (int p = 0; p < k; ++p)
+            for (int q = p + 1; q < k; ++q) {
+                if (A[p][q] == 0.0) continue;
+                const double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int r = 0; r < k; ++r) {
+                    const double ap = A[r][p], aq = A[r][q];
+                    A[r][p] = c * ap - s * aq;
+                    A[r][q] = s * ap + c * aq;
+                }
+                for (int r = 0; r < k; ++r) {
+                    const double ap = A[p][r], aq = A[q][r];
+                    A[p][r] = c * ap - s * aq;
+                    A[q][r] = s * ap + c * aq;
+                }
+            }
+    }
+    double lo = A[0][0], hi = A[0][0];
+    for (int i = 1; i < k; ++i) { lo = fmin(lo, A[i][i]); hi = fmax(hi, A[i][i]); }
+    out[0] = lo;
+    out[1] = hi + fabs(beta[k - 1]);
+}
+
+template <typename R, bool CPLX>
+int dot_t(hub_t h, const void* x, const void* y, double* out, int op) {
+    using T = typename VT<R, CPLX>::T;
+    double* part = h->d_scal + 1024;   // d_scal holds 4096 doubles
+    k_dot_partial<R, CPLX><<<RBLK, 256, 0, h->stream>>>((const T*)x, (const T*)y, h->Nd, part);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    k_dot_final<<<1, RBLK, 0, h->stream>>>(part, RBLK, out, op);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    return HUB_OK;
+}
+
+template <typename R, bool CPLX>
+int lanczos_t(hub_t h, int spin, int steps, const void* v0, double* lo, double* up) {
+    using T = typename VT<R, CPLX>::T;
+    const size_t vb = (size_t)h->Nd * sizeof(T);
+    int rc;
+    if ((rc = ensure(h, &h->d_work, &h->work_bytes, std::max(h->work_bytes, 3 * vb)))) return rc;
+    T* v = (T*)h->d_work;
+    T* vp = v + h->Nd;
+    T* w = vp + h->Nd;
+    double* sc = h->d_scal;            // [0..63] alpha, [64..128] beta, [200..201] bounds, [210] norm
+    const unsigned nb = (unsigned)((h->Nd + 255) / 256);
+    if ((rc = dot_t<R, CPLX>(h, v0, v0, sc + 210, 1))) return rc;
+    k_lanczos_axpy<R, CPLX><<<nb, 256, 0, h->stream>>>(0, v, (const T*)v0, nullptr, h->Nd, sc, 210, -1);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    for (int j = 0; j < steps; ++j) {
+        if ((rc = apply_H_internal(h, spin, v, (int)h->Nd, w, 1, 1.0, 0.0, nullptr, 0.0))) return rc;
+        if ((rc = dot_t<R, CPLX>(h, v, w, sc + j, 0))) return rc;                    // alpha_j
+        k_lanczos_axpy<R, CPLX><<<nb, 256, 0, h->stream>>>(1, w, v, vp, h->Nd, sc, j, j > 0 ? 64 + j - 1 : -1);
+        HUB_CUDA_TRY(h, cudaGetLastError());
+        if ((rc = dot_t<R, CPLX>(h, w, w, sc + 64 + j, 1))) return rc;             // beta_{j+1}
+        // vprev <- v ; v <- w / beta
+        HUB_CUDA_TRY(h, cudaMemcpyAsync(vp, v, vb, cudaMemcpyDeviceToDevice, h->stream));
+        k_lanczos_axpy<R, CPLX><<<nb, 256, 0, h->stream>>>(0, v, w, nullptr, h->Nd, sc, 64 + j, -1);
+        HUB_CUDA_TRY(h, cudaGetLastError());
+    }
+    k_tridiag_bounds<<<1, 32, 0, h->stream>>>(sc, sc + 64, steps, sc + 200);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    double b[2];
+    HUB_CUDA_TRY(h, cudaMemcpyAsync(b, sc + 200, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    HUB_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    *lo = b[0];
+    *up = b[1];
+    return HUB_OK;
+}
+
+}  // namespace
+
+int launch_copy_convert_veff(hub_t h, const double* src, void* dst) {
+    const unsigned nb = (unsigned)((h->Nd + 255) / 256);
+    if (h->esize == 8) k_convert<double><<<nb, 256, 0, h->stream>>>(src, (double*)dst, h->Nd);
+    else k_convert<float><<<nb, 256, 0, h->stream>>>(src, (float*)dst, h->Nd);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    return HUB_OK;
+}
+
+int launch_copy_block(hub_t h, const void* src, int lds, void* dst, int ldd, int ncol) {
+    if (ncol == 0) return HUB_OK;
+    dim3 grid((unsigned)((h->Nd + 255) / 256), ncol);
+    const int es = h->esize * (h->cplx ? 2 : 1);
+    if (es == 16)
+        k_copy_block<double2><<<grid, 256, 0, h->stream>>>((const double2*)src, lds, (double2*)dst, ldd, h->Nd);
+    else if (es == 8)
+        k_copy_block<double><<<grid, 256, 0, h->stream>>>((const double*)src, lds, (double*)dst, ldd, h->Nd);
+    else
+        k_copy_block<float><<<grid, 256, 0, h->stream>>>((const float*)src, lds, (float*)dst, ldd, h->Nd);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    return HUB_OK;
+}
+
+int launch_lanczos(hub_t h, int spin, int steps, const void* v0, double* lo, double* up) {
+    if (h->esize == 8) return h->cplx ? lanczos_t<double, true>(h, spin, steps, v0, lo, up)
+                                      : lanczos_t<double, false>(h, spin, steps, v0, lo, up);
+    return h->cplx ? lanczos_t<float, true>(h, spin, steps, v0, lo, up)
+                   : lanczos_t<float, false>(h, spin, steps, v0, lo, up);
+}
+
+}  // namespace hub

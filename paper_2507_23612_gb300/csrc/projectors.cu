@@ -1,0 +1,588 @@
+// Atom-centred localized functions on the grid: KB-type nonlocal projectors and Hubbard
+// orbitals share one machinery (Sec. II.B: the DFT+U implementation mirrors the nonlocal
+// pseudopotential; all integrals of one atom are computed simultaneously).
+//
+// A "site" is one (atom, kind) pair with nproj functions  radial(|x - R - T|) Y_lm  summed
+// over lattice images T within the cutoff, times exp(i k.T) (Sec. II.A.1, Bloch-mapped
+// orbitals).  Every site keeps the sorted list of grid points any of its images touches
+// and the values there (point-major).  Three kernels use the tables:
+//   gather:    C[row, n] = dV * sum_l conj(vals[l, p]) X[idx[l], n]      (<phi_p|x_n>)
+//   transform: W = gamma .* C (KB) or W = M C with M = (U/2)(I - 2 D) (Hubbard, Eq. DerED)
+//   scatter:   Y[g, n] += alpha * sum_{entries e at g} vals_e . W[rows_e, n]
+// The scatter walks a per-grid-point CSR so that no two threads write the same element.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "hub_internal.cuh"
+#include "cplx.cuh"
+
+namespace hub {
+
+namespace {
+
+constexpr int GSUB_MAX = 128;  // points per gather sub-tile
+constexpr int GITEM = 1024;    // points per gather work item
+constexpr int GNB = 16;        // columns per gather CTA
+constexpr int SNB = 8;         // columns per scatter thread
+
+__device__ __forceinline__ void solid_harmonics(int l, double x, double y, double z, double* out) {
+    // r^l Y_lm for the real orthonormal harmonics, m = -l..l (no Condon-Shortley sign)
+    const double PI = 3.14159265358979323846;
+    if (l == 0) {
+        out[0] = 0.5 / sqrt(PI);
+    } else if (l == 1) {
+        const double k = sqrt(3.0 / (4.0 * PI));
+        out[0] = k * y; out[1] = k * z; out[2] = k * x;
+    } else {
+        const double k1 = 0.5 * sqrt(15.0 / PI), k0 = 0.25 * sqrt(5.0 / PI), k2 = 0.25 * sqrt(15.0 / PI);
+        out[0] = k1 * x * y;
+        out[1] = k1 * y * z;
+        out[2] = k0 * (2.0 * z * z - x * x - y * y);
+        out[3] = k1 * x * z;
+        out[4] = k2 * (x * x - y * y);
+    }
+}
+
+template <typename R, bool CPLX>
+__global__ void k_table_values(const SiteDev* __restrict__ sites, const int* __restrict__ items,
+                               const int* __restrict__ idx, R* __restrict__ vals, int n1, int n2,
+                               double h1, double h2, double h3, double L1, double L2, double L3,
+                               double k1, double k2, double k3) {
+    const int it = blockIdx.x;
+    const int s = items[3 * it], first = items[3 * it + 1], cnt = items[3 * it + 2];
+    const SiteDev S = sites[s];
+    for (int l = threadIdx.x; l < cnt; l += blockDim.x) {
+        const int row = first + l;               // absolute table row
+        const int g = idx[row];
+        const int i1 = g % n1, i2 = (g / n1) % n2, i3 = g / (n1 * n2);
+        const double x = i1 * h1, y = i2 * h2, z = i3 * h3;
+        double re[kMaxProj], im[kMaxProj];
+        for (int p = 0; p < kMaxProj; ++p) { re[p] = 0.0; im[p] = 0.0; }
+        for (int t1 = S.tlo[0]; t1 <= S.thi[0]; ++t1)
+            for (int t2 = S.tlo[1]; t2 <= S.thi[1]; ++t2)
+                for (int t3 = S.tlo[2]; t3 <= S.thi[2]; ++t3) {
+                    const double T1 = t1 * L1, T2 = t2 * L2, T3 = t3 * L3;
+                    const double dx = x - S.R[0] - T1, dy = y - S.R[1] - T2, dz = z - S.R[2] - T3;
+                    const double r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 >= S.rc * S.rc) continue;
+                    double c = 1.0, sn = 0.0;
+                    if (CPLX) sincos(k1 * T1 + k2 * T2 + k3 * T3, &sn, &c);
+                    int p = 0;
+                    for (int ch = 0; ch < S.nch; ++ch) {
+                        double ylm[5];
+                        solid_harmonics(S.l[ch], dx, dy, dz, ylm);
+                        const double rad = S.N[ch] * exp(-r2 / (2.0 * S.rs[ch] * S.rs[ch]));
+                        for (int m = 0; m < 2 * S.l[ch] + 1; ++m, ++p) {
+                            re[p] += c * rad * ylm[m];
+                            im[p] += sn * rad * ylm[m];
+                        }
+                    }
+                }
+        R* out = vals + (size_t)(CPLX ? 2 : 1) * (S.val_off + (size_t)(row - S.pt_off) * S.nproj);
+        for (int p = 0; p < S.nproj; ++p) {
+            if (CPLX) { out[2 * p] = (R)re[p]; out[2 * p + 1] = (R)im[p]; }
+            else out[p] = (R)re[p];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------- gather
+template <typename R, bool CPLX>
+__global__ void __launch_bounds__(128)
+k_gather(const typename VT<R, CPLX>::T* __restrict__ X, int ld, int ncol,
+         const SiteDev* __restrict__ sites, const int* __restrict__ items,
+         const int* __restrict__ idx, const typename VT<R, CPLX>::T* __restrict__ vals,
+         typename VT<double, CPLX>::T* __restrict__ part) {
+    using T = typename VT<R, CPLX>::T;
+    using D = typename VT<double, CPLX>::T;
+    constexpr int GSUB = sizeof(T) == 16 ? 64 : GSUB_MAX;   // keep static smem under 48 KB
+    __shared__ T xs[GSUB][GNB + 1];
+    __shared__ T vs[GSUB][kMaxProj];
+    const int it = blockIdx.x;
+    const int s = items[3 * it], first = items[3 * it + 1], cnt = items[3 * it + 2];
+    const int np = sites[s].nproj;
+    const int val0 = sites[s].val_off + (first - sites[s].pt_off) * np;
+    const int c0 = blockIdx.y * GNB;
+    const int nout = np * GNB;
+    // each thread owns up to two outputs (p, j)
+    const int o0 = threadIdx.x, o1 = threadIdx.x + 128;
+    T acc0 = zero_of(T()), acc1 = zero_of(T());
+    for (int base = 0; base < cnt; base += GSUB) {
+        const int m = min(GSUB, cnt - base);
+        for (int i = threadIdx.x; i < GSUB * GNB; i += 128) {
+            const int l = i % GSUB, j = i / GSUB;
+            const int c = c0 + j;
+            T v = zero_of(T());
+            if (l < m && c < ncol) v = X[(size_t)idx[first + base + l] + (size_t)c * ld];
+            xs[l][j] = v;
+        }
+        for (int i = threadIdx.x; i < GSUB * np; i += 128) {
+            const int l = i / np, p = i - l * np;
+            vs[l][p] = (l < m) ? vals[(size_t)val0 + (size_t)(base + l) * np + p] : zero_of(T());
+        }
+        __syncthreads();
+        if (o0 < nout) {
+            const int p = o0 / GNB, j = o0 % GNB;
+#pragma unroll 8
+            for (int l = 0; l < GSUB; ++l) acc0 = cfma_conj(vs[l][p], xs[l][j], acc0);
+        }
+        if (o1 < nout) {
+            const int p = o1 / GNB, j = o1 % GNB;
+#pragma unroll 8
+            for (int l = 0; l < GSUB; ++l) acc1 = cfma_conj(vs[l][p], xs[l][j], acc1);
+        }
+        __syncthreads();
+    }
+    auto store = [&](int o, T acc) {
+        const int p = o / GNB, j = o % GNB, c = c0 + j;
+        if (c >= ncol) return;
+        D v;
+        if constexpr (CPLX) v = make_double2((double)acc.x, (double)acc.y);
+        else v = (double)acc;
+        part[((size_t)it * kMaxProj + p) * ncol + c] = v;
+    };
+    if (o0 < nout) store(o0, acc0);
+    if (o1 < nout) store(o1, acc1);
+}
+
+// reduce partials of each site and apply the coefficient transform
+template <typename R, bool CPLX>
+__global__ void k_reduce_transform(int nsites, int ncol, double dV, const SiteDev* __restrict__ sites,
+                                   const int* __restrict__ item_first,
+                                   const typename VT<double, CPLX>::T* __restrict__ part,
+                                   const double* __restrict__ gamma, const double* __restrict__ M,
+                                   typename VT<double, CPLX>::T* __restrict__ C,
+                                   typename VT<R, CPLX>::T* __restrict__ W, int want_W) {
+    using D = typename VT<double, CPLX>::T;
+    using T = typename VT<R, CPLX>::T;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)nsites * ncol) return;
+    const int s = (int)(t / ncol), n = (int)(t - (long)s * ncol);
+    const SiteDev S = sites[s];
+    D c[kMaxProj];
+    for (int p = 0; p < S.nproj; ++p) {
+        D acc = zero_of(D());
+        for (int it = item_first[s]; it < item_first[s + 1]; ++it)
+            acc = add(acc, part[((size_t)it * kMaxProj + p) * ncol + n]);
+        c[p] = mulr(dV, acc);
+        C[(size_t)(S.proj_off + p) * ncol + n] = c[p];
+    }
+    if (!want_W) return;
+    for (int p = 0; p < S.nproj; ++p) {
+        D w = zero_of(D());
+        if (S.kind == 0) {
+            w = mulr(gamma[S.proj_off + p], c[p]);
+        } else {
+            // coefficient of phi_p: sum_m M[p][m] C_m  (M = (U/2)(I - 2D), Eq. DerED)
+            for (int m = 0; m < S.nproj; ++m) {
+                D mm;
+                if constexpr (CPLX) {
+                    const double* Mi = M + (size_t)S.hub_index * 50;
+                    mm = make_double2(Mi[2 * (p * 5 + m)], Mi[2 * (p * 5 + m) + 1]);
+                } else {
+                    mm = M[(size_t)S.hub_index * 25 + p * 5 + m];
+                }
+                w = cfma(mm, c[m], w);
+            }
+        }
+        T wv;
+        if constexpr (CPLX) wv = T{(R)w.x, (R)w.y};
+        else wv = (R)w;
+        W[(size_t)(S.proj_off + p) * ncol + n] = wv;
+    }
+}
+
+// ---------------------------------------------------------------------------- scatter
+template <typename R, bool CPLX>
+__global__ void __launch_bounds__(256)
+k_scatter(typename VT<R, CPLX>::T* __restrict__ Y, int ld, int ncol, long Nd,
+          const int* __restrict__ csr_off, const int* __restrict__ csr_val,
+          const int* __restrict__ csr_w, const int* __restrict__ csr_np,
+          const typename VT<R, CPLX>::T* __restrict__ vals,
+          const typename VT<R, CPLX>::T* __restrict__ W, R alpha) {
+    using T = typename VT<R, CPLX>::T;
+    const long g = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= Nd) return;
+    const int e0 = csr_off[g], e1 = csr_off[g + 1];
+    if (e0 == e1) return;
+    const int c0 = blockIdx.y * SNB;
+    T acc[SNB];
+#pragma unroll
+    for (int j = 0; j < SNB; ++j) acc[j] = zero_of(T());
+    for (int e = e0; e < e1; ++e) {
+        const int vb = csr_val[e], wr = csr_w[e], np = csr_np[e];
+        for (int p = 0; p < np; ++p) {
+            const T v = vals[vb + p];
+            const T* wrow = W + (size_t)(wr + p) * ncol + c0;
+#pragma unroll
+            for (int j = 0; j < SNB; ++j)
+                if (c0 + j < ncol) acc[j] = cfma(v, wrow[j], acc[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < SNB; ++j) {
+        if (c0 + j < ncol) {
+            T* y = Y + (size_t)(c0 + j) * ld + g;
+            *y = fmar(alpha, acc[j], *y);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------- occupation
+template <bool CPLX>
+__global__ void k_occupation(int ncol, const SiteDev* __restrict__ sites, const int* __restrict__ hub_sites,
+                             const typename VT<double, CPLX>::T* __restrict__ C,
+                             const double* __restrict__ f, double kweight,
+                             double* __restrict__ D, double* __restrict__ eu, const double* __restrict__ U) {
+    using Dt = typename VT<double, CPLX>::T;
+    const int hsite = blockIdx.x;
+    const SiteDev S = sites[hub_sites[hsite]];
+    __shared__ double red[25][2][33];
+    double are[25], aim[25];
+    for (int q = 0; q < 25; ++q) { are[q] = 0.0; aim[q] = 0.0; }
+    for (int n = threadIdx.x; n < ncol; n += blockDim.x) {
+        Dt c[5];
+        for (int m = 0; m < 5; ++m) c[m] = C[(size_t)(S.proj_off + m) * ncol + n];
+        const double fn = f[n];
+        for (int m = 0; m < 5; ++m)
+            for (int mp = 0; mp < 5; ++mp) {
+                // D_mm' += f_n C_m conj(C_m')
+                if constexpr (CPLX) {
+                    are[m * 5 + mp] += fn * (c[m].x * c[mp].x + c[m].y * c[mp].y);
+                    aim[m * 5 + mp] += fn * (c[m].y * c[mp].x - c[m].x * c[mp].y);
+                } else {
+                    are[m * 5 + mp] += fn * c[m] * c[mp];
+                }
+            }
+    }
+    // deterministic block reduction: warp shuffles, then warp 0 over the warps
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int q = 0; q < 25; ++q) {
+        double vr = are[q], vi = aim[q];
+        for (int o = 16; o > 0; o >>= 1) {
+            vr += __shfl_down_sync(0xffffffffu, vr, o);
+            vi += __shfl_down_sync(0xffffffffu, vi, o);
+        }
+        if (lane == 0) { red[q][0][wid] = vr; red[q][1][wid] = vi; }
+    }
+    __syncthreads();
+    __shared__ double Dm[25][2];
+    if (threadIdx.x < 25) {
+        double vr = 0.0, vi = 0.0;
+        for (int w = 0; w < nw; ++w) { vr += red[threadIdx.x][0][w]; vi += red[threadIdx.x][1][w]; }
+        Dm[threadIdx.x][0] = kweight * vr;
+        Dm[threadIdx.x][1] = kweight * vi;
+        D[(size_t)hsite * 50 + 2 * threadIdx.x] = kweight * vr;
+        D[(size_t)hsite * 50 + 2 * threadIdx.x + 1] = kweight * vi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // E_U contribution (U/2) Tr(D - D^2); Tr(D^2) = sum_mm' D_mm' D_m'm
+        double tr = 0.0, tr2 = 0.0;
+        for (int m = 0; m < 5; ++m) {
+            tr += Dm[m * 5 + m][0];
+            for (int mp = 0; mp < 5; ++mp)
+                tr2 += Dm[m * 5 + mp][0] * Dm[mp * 5 + m][0] - Dm[m * 5 + mp][1] * Dm[mp * 5 + m][1];
+        }
+        eu[hsite] = 0.5 * U[hsite] * (tr - tr2);
+    }
+}
+
+__global__ void k_sum_serial(const double* __restrict__ x, int n, double* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += x[i];
+        *out = s;
+    }
+}
+
+double radial_norm(int l, double rs) {
+    return std::sqrt(2.0 / (std::tgamma(l + 1.5) * std::pow(rs, 2 * l + 3)));
+}
+
+template <typename Tp>
+int upload(hub_t h, Tp** dptr, const std::vector<Tp>& v) {
+    if (*dptr) { cudaFree(*dptr); *dptr = nullptr; }
+    if (v.empty()) return HUB_OK;
+    HUB_CUDA_TRY(h, cudaMalloc((void**)dptr, v.size() * sizeof(Tp)));
+    HUB_CUDA_TRY(h, cudaMemcpy(*dptr, v.data(), v.size() * sizeof(Tp), cudaMemcpyHostToDevice));
+    return HUB_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------- host side
+
+void free_table(Table& t) {
+    void* ptrs[] = {t.d_sites, t.d_items, t.d_item_first, t.d_idx, t.d_vals, t.d_csr_off,
+                    t.d_csr_val, t.d_csr_w, t.d_csr_np, t.d_gamma, t.d_hub_sites, t.d_U,
+                    t.d_M[0], t.d_M[1]};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    t = Table();
+}
+
+static int floordiv_host(double a) { return (int)std::floor(a); }
+
+int build_tables(hub_t h, int natoms, const double* pos, const int* kb_nchan, const int* kb_l,
+                 const double* kb_rs, const double* kb_gamma, const double* kb_rc,
+                 const int* hub_l, const double* hub_rs, const double* hub_rc,
+                 const double* hub_U) {
+    Table t;
+    const int n[3] = {h->n1, h->n2, h->n3};
+    std::vector<std::vector<int>> site_pts;
+    std::vector<double> gamma_rows;
+    int ch_base = 0;
+    for (int a = 0; a < natoms; ++a) {
+        const double* R = pos + 3 * a;
+        const int nch = kb_nchan ? kb_nchan[a] : 0;
+        for (int kind = 0; kind < 2; ++kind) {
+            SiteDev S{};
+            S.R[0] = R[0]; S.R[1] = R[1]; S.R[2] = R[2];
+            S.hub_index = -1;
+            S.kind = kind;
+            if (kind == 0) {
+                if (nch <= 0) continue;
+                if (nch > 3) return fail(h, HUB_EINVAL, "at most 3 KB channels per atom");
+                S.rc = kb_rc[a];
+                S.nch = nch;
+                for (int c = 0; c < nch; ++c) {
+                    S.l[c] = kb_l[ch_base + c];
+                    S.rs[c] = kb_rs[ch_base + c];
+                    if (S.l[c] < 0 || S.l[c] > 2 || S.rs[c] <= 0)
+                        return fail(h, HUB_EINVAL, "KB channel needs 0 <= l <= 2 and rs > 0");
+                    S.N[c] = radial_norm(S.l[c], S.rs[c]);
+                }
+            } else {
+                if (!hub_l || hub_l[a] < 0) continue;
+                if (hub_l[a] != 2) return fail(h, HUB_EINVAL, "only d (l = 2) Hubbard shells");
+                S.rc = hub_rc[a];
+                S.nch = 1;
+                S.l[0] = 2;
+                S.rs[0] = hub_rs[a];
+                if (S.rs[0] <= 0) return fail(h, HUB_EINVAL, "Hubbard rs must be > 0");
+                S.N[0] = radial_norm(2, hub_rs[a]);
+                S.hub_index = (int)t.h_U.size();
+                t.h_U.push_back(hub_U[a]);
+                t.h_hub_sites.push_back((int)t.h_sites.size());
+            }
+            if (!(S.rc > 0)) return fail(h, HUB_EINVAL, "cutoff radius must be > 0");
+            int np = 0;
+            for (int c = 0; c < S.nch; ++c) np += 2 * S.l[c] + 1;
+            S.nproj = np;
+            // grid points within rc of any lattice image R + T
+            std::vector<int> pts;
+            int tlo[3], thi[3], tmin[3] = {1 << 30, 1 << 30, 1 << 30}, tmax[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+            for (int ax = 0; ax < 3; ++ax) {
+                tlo[ax] = floordiv_host((-R[ax] - S.rc) / h->L[ax]) - 1;
+                thi[ax] = floordiv_host((h->L[ax] - R[ax] + S.rc) / h->L[ax]) + 1;
+            }
+            for (int t1 = tlo[0]; t1 <= thi[0]; ++t1)
+                for (int t2 = tlo[1]; t2 <= thi[1]; ++t2)
+                    for (int t3 = tlo[2]; t3 <= thi[2]; ++t3) {
+                        const int tt[3] = {t1, t2, t3};
+                        double c[3];
+                        int lo[3], hi[3];
+                        bool empty = false;
+                        for (int ax = 0; ax < 3; ++ax) {
+                            c[ax] = R[ax] + tt[ax] * h->L[ax];
+                            lo[ax] = std::max((int)std::ceil((c[ax] - S.rc) / h->h[ax]), 0);
+                            hi[ax] = std::min((int)std::floor((c[ax] + S.rc) / h->h[ax]), n[ax] - 1);
+                            if (hi[ax] < lo[ax]) empty = true;
+                        }
+                        if (empty) continue;
+                        bool any = false;
+                        for (int k3 = lo[2]; k3 <= hi[2]; ++k3) {
+                            const double dz = k3 * h->h[2] - c[2];
+                            for (int k2 = lo[1]; k2 <= hi[1]; ++k2) {
+                                const double dy = k2 * h->h[1] - c[1];
+                                for (int k1 = lo[0]; k1 <= hi[0]; ++k1) {
+                                    const double dx = k1 * h->h[0] - c[0];
+                                    if (dx * dx + dy * dy + dz * dz < S.rc * S.rc) {
+                                        pts.push_back(k1 + n[0] * (k2 + n[1] * k3));
+                                        any = true;
+                                    }
+                                }
+                            }
+                        }
+                        if (any)
+                            for (int ax = 0; ax < 3; ++ax) {
+                                tmin[ax] = std::min(tmin[ax], tt[ax]);
+                                tmax[ax] = std::max(tmax[ax], tt[ax]);
+                            }
+                    }
+            std::sort(pts.begin(), pts.end());
+            pts.erase(std::unique(pts.begin(), pts.end()), pts.end());
+            if (pts.empty()) continue;   // cannot happen for rc > 0 and a grid inside the cell
+            for (int ax = 0; ax < 3; ++ax) { S.tlo[ax] = tmin[ax]; S.thi[ax] = tmax[ax]; }
+            S.npts = (int)pts.size();
+            S.pt_off = t.npts;
+            S.val_off = t.nvals;
+            S.proj_off = t.nproj;
+            if ((long)t.nvals + (long)S.npts * np > 2000000000L)
+                return fail(h, HUB_EINVAL, "projector tables exceed 2^31 values");
+            t.npts += S.npts;
+            t.nvals += S.npts * np;
+            t.nproj += np;
+            for (int c = 0; c < S.nch; ++c)
+                for (int m = 0; m < 2 * S.l[c] + 1; ++m)
+                    gamma_rows.push_back(kind == 0 ? kb_gamma[ch_base + c] : 0.0);
+            t.h_sites.push_back(S);
+            site_pts.push_back(std::move(pts));
+        }
+        ch_base += nch;
+    }
+    t.nsites = (int)t.h_sites.size();
+    t.nhub = (int)t.h_U.size();
+
+    // flat row -> grid index, gather items, CSR of entries per grid point
+    std::vector<int> idx(t.npts);
+    std::vector<int> items;
+    t.h_item_first.assign(t.nsites + 1, 0);
+    for (int s = 0; s < t.nsites; ++s) {
+        const SiteDev& S = t.h_sites[s];
+        std::copy(site_pts[s].begin(), site_pts[s].end(), idx.begin() + S.pt_off);
+        t.h_item_first[s] = (int)items.size() / 3;
+        for (int f = 0; f < S.npts; f += GITEM) {
+            items.push_back(s);
+            items.push_back(S.pt_off + f);
+            items.push_back(std::min(GITEM, S.npts - f));
+        }
+    }
+    t.nitems = (int)items.size() / 3;
+    t.h_item_first[t.nsites] = t.nitems;
+    std::vector<int> csr_off(h->Nd + 1, 0);
+    for (int r = 0; r < t.npts; ++r) csr_off[idx[r] + 1]++;
+    for (long g = 0; g < h->Nd; ++g) csr_off[g + 1] += csr_off[g];
+    std::vector<int> fill(csr_off.begin(), csr_off.end() - 1);
+    std::vector<int> csr_val(t.npts), csr_w(t.npts), csr_np(t.npts);
+    for (int s = 0; s < t.nsites; ++s) {
+        const SiteDev& S = t.h_sites[s];
+        for (int l = 0; l < S.npts; ++l) {
+            const int e = fill[idx[S.pt_off + l]]++;
+            csr_val[e] = S.val_off + l * S.nproj;
+            csr_w[e] = S.proj_off;
+            csr_np[e] = S.nproj;
+        }
+    }
+
+    int rc;
+    if ((rc = upload(h, &t.d_sites, t.h_sites))) return rc;
+    if ((rc = upload(h, &t.d_items, items))) return rc;
+    if ((rc = upload(h, &t.d_item_first, t.h_item_first))) return rc;
+    if ((rc = upload(h, &t.d_idx, idx))) return rc;
+    if ((rc = upload(h, &t.d_csr_off, csr_off))) return rc;
+    if ((rc = upload(h, &t.d_csr_val, csr_val))) return rc;
+    if ((rc = upload(h, &t.d_csr_w, csr_w))) return rc;
+    if ((rc = upload(h, &t.d_csr_np, csr_np))) return rc;
+    if ((rc = upload(h, &t.d_gamma, gamma_rows))) return rc;
+    if ((rc = upload(h, &t.d_hub_sites, t.h_hub_sites))) return rc;
+    if ((rc = upload(h, &t.d_U, t.h_U))) return rc;
+    const size_t vbytes = (size_t)t.nvals * h->esize * (h->cplx ? 2 : 1);
+    if (vbytes) {
+        HUB_CUDA_TRY(h, cudaMalloc(&t.d_vals, vbytes));
+        dim3 grid(t.nitems);
+        const double* kp = h->kpt;
+        if (h->esize == 8) {
+            if (h->cplx)
+                k_table_values<double, true><<<grid, 256, 0, h->stream>>>(t.d_sites, t.d_items, t.d_idx, (double*)t.d_vals, h->n1, h->n2, h->h[0], h->h[1], h->h[2], h->L[0], h->L[1], h->L[2], kp[0], kp[1], kp[2]);
+            else
+                k_table_values<double, false><<<grid, 256, 0, h->stream>>>(t.d_sites, t.d_items, t.d_idx, (double*)t.d_vals, h->n1, h->n2, h->h[0], h->h[1], h->h[2], h->L[0], h->L[1], h->L[2], kp[0], kp[1], kp[2]);
+        } else {
+            if (h->cplx)
+                k_table_values<float, true><<<grid, 256, 0, h->stream>>>(t.d_sites, t.d_items, t.d_idx, (float*)t.d_vals, h->n1, h->n2, h->h[0], h->h[1], h->h[2], h->L[0], h->L[1], h->L[2], kp[0], kp[1], kp[2]);
+            else
+                k_table_values<float, false><<<grid, 256, 0, h->stream>>>(t.d_sites, t.d_items, t.d_idx, (float*)t.d_vals, h->n1, h->n2, h->h[0], h->h[1], h->h[2], h->L[0], h->L[1], h->L[2], kp[0], kp[1], kp[2]);
+        }
+        HUB_CUDA_TRY(h, cudaGetLastError());
+    }
+    const size_t mbytes = (size_t)std::max(t.nhub, 1) * 25 * sizeof(double) * (h->cplx ? 2 : 1);
+    for (int s = 0; s < 2; ++s) {
+        HUB_CUDA_TRY(h, cudaMalloc((void**)&t.d_M[s], mbytes));
+        HUB_CUDA_TRY(h, cudaMemsetAsync(t.d_M[s], 0, mbytes, h->stream));
+    }
+    // the D = 0 coefficients M = (U/2) I
+    for (int s = 0; s < 2; ++s) {
+        std::vector<double> M((size_t)std::max(t.nhub, 1) * 25 * (h->cplx ? 2 : 1), 0.0);
+        for (int i = 0; i < t.nhub; ++i)
+            for (int m = 0; m < 5; ++m) M[(size_t)(i * 25 + m * 5 + m) * (h->cplx ? 2 : 1)] = 0.5 * t.h_U[i];
+        HUB_CUDA_TRY(h, cudaMemcpyAsync(t.d_M[s], M.data(), M.size() * sizeof(double),
+                                        cudaMemcpyHostToDevice, h->stream));
+    }
+    HUB_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    free_table(h->proj);
+    h->proj = std::move(t);
+    return HUB_OK;
+}
+
+template <typename R, bool CPLX>
+static int gather_t(hub_t h, const void* X, int ncol, int ld, int spin, bool want_W) {
+    using T = typename VT<R, CPLX>::T;
+    using D = typename VT<double, CPLX>::T;
+    Table& t = h->proj;
+    int rc;
+    if ((rc = ensure(h, &h->d_part, &h->part_bytes, (size_t)t.nitems * kMaxProj * ncol * sizeof(D)))) return rc;
+    if ((rc = ensure(h, &h->d_C, &h->C_bytes, (size_t)t.nproj * ncol * sizeof(D)))) return rc;
+    if ((rc = ensure(h, &h->d_W, &h->W_bytes, (size_t)t.nproj * ncol * sizeof(T)))) return rc;
+    dim3 g1(t.nitems, (ncol + GNB - 1) / GNB);
+    k_gather<R, CPLX><<<g1, 128, 0, h->stream>>>((const T*)X, ld, ncol, t.d_sites, t.d_items, t.d_idx,
+                                                 (const T*)t.d_vals, (D*)h->d_part);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    const long nthr = (long)t.nsites * ncol;
+    k_reduce_transform<R, CPLX><<<(unsigned)((nthr + 127) / 128), 128, 0, h->stream>>>(
+        t.nsites, ncol, h->dV, t.d_sites, t.d_item_first, (const D*)h->d_part, t.d_gamma,
+        t.d_M[spin], (D*)h->d_C, (T*)h->d_W, want_W ? 1 : 0);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    return HUB_OK;
+}
+
+int launch_gather(hub_t h, const void* X, int ncol, int ld, int spin, bool want_W) {
+    if (ncol == 0 || h->proj.nsites == 0) return HUB_OK;
+    if (h->esize == 8) return h->cplx ? gather_t<double, true>(h, X, ncol, ld, spin, want_W)
+                                      : gather_t<double, false>(h, X, ncol, ld, spin, want_W);
+    return h->cplx ? gather_t<float, true>(h, X, ncol, ld, spin, want_W)
+                   : gather_t<float, false>(h, X, ncol, ld, spin, want_W);
+}
+
+template <typename R, bool CPLX>
+static int scatter_t(hub_t h, void* Y, int ncol, int ld, double alpha) {
+    using T = typename VT<R, CPLX>::T;
+    Table& t = h->proj;
+    dim3 grid((unsigned)((h->Nd + 255) / 256), (ncol + SNB - 1) / SNB);
+    k_scatter<R, CPLX><<<grid, 256, 0, h->stream>>>((T*)Y, ld, ncol, h->Nd, t.d_csr_off, t.d_csr_val,
+                                                    t.d_csr_w, t.d_csr_np, (const T*)t.d_vals,
+                                                    (const T*)h->d_W, (R)alpha);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    return HUB_OK;
+}
+
+int launch_scatter(hub_t h, void* Y, int ncol, int ld, double alpha) {
+    if (ncol == 0 || h->proj.nsites == 0) return HUB_OK;
+    if (h->esize == 8) return h->cplx ? scatter_t<double, true>(h, Y, ncol, ld, alpha)
+                                      : scatter_t<double, false>(h, Y, ncol, ld, alpha);
+    return h->cplx ? scatter_t<float, true>(h, Y, ncol, ld, alpha)
+                   : scatter_t<float, false>(h, Y, ncol, ld, alpha);
+}
+
+int launch_occupation(hub_t h, int ncol, const double* f_dev, double kweight, double* D_dev) {
+    Table& t = h->proj;
+    if (t.nhub == 0) {
+        HUB_CUDA_TRY(h, cudaMemsetAsync(h->d_scal, 0, sizeof(double), h->stream));
+        return HUB_OK;
+    }
+    double* eu = h->d_scal + 256;   // per-atom E_U contributions (slots 256..375)
+    if (t.nhub > 120) return fail(h, HUB_EINVAL, "more than 120 Hubbard atoms not supported");
+    if (h->cplx)
+        k_occupation<true><<<t.nhub, 256, 0, h->stream>>>(ncol, t.d_sites, t.d_hub_sites, (const double2*)h->d_C,
+                                                         f_dev, kweight, D_dev, eu, t.d_U);
+    else
+        k_occupation<false><<<t.nhub, 256, 0, h->stream>>>(ncol, t.d_sites, t.d_hub_sites, (const double*)h->d_C,
+                                                          f_dev, kweight, D_dev, eu, t.d_U);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    k_sum_serial<<<1, 32, 0, h->stream>>>(eu, t.nhub, h->d_scal);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    return HUB_OK;
+}
+
+}  // namespace hub

@@ -1,0 +1,166 @@
+// Fused finite-difference stencil: Laplacian (2*n0-th order, Sec. II.B) + local potential
+// + Chebyshev three-term recurrence update, with the Bloch-periodic index wrap.
+//
+//   Yout = alpha * (-1/2 Lap_h Y + V .* Y - shift * Y) + beta * Yprev
+//
+// Layout: Y[g + col*ld], g = x + n1*(y + n2*z).  One CTA owns a TX x TY tile of the x-y
+// plane for one column and marches along z over a chunk of planes.  The z-neighbours live
+// in a register queue of 2*NH+1 values per thread (each plane is read from HBM once per
+// chunk); the x/y neighbours of the current plane are staged in shared memory together
+// with an NH-wide halo (halo reads hit L2).  Slots beyond the grid hold the wrapped
+// value times the Bloch factor exp(i k_a L_a)^wraps, so ragged tiles and grids smaller
+// than the stencil need no special cases.  Yprev may alias Yout (each element is read
+// and written by the same thread).
+#include "hub_internal.cuh"
+#include "cplx.cuh"
+
+namespace hub {
+
+template <typename R>
+struct StencilDev {
+    const void* Y;
+    const void* Yprev;
+    void* Yout;
+    const R* V;
+    int n1, n2, n3, ld;
+    R w[3][6];
+    R center, alpha, beta;
+    double ph[3][2];
+    int zchunk, nzc;
+};
+
+__device__ __forceinline__ int floordiv(int a, int n) {
+    int q = a / n;
+    return (a % n != 0 && a < 0) ? q - 1 : q;
+}
+
+template <typename R, bool CPLX, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY)
+k_stencil(StencilDev<R> a) {
+    constexpr int NH = 6;
+    constexpr int SX = TX + 2 * NH, SY = TY + 2 * NH;
+    using T = typename VT<R, CPLX>::T;
+    __shared__ T s[SY][SX];
+    __shared__ int sxg[SX], syg[SY];
+    __shared__ T sxp[SX], syp[SY];
+
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int col = blockIdx.z / a.nzc;
+    const int zc = blockIdx.z - col * a.nzc;
+    const int z0 = zc * a.zchunk;
+    const int z1 = min(z0 + a.zchunk, a.n3);
+    const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
+    const size_t plane = (size_t)n1 * n2;
+
+    for (int i = tid; i < SX; i += TX * TY) {
+        int g = blockIdx.x * TX - NH + i;
+        int w = floordiv(g, n1);
+        sxg[i] = g - w * n1;
+        sxp[i] = phase_pow<T>(a.ph[0][0], a.ph[0][1], w);
+    }
+    for (int i = tid; i < SY; i += TX * TY) {
+        int g = blockIdx.y * TY - NH + i;
+        int w = floordiv(g, n2);
+        syg[i] = g - w * n2;
+        syp[i] = phase_pow<T>(a.ph[1][0], a.ph[1][1], w);
+    }
+    __syncthreads();
+
+    const T* __restrict__ Y = reinterpret_cast<const T*>(a.Y) + (size_t)col * a.ld;
+    const T* Yp = a.Yprev ? reinterpret_cast<const T*>(a.Yprev) + (size_t)col * a.ld : nullptr;
+    T* Yo = reinterpret_cast<T*>(a.Yout) + (size_t)col * a.ld;
+
+    const int gx = sxg[tx + NH], gy = syg[ty + NH];
+    const T pxy = cmul(sxp[tx + NH], syp[ty + NH]);
+    const bool active = (blockIdx.x * TX + tx < n1) && (blockIdx.y * TY + ty < n2);
+    const size_t colofs = (size_t)gy * n1 + gx;
+
+    T q[2 * NH + 1];
+#pragma unroll
+    for (int j = 0; j < 2 * NH + 1; ++j) {
+        int zz = z0 - NH + j;
+        int w = floordiv(zz, n3);
+        int zw = zz - w * n3;
+        q[j] = cmul(cmul(Y[(size_t)zw * plane + colofs], pxy),
+                    phase_pow<T>(a.ph[2][0], a.ph[2][1], w));
+    }
+
+    for (int z = z0; z < z1; ++z) {
+        s[ty + NH][tx + NH] = q[NH];
+        const size_t zofs = (size_t)z * plane;
+        for (int i = tid; i < SX * SY; i += TX * TY) {
+            int ix = i % SX, iy = i / SX;
+            bool interior = (ix >= NH) && (ix < TX + NH) && (iy >= NH) && (iy < TY + NH);
+            if (!interior)
+                s[iy][ix] = cmul(Y[zofs + (size_t)syg[iy] * n1 + sxg[ix]], cmul(sxp[ix], syp[iy]));
+        }
+        __syncthreads();
+        if (active) {
+            const size_t g = zofs + colofs;
+            T acc = mulr(a.center + a.alpha * a.V[g], q[NH]);
+#pragma unroll
+            for (int p = 1; p <= NH; ++p) {
+                acc = fmar(a.w[2][p - 1], add(q[NH + p], q[NH - p]), acc);
+                acc = fmar(a.w[0][p - 1], add(s[ty + NH][tx + NH + p], s[ty + NH][tx + NH - p]), acc);
+                acc = fmar(a.w[1][p - 1], add(s[ty + NH + p][tx + NH], s[ty + NH - p][tx + NH]), acc);
+            }
+            if (Yp) acc = fmar(a.beta, Yp[g], acc);
+            Yo[g] = acc;
+        }
+        __syncthreads();
+        if (z + 1 < z1) {
+#pragma unroll
+            for (int j = 0; j < 2 * NH; ++j) q[j] = q[j + 1];
+            int zz = z + NH + 1;
+            int w = floordiv(zz, n3);
+            int zw = zz - w * n3;
+            q[2 * NH] = cmul(cmul(Y[(size_t)zw * plane + colofs], pxy),
+                             phase_pow<T>(a.ph[2][0], a.ph[2][1], w));
+        }
+    }
+}
+
+template <typename R, bool CPLX>
+static int run(hub_t h, const StencilArgs& s) {
+    constexpr int TX = 32, TY = 8;
+    StencilDev<R> d;
+    d.Y = s.Y;
+    d.Yprev = s.Yprev;
+    d.Yout = s.Yout;
+    d.V = reinterpret_cast<const R*>(s.V);
+    d.n1 = s.n1; d.n2 = s.n2; d.n3 = s.n3; d.ld = s.ld;
+    for (int a = 0; a < 3; ++a) {
+        for (int p = 0; p < 6; ++p) d.w[a][p] = (R)(p < s.n0 ? s.w[a][p] : 0.0);
+        d.ph[a][0] = s.phase[a][0];
+        d.ph[a][1] = s.phase[a][1];
+    }
+    d.center = (R)s.center;
+    d.alpha = (R)s.alpha;
+    d.beta = (R)s.beta;
+    const int tiles = ((s.n1 + TX - 1) / TX) * ((s.n2 + TY - 1) / TY);
+    // enough CTAs to fill the GPU several times over, but chunks long enough that the
+    // 2*NH-plane queue fill stays a small overhead
+    const long want = 8L * h->num_sms;
+    long per = (long)tiles * s.ncol;
+    int nzc = 1;
+    if (per < want) nzc = (int)((want + per - 1) / per);
+    int zchunk = (s.n3 + nzc - 1) / nzc;
+    if (zchunk < 8) zchunk = s.n3 < 8 ? s.n3 : 8;
+    nzc = (s.n3 + zchunk - 1) / zchunk;
+    while ((long)s.ncol * nzc > 65535) { zchunk *= 2; nzc = (s.n3 + zchunk - 1) / zchunk; }
+    d.zchunk = zchunk;
+    d.nzc = nzc;
+    dim3 grid((s.n1 + TX - 1) / TX, (s.n2 + TY - 1) / TY, s.ncol * nzc);
+    k_stencil<R, CPLX, TX, TY><<<grid, TX * TY, 0, h->stream>>>(d);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    return HUB_OK;
+}
+
+int launch_stencil(hub_t h, const StencilArgs& a) {
+    if (a.ncol == 0) return HUB_OK;
+    if (h->esize == 8) return h->cplx ? run<double, true>(h, a) : run<double, false>(h, a);
+    return h->cplx ? run<float, true>(h, a) : run<float, false>(h, a);
+}
+
+}  // namespace hub
