@@ -1,0 +1,345 @@
+#!/usr/bin/env python3
+"""Benchmark of the DFT+U CheFSI hot path on GB300.
+
+Metric: H.psi throughput in Gpt.orb/s (grid points x orbitals x H applications per second,
+/1e9) over whole SCF iterations.  Default workload: the rutile-shaped 2x2x3 supercell
+(24 Ti + 48 O, 17.36 x 17.36 x 16.78 bohr, 88x88x84 grid), 348 orbitals per spin, two spin
+channels, 12th-order FD, Chebyshev degree 24, FP64.  One step = one SCF iteration through the
+library's public entry point hub_scf_iterate: per spin a degree-24 filter and a Rayleigh-Ritz
+projection (25 H applications), then Fermi level, occupation matrices, E_U and Pulay mixing.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec f64|f32|mixed]
+        python bench.py --impl reference ...      (the CPU oracle arm)
+Multi-GPU (torchrun, one rank per GPU): each rank runs an independent replica of the
+workload (spin channels / snapshots are independent units): weak scaling, no collective on
+the data path.  Inputs are synthetic (seeded); every orbital block is larger than L2.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PREC = {"f64": 0, "f32": 1, "mixed": 2}
+DTYPE_NAME = {"f64": "f64", "f32": "f32", "mixed": "f32+bf16"}
+# FP64 pipe of one GB300: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (max SM clock)
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+# algorithmic work per point-orbital of one stencil pass (12th order, symmetric pairing):
+# 18 adds + 18 FMAs for the 36 neighbours, 1 FMA for alpha*V + centre, 1 multiply, 1 FMA
+# for beta*Yprev  -> 18 + 36 + 2 + 1 + 2 = 59 flop; bytes: read Y, read Yprev, write Yout
+STENCIL_FLOP = 59.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hub", choices=["hub", "reference"])
+    ap.add_argument("--prec", default="f64", choices=list(PREC))
+    ap.add_argument("--workload", default="rutile", choices=["rutile", "tiny"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--scf-tts", action="store_true",
+                    help="also run one cold-start SCF to convergence and report its time")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def make_workload(name):
+    import workloads as w
+    return w.rutile() if name == "rutile" else w.tiny()
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ CPU oracle
+CPU_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import workloads as w
+from oracle import hubbard as o
+wl = {make!s}
+H = o.build_hamiltonian(wl, 0)
+X = w.random_orbitals(wl.Nd, {cols}, 77).T.copy()
+H.apply(X)
+n, t0 = 0, time.perf_counter()
+while True:
+    X = H.apply(X)
+    X /= np.linalg.norm(X, axis=0)
+    n += 1
+    if time.perf_counter() - t0 > {secs}:
+        break
+dt = time.perf_counter() - t0
+print(json.dumps({{"applications": n, "seconds": dt, "cols": {cols}, "Nd": wl.Nd}}))
+"""
+
+
+def cpu_oracle_sample(workload: str, seconds: float, cols: int = 2):
+    """Time the oracle's H application on a bounded sample, single-threaded numpy."""
+    make = "w.rutile()" if workload == "rutile" else "w.tiny()"
+    code = CPU_SNIPPET.format(root=ROOT, make=make, cols=cols, secs=seconds)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError("CPU oracle sample failed: " + r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    value = d["Nd"] * d["cols"] * d["applications"] / d["seconds"] / 1e9
+    return value, d
+
+
+# ------------------------------------------------------------------------------ hub arm
+def run_hub(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2507_23612_gb300 import Hub, scf_params
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    wl = make_workload(args.workload)
+    nspin = wl.nspin
+    hub = Hub(wl.n, wl.L, wl.fd_half_order, prec=PREC[args.prec], stream=stream)
+    hub.set_veff(torch.tensor(wl.veff, device=dev))
+    hub.set_atoms(wl.atoms)
+    dt = hub.dtype
+    # each rank is an independent replica: its own seeded starting orbitals
+    X0 = [wl.orbitals(s + 2 * rank) for s in range(nspin)]
+    Xs = [torch.tensor(x, device=dev).to(dt).contiguous() for x in X0]
+    v0s = [torch.tensor(wl.lanczos_start(s), device=dev).to(dt).contiguous() for s in range(nspin)]
+    p = scf_params(nspin=nspin, ncol=wl.ncol, ld=wl.Nd, degree=wl.degree, max_iter=1000,
+                   first_passes=3 if args.workload == "rutile" else 1, lanczos_steps=10,
+                   pulay_history=7, natoms=len(wl.atoms), pulay_beta=0.3,
+                   kT=wl.kT if wl.kT > 0 else 0.005, n_elec=wl.n_elec, tol_e_atom=1e-5, tol_D=1e-4)
+    hub.scf_begin(p, Xs, v0s, wl.D0)
+    for _ in range(args.warmup):
+        hub.scf_iterate()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    hub.profile(-1)
+    hub.profile(1)
+    n0 = hub.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    last = None
+    for _ in range(args.steps):
+        last = hub.scf_iterate()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = hub.launch_count() - n0
+    hub.profile(0)
+    prof = hub.profile_read()
+    clocks = sampler.stop()
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ptorb_step = nspin * (wl.degree + 1) * wl.Nd * wl.ncol
+    value = ptorb_step * args.steps * world / (ms / 1e3) / 1e9
+
+    # e2e: the same step through the public API with the orbitals on the host (pinned):
+    # every step copies the blocks host->device, iterates, and copies the blocks, the
+    # eigenvalues and D back to the host.
+    e2e = None
+    if not args.no_e2e:
+        hosts = [torch.empty(x.shape, dtype=dt, pin_memory=True) for x in Xs]
+        for hx, x in zip(hosts, Xs):
+            hx.copy_(x)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for hx, x in zip(hosts, Xs):
+                x.copy_(hx, non_blocking=True)
+            hub.scf_iterate()
+            for hx, x in zip(hosts, Xs):
+                hx.copy_(x, non_blocking=True)
+            eig, occ, D = hub.scf_get()
+            torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        bx = sum(x.numel() * x.element_size() for x in Xs)
+        e2e = {"value": ptorb_step * args.steps * world / t_e2e / 1e9, "unit": "Gpt·orb/s",
+               "h2d_bytes_per_step": bx,
+               "d2h_bytes_per_step": bx + 8 * (eig.size + occ.size + D.size)}
+
+    tts = None
+    if args.scf_tts:
+        Xs2 = [torch.tensor(x, device=dev).to(dt).contiguous() for x in X0]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hub.scf_begin(p, Xs2, v0s, wl.D0)
+        res = hub.scf_run()
+        torch.cuda.synchronize()
+        tts = {"seconds": time.perf_counter() - t0, "iterations": res["iter"],
+               "converged": bool(res["converged"]), "E_Ha": res["E"], "E_U_Ha": res["E_U"],
+               "criterion": "|dE|/atom < 1e-5 Ha twice and max|dD| < 1e-4"}
+
+    # dominant kernel and its roofline
+    dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 0))
+    roof = None
+    if dom[0] == "stencil":
+        flops = STENCIL_FLOP * wl.Nd * wl.ncol * dom[1][1]      # every timed launch: ncol columns
+        achieved = flops / (dom[1][0] / 1e3) / 1e12
+        if args.prec == "f64":
+            peak = FP64_PEAK_GFLOPS / 1e3
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": "k_stencil<double>",
+                    "peak_source": "FP64 pipe: 152 SM x 2 FMA/clk x 2.07 GHz (probe: 1.196)"}
+        else:
+            bytes_ = 12.0 * wl.Nd * wl.ncol * dom[1][1]
+            gbs = bytes_ / (dom[1][0] / 1e3) / 1e9
+            peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
+                if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+            roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                    "frac": gbs / peak, "traffic": None, "kernel": "k_stencil<float>"}
+    breakdown = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / ms, 4)}
+                 for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+    return {"value": value, "ms": ms, "launches": launches, "e2e": e2e, "tts": tts,
+            "roofline": roof, "kernels": breakdown, "clocks": clocks, "last": last, "wl": wl}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    wl_name = {"rutile": "rutile-2x2x3-72atoms-88x88x84-348orb-2spin-degree24",
+               "tiny": "tiny-24^3-2atoms-32orb-degree20"}[args.workload]
+    metric = "H·psi throughput over SCF iterations"
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        cores = 1
+        vals = []
+        for _ in range(args.warmup):
+            cpu_oracle_sample(args.workload, 2.0)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            v, d = cpu_oracle_sample(args.workload, 8.0)
+            vals.append(v)
+        wall = time.perf_counter() - t0
+        value = sum(vals) / len(vals)
+        sample = (f"oracle H applications to {d['cols']} orbitals of the {wl_name} workload, "
+                  f"about 8 s per step, one numpy thread")
+        print(json.dumps({
+            "metric": metric, "value": value, "unit": "Gpt·orb/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": wl_name, "sample": "bounded oracle sample"},
+            "cpu_baseline": {"value": value, "unit": "Gpt·orb/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "Gpt·orb/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}))
+        return 0
+
+    if world > 1:
+        import torch
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.distributed.init_process_group("nccl", rank=rank, world_size=world,
+                                             device_id=torch.device("cuda", local_rank))
+    r = run_hub(args, rank, world, local_rank)
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            v, d = cpu_oracle_sample(args.workload, args.cpu_seconds)
+            cpu = {"value": v, "unit": "Gpt·orb/s", "cores": 1, "kind": "oracle",
+                   "sample": f"{d['applications']} oracle H applications to {d['cols']} orbitals of "
+                             f"the full {wl_name} grid ({d['seconds']:.1f} s, one numpy thread)"}
+        wl = r["wl"]
+        line = {
+            "metric": metric, "value": r["value"], "unit": "Gpt·orb/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE_NAME[args.prec], "data": "synthetic",
+            "config": {"workload": wl_name, "grid": list(wl.n), "orbitals_per_spin": wl.ncol,
+                       "spins": wl.nspin, "chebyshev_degree": wl.degree,
+                       "h_applications_per_step": wl.nspin * (wl.degree + 1),
+                       "step": "one SCF iteration (filter + Rayleigh-Ritz per spin, occupations, D, E_U, Pulay)",
+                       "l2": "inputs larger than L2 (each orbital block %.2f GB)" % (wl.Nd * wl.ncol * (8 if args.prec == 'f64' else 4) / 1e9),
+                       "parallelism": f"replicas x{world}"},
+            "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"],
+            "gpu_launches": r["launches"], "clocks": r["clocks"],
+            "kernels": r["kernels"],
+        }
+        if r["tts"]:
+            line["scf_time_to_solution"] = r["tts"]
+        print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -63,7 +63,7 @@ typedef enum {
 /* Create a handle for one grid, one Bloch wavevector and one precision.
  *   n1,n2,n3      grid points per axis (each >= 1)
  *   L1,L2,L3      cell side lengths in bohr (h_a = L_a / n_a)
- *   fd_half_order n0 of the 2*n0-th order centred Laplacian (Sec. II.B); 1 <= n0 <= 8
+ *   fd_half_order n0 of the 2*n0-th order centred Laplacian (Sec. II.B); 1 <= n0 <= 6
  *   ncomplex      0: real orbitals (Gamma point, kpt ignored); 1: complex Bloch orbitals
  *   kpt           Bloch wavevector (bohr^-1, Cartesian), host [3]; NULL means Gamma.
  *                 Wrap convention: psi(x + L_a e_a) = exp(i k_a L_a) psi(x).
@@ -194,6 +194,39 @@ int hub_scf_run(hub_t h, hub_scf_result* res);
 /* Results of the last iteration: eig/occ host [nspin*ncol] (may be NULL),
  * D_out host [nspin*nhub*25] (may be NULL). */
 int hub_scf_get(hub_t h, double* eig, double* occ, double* D_out);
+
+/* ---------------------------------------------------------------------------------
+ * Measurement.  Every kernel launch of a handle is counted; with profiling on, each launch
+ * is also bracketed by a pair of CUDA events recorded on the handle's stream (the stream
+ * the kernel runs on), so per-kernel device time can be read back without a profiler.
+ * --------------------------------------------------------------------------------- */
+typedef enum {
+    HUB_K_STENCIL = 0,    /* fused FD Laplacian + V_eff + recurrence axpby */
+    HUB_K_GATHER,         /* projector / orbital inner products */
+    HUB_K_TRANSFORM,      /* reduction of gather partials + gamma / M coefficients */
+    HUB_K_SCATTER,        /* projector scatter into H X */
+    HUB_K_GRAM,           /* X^T Y split-K partial products */
+    HUB_K_GRAM_REDUCE,    /* reduction of the split-K partials */
+    HUB_K_ROTATE,         /* X Q */
+    HUB_K_CHOLESKY,
+    HUB_K_TRI_INVERSE,
+    HUB_K_DGEMM,          /* small n x n products */
+    HUB_K_JACOBI,         /* subspace eigensolver */
+    HUB_K_EIG_MISC,       /* symmetrise, identity, sort */
+    HUB_K_OCCUPATION,     /* D and E_U reduction */
+    HUB_K_LANCZOS,        /* Lanczos vector updates and dot products */
+    HUB_K_COPY,           /* block copies and conversions */
+    HUB_K_TABLE,          /* projector table values */
+    HUB_K_COUNT
+} hub_kernel_kind;
+
+/* enable = 1: start recording events; 0: stop (records kept); -1: drop all records. */
+int hub_profile(hub_t h, int enable);
+/* Sum of recorded device time (ms) and number of recorded launches of one kernel kind.
+ * Synchronises the handle's stream. */
+int hub_profile_read(hub_t h, int kind, double* total_ms, long long* launches);
+/* Kernels launched by this handle since it was created. */
+int hub_launch_count(hub_t h, long long* launches);
 
 /* Library build information: writes a short string (arch, version) into buf. */
 int hub_version(char* buf, int len);

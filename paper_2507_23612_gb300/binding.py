@@ -58,7 +58,14 @@ _SIGS = {
     "hub_scf_run": [_P, C.POINTER(scf_result)],
     "hub_scf_get": [_P, _PD, _PD, _PD],
     "hub_version": [C.c_char_p, _I],
+    "hub_profile": [_P, _I],
+    "hub_profile_read": [_P, _I, _PD, C.POINTER(C.c_longlong)],
+    "hub_launch_count": [_P, C.POINTER(C.c_longlong)],
 }
+
+KERNEL_KINDS = ["stencil", "gather", "transform", "scatter", "gram", "gram_reduce", "rotate",
+                "cholesky", "tri_inverse", "dgemm", "jacobi", "eig_misc", "occupation",
+                "lanczos", "copy", "table"]
 
 
 def load_library(path: str | None = None) -> C.CDLL:
@@ -212,6 +219,24 @@ class Hub:
         self._check(self.lib.hub_lanczos_bound(self.h, spin, steps, _tptr(v0), C.byref(lo), C.byref(up)),
                     "hub_lanczos_bound")
         return lo.value, up.value
+
+    # ------------------------------------------------------------------ measurement
+    def profile(self, enable: int):
+        self._check(self.lib.hub_profile(self.h, int(enable)), "hub_profile")
+
+    def profile_read(self) -> dict:
+        out = {}
+        for k, name in enumerate(KERNEL_KINDS):
+            t, n = C.c_double(), C.c_longlong()
+            self._check(self.lib.hub_profile_read(self.h, k, C.byref(t), C.byref(n)), "hub_profile_read")
+            if n.value:
+                out[name] = (t.value, n.value)
+        return out
+
+    def launch_count(self) -> int:
+        n = C.c_longlong()
+        self._check(self.lib.hub_launch_count(self.h, C.byref(n)), "hub_launch_count")
+        return n.value
 
     # ------------------------------------------------------------------ SCF driver
     def scf_begin(self, params: scf_params, Xs, v0s, D0):

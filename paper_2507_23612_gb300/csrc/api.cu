@@ -177,6 +177,7 @@ int hub_create_grid(hub_t* out, int n1, int n2, int n3, double L1, double L2, do
 int hub_destroy(hub_t h) {
     if (!h) return HUB_OK;
     cudaStreamSynchronize(h->stream);
+    for (auto& e : h->prof) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     free_table(h->proj);
     void* ptrs[] = {h->d_veff, h->d_work, h->d_work2, h->d_part, h->d_C, h->d_W, h->d_small,
                     h->d_gpart, h->d_bf16, h->d_aux, h->d_flags, h->d_bar, h->d_scal};
@@ -600,6 +601,43 @@ int hub_scf_run(hub_t h, hub_scf_result* res) {
     }
     if (res) *res = r;
     return r.converged ? HUB_OK : fail(h, HUB_ENOCONV, "SCF reached max_iter");
+}
+
+int hub_profile(hub_t h, int enable) {
+    if (!h) return HUB_EINVAL;
+    if (enable < 0) {
+        cudaStreamSynchronize(h->stream);
+        for (auto& e : h->prof) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+        h->prof.clear();
+        h->prof_on = 0;
+        return HUB_OK;
+    }
+    h->prof_on = enable ? 1 : 0;
+    return HUB_OK;
+}
+
+int hub_profile_read(hub_t h, int kind, double* total_ms, long long* launches) {
+    if (!h || !total_ms || !launches) return HUB_EINVAL;
+    if (kind < 0 || kind >= HUB_K_COUNT) return fail(h, HUB_EINVAL, "unknown kernel kind");
+    HUB_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    double t = 0.0;
+    long long n = 0;
+    for (auto& e : h->prof) {
+        if (e.kind != kind) continue;
+        float ms = 0.f;
+        HUB_CUDA_TRY(h, cudaEventElapsedTime(&ms, e.a, e.b));
+        t += ms;
+        n++;
+    }
+    *total_ms = t;
+    *launches = n;
+    return HUB_OK;
+}
+
+int hub_launch_count(hub_t h, long long* launches) {
+    if (!h || !launches) return HUB_EINVAL;
+    *launches = h->launches;
+    return HUB_OK;
 }
 
 int hub_scf_get(hub_t h, double* eig, double* occ, double* D_out) {

@@ -310,6 +310,7 @@ int dense_gemm(hub_t h, bool ta, bool tb, int m, int n, int k, double alpha, con
                int lda, const double* B, int ldb, double beta, double* C, int ldc) {
     if (m == 0 || n == 0) return HUB_OK;
     dim3 grid((n + 31) / 32, (m + 31) / 32);
+    ProfScope ps(h, HUB_K_DGEMM);
     k_dgemm<<<grid, 256, 0, h->stream>>>(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
     HUB_CUDA_TRY(h, cudaGetLastError());
     return HUB_OK;
@@ -318,11 +319,11 @@ int dense_gemm(hub_t h, bool ta, bool tb, int m, int n, int k, double alpha, con
 int dense_cholesky(hub_t h, double* A, int n) {
     for (int j0 = 0; j0 < n; j0 += NB) {
         const int jb = std::min(NB, n - j0);
-        k_potf2<<<1, 256, 0, h->stream>>>(A, n, j0, jb, h->d_flags);
+        { ProfScope ps(h, HUB_K_CHOLESKY); k_potf2<<<1, 256, 0, h->stream>>>(A, n, j0, jb, h->d_flags); }
         HUB_CUDA_TRY(h, cudaGetLastError());
         const int rest = n - j0 - jb;
         if (rest <= 0) continue;
-        k_trsm_rows<<<(rest + 127) / 128, 128, 0, h->stream>>>(A, n, j0, jb, n);
+        { ProfScope ps(h, HUB_K_CHOLESKY); k_trsm_rows<<<(rest + 127) / 128, 128, 0, h->stream>>>(A, n, j0, jb, n); }
         HUB_CUDA_TRY(h, cudaGetLastError());
         double* A21 = A + (size_t)(j0 + jb) * n + j0;
         double* A22 = A + (size_t)(j0 + jb) * n + (j0 + jb);
@@ -335,6 +336,7 @@ int dense_cholesky(hub_t h, double* A, int n) {
 int dense_tri_inverse(hub_t h, const double* L, double* Linv, int n) {
     const int threads = 256;
     const long warps = n;
+    ProfScope ps(h, HUB_K_TRI_INVERSE);
     k_tri_inverse<<<(unsigned)((warps * 32 + threads - 1) / threads), threads, 0, h->stream>>>(L, Linv, n);
     HUB_CUDA_TRY(h, cudaGetLastError());
     return HUB_OK;
@@ -342,6 +344,7 @@ int dense_tri_inverse(hub_t h, const double* L, double* Linv, int n) {
 
 int dense_symmetrize(hub_t h, double* A, int n) {
     const long tot = (long)n * n;
+    ProfScope ps(h, HUB_K_EIG_MISC);
     k_symmetrize<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(A, n);
     HUB_CUDA_TRY(h, cudaGetLastError());
     return HUB_OK;
@@ -360,7 +363,7 @@ int dense_jacobi_eigh(hub_t h, double* A, double* V, double* eig, int n) {
     double* Vt = A1 + nn;
     double* rot = Vt + nn;
     unsigned long long* red = (unsigned long long*)(rot + N);   // 4 slots
-    k_eye<<<(unsigned)((nn + 255) / 256), 256, 0, h->stream>>>(Vt, n);
+    { ProfScope ps(h, HUB_K_EIG_MISC); k_eye<<<(unsigned)((nn + 255) / 256), 256, 0, h->stream>>>(Vt, n); }
     HUB_CUDA_TRY(h, cudaGetLastError());
     HUB_CUDA_TRY(h, cudaMemsetAsync(red, 0, 4 * sizeof(unsigned long long), h->stream));
     HUB_CUDA_TRY(h, cudaMemsetAsync(h->d_bar, 0, 4 * sizeof(unsigned int), h->stream));
@@ -374,9 +377,12 @@ int dense_jacobi_eigh(hub_t h, double* A, double* V, double* eig, int n) {
     unsigned int* bar = h->d_bar;
     int* flags = h->d_flags;
     void* args[] = {&A, &A1, &Vt, &n, (void*)&N, &rot, &max_sweeps, &tol, &bar, &flags, &red};
-    HUB_CUDA_TRY(h, cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(blocks), dim3(256), args, 0,
-                                                h->stream));
-    k_sort_eig<<<(n + 127) / 128, 128, 0, h->stream>>>(A, Vt, n, eig, V);
+    {
+        ProfScope ps(h, HUB_K_JACOBI);
+        HUB_CUDA_TRY(h, cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(blocks), dim3(256), args, 0,
+                                                    h->stream));
+    }
+    { ProfScope ps(h, HUB_K_EIG_MISC); k_sort_eig<<<(n + 127) / 128, 128, 0, h->stream>>>(A, Vt, n, eig, V); }
     HUB_CUDA_TRY(h, cudaGetLastError());
     return HUB_OK;
 }

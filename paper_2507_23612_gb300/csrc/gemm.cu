@@ -139,12 +139,14 @@ int gram_t(hub_t h, const void* A, int lda, const void* B, int ldb, int m, int n
         return rc;
     double* part = (double*)h->d_gpart;
     dim3 grid((unsigned)(tm * tn), splits);
+    { ProfScope ps(h, HUB_K_GRAM);
     k_gram_partial<T><<<grid, 256, 0, h->stream>>>((const T*)A, lda, (const T*)B, ldb, K, m, n, chunk,
-                                                   tn, sym ? 1 : 0, part);
+                                                   tn, sym ? 1 : 0, part); }
     HUB_CUDA_TRY(h, cudaGetLastError());
     const long tot = (long)m * n;
+    { ProfScope ps(h, HUB_K_GRAM_REDUCE);
     k_gram_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(part, splits, m, n, alpha,
-                                                                        sym ? 1 : 0, G);
+                                                                        sym ? 1 : 0, G); }
     HUB_CUDA_TRY(h, cudaGetLastError());
     return HUB_OK;
 }
@@ -163,6 +165,7 @@ int launch_rotate(hub_t h, const void* X, int ldx, const double* Q, int k, int n
     if (h->cplx) return fail(h, HUB_EINVAL, "Rayleigh-Ritz supports real orbitals only");
     if (n == 0) return HUB_OK;
     dim3 grid((unsigned)((h->Nd + BM - 1) / BM), (n + BN - 1) / BN);
+    ProfScope ps(h, HUB_K_ROTATE);
     if (h->esize == 8)
         k_rotate<double><<<grid, 256, 0, h->stream>>>((const double*)X, ldx, Q, k, n, h->Nd, (double*)Y, ldy);
     else

@@ -69,6 +69,12 @@ struct Table {
     std::vector<double> h_M[2];
 };
 
+// ---------------------------------------------------------------------------- profiling
+struct ProfEvt {
+    int kind;
+    cudaEvent_t a, b;
+};
+
 // ---------------------------------------------------------------------------- handle
 struct ScfState;
 void free_table(Table& t);
@@ -113,12 +119,35 @@ struct hub_ctx {
 
     hub::ScfState* scf = nullptr;
 
+    long long launches = 0;       // kernels launched by this handle
+    int prof_on = 0;              // record a CUDA event pair around every launch
+    std::vector<hub::ProfEvt> prof;
+
     std::string last_error;
 };
 
 namespace hub {
 
 int fail(hub_t h, int code, const std::string& msg);
+
+// Counts one kernel launch; with profiling on, brackets it with CUDA events on the handle's
+// stream (the stream the kernel runs on), so durations are measured where the work runs.
+struct ProfScope {
+    hub_t h;
+    int kind;
+    cudaEvent_t a = nullptr;
+    ProfScope(hub_t h_, int k) : h(h_), kind(k) {
+        h->launches++;
+        if (h->prof_on && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, h->stream);
+    }
+    ~ProfScope() {
+        if (!a) return;
+        cudaEvent_t b;
+        if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+        cudaEventRecord(b, h->stream);
+        h->prof.push_back(ProfEvt{kind, a, b});
+    }
+};
 int ensure(hub_t h, void** p, size_t* have, size_t need);
 
 // flags

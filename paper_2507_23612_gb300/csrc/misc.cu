@@ -125,9 +125,9 @@ template <typename R, bool CPLX>
 int dot_t(hub_t h, const void* x, const void* y, double* out, int op) {
     using T = typename VT<R, CPLX>::T;
     double* part = h->d_scal + 1024;   // d_scal holds 4096 doubles
-    k_dot_partial<R, CPLX><<<RBLK, 256, 0, h->stream>>>((const T*)x, (const T*)y, h->Nd, part);
+    { ProfScope ps(h, HUB_K_LANCZOS); k_dot_partial<R, CPLX><<<RBLK, 256, 0, h->stream>>>((const T*)x, (const T*)y, h->Nd, part); }
     HUB_CUDA_TRY(h, cudaGetLastError());
-    k_dot_final<<<1, RBLK, 0, h->stream>>>(part, RBLK, out, op);
+    { ProfScope ps(h, HUB_K_LANCZOS); k_dot_final<<<1, RBLK, 0, h->stream>>>(part, RBLK, out, op); }
     HUB_CUDA_TRY(h, cudaGetLastError());
     return HUB_OK;
 }
@@ -144,20 +144,23 @@ int lanczos_t(hub_t h, int spin, int steps, const void* v0, double* lo, double* 
     double* sc = h->d_scal;            // [0..63] alpha, [64..128] beta, [200..201] bounds, [210] norm
     const unsigned nb = (unsigned)((h->Nd + 255) / 256);
     if ((rc = dot_t<R, CPLX>(h, v0, v0, sc + 210, 1))) return rc;
-    k_lanczos_axpy<R, CPLX><<<nb, 256, 0, h->stream>>>(0, v, (const T*)v0, nullptr, h->Nd, sc, 210, -1);
+    { ProfScope ps(h, HUB_K_LANCZOS);
+    k_lanczos_axpy<R, CPLX><<<nb, 256, 0, h->stream>>>(0, v, (const T*)v0, nullptr, h->Nd, sc, 210, -1); }
     HUB_CUDA_TRY(h, cudaGetLastError());
     for (int j = 0; j < steps; ++j) {
         if ((rc = apply_H_internal(h, spin, v, (int)h->Nd, w, 1, 1.0, 0.0, nullptr, 0.0))) return rc;
         if ((rc = dot_t<R, CPLX>(h, v, w, sc + j, 0))) return rc;                    // alpha_j
-        k_lanczos_axpy<R, CPLX><<<nb, 256, 0, h->stream>>>(1, w, v, vp, h->Nd, sc, j, j > 0 ? 64 + j - 1 : -1);
+        { ProfScope ps(h, HUB_K_LANCZOS);
+        k_lanczos_axpy<R, CPLX><<<nb, 256, 0, h->stream>>>(1, w, v, vp, h->Nd, sc, j, j > 0 ? 64 + j - 1 : -1); }
         HUB_CUDA_TRY(h, cudaGetLastError());
         if ((rc = dot_t<R, CPLX>(h, w, w, sc + 64 + j, 1))) return rc;             // beta_{j+1}
         // vprev <- v ; v <- w / beta
         HUB_CUDA_TRY(h, cudaMemcpyAsync(vp, v, vb, cudaMemcpyDeviceToDevice, h->stream));
-        k_lanczos_axpy<R, CPLX><<<nb, 256, 0, h->stream>>>(0, v, w, nullptr, h->Nd, sc, 64 + j, -1);
+        { ProfScope ps(h, HUB_K_LANCZOS);
+        k_lanczos_axpy<R, CPLX><<<nb, 256, 0, h->stream>>>(0, v, w, nullptr, h->Nd, sc, 64 + j, -1); }
         HUB_CUDA_TRY(h, cudaGetLastError());
     }
-    k_tridiag_bounds<<<1, 32, 0, h->stream>>>(sc, sc + 64, steps, sc + 200);
+    { ProfScope ps(h, HUB_K_LANCZOS); k_tridiag_bounds<<<1, 32, 0, h->stream>>>(sc, sc + 64, steps, sc + 200); }
     HUB_CUDA_TRY(h, cudaGetLastError());
     double b[2];
     HUB_CUDA_TRY(h, cudaMemcpyAsync(b, sc + 200, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -171,6 +174,7 @@ int lanczos_t(hub_t h, int spin, int steps, const void* v0, double* lo, double* 
 
 int launch_copy_convert_veff(hub_t h, const double* src, void* dst) {
     const unsigned nb = (unsigned)((h->Nd + 255) / 256);
+    ProfScope ps(h, HUB_K_COPY);
     if (h->esize == 8) k_convert<double><<<nb, 256, 0, h->stream>>>(src, (double*)dst, h->Nd);
     else k_convert<float><<<nb, 256, 0, h->stream>>>(src, (float*)dst, h->Nd);
     HUB_CUDA_TRY(h, cudaGetLastError());
@@ -181,6 +185,7 @@ int launch_copy_block(hub_t h, const void* src, int lds, void* dst, int ldd, int
     if (ncol == 0) return HUB_OK;
     dim3 grid((unsigned)((h->Nd + 255) / 256), ncol);
     const int es = h->esize * (h->cplx ? 2 : 1);
+    ProfScope ps(h, HUB_K_COPY);
     if (es == 16)
         k_copy_block<double2><<<grid, 256, 0, h->stream>>>((const double2*)src, lds, (double2*)dst, ldd, h->Nd);
     else if (es == 8)

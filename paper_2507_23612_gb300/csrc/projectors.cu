@@ -484,6 +484,7 @@ int build_tables(hub_t h, int natoms, const double* pos, const int* kb_nchan, co
         HUB_CUDA_TRY(h, cudaMalloc(&t.d_vals, vbytes));
         dim3 grid(t.nitems);
         const double* kp = h->kpt;
+        ProfScope ps(h, HUB_K_TABLE);
         if (h->esize == 8) {
             if (h->cplx)
                 k_table_values<double, true><<<grid, 256, 0, h->stream>>>(t.d_sites, t.d_items, t.d_idx, (double*)t.d_vals, h->n1, h->n2, h->h[0], h->h[1], h->h[2], h->L[0], h->L[1], h->L[2], kp[0], kp[1], kp[2]);
@@ -526,13 +527,15 @@ static int gather_t(hub_t h, const void* X, int ncol, int ld, int spin, bool wan
     if ((rc = ensure(h, &h->d_C, &h->C_bytes, (size_t)t.nproj * ncol * sizeof(D)))) return rc;
     if ((rc = ensure(h, &h->d_W, &h->W_bytes, (size_t)t.nproj * ncol * sizeof(T)))) return rc;
     dim3 g1(t.nitems, (ncol + GNB - 1) / GNB);
+    { ProfScope ps(h, HUB_K_GATHER);
     k_gather<R, CPLX><<<g1, 128, 0, h->stream>>>((const T*)X, ld, ncol, t.d_sites, t.d_items, t.d_idx,
-                                                 (const T*)t.d_vals, (D*)h->d_part);
+                                                 (const T*)t.d_vals, (D*)h->d_part); }
     HUB_CUDA_TRY(h, cudaGetLastError());
     const long nthr = (long)t.nsites * ncol;
+    { ProfScope ps(h, HUB_K_TRANSFORM);
     k_reduce_transform<R, CPLX><<<(unsigned)((nthr + 127) / 128), 128, 0, h->stream>>>(
         t.nsites, ncol, h->dV, t.d_sites, t.d_item_first, (const D*)h->d_part, t.d_gamma,
-        t.d_M[spin], (D*)h->d_C, (T*)h->d_W, want_W ? 1 : 0);
+        t.d_M[spin], (D*)h->d_C, (T*)h->d_W, want_W ? 1 : 0); }
     HUB_CUDA_TRY(h, cudaGetLastError());
     return HUB_OK;
 }
@@ -550,6 +553,7 @@ static int scatter_t(hub_t h, void* Y, int ncol, int ld, double alpha) {
     using T = typename VT<R, CPLX>::T;
     Table& t = h->proj;
     dim3 grid((unsigned)((h->Nd + 255) / 256), (ncol + SNB - 1) / SNB);
+    ProfScope ps(h, HUB_K_SCATTER);
     k_scatter<R, CPLX><<<grid, 256, 0, h->stream>>>((T*)Y, ld, ncol, h->Nd, t.d_csr_off, t.d_csr_val,
                                                     t.d_csr_w, t.d_csr_np, (const T*)t.d_vals,
                                                     (const T*)h->d_W, (R)alpha);
@@ -573,13 +577,17 @@ int launch_occupation(hub_t h, int ncol, const double* f_dev, double kweight, do
     }
     double* eu = h->d_scal + 256;   // per-atom E_U contributions (slots 256..375)
     if (t.nhub > 120) return fail(h, HUB_EINVAL, "more than 120 Hubbard atoms not supported");
+    {
+    ProfScope ps(h, HUB_K_OCCUPATION);
     if (h->cplx)
         k_occupation<true><<<t.nhub, 256, 0, h->stream>>>(ncol, t.d_sites, t.d_hub_sites, (const double2*)h->d_C,
                                                          f_dev, kweight, D_dev, eu, t.d_U);
     else
         k_occupation<false><<<t.nhub, 256, 0, h->stream>>>(ncol, t.d_sites, t.d_hub_sites, (const double*)h->d_C,
                                                           f_dev, kweight, D_dev, eu, t.d_U);
+    }
     HUB_CUDA_TRY(h, cudaGetLastError());
+    ProfScope ps2(h, HUB_K_OCCUPATION);
     k_sum_serial<<<1, 32, 0, h->stream>>>(eu, t.nhub, h->d_scal);
     HUB_CUDA_TRY(h, cudaGetLastError());
     return HUB_OK;

@@ -152,6 +152,7 @@ static int run(hub_t h, const StencilArgs& s) {
     d.zchunk = zchunk;
     d.nzc = nzc;
     dim3 grid((s.n1 + TX - 1) / TX, (s.n2 + TY - 1) / TY, s.ncol * nzc);
+    ProfScope ps(h, HUB_K_STENCIL);
     k_stencil<R, CPLX, TX, TY><<<grid, TX * TY, 0, h->stream>>>(d);
     HUB_CUDA_TRY(h, cudaGetLastError());
     return HUB_OK;
