@@ -136,6 +136,16 @@ int hub_chefsi_filter(hub_t h, int spin, void* X, int ncol, int ld, int degree,
 int hub_rayleigh_ritz(hub_t h, int spin, void* X, int ncol, int ld, double* eig_host,
                       void* work);
 
+/* Block product of Rayleigh-Ritz (CheFSI, Sec. II.B): G = alpha * A^T B for two real
+ * column blocks A [ld x ncol_a] and B [ld x ncol_b] (device, handle element type), summed
+ * over the Nd grid rows; with alpha = dV this is the overlap <A|B> (the Gram matrix
+ * S = <X|X>, or <X|HX> with B = H X).  G_dev: device double, row-major
+ * [ncol_a x ncol_b], overwritten.  When A == B and ncol_a == ncol_b only the upper tiles
+ * are computed and mirrored.  Uses handle-owned split-K scratch (allocated on first use).
+ * Real orbitals only.  Errors: HUB_EINVAL. */
+int hub_gram(hub_t h, const void* A, int ncol_a, const void* B, int ncol_b, int ld,
+             double alpha, double* G_dev);
+
 /* Occupation matrices and Hubbard energy of one (spin, k) block (Eq. orbital_occup_ext,
  * Eq. E_U):  D^I_mm' = kweight sum_n f_n <psi_n|phi_m'><phi_m|psi_n>,
  *            EU = sum_I (U_I/2) Tr(D^I - D^I D^I)   (of this D alone).

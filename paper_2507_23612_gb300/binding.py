@@ -52,6 +52,7 @@ _SIGS = {
     "hub_chefsi_filter": [_P, _I, _P, _I, _I, _I, _D, _D, _D, _P],
     "hub_rayleigh_ritz": [_P, _I, _P, _I, _I, _PD, _P],
     "hub_occupation": [_P, _I, _P, _I, _I, _PD, _D, _PD, _PD, _PD],
+    "hub_gram": [_P, _P, _I, _P, _I, _I, _D, _P],
     "hub_lanczos_bound": [_P, _I, _I, _P, _PD, _PD],
     "hub_scf_begin": [_P, C.POINTER(scf_params), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), _PD],
     "hub_scf_iterate": [_P, C.POINTER(scf_result)],
@@ -203,6 +204,15 @@ class Hub:
         self._check(self.lib.hub_rayleigh_ritz(self.h, spin, _tptr(X), ncol, ld, _dptr(eig),
                                                _tptr(work)), "hub_rayleigh_ritz")
         return eig
+
+    def gram(self, A, B, alpha: float, G):
+        """G (device double [ncol_a, ncol_b]) = alpha * A B^T for row-stored blocks."""
+        na, ld = A.shape
+        nb, ldb = B.shape
+        if ld != ldb:
+            raise ValueError("A and B need the same leading dimension")
+        self._check(self.lib.hub_gram(self.h, _tptr(A), na, _tptr(B), nb, ld, float(alpha), _tptr(G)),
+                    "hub_gram")
 
     def occupation(self, spin: int, X, f, kweight: float = 1.0):
         ncol, ld = X.shape

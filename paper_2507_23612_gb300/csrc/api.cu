@@ -341,6 +341,18 @@ int hub_rayleigh_ritz(hub_t h, int spin, void* X, int ncol, int ld, double* eig_
     return HUB_OK;
 }
 
+int hub_gram(hub_t h, const void* A, int ncol_a, const void* B, int ncol_b, int ld, double alpha,
+             double* G_dev) {
+    if (!h) return HUB_EINVAL;
+    if (h->cplx) return fail(h, HUB_EINVAL, "hub_gram supports real orbitals only");
+    if (ncol_a < 0 || ncol_b < 0) return fail(h, HUB_EINVAL, "negative column count");
+    if ((long)ld < h->Nd) return fail(h, HUB_EINVAL, "ld must be >= n1*n2*n3");
+    if (ncol_a == 0 || ncol_b == 0) return HUB_OK;
+    if (!A || !B || !G_dev) return fail(h, HUB_EINVAL, "NULL pointer");
+    const bool sym = (A == B) && (ncol_a == ncol_b);
+    return launch_gram(h, A, ld, B, ld, ncol_a, ncol_b, alpha, sym, G_dev);
+}
+
 int hub_occupation(hub_t h, int spin, const void* X, int ncol, int ld, const double* f_host,
                    double kweight, double* D_re_out, double* D_im_out, double* EU_out) {
     int rc = check_block(h, spin, X, ncol, ld);

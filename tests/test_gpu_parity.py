@@ -214,3 +214,22 @@ def test_tiny_cell_one_pass():
     Dr, _, eu = hb.occupation(0, Xd, f)
     assert rel(Dr, D_ref) < TOL64
     assert abs(2 * eu - EU_ref) < 1e-10 * abs(EU_ref)
+
+
+@pytest.mark.parametrize("prec,tol", [(HUB_F64, TOL64), (HUB_F32, 2e-6)])
+def test_gram_block_product(prec, tol):
+    """hub_gram against the oracle's grid inner product <A|B> = dV A^T B."""
+    wl = w.small_test_system(n=(20, 24, 28), ncol=37, natoms=1)
+    g = o.Grid(wl.n, wl.L)
+    A = wl.orbitals()
+    B = w.random_orbitals(wl.Nd, 29, 5)
+    hb = make_hub(wl, prec)
+    Ad, Bd = to_dev(A, hb.dtype), to_dev(B, hb.dtype)
+    G = torch.empty(37, 29, dtype=torch.float64, device="cuda")
+    hb.gram(Ad, Bd, g.dV, G)
+    ref = g.inner(Ad.double().cpu().numpy().T, Bd.double().cpu().numpy().T)
+    assert rel(G.cpu().numpy(), ref) < tol
+    S = torch.empty(37, 37, dtype=torch.float64, device="cuda")
+    hb.gram(Ad, Ad, g.dV, S)                    # symmetric path: upper tiles mirrored
+    refS = g.inner(Ad.double().cpu().numpy().T, Ad.double().cpu().numpy().T)
+    assert rel(S.cpu().numpy(), refS) < tol
