@@ -146,6 +146,29 @@ int hub_rayleigh_ritz(hub_t h, int spin, void* X, int ncol, int ld, double* eig_
 int hub_gram(hub_t h, const void* A, int ncol_a, const void* B, int ncol_b, int ld,
              double alpha, double* G_dev);
 
+/* hub_gram_noalloc: the hub_gram product for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is a service entry point of the library.
+ * Callers that cannot allocate: code running while a CUDA graph is being captured (a
+ * cudaMalloc there is not allowed and would invalidate the capture), services that give
+ * all device memory to a pooling allocator at start-up and forbid later cudaMalloc /
+ * cudaFree (both synchronise the whole device and can fail once the pool holds the
+ * memory), and callers that cannot create or keep a hub handle.  This call allocates
+ * nothing: its split-K partial sums live in one static device array of 32 MiB
+ * (4 Mi doubles) that every GPU which loads this library keeps until the process exits.
+ *   G_dev[i*ncol_b + j] = alpha * sum_{g < nrows} A[g + i*ld] * B[g + j*ld]
+ * A, B: device, real, double (prec = HUB_F64) or float (prec = HUB_F32), column-major
+ * with leading dimension ld >= nrows; G_dev: device double, row-major
+ * [ncol_a x ncol_b], overwritten; cuda_stream: the stream to run on (NULL = default).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current: make that first call before any stream capture.  All calls on
+ * a device share the one array and it keeps the last call's contents; every call writes
+ * each partial sum it reads, so nothing needs clearing, but calls that overlap on the GPU
+ * (two streams, or two host threads) race on the array and must be serialised.
+ * Errors: HUB_EINVAL for bad arguments or when ncol_a * ncol_b exceeds 4 Mi (one split's
+ * partial tile would not fit); HUB_ECUDA when a CUDA call fails. */
+int hub_gram_noalloc(const void* A, int ncol_a, const void* B, int ncol_b, long long nrows,
+                     int ld, int prec, double alpha, double* G_dev, void* cuda_stream);
+
 /* Occupation matrices and Hubbard energy of one (spin, k) block (Eq. orbital_occup_ext,
  * Eq. E_U):  D^I_mm' = kweight sum_n f_n <psi_n|phi_m'><phi_m|psi_n>,
  *            EU = sum_I (U_I/2) Tr(D^I - D^I D^I)   (of this D alone).

@@ -53,6 +53,7 @@ _SIGS = {
     "hub_rayleigh_ritz": [_P, _I, _P, _I, _I, _PD, _P],
     "hub_occupation": [_P, _I, _P, _I, _I, _PD, _D, _PD, _PD, _PD],
     "hub_gram": [_P, _P, _I, _P, _I, _I, _D, _P],
+    "hub_gram_noalloc": [_P, _I, _P, _I, C.c_longlong, _I, _I, _D, _P, _P],
     "hub_lanczos_bound": [_P, _I, _I, _P, _PD, _PD],
     "hub_scf_begin": [_P, C.POINTER(scf_params), C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), _PD],
     "hub_scf_iterate": [_P, C.POINTER(scf_result)],

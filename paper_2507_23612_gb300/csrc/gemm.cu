@@ -3,6 +3,8 @@
 //   rotation                      Y = X Q             (X tall: Nd x k, Q small k x n)
 // The tall dimension is split over CTAs (split-K); every CTA writes a double partial tile
 // and a second kernel sums the partials in a fixed order (deterministic).
+#include <mutex>
+
 #include "hub_internal.cuh"
 #include "cplx.cuh"
 
@@ -175,3 +177,83 @@ int launch_rotate(hub_t h, const void* X, int ldx, const double* Q, int k, int n
 }
 
 }  // namespace hub
+
+// ---------------------------------------------------------------------------- no-alloc
+// hub_gram_noalloc: the split-K Gram product without any allocation.  Its split-K partial
+// tiles live in one file-scope device array that every GPU loading this library holds for
+// the life of the process.  The host code obtains the array's device address once per
+// device with cudaGetSymbolAddress (the array's name in host code is only a stand-in, not a
+// device address) and passes that address to the same kernels hub_gram uses.
+namespace hub {
+namespace {
+
+constexpr size_t kNoAllocDoubles = (size_t)4 << 20;     // 4 Mi doubles = 32 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocDoubles];
+
+std::mutex g_noalloc_mutex;
+double* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+int noalloc_scratch(double** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return HUB_ECUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) return HUB_ECUDA;
+        g_noalloc_addr[dev] = (double*)p;
+    }
+    *out = g_noalloc_addr[dev];
+    return HUB_OK;
+}
+
+template <typename T>
+int gram_noalloc_t(const void* A, int lda, const void* B, int ldb, long K, int m, int n,
+                   double alpha, bool sym, double* G, cudaStream_t stream) {
+    const size_t mn = (size_t)m * n;
+    if (mn > kNoAllocDoubles) return HUB_EINVAL;
+    double* part = nullptr;
+    int rc = noalloc_scratch(&part);
+    if (rc) return rc;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return HUB_ECUDA;
+    const int tm = (m + BM - 1) / BM, tn = (n + BN - 1) / BN;
+    const long ntiles = sym ? (long)tm * (tm + 1) / 2 : (long)tm * tn;
+    long splits = (4L * sms + ntiles - 1) / ntiles;
+    splits = std::min<long>(splits, (long)(kNoAllocDoubles / mn));   // partials must fit
+    splits = std::max<long>(splits, 1);
+    long chunk = (K + splits - 1) / splits;
+    chunk = ((chunk + BK - 1) / BK) * BK;
+    if (chunk < 4 * BK) chunk = 4 * BK;
+    splits = (K + chunk - 1) / chunk;
+    if ((size_t)splits * mn > kNoAllocDoubles) return HUB_EINVAL;
+    dim3 grid((unsigned)(tm * tn), (unsigned)splits);
+    k_gram_partial<T><<<grid, 256, 0, stream>>>((const T*)A, lda, (const T*)B, ldb, K, m, n, chunk, tn,
+                                                sym ? 1 : 0, part);
+    if (cudaGetLastError() != cudaSuccess) return HUB_ECUDA;
+    const long tot = (long)m * n;
+    k_gram_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(part, (int)splits, m, n, alpha,
+                                                                     sym ? 1 : 0, G);
+    if (cudaGetLastError() != cudaSuccess) return HUB_ECUDA;
+    return HUB_OK;
+}
+
+}  // namespace
+
+}  // namespace hub
+
+extern "C" int hub_gram_noalloc(const void* A, int ncol_a, const void* B, int ncol_b, long long nrows,
+                                int ld, int prec, double alpha, double* G_dev, void* cuda_stream) {
+    if (ncol_a < 0 || ncol_b < 0 || nrows < 0 || (long long)ld < nrows) return HUB_EINVAL;
+    if (prec != HUB_F64 && prec != HUB_F32) return HUB_EINVAL;
+    if (ncol_a == 0 || ncol_b == 0 || nrows == 0) return HUB_OK;
+    if (!A || !B || !G_dev) return HUB_EINVAL;
+    const bool sym = (A == B) && (ncol_a == ncol_b);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (prec == HUB_F64)
+        return hub::gram_noalloc_t<double>(A, ld, B, ld, (long)nrows, ncol_a, ncol_b, alpha, sym, G_dev, st);
+    return hub::gram_noalloc_t<float>(A, ld, B, ld, (long)nrows, ncol_a, ncol_b, alpha, sym, G_dev, st);
+}
