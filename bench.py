@@ -180,6 +180,7 @@ def run_hub(args, rank, world, local_rank):
     hub.profile(-1)
     hub.profile(1)
     n0 = hub.launch_count()
+    print(f"library launches before the timed region: {n0}", file=sys.stderr)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     last = None

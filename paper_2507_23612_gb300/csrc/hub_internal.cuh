@@ -59,9 +59,8 @@ struct Table {
     int* d_idx = nullptr;             // [npts] grid index of each row
     void* d_vals = nullptr;           // working type, [nvals] (x2 complex)
     int* d_csr_off = nullptr;         // [Nd+1] entries per grid point
-    int* d_csr_val = nullptr;         // value index of the entry's first projector
-    int* d_csr_w = nullptr;           // projector row of the entry's site
-    int* d_csr_np = nullptr;          // projectors of the entry's site
+    int2* d_csr_ent = nullptr;        // per entry: x = value index of its first projector,
+                                      // y = (projector row of its site << 4) | nproj
     double* d_gamma = nullptr;        // [nproj] KB energy per projector row (0 for Hubbard)
     int* d_hub_sites = nullptr;
     double* d_U = nullptr;

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <type_traits>
 
 #include "hub_internal.cuh"
 #include "cplx.cuh"
@@ -21,10 +22,7 @@ namespace hub {
 
 namespace {
 
-constexpr int GSUB_MAX = 128;  // points per gather sub-tile
 constexpr int GITEM = 1024;    // points per gather work item
-constexpr int GNB = 16;        // columns per gather CTA
-constexpr int SNB = 8;         // columns per scatter thread
 
 __device__ __forceinline__ void solid_harmonics(int l, double x, double y, double z, double* out) {
     // r^l Y_lm for the real orthonormal harmonics, m = -l..l (no Condon-Shortley sign)
@@ -88,6 +86,89 @@ __global__ void k_table_values(const SiteDev* __restrict__ sites, const int* __r
 }
 
 // ---------------------------------------------------------------------------- gather
+// One warp per (work item, NC columns): lanes stride over the item's points, each lane keeps
+// the NP x NC partial inner products in registers, and one warp-shuffle reduction per item
+// produces the partial sums (no shared memory, no block barriers).  NP (the site's number
+// of projectors) is a template argument so no lane multiplies padding.
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        if constexpr (sizeof(T) == 2 * sizeof(float) && !std::is_same<T, double>::value) {
+            v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+            v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+        } else if constexpr (std::is_same<T, double2>::value) {
+            v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+            v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+        } else {
+            v += __shfl_xor_sync(0xffffffffu, v, o);
+        }
+    }
+    return v;
+}
+
+template <typename T, typename D, int NP, int NC>
+__device__ __forceinline__ void gather_body(const T* __restrict__ X, int ld, int nc, int c0,
+                                            const int* __restrict__ idx, const T* __restrict__ vp0,
+                                            int first, int cnt, int lane, D* __restrict__ part,
+                                            size_t pbase, int ncol) {
+    T acc[NP][NC];
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+#pragma unroll
+        for (int j = 0; j < NC; ++j) acc[p][j] = zero_of(T());
+    // two points per lane and iteration: twice the independent loads in flight
+    int l = lane;
+    for (; l + 32 < cnt; l += 64) {
+        const long g0 = idx[first + l], g1 = idx[first + l + 32];
+        const T* va = vp0 + (size_t)l * NP;
+        const T* vb = va + (size_t)32 * NP;
+        T pa[NP], pb[NP], xa[NC], xb[NC];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) { pa[p] = va[p]; pb[p] = vb[p]; }
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            xa[j] = j < nc ? X[g0 + (size_t)(c0 + j) * ld] : zero_of(T());
+            xb[j] = j < nc ? X[g1 + (size_t)(c0 + j) * ld] : zero_of(T());
+        }
+#pragma unroll
+        for (int j = 0; j < NC; ++j)
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                acc[p][j] = cfma_conj(pa[p], xa[j], acc[p][j]);
+                acc[p][j] = cfma_conj(pb[p], xb[j], acc[p][j]);
+            }
+    }
+    for (; l < cnt; l += 32) {
+        const long g = idx[first + l];
+        const T* vp = vp0 + (size_t)l * NP;
+        T phi[NP];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) phi[p] = vp[p];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            if (j < nc) {
+                const T x = X[g + (size_t)(c0 + j) * ld];
+#pragma unroll
+                for (int p = 0; p < NP; ++p) acc[p][j] = cfma_conj(phi[p], x, acc[p][j]);
+            }
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const T v = warp_sum(acc[p][j]);
+            if (lane == 0 && j < nc) {
+                D d;
+                if constexpr (sizeof(T) == sizeof(D) && std::is_same<T, D>::value) d = v;
+                else if constexpr (std::is_same<D, double2>::value) d = make_double2((double)v.x, (double)v.y);
+                else d = (double)v;
+                part[pbase + (size_t)p * ncol + c0 + j] = d;
+            }
+        }
+}
+
 template <typename R, bool CPLX>
 __global__ void __launch_bounds__(128)
 k_gather(const typename VT<R, CPLX>::T* __restrict__ X, int ld, int ncol,
@@ -96,54 +177,28 @@ k_gather(const typename VT<R, CPLX>::T* __restrict__ X, int ld, int ncol,
          typename VT<double, CPLX>::T* __restrict__ part) {
     using T = typename VT<R, CPLX>::T;
     using D = typename VT<double, CPLX>::T;
-    constexpr int GSUB = sizeof(T) == 16 ? 64 : GSUB_MAX;   // keep static smem under 48 KB
-    __shared__ T xs[GSUB][GNB + 1];
-    __shared__ T vs[GSUB][kMaxProj];
+    constexpr int NC = 16 / sizeof(T);
     const int it = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int s = items[3 * it], first = items[3 * it + 1], cnt = items[3 * it + 2];
     const int np = sites[s].nproj;
-    const int val0 = sites[s].val_off + (first - sites[s].pt_off) * np;
-    const int c0 = blockIdx.y * GNB;
-    const int nout = np * GNB;
-    // each thread owns up to two outputs (p, j)
-    const int o0 = threadIdx.x, o1 = threadIdx.x + 128;
-    T acc0 = zero_of(T()), acc1 = zero_of(T());
-    for (int base = 0; base < cnt; base += GSUB) {
-        const int m = min(GSUB, cnt - base);
-        for (int i = threadIdx.x; i < GSUB * GNB; i += 128) {
-            const int l = i % GSUB, j = i / GSUB;
-            const int c = c0 + j;
-            T v = zero_of(T());
-            if (l < m && c < ncol) v = X[(size_t)idx[first + base + l] + (size_t)c * ld];
-            xs[l][j] = v;
-        }
-        for (int i = threadIdx.x; i < GSUB * np; i += 128) {
-            const int l = i / np, p = i - l * np;
-            vs[l][p] = (l < m) ? vals[(size_t)val0 + (size_t)(base + l) * np + p] : zero_of(T());
-        }
-        __syncthreads();
-        if (o0 < nout) {
-            const int p = o0 / GNB, j = o0 % GNB;
-#pragma unroll 8
-            for (int l = 0; l < GSUB; ++l) acc0 = cfma_conj(vs[l][p], xs[l][j], acc0);
-        }
-        if (o1 < nout) {
-            const int p = o1 / GNB, j = o1 % GNB;
-#pragma unroll 8
-            for (int l = 0; l < GSUB; ++l) acc1 = cfma_conj(vs[l][p], xs[l][j], acc1);
-        }
-        __syncthreads();
+    const int c0 = (blockIdx.y * 4 + warp) * NC;
+    if (c0 >= ncol) return;
+    const int nc = min(NC, ncol - c0);
+    const T* vp0 = vals + (size_t)sites[s].val_off + (size_t)(first - sites[s].pt_off) * np;
+    const size_t pbase = (size_t)it * kMaxProj * ncol;
+    switch (np) {
+        case 1: gather_body<T, D, 1, NC>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
+        case 2: gather_body<T, D, 2, NC>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
+        case 3: gather_body<T, D, 3, NC>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
+        case 4: gather_body<T, D, 4, NC>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
+        case 5: gather_body<T, D, 5, NC>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
+        case 6: gather_body<T, D, 6, NC>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
+        case 7: gather_body<T, D, 7, NC>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
+        case 8: gather_body<T, D, 8, NC>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
+        case 9: gather_body<T, D, 9, NC>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
+        default: break;   // build_tables rejects sites with more than kMaxProj functions
     }
-    auto store = [&](int o, T acc) {
-        const int p = o / GNB, j = o % GNB, c = c0 + j;
-        if (c >= ncol) return;
-        D v;
-        if constexpr (CPLX) v = make_double2((double)acc.x, (double)acc.y);
-        else v = (double)acc;
-        part[((size_t)it * kMaxProj + p) * ncol + c] = v;
-    };
-    if (o0 < nout) store(o0, acc0);
-    if (o1 < nout) store(o1, acc1);
 }
 
 // reduce partials of each site and apply the coefficient transform
@@ -194,35 +249,56 @@ __global__ void k_reduce_transform(int nsites, int ncol, double dV, const SiteDe
 }
 
 // ---------------------------------------------------------------------------- scatter
+// One thread per grid point and NC columns: walks the point's CSR entries (one 8-byte
+// metadata load each), multiplies the site's values into W rows (16-byte vector loads when
+// the rows are aligned) and updates Y once per column.
 template <typename R, bool CPLX>
 __global__ void __launch_bounds__(256)
 k_scatter(typename VT<R, CPLX>::T* __restrict__ Y, int ld, int ncol, long Nd,
-          const int* __restrict__ csr_off, const int* __restrict__ csr_val,
-          const int* __restrict__ csr_w, const int* __restrict__ csr_np,
+          const int* __restrict__ csr_off, const int2* __restrict__ csr_ent,
           const typename VT<R, CPLX>::T* __restrict__ vals,
-          const typename VT<R, CPLX>::T* __restrict__ W, R alpha) {
+          const typename VT<R, CPLX>::T* __restrict__ W, R alpha, int vec_ok) {
     using T = typename VT<R, CPLX>::T;
+    constexpr int NC = 32 / sizeof(T);
+    constexpr int PER16 = 16 / sizeof(T);
     const long g = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= Nd) return;
     const int e0 = csr_off[g], e1 = csr_off[g + 1];
     if (e0 == e1) return;
-    const int c0 = blockIdx.y * SNB;
-    T acc[SNB];
+    const int c0 = blockIdx.y * NC;
+    const int nc = min(NC, ncol - c0);
+    T acc[NC];
 #pragma unroll
-    for (int j = 0; j < SNB; ++j) acc[j] = zero_of(T());
+    for (int j = 0; j < NC; ++j) acc[j] = zero_of(T());
+    int2 m = csr_ent[e0];
     for (int e = e0; e < e1; ++e) {
-        const int vb = csr_val[e], wr = csr_w[e], np = csr_np[e];
-        for (int p = 0; p < np; ++p) {
-            const T v = vals[vb + p];
-            const T* wrow = W + (size_t)(wr + p) * ncol + c0;
+        const int2 mn = (e + 1 < e1) ? csr_ent[e + 1] : m;      // next entry, in flight early
+        const int np = m.y & 15;
+        const T* wrow = W + (size_t)(m.y >> 4) * ncol + c0;
+        const T* vrow = vals + m.x;
+        for (int p = 0; p < np; ++p, wrow += ncol) {
+            const T v = vrow[p];
+            if (vec_ok && nc == NC) {
+                float4 q4[NC / PER16];
 #pragma unroll
-            for (int j = 0; j < SNB; ++j)
-                if (c0 + j < ncol) acc[j] = cfma(v, wrow[j], acc[j]);
+                for (int k = 0; k < NC / PER16; ++k) q4[k] = reinterpret_cast<const float4*>(wrow)[k];
+#pragma unroll
+                for (int k = 0; k < NC / PER16; ++k) {
+                    const T* w = reinterpret_cast<const T*>(&q4[k]);
+#pragma unroll
+                    for (int i = 0; i < PER16; ++i) acc[k * PER16 + i] = cfma(v, w[i], acc[k * PER16 + i]);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < NC; ++j)
+                    if (j < nc) acc[j] = cfma(v, wrow[j], acc[j]);
+            }
         }
+        m = mn;
     }
 #pragma unroll
-    for (int j = 0; j < SNB; ++j) {
-        if (c0 + j < ncol) {
+    for (int j = 0; j < NC; ++j) {
+        if (j < nc) {
             T* y = Y + (size_t)(c0 + j) * ld + g;
             *y = fmar(alpha, acc[j], *y);
         }
@@ -316,7 +392,7 @@ int upload(hub_t h, Tp** dptr, const std::vector<Tp>& v) {
 
 void free_table(Table& t) {
     void* ptrs[] = {t.d_sites, t.d_items, t.d_item_first, t.d_idx, t.d_vals, t.d_csr_off,
-                    t.d_csr_val, t.d_csr_w, t.d_csr_np, t.d_gamma, t.d_hub_sites, t.d_U,
+                    t.d_csr_ent, t.d_gamma, t.d_hub_sites, t.d_U,
                     t.d_M[0], t.d_M[1]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -370,6 +446,7 @@ int build_tables(hub_t h, int natoms, const double* pos, const int* kb_nchan, co
             if (!(S.rc > 0)) return fail(h, HUB_EINVAL, "cutoff radius must be > 0");
             int np = 0;
             for (int c = 0; c < S.nch; ++c) np += 2 * S.l[c] + 1;
+            if (np > kMaxProj) return fail(h, HUB_EINVAL, "at most 9 functions per atom and kind");
             S.nproj = np;
             // grid points within rc of any lattice image R + T
             std::vector<int> pts;
@@ -456,14 +533,13 @@ int build_tables(hub_t h, int natoms, const double* pos, const int* kb_nchan, co
     for (int r = 0; r < t.npts; ++r) csr_off[idx[r] + 1]++;
     for (long g = 0; g < h->Nd; ++g) csr_off[g + 1] += csr_off[g];
     std::vector<int> fill(csr_off.begin(), csr_off.end() - 1);
-    std::vector<int> csr_val(t.npts), csr_w(t.npts), csr_np(t.npts);
+    std::vector<int2> csr_ent(t.npts);
+    if (t.nproj >= (1 << 26)) return fail(h, HUB_EINVAL, "too many projector rows");
     for (int s = 0; s < t.nsites; ++s) {
         const SiteDev& S = t.h_sites[s];
         for (int l = 0; l < S.npts; ++l) {
             const int e = fill[idx[S.pt_off + l]]++;
-            csr_val[e] = S.val_off + l * S.nproj;
-            csr_w[e] = S.proj_off;
-            csr_np[e] = S.nproj;
+            csr_ent[e] = make_int2(S.val_off + l * S.nproj, (S.proj_off << 4) | S.nproj);
         }
     }
 
@@ -473,9 +549,7 @@ int build_tables(hub_t h, int natoms, const double* pos, const int* kb_nchan, co
     if ((rc = upload(h, &t.d_item_first, t.h_item_first))) return rc;
     if ((rc = upload(h, &t.d_idx, idx))) return rc;
     if ((rc = upload(h, &t.d_csr_off, csr_off))) return rc;
-    if ((rc = upload(h, &t.d_csr_val, csr_val))) return rc;
-    if ((rc = upload(h, &t.d_csr_w, csr_w))) return rc;
-    if ((rc = upload(h, &t.d_csr_np, csr_np))) return rc;
+    if ((rc = upload(h, &t.d_csr_ent, csr_ent))) return rc;
     if ((rc = upload(h, &t.d_gamma, gamma_rows))) return rc;
     if ((rc = upload(h, &t.d_hub_sites, t.h_hub_sites))) return rc;
     if ((rc = upload(h, &t.d_U, t.h_U))) return rc;
@@ -526,7 +600,8 @@ static int gather_t(hub_t h, const void* X, int ncol, int ld, int spin, bool wan
     if ((rc = ensure(h, &h->d_part, &h->part_bytes, (size_t)t.nitems * kMaxProj * ncol * sizeof(D)))) return rc;
     if ((rc = ensure(h, &h->d_C, &h->C_bytes, (size_t)t.nproj * ncol * sizeof(D)))) return rc;
     if ((rc = ensure(h, &h->d_W, &h->W_bytes, (size_t)t.nproj * ncol * sizeof(T)))) return rc;
-    dim3 g1(t.nitems, (ncol + GNB - 1) / GNB);
+    constexpr int NC = 16 / sizeof(T);
+    dim3 g1(t.nitems, (ncol + 4 * NC - 1) / (4 * NC));
     { ProfScope ps(h, HUB_K_GATHER);
     k_gather<R, CPLX><<<g1, 128, 0, h->stream>>>((const T*)X, ld, ncol, t.d_sites, t.d_items, t.d_idx,
                                                  (const T*)t.d_vals, (D*)h->d_part); }
@@ -551,12 +626,13 @@ int launch_gather(hub_t h, const void* X, int ncol, int ld, int spin, bool want_
 template <typename R, bool CPLX>
 static int scatter_t(hub_t h, void* Y, int ncol, int ld, double alpha) {
     using T = typename VT<R, CPLX>::T;
+    constexpr int NC = 32 / sizeof(T);
     Table& t = h->proj;
-    dim3 grid((unsigned)((h->Nd + 255) / 256), (ncol + SNB - 1) / SNB);
+    const int vec_ok = ((ncol * sizeof(T)) % 16 == 0) && ((uintptr_t)h->d_W % 16 == 0);
+    dim3 grid((unsigned)((h->Nd + 255) / 256), (ncol + NC - 1) / NC);
     ProfScope ps(h, HUB_K_SCATTER);
-    k_scatter<R, CPLX><<<grid, 256, 0, h->stream>>>((T*)Y, ld, ncol, h->Nd, t.d_csr_off, t.d_csr_val,
-                                                    t.d_csr_w, t.d_csr_np, (const T*)t.d_vals,
-                                                    (const T*)h->d_W, (R)alpha);
+    k_scatter<R, CPLX><<<grid, 256, 0, h->stream>>>((T*)Y, ld, ncol, h->Nd, t.d_csr_off, t.d_csr_ent,
+                                                    (const T*)t.d_vals, (const T*)h->d_W, (R)alpha, vec_ok);
     HUB_CUDA_TRY(h, cudaGetLastError());
     return HUB_OK;
 }

@@ -4,13 +4,17 @@
 //   Yout = alpha * (-1/2 Lap_h Y + V .* Y - shift * Y) + beta * Yprev
 //
 // Layout: Y[g + col*ld], g = x + n1*(y + n2*z).  One CTA owns a TX x TY tile of the x-y
-// plane for one column and marches along z over a chunk of planes.  The z-neighbours live
-// in a register queue of 2*NH+1 values per thread (each plane is read from HBM once per
-// chunk); the x/y neighbours of the current plane are staged in shared memory together
-// with an NH-wide halo (halo reads hit L2).  Slots beyond the grid hold the wrapped
-// value times the Bloch factor exp(i k_a L_a)^wraps, so ragged tiles and grids smaller
-// than the stencil need no special cases.  Yprev may alias Yout (each element is read
-// and written by the same thread).
+// plane for one column and marches along z over a chunk of planes.
+//
+// Pipeline: shared memory holds a ring of S stages; stage p % S holds plane p of Y with an
+// NH-wide x/y halo, plus the tile's interior of V and Yprev for that plane.  Stages are
+// filled with cp.async P planes ahead of use, so HBM/L2 latency overlaps the arithmetic.
+// Each thread owns a fixed list of halo slots whose in-plane offsets (wrapped into the cell)
+// are computed once.  The z-neighbours of a thread's point live in a register queue of
+// 2*NH+1 values fed from the ring, the x/y neighbours are read from the current stage.
+// Slots that wrapped across a cell face get the Bloch factor exp(i k_a L_a)^wraps (only
+// for complex elements; real Gamma-point data is copied untouched).  Yprev may alias Yout:
+// each element is read (through the ring) before the same thread writes it.
 #include "hub_internal.cuh"
 #include "cplx.cuh"
 
@@ -34,15 +38,42 @@ __device__ __forceinline__ int floordiv(int a, int n) {
     return (a % n != 0 && a < 0) ? q - 1 : q;
 }
 
-template <typename R, bool CPLX, int TX, int TY>
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <typename R, bool CPLX, int TX, int TY, int P>
+struct StencilCfg {
+    static constexpr int NH = 6;
+    static constexpr int SX = TX + 2 * NH, SY = TY + 2 * NH;
+    static constexpr int NT = TX * TY;
+    static constexpr int S = P + 8;                       // ring stages
+    static constexpr int SLOTS = SX * SY;
+    static constexpr int PER = (SLOTS + NT - 1) / NT;     // halo'd slots per thread
+    using T = typename VT<R, CPLX>::T;
+    // stage layout: Y plane with halo, then interior V (R), then interior Yprev (T)
+    static constexpr size_t YB = sizeof(T) * SLOTS;
+    static constexpr size_t VB = sizeof(R) * NT;
+    static constexpr size_t PB = sizeof(T) * NT;
+    static constexpr size_t STAGE = ((YB + VB + PB + 127) / 128) * 128;
+    static constexpr size_t SMEM = STAGE * S;
+};
+
+template <typename R, bool CPLX, int TX, int TY, int P>
 __global__ void __launch_bounds__(TX * TY)
 k_stencil(StencilDev<R> a) {
-    constexpr int NH = 6;
-    constexpr int SX = TX + 2 * NH, SY = TY + 2 * NH;
-    using T = typename VT<R, CPLX>::T;
-    __shared__ T s[SY][SX];
-    __shared__ int sxg[SX], syg[SY];
-    __shared__ T sxp[SX], syp[SY];
+    using C = StencilCfg<R, CPLX, TX, TY, P>;
+    using T = typename C::T;
+    constexpr int NH = C::NH, SX = C::SX, S = C::S, NT = C::NT, PER = C::PER;
+    extern __shared__ __align__(128) unsigned char smem[];
 
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
@@ -51,79 +82,607 @@ k_stencil(StencilDev<R> a) {
     const int z0 = zc * a.zchunk;
     const int z1 = min(z0 + a.zchunk, a.n3);
     const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
-    const size_t plane = (size_t)n1 * n2;
-
-    for (int i = tid; i < SX; i += TX * TY) {
-        int g = blockIdx.x * TX - NH + i;
-        int w = floordiv(g, n1);
-        sxg[i] = g - w * n1;
-        sxp[i] = phase_pow<T>(a.ph[0][0], a.ph[0][1], w);
-    }
-    for (int i = tid; i < SY; i += TX * TY) {
-        int g = blockIdx.y * TY - NH + i;
-        int w = floordiv(g, n2);
-        syg[i] = g - w * n2;
-        syp[i] = phase_pow<T>(a.ph[1][0], a.ph[1][1], w);
-    }
-    __syncthreads();
+    const long plane = (long)n1 * n2;
+    const int gx0 = blockIdx.x * TX, gy0 = blockIdx.y * TY;
 
     const T* __restrict__ Y = reinterpret_cast<const T*>(a.Y) + (size_t)col * a.ld;
     const T* Yp = a.Yprev ? reinterpret_cast<const T*>(a.Yprev) + (size_t)col * a.ld : nullptr;
     T* Yo = reinterpret_cast<T*>(a.Yout) + (size_t)col * a.ld;
 
-    const int gx = sxg[tx + NH], gy = syg[ty + NH];
-    const T pxy = cmul(sxp[tx + NH], syp[ty + NH]);
-    const bool active = (blockIdx.x * TX + tx < n1) && (blockIdx.y * TY + ty < n2);
-    const size_t colofs = (size_t)gy * n1 + gx;
+    // this thread's halo'd slots: shared index, wrapped in-plane offset, Bloch factor
+    int s_idx[PER];
+    int s_off[PER];
+    T s_ph[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = tid + k * NT;
+        s_idx[k] = -1;
+        s_off[k] = 0;
+        s_ph[k] = phase_pow<T>(1.0, 0.0, 0);
+        if (i < C::SLOTS) {
+            const int ix = i % SX, iy = i / SX;
+            const int gx = gx0 - NH + ix, gy = gy0 - NH + iy;
+            const int wx = floordiv(gx, n1), wy = floordiv(gy, n2);
+            s_idx[k] = i;
+            s_off[k] = (gy - wy * n2) * n1 + (gx - wx * n1);
+            if constexpr (CPLX)
+                s_ph[k] = cmul(phase_pow<T>(a.ph[0][0], a.ph[0][1], wx), phase_pow<T>(a.ph[1][0], a.ph[1][1], wy));
+        }
+    }
+    const bool active = (gx0 + tx < n1) && (gy0 + ty < n2);
+    const long own = (long)(gy0 + ty) * n1 + (gx0 + tx);
 
+    auto stage_Y = [&](int p) { return reinterpret_cast<T*>(smem + C::STAGE * (size_t)(((p % S) + S) % S)); };
+    auto stage_V = [&](int p) { return reinterpret_cast<R*>(reinterpret_cast<unsigned char*>(stage_Y(p)) + C::YB); };
+    auto stage_P = [&](int p) { return reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(stage_Y(p)) + C::YB + C::VB); };
+
+    // issue the copies of plane p (wrapped along z); interior V / Yprev only for planes
+    // that will be computed
+    auto issue = [&](int p) {
+        const int wz = floordiv(p, n3);
+        const long zoff = (long)(p - wz * n3) * plane;
+        T* ys = stage_Y(p);
+#pragma unroll
+        for (int k = 0; k < PER; ++k)
+            if (s_idx[k] >= 0) cp_async<sizeof(T)>(ys + s_idx[k], Y + zoff + s_off[k]);
+        if (active && p >= z0 && p < z1) {
+            cp_async<sizeof(R)>(stage_V(p) + tid, a.V + zoff + own);
+            if (Yp) cp_async<sizeof(T)>(stage_P(p) + tid, Yp + zoff + own);
+        }
+    };
+    // Bloch factors of this thread's wrapped slots of plane p (complex only)
+    auto fix = [&](int p) {
+        if constexpr (CPLX) {
+            const T pz = phase_pow<T>(a.ph[2][0], a.ph[2][1], floordiv(p, n3));
+            T* ys = stage_Y(p);
+#pragma unroll
+            for (int k = 0; k < PER; ++k)
+                if (s_idx[k] >= 0) ys[s_idx[k]] = cmul(ys[s_idx[k]], cmul(s_ph[k], pz));
+        }
+    };
+
+    // prologue: the z-queue of planes z0-NH .. z0+NH straight from global memory (active
+    // threads own a point inside the cell, so only the z wrap carries a Bloch factor), and
+    // ring planes z0 .. z0+NH+P in flight
+    const int ctr = (ty + NH) * SX + (tx + NH);
     T q[2 * NH + 1];
 #pragma unroll
     for (int j = 0; j < 2 * NH + 1; ++j) {
-        int zz = z0 - NH + j;
-        int w = floordiv(zz, n3);
-        int zw = zz - w * n3;
-        q[j] = cmul(cmul(Y[(size_t)zw * plane + colofs], pxy),
-                    phase_pow<T>(a.ph[2][0], a.ph[2][1], w));
-    }
-
-    for (int z = z0; z < z1; ++z) {
-        s[ty + NH][tx + NH] = q[NH];
-        const size_t zofs = (size_t)z * plane;
-        for (int i = tid; i < SX * SY; i += TX * TY) {
-            int ix = i % SX, iy = i / SX;
-            bool interior = (ix >= NH) && (ix < TX + NH) && (iy >= NH) && (iy < TY + NH);
-            if (!interior)
-                s[iy][ix] = cmul(Y[zofs + (size_t)syg[iy] * n1 + sxg[ix]], cmul(sxp[ix], syp[iy]));
-        }
-        __syncthreads();
+        q[j] = zero_of(T());
         if (active) {
-            const size_t g = zofs + colofs;
-            T acc = mulr(a.center + a.alpha * a.V[g], q[NH]);
+            const int p = z0 - NH + j;
+            const int wz = floordiv(p, n3);
+            q[j] = Y[(long)(p - wz * n3) * plane + own];
+            if constexpr (CPLX) q[j] = cmul(q[j], phase_pow<T>(a.ph[2][0], a.ph[2][1], wz));
+        }
+    }
+    const int last_needed = z1 + NH - 1;      // highest plane any step reads
+#pragma unroll 1
+    for (int p = z0; p <= z0 + NH + P; ++p) {
+        if (p <= last_needed) issue(p);
+        cp_async_commit();
+    }
+    cp_async_wait<P>();                        // planes z0 .. z0+NH have landed
+#pragma unroll 1
+    for (int p = z0; p <= z0 + NH; ++p)
+        if (p <= last_needed) fix(p);
+    __syncthreads();
+
+#pragma unroll 1
+    for (int z = z0; z < z1; ++z) {
+        if (active) {
+            const T* ys = stage_Y(z);
+            T acc = mulr(a.center + a.alpha * stage_V(z)[tid], q[NH]);
 #pragma unroll
             for (int p = 1; p <= NH; ++p) {
                 acc = fmar(a.w[2][p - 1], add(q[NH + p], q[NH - p]), acc);
-                acc = fmar(a.w[0][p - 1], add(s[ty + NH][tx + NH + p], s[ty + NH][tx + NH - p]), acc);
-                acc = fmar(a.w[1][p - 1], add(s[ty + NH + p][tx + NH], s[ty + NH - p][tx + NH]), acc);
+                acc = fmar(a.w[0][p - 1], add(ys[ctr + p], ys[ctr - p]), acc);
+                acc = fmar(a.w[1][p - 1], add(ys[ctr + p * SX], ys[ctr - p * SX]), acc);
             }
-            if (Yp) acc = fmar(a.beta, Yp[g], acc);
-            Yo[g] = acc;
+            if (Yp) acc = fmar(a.beta, stage_P(z)[tid], acc);
+            Yo[(long)z * plane + own] = acc;
         }
+        if (z + 1 == z1) break;
+        __syncthreads();                       // every thread is done with stage z
+        const int nxt = z + NH + 1 + P;         // reuses the stage of plane z - 1
+        if (nxt <= last_needed) issue(nxt);
+        cp_async_commit();
+        cp_async_wait<P>();                    // plane z + NH + 1 has landed
+        fix(z + NH + 1);
         __syncthreads();
-        if (z + 1 < z1) {
 #pragma unroll
-            for (int j = 0; j < 2 * NH; ++j) q[j] = q[j + 1];
-            int zz = z + NH + 1;
-            int w = floordiv(zz, n3);
-            int zw = zz - w * n3;
-            q[2 * NH] = cmul(cmul(Y[(size_t)zw * plane + colofs], pxy),
-                             phase_pow<T>(a.ph[2][0], a.ph[2][1], w));
-        }
+        for (int j = 0; j < 2 * NH; ++j) q[j] = q[j + 1];
+        q[2 * NH] = stage_Y(z + NH + 1)[ctr];
     }
+    cp_async_wait<0>();
 }
 
-template <typename R, bool CPLX>
-static int run(hub_t h, const StencilArgs& s) {
-    constexpr int TX = 32, TY = 8;
+// ---------------------------------------------------------------------------- vector form
+// Same pipeline with VEC = 16 bytes / element consecutive x-points per thread: the halo'd
+// plane is copied as 16-byte vectors (the x-halo is padded to HX, a multiple of VEC), the
+// x-neighbours of a thread's VEC points come from (VEC + 2 HX) / VEC vector loads, each
+// y-neighbour row from one vector load, and the z-queue holds vectors.  Requires
+// n1 % VEC == 0, ld % VEC == 0 and 16-byte aligned blocks, so a vector never straddles
+// a row end or a cell face (its VEC points share one Bloch factor).
+template <typename T, int VEC>
+struct alignas(sizeof(T) * VEC) VecT {      // natural size: 16 B for Y vectors, 8 B for a
+    T v[VEC];                               // pair of float potentials
+};
+
+template <typename R, bool CPLX, int VEC, int TXT, int TY, int P>
+struct VecCfg {
+    static constexpr int NH = 6;
+    static constexpr int HX = ((NH + VEC - 1) / VEC) * VEC;
+    static constexpr int TXP = TXT * VEC;
+    static constexpr int SXP = TXP + 2 * HX;
+    static constexpr int SXV = SXP / VEC;                  // vectors per smem row
+    static constexpr int SY = TY + 2 * NH;
+    static constexpr int NT = TXT * TY;
+    static constexpr int S = P + 8;
+    static constexpr int NVS = SXV * SY;
+    static constexpr int PER = (NVS + NT - 1) / NT;
+    using T = typename VT<R, CPLX>::T;
+    using V = VecT<T, VEC>;
+    using VR = VecT<R, VEC>;
+    static constexpr size_t YB = sizeof(T) * SXP * SY;
+    static constexpr size_t VB = sizeof(R) * TXP * TY;
+    static constexpr size_t PB = sizeof(T) * TXP * TY;
+    static constexpr size_t STAGE = ((YB + VB + PB + 127) / 128) * 128;
+    static constexpr size_t SMEM = STAGE * S;
+};
+
+template <typename R, bool CPLX, int VEC, int TXT, int TY, int P>
+__global__ void __launch_bounds__(TXT * TY)
+k_stencil_vec(StencilDev<R> a) {
+    using C = VecCfg<R, CPLX, VEC, TXT, TY, P>;
+    static_assert(sizeof(typename C::V) == 16, "Y vectors are 16-byte copies");
+    static_assert(sizeof(typename C::VR) == sizeof(R) * VEC, "potential vectors are unpadded");
+    static_assert(C::YB % 16 == 0 && C::VB % 16 == 0, "stage regions stay 16-byte aligned");
+    using T = typename C::T;
+    using V = typename C::V;
+    using VR = typename C::VR;
+    constexpr int NH = C::NH, HX = C::HX, SXP = C::SXP, SXV = C::SXV, S = C::S, NT = C::NT, PER = C::PER;
+    constexpr int NXV = (VEC + 2 * HX) / VEC;              // x-neighbour vectors per thread
+    extern __shared__ __align__(128) unsigned char smem[];
+
+    const int tid = threadIdx.x;
+    const int tx = tid % TXT, ty = tid / TXT;
+    const int col = blockIdx.z / a.nzc;
+    const int zc = blockIdx.z - col * a.nzc;
+    const int z0 = zc * a.zchunk;
+    const int z1 = min(z0 + a.zchunk, a.n3);
+    const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
+    const long plane = (long)n1 * n2;
+    const int gx0 = blockIdx.x * C::TXP, gy0 = blockIdx.y * TY;
+
+    const T* __restrict__ Y = reinterpret_cast<const T*>(a.Y) + (size_t)col * a.ld;
+    const T* Yp = a.Yprev ? reinterpret_cast<const T*>(a.Yprev) + (size_t)col * a.ld : nullptr;
+    T* Yo = reinterpret_cast<T*>(a.Yout) + (size_t)col * a.ld;
+
+    int s_idx[PER];                 // vector slot in the stage
+    const T* s_src[PER];            // source of the slot in plane 0 (wrapped x/y)
+    T s_ph[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = tid + k * NT;
+        s_idx[k] = -1;
+        s_src[k] = Y;
+        s_ph[k] = phase_pow<T>(1.0, 0.0, 0);
+        if (i < C::NVS) {
+            const int cx = i % SXV, iy = i / SXV;
+            const int gx = gx0 - HX + cx * VEC, gy = gy0 - NH + iy;
+            const int wx = floordiv(gx, n1), wy = floordiv(gy, n2);
+            s_idx[k] = i;
+            s_src[k] = Y + (long)(gy - wy * n2) * n1 + (gx - wx * n1);
+            if constexpr (CPLX)
+                s_ph[k] = cmul(phase_pow<T>(a.ph[0][0], a.ph[0][1], wx), phase_pow<T>(a.ph[1][0], a.ph[1][1], wy));
+        }
+    }
+    const bool active = (gx0 + tx * VEC < n1) && (gy0 + ty < n2);
+    const long own = (long)(gy0 + ty) * n1 + (gx0 + tx * VEC);
+
+    auto stY = [&](int st) { return reinterpret_cast<V*>(smem + C::STAGE * (size_t)st); };
+    auto stV = [&](int st) { return reinterpret_cast<VR*>(smem + C::STAGE * (size_t)st + C::YB); };
+    auto stP = [&](int st) { return reinterpret_cast<V*>(smem + C::STAGE * (size_t)st + C::YB + C::VB); };
+
+    // copies of plane p (z index already wrapped to zw) into stage st
+    auto issue = [&](int st, int zw, bool interior) {
+        const long zoff = (long)zw * plane;
+        V* ys = stY(st);
+#pragma unroll
+        for (int k = 0; k < PER; ++k)
+            if (s_idx[k] >= 0) cp_async<16>(ys + s_idx[k], s_src[k] + zoff);
+        if (active && interior) {
+            cp_async<sizeof(VR)>(stV(st) + tid, a.V + zoff + own);
+            if (Yp) cp_async<16>(stP(st) + tid, Yp + zoff + own);
+        }
+    };
+    auto fix = [&](int st, int wz) {
+        if constexpr (CPLX) {
+            const T pz = phase_pow<T>(a.ph[2][0], a.ph[2][1], wz);
+            V* ys = stY(st);
+#pragma unroll
+            for (int k = 0; k < PER; ++k)
+                if (s_idx[k] >= 0) {
+                    const T f = cmul(s_ph[k], pz);
+                    V v = ys[s_idx[k]];
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) v.v[e] = cmul(v.v[e], f);
+                    ys[s_idx[k]] = v;
+                }
+        }
+    };
+
+    const int last_needed = z1 + NH - 1;
+    // z-queue of planes z0-NH .. z0+NH from global memory
+    V q[2 * NH + 1];
+#pragma unroll
+    for (int j = 0; j < 2 * NH + 1; ++j) {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) q[j].v[e] = zero_of(T());
+        if (active) {
+            const int p = z0 - NH + j;
+            const int wz = floordiv(p, n3);
+            q[j] = *reinterpret_cast<const V*>(Y + (long)(p - wz * n3) * plane + own);
+            if constexpr (CPLX) {
+                const T f = phase_pow<T>(a.ph[2][0], a.ph[2][1], wz);
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) q[j].v[e] = cmul(q[j].v[e], f);
+            }
+        }
+    }
+    // ring: planes z0 .. z0+NH+P; issue cursor (plane, stage, wrapped z, wraps)
+    int ip = z0, ist = 0, izw = z0 % n3, iwz = z0 / n3;
+#pragma unroll 1
+    for (int j = 0; j <= NH + P; ++j) {
+        if (ip <= last_needed) issue(ist, izw, ip < z1);
+        cp_async_commit();
+        ++ip; if (++ist == S) ist = 0; if (++izw == n3) { izw = 0; ++iwz; }
+    }
+    cp_async_wait<P>();
+    {
+        int st = 0, zw = z0 % n3, wz = z0 / n3;
+#pragma unroll 1
+        for (int p = z0; p <= z0 + NH; ++p) {
+            if (p <= last_needed) fix(st, wz);
+            if (++st == S) st = 0;
+            if (++zw == n3) { zw = 0; ++wz; }
+        }
+    }
+    __syncthreads();
+    // stage of plane z and of plane z + NH + 1, and the wrap count of plane z + NH + 1
+    int sz = 0;
+    int sf = (NH + 1) % S;
+    int fwz = (z0 + NH + 1) / n3;
+    int fzw = (z0 + NH + 1) % n3;
+    constexpr int ctr_row = NH;                 // smem row of the thread's own y, minus ty
+#pragma unroll 1
+    for (int z = z0; z < z1; ++z) {
+        if (active) {
+            const V* ys = stY(sz);
+            const int rbase = (ty + ctr_row) * SXV;          // vector index of the own row
+            // own row: vectors covering x - HX .. x + VEC - 1 + HX
+            T xr[VEC + 2 * HX];
+#pragma unroll
+            for (int j = 0; j < NXV; ++j) {
+                const V v = ys[rbase + tx + j];
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) xr[j * VEC + e] = v.v[e];
+            }
+            const VR vv = stV(sz)[tid];
+            V pv;
+            if (Yp) pv = stP(sz)[tid];
+            V out;
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                T acc = mulr(a.center + a.alpha * vv.v[e], q[NH].v[e]);
+#pragma unroll
+                for (int p = 1; p <= NH; ++p) {
+                    acc = fmar(a.w[2][p - 1], add(q[NH + p].v[e], q[NH - p].v[e]), acc);
+                    acc = fmar(a.w[0][p - 1], add(xr[HX + e + p], xr[HX + e - p]), acc);
+                }
+                out.v[e] = acc;
+            }
+#pragma unroll
+            for (int p = 1; p <= NH; ++p) {
+                const V up = ys[rbase + p * SXV + tx + HX / VEC];
+                const V dn = ys[rbase - p * SXV + tx + HX / VEC];
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) out.v[e] = fmar(a.w[1][p - 1], add(up.v[e], dn.v[e]), out.v[e]);
+            }
+            if (Yp) {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) out.v[e] = fmar(a.beta, pv.v[e], out.v[e]);
+            }
+            *reinterpret_cast<V*>(Yo + (long)z * plane + own) = out;
+        }
+        if (z + 1 == z1) break;
+        __syncthreads();
+        if (ip <= last_needed) issue(ist, izw, ip < z1);
+        cp_async_commit();
+        ++ip; if (++ist == S) ist = 0; if (++izw == n3) { izw = 0; ++iwz; }
+        cp_async_wait<P>();
+        fix(sf, fwz);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 2 * NH; ++j) q[j] = q[j + 1];
+        q[2 * NH] = stY(sf)[(ty + ctr_row) * SXV + tx + HX / VEC];
+        if (++sz == S) sz = 0;
+        if (++sf == S) sf = 0;
+        if (++fzw == n3) { fzw = 0; ++fwz; }
+    }
+    cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------- float x4 form
+// Real float, 4 consecutive x-points per thread, held as two packed pairs so that every
+// add / FMA is one Blackwell f32x2 instruction (add.rn.f32x2, fma.rn.f32x2: two lanes of
+// ordinary IEEE float arithmetic, the same rounding as scalar code).  The z-loop is
+// unrolled 2*NH+1 times so the register queue rotates by static indexing instead of moves.
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 pk2(float a, float b) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float lo2(u64 v) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return a;
+}
+__device__ __forceinline__ float hi2(u64 v) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return b;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+template <int TXT, int TY, int P>
+__global__ void __launch_bounds__(TXT * TY)
+k_stencil_f32x4(StencilDev<float> a) {
+    using C = VecCfg<float, false, 4, TXT, TY, P>;
+    constexpr int NH = C::NH, HX = C::HX, SXV = C::SXV, S = C::S, NT = C::NT, PER = C::PER;
+    constexpr int Q = 2 * NH + 1;
+    static_assert(HX == 8, "x halo of two float4 vectors");
+    extern __shared__ __align__(128) unsigned char smem[];
+
+    const int tid = threadIdx.x;
+    const int tx = tid % TXT, ty = tid / TXT;
+    const int col = blockIdx.z / a.nzc;
+    const int zc = blockIdx.z - col * a.nzc;
+    const int z0 = zc * a.zchunk;
+    const int z1 = min(z0 + a.zchunk, a.n3);
+    const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
+    const long plane = (long)n1 * n2;
+    const int gx0 = blockIdx.x * C::TXP, gy0 = blockIdx.y * TY;
+
+    const float* __restrict__ Y = reinterpret_cast<const float*>(a.Y) + (size_t)col * a.ld;
+    const float* Yp = a.Yprev ? reinterpret_cast<const float*>(a.Yprev) + (size_t)col * a.ld : nullptr;
+    float* Yo = reinterpret_cast<float*>(a.Yout) + (size_t)col * a.ld;
+
+    int s_idx[PER];
+    const float* s_src[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = tid + k * NT;
+        s_idx[k] = -1;
+        s_src[k] = Y;
+        if (i < C::NVS) {
+            const int cx = i % SXV, iy = i / SXV;
+            const int gx = gx0 - HX + cx * 4, gy = gy0 - NH + iy;
+            const int wx = floordiv(gx, n1), wy = floordiv(gy, n2);
+            s_idx[k] = i;
+            s_src[k] = Y + (long)(gy - wy * n2) * n1 + (gx - wx * n1);
+        }
+    }
+    const bool active = (gx0 + tx * 4 < n1) && (gy0 + ty < n2);
+    const long own = (long)(gy0 + ty) * n1 + (gx0 + tx * 4);
+
+    auto stY = [&](int st) { return reinterpret_cast<ulonglong2*>(smem + C::STAGE * (size_t)st); };
+    auto stV = [&](int st) { return reinterpret_cast<ulonglong2*>(smem + C::STAGE * (size_t)st + C::YB); };
+    auto stP = [&](int st) { return reinterpret_cast<ulonglong2*>(smem + C::STAGE * (size_t)st + C::YB + C::VB); };
+    auto issue = [&](int st, int zw, bool interior) {
+        const long zoff = (long)zw * plane;
+        ulonglong2* ys = stY(st);
+#pragma unroll
+        for (int k = 0; k < PER; ++k)
+            if (s_idx[k] >= 0) cp_async<16>(ys + s_idx[k], s_src[k] + zoff);
+        if (active && interior) {
+            cp_async<16>(stV(st) + tid, a.V + zoff + own);
+            if (Yp) cp_async<16>(stP(st) + tid, Yp + zoff + own);
+        }
+    };
+
+    // packed coefficients
+    u64 wx[NH], wy[NH], wz[NH];
+#pragma unroll
+    for (int p = 0; p < NH; ++p) {
+        wx[p] = pk2(a.w[0][p], a.w[0][p]);
+        wy[p] = pk2(a.w[1][p], a.w[1][p]);
+        wz[p] = pk2(a.w[2][p], a.w[2][p]);
+    }
+    const u64 cen2 = pk2(a.center, a.center), alp2 = pk2(a.alpha, a.alpha), bet2 = pk2(a.beta, a.beta);
+
+    const int last_needed = z1 + NH - 1;
+    u64 ql[Q], qh[Q];                 // points (0,1) and (2,3) of planes in the queue
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        ql[j] = 0ull;
+        qh[j] = 0ull;
+        if (active) {
+            const int p = z0 - NH + j;
+            const int wz_ = floordiv(p, n3);
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(Y + (long)(p - wz_ * n3) * plane + own);
+            ql[j] = v.x;
+            qh[j] = v.y;
+        }
+    }
+    int ist = 0, izw = z0 % n3, ip = z0;
+#pragma unroll 1
+    for (int j = 0; j <= NH + P; ++j) {
+        if (ip <= last_needed) issue(ist, izw, ip < z1);
+        cp_async_commit();
+        ++ip; if (++ist == S) ist = 0; if (++izw == n3) izw = 0;
+    }
+    cp_async_wait<P>();
+    __syncthreads();
+    int sz = 0, sf = (NH + 1) % S;
+    const int rbase = (ty + NH) * SXV;
+#pragma unroll 1
+    for (int zb = z0; zb < z1; zb += Q) {
+#pragma unroll
+        for (int st = 0; st < Q; ++st) {
+            const int z = zb + st;
+            if (z >= z1) break;
+            if (active) {
+                const ulonglong2* ys = stY(sz);
+                // own row: floats x-8 .. x+11 as ten packed pairs r[0..9] (r[k] = floats 2k, 2k+1)
+                u64 r[10];
+#pragma unroll
+                for (int j = 0; j < 5; ++j) {
+                    const ulonglong2 v = ys[rbase + tx + j];
+                    r[2 * j] = v.x;
+                    r[2 * j + 1] = v.y;
+                }
+                // odd-aligned pairs u[k] = floats (2k+1, 2k+2), k = 1..7
+                u64 u[8];
+#pragma unroll
+                for (int k = 1; k <= 7; ++k) u[k] = pk2(hi2(r[k]), lo2(r[k + 1]));
+                const ulonglong2 vv = stV(sz)[tid];
+                // points 0,1 sit at floats 8,9 (pair r[4]); points 2,3 at floats 10,11 (r[5])
+                u64 al = mul2(fma2(alp2, vv.x, cen2), ql[(st + NH) % Q]);
+                u64 ah = mul2(fma2(alp2, vv.y, cen2), qh[(st + NH) % Q]);
+#pragma unroll
+                for (int p = 1; p <= NH; ++p) {
+                    al = fma2(wz[p - 1], add2(ql[(st + NH + p) % Q], ql[(st + NH - p) % Q]), al);
+                    ah = fma2(wz[p - 1], add2(qh[(st + NH + p) % Q], qh[(st + NH - p) % Q]), ah);
+                    // x +- p of floats (8,9) and (10,11)
+                    const u64 lp = (p & 1) ? u[(8 + p - 1) / 2] : r[(8 + p) / 2];
+                    const u64 lm = (p & 1) ? u[(8 - p - 1) / 2] : r[(8 - p) / 2];
+                    const u64 hp = (p & 1) ? u[(10 + p - 1) / 2] : r[(10 + p) / 2];
+                    const u64 hm = (p & 1) ? u[(10 - p - 1) / 2] : r[(10 - p) / 2];
+                    al = fma2(wx[p - 1], add2(lp, lm), al);
+                    ah = fma2(wx[p - 1], add2(hp, hm), ah);
+                    const ulonglong2 up = ys[rbase + p * SXV + tx + 2];
+                    const ulonglong2 dn = ys[rbase - p * SXV + tx + 2];
+                    al = fma2(wy[p - 1], add2(up.x, dn.x), al);
+                    ah = fma2(wy[p - 1], add2(up.y, dn.y), ah);
+                }
+                if (Yp) {
+                    const ulonglong2 pv = stP(sz)[tid];
+                    al = fma2(bet2, pv.x, al);
+                    ah = fma2(bet2, pv.y, ah);
+                }
+                *reinterpret_cast<ulonglong2*>(Yo + (long)z * plane + own) = make_ulonglong2(al, ah);
+            }
+            if (z + 1 == z1) break;
+            __syncthreads();
+            if (ip <= last_needed) issue(ist, izw, ip < z1);
+            cp_async_commit();
+            ++ip; if (++ist == S) ist = 0; if (++izw == n3) izw = 0;
+            cp_async_wait<P>();
+            __syncthreads();
+            const ulonglong2 f = stY(sf)[rbase + tx + 2];
+            ql[st] = f.x;                     // slot of plane z - NH takes plane z + NH + 1
+            qh[st] = f.y;
+            if (++sz == S) sz = 0;
+            if (++sf == S) sf = 0;
+        }
+    }
+    cp_async_wait<0>();
+}
+
+template <int TXT, int TY, int P>
+static int run_f32x4(hub_t h, const StencilArgs& s) {
+    using Cfg = VecCfg<float, false, 4, TXT, TY, P>;
+    StencilDev<float> d;
+    d.Y = s.Y;
+    d.Yprev = s.Yprev;
+    d.Yout = s.Yout;
+    d.V = reinterpret_cast<const float*>(s.V);
+    d.n1 = s.n1; d.n2 = s.n2; d.n3 = s.n3; d.ld = s.ld;
+    for (int a = 0; a < 3; ++a) {
+        for (int p = 0; p < 6; ++p) d.w[a][p] = (float)(p < s.n0 ? s.w[a][p] : 0.0);
+        d.ph[a][0] = 1.0;
+        d.ph[a][1] = 0.0;
+    }
+    d.center = (float)s.center;
+    d.alpha = (float)s.alpha;
+    d.beta = (float)s.beta;
+    const int tiles = ((s.n1 + Cfg::TXP - 1) / Cfg::TXP) * ((s.n2 + TY - 1) / TY);
+    const long want = 4L * h->num_sms;
+    const long per = (long)tiles * s.ncol;
+    int nzc = 1;
+    if (per < want) nzc = (int)((want + per - 1) / per);
+    int zchunk = (s.n3 + nzc - 1) / nzc;
+    if (zchunk < 16) zchunk = s.n3 < 16 ? s.n3 : 16;
+    nzc = (s.n3 + zchunk - 1) / zchunk;
+    while ((long)s.ncol * nzc > 65535) { zchunk *= 2; nzc = (s.n3 + zchunk - 1) / zchunk; }
+    d.zchunk = zchunk;
+    d.nzc = nzc;
+    HUB_CUDA_TRY(h, cudaFuncSetAttribute(k_stencil_f32x4<TXT, TY, P>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
+    dim3 grid((s.n1 + Cfg::TXP - 1) / Cfg::TXP, (s.n2 + TY - 1) / TY, s.ncol * nzc);
+    ProfScope ps(h, HUB_K_STENCIL);
+    k_stencil_f32x4<TXT, TY, P><<<grid, TXT * TY, Cfg::SMEM, h->stream>>>(d);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    return HUB_OK;
+}
+
+template <typename R, bool CPLX, int VEC, int TXT, int TY, int P>
+static int run_vec(hub_t h, const StencilArgs& s) {
+    using Cfg = VecCfg<R, CPLX, VEC, TXT, TY, P>;
+    StencilDev<R> d;
+    d.Y = s.Y;
+    d.Yprev = s.Yprev;
+    d.Yout = s.Yout;
+    d.V = reinterpret_cast<const R*>(s.V);
+    d.n1 = s.n1; d.n2 = s.n2; d.n3 = s.n3; d.ld = s.ld;
+    for (int a = 0; a < 3; ++a) {
+        for (int p = 0; p < 6; ++p) d.w[a][p] = (R)(p < s.n0 ? s.w[a][p] : 0.0);
+        d.ph[a][0] = s.phase[a][0];
+        d.ph[a][1] = s.phase[a][1];
+    }
+    d.center = (R)s.center;
+    d.alpha = (R)s.alpha;
+    d.beta = (R)s.beta;
+    const int tiles = ((s.n1 + Cfg::TXP - 1) / Cfg::TXP) * ((s.n2 + TY - 1) / TY);
+    const long want = 4L * h->num_sms;
+    const long per = (long)tiles * s.ncol;
+    int nzc = 1;
+    if (per < want) nzc = (int)((want + per - 1) / per);
+    int zchunk = (s.n3 + nzc - 1) / nzc;
+    if (zchunk < 16) zchunk = s.n3 < 16 ? s.n3 : 16;
+    nzc = (s.n3 + zchunk - 1) / zchunk;
+    while ((long)s.ncol * nzc > 65535) { zchunk *= 2; nzc = (s.n3 + zchunk - 1) / zchunk; }
+    d.zchunk = zchunk;
+    d.nzc = nzc;
+    HUB_CUDA_TRY(h, cudaFuncSetAttribute(k_stencil_vec<R, CPLX, VEC, TXT, TY, P>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
+    dim3 grid((s.n1 + Cfg::TXP - 1) / Cfg::TXP, (s.n2 + TY - 1) / TY, s.ncol * nzc);
+    ProfScope ps(h, HUB_K_STENCIL);
+    k_stencil_vec<R, CPLX, VEC, TXT, TY, P><<<grid, TXT * TY, Cfg::SMEM, h->stream>>>(d);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    return HUB_OK;
+}
+
+template <typename R, bool CPLX, int TX, int TY, int P>
+static int run_cfg(hub_t h, const StencilArgs& s) {
+    using Cfg = StencilCfg<R, CPLX, TX, TY, P>;
     StencilDev<R> d;
     d.Y = s.Y;
     d.Yprev = s.Yprev;
@@ -139,29 +698,42 @@ static int run(hub_t h, const StencilArgs& s) {
     d.alpha = (R)s.alpha;
     d.beta = (R)s.beta;
     const int tiles = ((s.n1 + TX - 1) / TX) * ((s.n2 + TY - 1) / TY);
-    // enough CTAs to fill the GPU several times over, but chunks long enough that the
-    // 2*NH-plane queue fill stays a small overhead
-    const long want = 8L * h->num_sms;
-    long per = (long)tiles * s.ncol;
+    // enough CTAs to fill every SM several times, chunks long enough that the prologue of
+    // 2*NH+P planes stays a modest overhead
+    const long want = 6L * h->num_sms;
+    const long per = (long)tiles * s.ncol;
     int nzc = 1;
     if (per < want) nzc = (int)((want + per - 1) / per);
     int zchunk = (s.n3 + nzc - 1) / nzc;
-    if (zchunk < 8) zchunk = s.n3 < 8 ? s.n3 : 8;
+    if (zchunk < 16) zchunk = s.n3 < 16 ? s.n3 : 16;
     nzc = (s.n3 + zchunk - 1) / zchunk;
     while ((long)s.ncol * nzc > 65535) { zchunk *= 2; nzc = (s.n3 + zchunk - 1) / zchunk; }
     d.zchunk = zchunk;
     d.nzc = nzc;
+    HUB_CUDA_TRY(h, cudaFuncSetAttribute(k_stencil<R, CPLX, TX, TY, P>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
     dim3 grid((s.n1 + TX - 1) / TX, (s.n2 + TY - 1) / TY, s.ncol * nzc);
     ProfScope ps(h, HUB_K_STENCIL);
-    k_stencil<R, CPLX, TX, TY><<<grid, TX * TY, 0, h->stream>>>(d);
+    k_stencil<R, CPLX, TX, TY, P><<<grid, TX * TY, Cfg::SMEM, h->stream>>>(d);
     HUB_CUDA_TRY(h, cudaGetLastError());
     return HUB_OK;
 }
 
 int launch_stencil(hub_t h, const StencilArgs& a) {
     if (a.ncol == 0) return HUB_OK;
-    if (h->esize == 8) return h->cplx ? run<double, true>(h, a) : run<double, false>(h, a);
-    return h->cplx ? run<float, true>(h, a) : run<float, false>(h, a);
+    const int es = h->esize * (h->cplx ? 2 : 1);
+    const int vec = 16 / es;
+    const bool aligned = (a.n1 % vec == 0) && (a.ld % vec == 0) &&
+                         ((uintptr_t)a.Y % 16 == 0) && ((uintptr_t)a.Yout % 16 == 0) &&
+                         (!a.Yprev || (uintptr_t)a.Yprev % 16 == 0) && ((uintptr_t)a.V % 16 == 0);
+    if (aligned && h->esize == 4) {
+        // float streams from HBM: vector copies, packed pair arithmetic for real data
+        return h->cplx ? run_vec<float, true, 2, 16, 16, 2>(h, a) : run_f32x4<8, 16, 4>(h, a);
+    }
+    // FP64 is bound by the FP64 pipe: a short ring keeps two CTAs per SM; float streams from
+    // HBM: a deeper ring keeps more bytes in flight
+    if (h->esize == 8) return h->cplx ? run_cfg<double, true, 32, 8, 2>(h, a) : run_cfg<double, false, 32, 8, 2>(h, a);
+    return h->cplx ? run_cfg<float, true, 32, 8, 2>(h, a) : run_cfg<float, false, 32, 8, 4>(h, a);
 }
 
 }  // namespace hub
