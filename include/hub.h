@@ -113,6 +113,13 @@ int hub_num_hubbard_atoms(hub_t h, int* nhub);
  * that spin (Eq. DerED; coefficient of phi_m' is sum_m M_m'm <phi_m|psi>). */
 int hub_set_occupation_matrix(hub_t h, int spin, const double* D_re, const double* D_im);
 
+/* HUB_MIXED_BF16 handles: number of BF16 tensor-core products per Rayleigh-Ritz product.
+ * terms = 1: operands rounded to BF16 (8 significand bits), one product;
+ * terms = 3: every float operand split as hi + lo (hi = bf16(x), lo = bf16(x - hi)) and
+ * the product taken as hi*hi + hi*lo + lo*hi (about 16 significand bits).  Default 3.
+ * Accumulation is FP32 either way.  Errors: HUB_EINVAL. */
+int hub_set_bf16_terms(hub_t h, int terms);
+
 /* Y = H X for ncol columns (device, column-major, leading dimension ld):
  *   H = -1/2 Lap_h + V_eff + sum_I sum_p gamma_Ip |chi_Ip><chi_Ip|
  *       + sum_I sum_mm' (U_I/2)(delta_mm' - 2 D_m'm) |phi_Im'><phi_Im|
@@ -141,8 +148,9 @@ int hub_rayleigh_ritz(hub_t h, int spin, void* X, int ncol, int ld, double* eig_
  * over the Nd grid rows; with alpha = dV this is the overlap <A|B> (the Gram matrix
  * S = <X|X>, or <X|HX> with B = H X).  G_dev: device double, row-major
  * [ncol_a x ncol_b], overwritten.  When A == B and ncol_a == ncol_b only the upper tiles
- * are computed and mirrored.  Uses handle-owned split-K scratch (allocated on first use).
- * Real orbitals only.  Errors: HUB_EINVAL. */
+ * are computed and mirrored.  On HUB_MIXED_BF16 handles the product runs on the BF16
+ * tensor cores (see hub_set_bf16_terms) with float accumulation.  Uses handle-owned
+ * split-K scratch (allocated on first use).  Real orbitals only.  Errors: HUB_EINVAL. */
 int hub_gram(hub_t h, const void* A, int ncol_a, const void* B, int ncol_b, int ld,
              double alpha, double* G_dev);
 

@@ -60,6 +60,7 @@ _SIGS = {
     "hub_scf_run": [_P, C.POINTER(scf_result)],
     "hub_scf_get": [_P, _PD, _PD, _PD],
     "hub_version": [C.c_char_p, _I],
+    "hub_set_bf16_terms": [_P, _I],
     "hub_profile": [_P, _I],
     "hub_profile_read": [_P, _I, _PD, C.POINTER(C.c_longlong)],
     "hub_launch_count": [_P, C.POINTER(C.c_longlong)],
@@ -157,6 +158,9 @@ class Hub:
             pass
 
     # ------------------------------------------------------------------ setup
+    def set_bf16_terms(self, terms: int):
+        self._check(self.lib.hub_set_bf16_terms(self.h, int(terms)), "hub_set_bf16_terms")
+
     def set_veff(self, veff):
         self._check(self.lib.hub_set_veff(self.h, _tptr(veff)), "hub_set_veff")
 

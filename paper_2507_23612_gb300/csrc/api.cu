@@ -254,6 +254,13 @@ int hub_set_occupation_matrix(hub_t h, int spin, const double* D_re, const doubl
     return HUB_OK;
 }
 
+int hub_set_bf16_terms(hub_t h, int terms) {
+    if (!h) return HUB_EINVAL;
+    if (terms != 1 && terms != 3) return fail(h, HUB_EINVAL, "terms must be 1 or 3");
+    h->bf16_terms = terms;
+    return HUB_OK;
+}
+
 int hub_apply_H(hub_t h, int spin, const void* X, void* Y, int ncol, int ld) {
     int rc = check_block(h, spin, X, ncol, ld);
     if (rc) return rc;
@@ -350,6 +357,7 @@ int hub_gram(hub_t h, const void* A, int ncol_a, const void* B, int ncol_b, int 
     if (ncol_a == 0 || ncol_b == 0) return HUB_OK;
     if (!A || !B || !G_dev) return fail(h, HUB_EINVAL, "NULL pointer");
     const bool sym = (A == B) && (ncol_a == ncol_b);
+    if (h->prec == HUB_MIXED_BF16) return launch_gram_bf16(h, A, ld, B, ld, ncol_a, ncol_b, alpha, sym, G_dev);
     return launch_gram(h, A, ld, B, ld, ncol_a, ncol_b, alpha, sym, G_dev);
 }
 

@@ -91,6 +91,7 @@ struct hub_ctx {
     double kpt[3] = {0, 0, 0};
     int prec = HUB_F64;
     int esize = 8;                // bytes per real component of the working type
+    int bf16_terms = 3;           // HUB_MIXED_BF16: 1 = bf16 x bf16, 3 = hi/lo split products
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 0;
