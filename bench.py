@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--scf-tts", action="store_true",
                     help="also run one cold-start SCF to convergence and report its time")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--scf-compare", action="store_true",
+                    help="cold-start SCF to convergence in FP64, FP32 and mixed (BF16 with the "
+                         "precision ladder); report time to solution and errors against FP64")
     return ap.parse_args()
 
 
@@ -168,7 +171,8 @@ def run_hub(args, rank, world, local_rank):
     p = scf_params(nspin=nspin, ncol=wl.ncol, ld=wl.Nd, degree=wl.degree, max_iter=1000,
                    first_passes=3 if args.workload == "rutile" else 1, lanczos_steps=10,
                    pulay_history=7, natoms=len(wl.atoms), pulay_beta=0.3,
-                   kT=wl.kT if wl.kT > 0 else 0.005, n_elec=wl.n_elec, tol_e_atom=1e-5, tol_D=1e-4)
+                   kT=wl.kT if wl.kT > 0 else 0.005, n_elec=wl.n_elec, tol_e_atom=1e-5, tol_D=1e-4,
+                   ladder=1 if args.prec == "mixed" else 0, ladder_tol=1e-4)
     hub.scf_begin(p, Xs, v0s, wl.D0)
     for _ in range(args.warmup):
         hub.scf_iterate()
@@ -268,8 +272,58 @@ def run_hub(args, rank, world, local_rank):
             "roofline": roof, "kernels": breakdown, "clocks": clocks, "last": last, "wl": wl}
 
 
+def scf_compare(args):
+    """Cold-start SCF of the workload in each precision form; errors against the FP64 run."""
+    import numpy as np
+    import torch
+    from paper_2507_23612_gb300 import Hub, scf_params
+    dev = torch.device("cuda", 0)
+    wl = make_workload(args.workload)
+    X0 = [wl.orbitals(s) for s in range(wl.nspin)]
+    out = {}
+    for form in ("f64", "f32", "mixed"):
+        hub = Hub(wl.n, wl.L, wl.fd_half_order, prec=PREC[form])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hub.set_veff(torch.tensor(wl.veff, device=dev))
+        hub.set_atoms(wl.atoms)
+        Xs = [torch.tensor(x, device=dev).to(hub.dtype).contiguous() for x in X0]
+        v0s = [torch.tensor(wl.lanczos_start(s), device=dev).to(hub.dtype).contiguous()
+               for s in range(wl.nspin)]
+        p = scf_params(nspin=wl.nspin, ncol=wl.ncol, ld=wl.Nd, degree=wl.degree, max_iter=200,
+                       first_passes=3, lanczos_steps=10, pulay_history=7, natoms=len(wl.atoms),
+                       pulay_beta=0.3, kT=wl.kT if wl.kT > 0 else 0.005, n_elec=wl.n_elec,
+                       tol_e_atom=1e-5, tol_D=1e-4, ladder=1 if form == "mixed" else 0, ladder_tol=1e-4)
+        hub.scf_begin(p, Xs, v0s, wl.D0)
+        res = hub.scf_run()
+        torch.cuda.synchronize()
+        tts = time.perf_counter() - t0
+        eig, occ, D = hub.scf_get()
+        out[form] = {"seconds": tts, "iterations": res["iter"], "converged": bool(res["converged"]),
+                     "E": res["E"], "E_U": res["E_U"], "band": float(np.sum(occ * eig)), "D": D}
+        hub.close()
+        del Xs
+        torch.cuda.empty_cache()
+    nat = len(wl.atoms)
+    ref = out["f64"]
+    table = {}
+    for form, r in out.items():
+        table[form] = {"time_to_solution_s": round(r["seconds"], 3), "iterations": r["iterations"],
+                       "converged": r["converged"], "speedup_vs_f64": round(ref["seconds"] / r["seconds"], 2),
+                       "E_err_Ha_per_atom": abs(r["E"] - ref["E"]) / nat,
+                       "E_U_err_Ha_per_atom": abs(r["E_U"] - ref["E_U"]) / nat,
+                       "band_err_Ha_per_atom": abs(r["band"] - ref["band"]) / nat,
+                       "max_abs_dD": float(np.max(np.abs(r["D"] - ref["D"])))}
+    print(json.dumps({"scf_compare": table, "workload": args.workload,
+                      "criterion": "|dE|/atom < 1e-5 Ha twice and max|dD| < 1e-4",
+                      "E_f64_Ha": ref["E"], "E_U_f64_Ha": ref["E_U"]}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.scf_compare:
+        return scf_compare(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

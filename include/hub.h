@@ -113,11 +113,12 @@ int hub_num_hubbard_atoms(hub_t h, int* nhub);
  * that spin (Eq. DerED; coefficient of phi_m' is sum_m M_m'm <phi_m|psi>). */
 int hub_set_occupation_matrix(hub_t h, int spin, const double* D_re, const double* D_im);
 
-/* HUB_MIXED_BF16 handles: number of BF16 tensor-core products per Rayleigh-Ritz product.
- * terms = 1: operands rounded to BF16 (8 significand bits), one product;
+/* HUB_MIXED_BF16 handles: how the Rayleigh-Ritz block products are taken.
+ * terms = 1: operands rounded to BF16 (8 significand bits), one tensor-core product;
  * terms = 3: every float operand split as hi + lo (hi = bf16(x), lo = bf16(x - hi)) and
- * the product taken as hi*hi + hi*lo + lo*hi (about 16 significand bits).  Default 3.
- * Accumulation is FP32 either way.  Errors: HUB_EINVAL. */
+ *            the product taken as hi*hi + hi*lo + lo*hi (about 16 significand bits);
+ * terms = 0: float products on CUDA cores (24 significand bits).
+ * Tensor-core products accumulate in FP32.  Default 3.  Errors: HUB_EINVAL. */
 int hub_set_bf16_terms(hub_t h, int terms);
 
 /* Y = H X for ncol columns (device, column-major, leading dimension ld):
@@ -216,12 +217,19 @@ typedef struct {
     double n_elec;
     double tol_e_atom;    /* Ha/atom */
     double tol_D;
+    int ladder;           /* HUB_MIXED_BF16 only: 1 = one BF16 tensor-core product per
+                             Rayleigh-Ritz product until |dE|/natoms < ladder_tol, then float
+                             products (hub_set_bf16_terms 0) for the remaining iterations;
+                             0 = keep the handle's setting */
+    double ladder_tol;    /* Ha/atom */
 } hub_scf_params;
 
 typedef struct {
     int iter;             /* iterations done */
     int converged;        /* 1 once the criterion above holds */
     double E, E_band, E_U, dE, dD, mu;
+    int bf16_terms;       /* products used in this iteration on mixed handles (1, 3, 0) */
+    int jacobi_sweeps;    /* sweeps of the last subspace eigensolve */
 } hub_scf_result;
 
 /* Start an SCF: X[nspin] device blocks (ld*ncol each; updated in place every iteration),

@@ -29,13 +29,14 @@ class scf_params(C.Structure):
                 ("max_iter", C.c_int), ("first_passes", C.c_int), ("lanczos_steps", C.c_int),
                 ("pulay_history", C.c_int), ("natoms", C.c_int), ("pulay_beta", C.c_double),
                 ("kT", C.c_double), ("n_elec", C.c_double), ("tol_e_atom", C.c_double),
-                ("tol_D", C.c_double)]
+                ("tol_D", C.c_double), ("ladder", C.c_int), ("ladder_tol", C.c_double)]
 
 
 class scf_result(C.Structure):
     _fields_ = [("iter", C.c_int), ("converged", C.c_int), ("E", C.c_double),
                 ("E_band", C.c_double), ("E_U", C.c_double), ("dE", C.c_double),
-                ("dD", C.c_double), ("mu", C.c_double)]
+                ("dD", C.c_double), ("mu", C.c_double), ("bf16_terms", C.c_int),
+                ("jacobi_sweeps", C.c_int)]
 
 
 _P, _I, _D = C.c_void_p, C.c_int, C.c_double

@@ -39,10 +39,11 @@ int check_flags(hub_t h) {
     int f[8];
     HUB_CUDA_TRY(h, cudaMemcpyAsync(f, h->d_flags, sizeof(f), cudaMemcpyDeviceToHost, h->stream));
     HUB_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->last_sweeps = f[6];
     bool any = false;
-    for (int i = 0; i < 8; ++i) any |= f[i] != 0;
+    for (int i = 0; i < 6; ++i) any |= f[i] != 0;
     if (!any) return HUB_OK;
-    HUB_CUDA_TRY(h, cudaMemsetAsync(h->d_flags, 0, 8 * sizeof(int), h->stream));
+    HUB_CUDA_TRY(h, cudaMemsetAsync(h->d_flags, 0, 6 * sizeof(int), h->stream));
     HUB_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     if (f[FLAG_TIMEOUT]) return fail(h, HUB_ETIMEOUT, "a bounded device wait ran out");
     if (f[FLAG_NOTSPD]) return fail(h, HUB_ENOTSPD, "Gram matrix is not positive definite");
@@ -118,6 +119,7 @@ struct ScfState {
     bool have_bounds[2] = {false, false};
     int iter = 0;
     int small = 0;
+    bool laddered = false;            // switched to the hi/lo split
     bool have_prev = false;
     double E_prev = 0.0;
     hub_scf_result last{};
@@ -256,7 +258,7 @@ int hub_set_occupation_matrix(hub_t h, int spin, const double* D_re, const doubl
 
 int hub_set_bf16_terms(hub_t h, int terms) {
     if (!h) return HUB_EINVAL;
-    if (terms != 1 && terms != 3) return fail(h, HUB_EINVAL, "terms must be 1 or 3");
+    if (terms != 0 && terms != 1 && terms != 3) return fail(h, HUB_EINVAL, "terms must be 0, 1 or 3");
     h->bf16_terms = terms;
     return HUB_OK;
 }
@@ -320,8 +322,15 @@ int hub_rayleigh_ritz(hub_t h, int spin, void* X, int ncol, int ld, double* eig_
     double* Q = Vs + nn;
     double* eig = Q + nn;
     if ((rc = apply_H_internal(h, spin, X, ld, HX, ncol, 1.0, 0.0, nullptr, 0.0))) return rc;
-    if (h->prec == HUB_MIXED_BF16) {
-        if ((rc = launch_gram(h, X, ld, X, ld, n, n, h->dV, true, S))) return rc;
+    const bool tensor = (h->prec == HUB_MIXED_BF16) && h->bf16_terms > 0;
+    if (tensor) {
+        // the Gram matrix feeds the Cholesky factor: always the hi/lo split (about 16
+        // significand bits)
+        const int terms = h->bf16_terms;
+        h->bf16_terms = 3;
+        rc = launch_gram_bf16(h, X, ld, X, ld, n, n, h->dV, true, S);
+        h->bf16_terms = terms;
+        if (rc) return rc;
         if ((rc = launch_gram_bf16(h, X, ld, HX, ld, n, n, h->dV, true, Hs))) return rc;
     } else {
         if ((rc = launch_gram(h, X, ld, X, ld, n, n, h->dV, true, S))) return rc;
@@ -335,7 +344,7 @@ int hub_rayleigh_ritz(hub_t h, int spin, void* X, int ncol, int ld, double* eig_
     if ((rc = dense_symmetrize(h, Hs, n))) return rc;
     if ((rc = dense_jacobi_eigh(h, Hs, Vs, eig, n))) return rc;
     if ((rc = dense_gemm(h, true, false, n, n, n, 1.0, Linv, n, Vs, n, 0.0, Q, n))) return rc;
-    if (h->prec == HUB_MIXED_BF16) {
+    if (tensor) {
         if ((rc = launch_rotate_bf16(h, X, ld, Q, n, n, HX, ld))) return rc;
     } else {
         if ((rc = launch_rotate(h, X, ld, Q, n, n, HX, ld))) return rc;
@@ -357,7 +366,8 @@ int hub_gram(hub_t h, const void* A, int ncol_a, const void* B, int ncol_b, int 
     if (ncol_a == 0 || ncol_b == 0) return HUB_OK;
     if (!A || !B || !G_dev) return fail(h, HUB_EINVAL, "NULL pointer");
     const bool sym = (A == B) && (ncol_a == ncol_b);
-    if (h->prec == HUB_MIXED_BF16) return launch_gram_bf16(h, A, ld, B, ld, ncol_a, ncol_b, alpha, sym, G_dev);
+    if (h->prec == HUB_MIXED_BF16 && h->bf16_terms > 0)
+        return launch_gram_bf16(h, A, ld, B, ld, ncol_a, ncol_b, alpha, sym, G_dev);
     return launch_gram(h, A, ld, B, ld, ncol_a, ncol_b, alpha, sym, G_dev);
 }
 
@@ -546,6 +556,7 @@ int hub_scf_iterate(hub_t h, hub_scf_result* res) {
     const int ns = p.nspin;
     const double deg = ns == 1 ? 2.0 : 1.0;
     int rc;
+    if (p.ladder && h->prec == HUB_MIXED_BF16) h->bf16_terms = st.laddered ? 0 : 1;
     for (int s = 0; s < ns; ++s) {
         if ((rc = hub_set_occupation_matrix(h, s, st.D_in.data() + (size_t)s * nh * 25, nullptr))) return rc;
         const int passes = st.iter == 0 ? std::max(1, p.first_passes) : 1;
@@ -605,6 +616,13 @@ int hub_scf_iterate(hub_t h, hub_scf_result* res) {
     r.iter = st.iter;
     r.converged = (st.small >= 2 && dD < p.tol_D) ? 1 : 0;
     r.E = E; r.E_band = e_band; r.E_U = e_u; r.dE = dE; r.dD = dD; r.mu = mu;
+    r.bf16_terms = h->prec == HUB_MIXED_BF16 ? h->bf16_terms : 0;
+    r.jacobi_sweeps = h->last_sweeps;
+    if (p.ladder && !st.laddered && st.iter > 1 && std::fabs(dE) / std::max(1, p.natoms) < p.ladder_tol) {
+        st.laddered = true;
+        st.small = 0;       // the converged-energy count restarts at the finer precision
+        r.converged = 0;
+    }
     st.last = r;
     if (!r.converged) st.D_in = pulay_mix(st, st.D_in, st.D_out);
     if (res) *res = r;

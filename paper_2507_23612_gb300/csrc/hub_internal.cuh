@@ -113,13 +113,14 @@ struct hub_ctx {
     void* d_gpart = nullptr;      size_t gpart_bytes = 0;   // split-K GEMM partials
     void* d_bf16 = nullptr;       size_t bf16_bytes = 0;    // bf16 operand copies
     void* d_aux = nullptr;        size_t aux_bytes = 0;     // occupations and D output
-    int* d_flags = nullptr;       // [8] device error flags
+    int* d_flags = nullptr;       // [8] device error flags (0..5), Jacobi sweep count (6)
     unsigned int* d_bar = nullptr;  // [4] grid-barrier state
     double* d_scal = nullptr;     // [256] device scalars (Lanczos, reductions)
 
     hub::ScfState* scf = nullptr;
 
     long long launches = 0;       // kernels launched by this handle
+    int last_sweeps = 0;          // Jacobi sweeps of the last Rayleigh-Ritz (device slot 6)
     int prof_on = 0;              // record a CUDA event pair around every launch
     std::vector<hub::ProfEvt> prof;
 

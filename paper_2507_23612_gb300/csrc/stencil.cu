@@ -28,10 +28,33 @@ struct StencilDev {
     const R* V;
     int n1, n2, n3, ld;
     R w[3][6];
-    R center, alpha, beta;
+    R center, alpha, beta;    // float: centre without the kinetic part (difference form)
     double ph[3][2];
     int zchunk, nzc;
 };
+
+// Rounded weights and the centre coefficient.  Double uses the summation form
+//   c f0 + sum_p w_p (f+p + f-p),   c = alpha(-1/2 c0 sum h^-2 - shift).
+// Float uses the difference form
+//   alpha(-shift) f0 + sum_p w_p ((f+p + f-p) - 2 f0)
+// whose terms are small for smooth orbitals: the large kinetic centre (~100 Ha at h = 0.2)
+// never enters a partial sum, so rounding does not bias the Rayleigh quotients (with the
+// summation form float rounding shifted every low eigenvalue by ~1e-5 ||H|| eps-scaled),
+// and constants are annihilated for any rounded weights.
+template <typename R>
+static void fill_coefficients(const StencilArgs& s, StencilDev<R>& d) {
+    double wsum = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int p = 0; p < 6; ++p) {
+            const double w = p < s.n0 ? s.w[a][p] : 0.0;
+            d.w[a][p] = (R)w;
+            wsum += w;
+        }
+    // the kinetic centre is -2 sum w; the float form carries it inside the differences
+    d.center = sizeof(R) == 4 ? (R)(s.center + 2.0 * wsum) : (R)s.center;
+    d.alpha = (R)s.alpha;
+    d.beta = (R)s.beta;
+}
 
 __device__ __forceinline__ int floordiv(int a, int n) {
     int q = a / n;
@@ -173,11 +196,20 @@ k_stencil(StencilDev<R> a) {
         if (active) {
             const T* ys = stage_Y(z);
             T acc = mulr(a.center + a.alpha * stage_V(z)[tid], q[NH]);
+            const T c0 = q[NH];
 #pragma unroll
             for (int p = 1; p <= NH; ++p) {
-                acc = fmar(a.w[2][p - 1], add(q[NH + p], q[NH - p]), acc);
-                acc = fmar(a.w[0][p - 1], add(ys[ctr + p], ys[ctr - p]), acc);
-                acc = fmar(a.w[1][p - 1], add(ys[ctr + p * SX], ys[ctr - p * SX]), acc);
+                T sz = add(q[NH + p], q[NH - p]);
+                T sx = add(ys[ctr + p], ys[ctr - p]);
+                T sy = add(ys[ctr + p * SX], ys[ctr - p * SX]);
+                if constexpr (sizeof(R) == 4) {
+                    sz = fmar((R)-2, c0, sz);
+                    sx = fmar((R)-2, c0, sx);
+                    sy = fmar((R)-2, c0, sy);
+                }
+                acc = fmar(a.w[2][p - 1], sz, acc);
+                acc = fmar(a.w[0][p - 1], sx, acc);
+                acc = fmar(a.w[1][p - 1], sy, acc);
             }
             if (Yp) acc = fmar(a.beta, stage_P(z)[tid], acc);
             Yo[(long)z * plane + own] = acc;
@@ -376,10 +408,17 @@ k_stencil_vec(StencilDev<R> a) {
 #pragma unroll
             for (int e = 0; e < VEC; ++e) {
                 T acc = mulr(a.center + a.alpha * vv.v[e], q[NH].v[e]);
+                const T c0 = q[NH].v[e];
 #pragma unroll
                 for (int p = 1; p <= NH; ++p) {
-                    acc = fmar(a.w[2][p - 1], add(q[NH + p].v[e], q[NH - p].v[e]), acc);
-                    acc = fmar(a.w[0][p - 1], add(xr[HX + e + p], xr[HX + e - p]), acc);
+                    T sz = add(q[NH + p].v[e], q[NH - p].v[e]);
+                    T sx = add(xr[HX + e + p], xr[HX + e - p]);
+                    if constexpr (sizeof(R) == 4) {
+                        sz = fmar((R)-2, c0, sz);
+                        sx = fmar((R)-2, c0, sx);
+                    }
+                    acc = fmar(a.w[2][p - 1], sz, acc);
+                    acc = fmar(a.w[0][p - 1], sx, acc);
                 }
                 out.v[e] = acc;
             }
@@ -388,7 +427,11 @@ k_stencil_vec(StencilDev<R> a) {
                 const V up = ys[rbase + p * SXV + tx + HX / VEC];
                 const V dn = ys[rbase - p * SXV + tx + HX / VEC];
 #pragma unroll
-                for (int e = 0; e < VEC; ++e) out.v[e] = fmar(a.w[1][p - 1], add(up.v[e], dn.v[e]), out.v[e]);
+                for (int e = 0; e < VEC; ++e) {
+                    T sy = add(up.v[e], dn.v[e]);
+                    if constexpr (sizeof(R) == 4) sy = fmar((R)-2, q[NH].v[e], sy);
+                    out.v[e] = fmar(a.w[1][p - 1], sy, out.v[e]);
+                }
             }
             if (Yp) {
 #pragma unroll
@@ -516,6 +559,7 @@ k_stencil_f32x4(StencilDev<float> a) {
         wz[p] = pk2(a.w[2][p], a.w[2][p]);
     }
     const u64 cen2 = pk2(a.center, a.center), alp2 = pk2(a.alpha, a.alpha), bet2 = pk2(a.beta, a.beta);
+    const u64 m2 = pk2(-2.0f, -2.0f);
 
     const int last_needed = z1 + NH - 1;
     u64 ql[Q], qh[Q];                 // points (0,1) and (2,3) of planes in the queue
@@ -564,23 +608,25 @@ k_stencil_f32x4(StencilDev<float> a) {
                 for (int k = 1; k <= 7; ++k) u[k] = pk2(hi2(r[k]), lo2(r[k + 1]));
                 const ulonglong2 vv = stV(sz)[tid];
                 // points 0,1 sit at floats 8,9 (pair r[4]); points 2,3 at floats 10,11 (r[5])
-                u64 al = mul2(fma2(alp2, vv.x, cen2), ql[(st + NH) % Q]);
-                u64 ah = mul2(fma2(alp2, vv.y, cen2), qh[(st + NH) % Q]);
+                const u64 cl = ql[(st + NH) % Q], ch = qh[(st + NH) % Q];
+                u64 al = mul2(fma2(alp2, vv.x, cen2), cl);
+                u64 ah = mul2(fma2(alp2, vv.y, cen2), ch);
 #pragma unroll
                 for (int p = 1; p <= NH; ++p) {
-                    al = fma2(wz[p - 1], add2(ql[(st + NH + p) % Q], ql[(st + NH - p) % Q]), al);
-                    ah = fma2(wz[p - 1], add2(qh[(st + NH + p) % Q], qh[(st + NH - p) % Q]), ah);
+                    // difference form: w ((f+p + f-p) - 2 f0)
+                    al = fma2(wz[p - 1], fma2(m2, cl, add2(ql[(st + NH + p) % Q], ql[(st + NH - p) % Q])), al);
+                    ah = fma2(wz[p - 1], fma2(m2, ch, add2(qh[(st + NH + p) % Q], qh[(st + NH - p) % Q])), ah);
                     // x +- p of floats (8,9) and (10,11)
                     const u64 lp = (p & 1) ? u[(8 + p - 1) / 2] : r[(8 + p) / 2];
                     const u64 lm = (p & 1) ? u[(8 - p - 1) / 2] : r[(8 - p) / 2];
                     const u64 hp = (p & 1) ? u[(10 + p - 1) / 2] : r[(10 + p) / 2];
                     const u64 hm = (p & 1) ? u[(10 - p - 1) / 2] : r[(10 - p) / 2];
-                    al = fma2(wx[p - 1], add2(lp, lm), al);
-                    ah = fma2(wx[p - 1], add2(hp, hm), ah);
+                    al = fma2(wx[p - 1], fma2(m2, cl, add2(lp, lm)), al);
+                    ah = fma2(wx[p - 1], fma2(m2, ch, add2(hp, hm)), ah);
                     const ulonglong2 up = ys[rbase + p * SXV + tx + 2];
                     const ulonglong2 dn = ys[rbase - p * SXV + tx + 2];
-                    al = fma2(wy[p - 1], add2(up.x, dn.x), al);
-                    ah = fma2(wy[p - 1], add2(up.y, dn.y), ah);
+                    al = fma2(wy[p - 1], fma2(m2, cl, add2(up.x, dn.x)), al);
+                    ah = fma2(wy[p - 1], fma2(m2, ch, add2(up.y, dn.y)), ah);
                 }
                 if (Yp) {
                     const ulonglong2 pv = stP(sz)[tid];
@@ -615,14 +661,11 @@ static int run_f32x4(hub_t h, const StencilArgs& s) {
     d.Yout = s.Yout;
     d.V = reinterpret_cast<const float*>(s.V);
     d.n1 = s.n1; d.n2 = s.n2; d.n3 = s.n3; d.ld = s.ld;
+    fill_coefficients<float>(s, d);
     for (int a = 0; a < 3; ++a) {
-        for (int p = 0; p < 6; ++p) d.w[a][p] = (float)(p < s.n0 ? s.w[a][p] : 0.0);
         d.ph[a][0] = 1.0;
         d.ph[a][1] = 0.0;
     }
-    d.center = (float)s.center;
-    d.alpha = (float)s.alpha;
-    d.beta = (float)s.beta;
     const int tiles = ((s.n1 + Cfg::TXP - 1) / Cfg::TXP) * ((s.n2 + TY - 1) / TY);
     const long want = 4L * h->num_sms;
     const long per = (long)tiles * s.ncol;
@@ -652,14 +695,11 @@ static int run_vec(hub_t h, const StencilArgs& s) {
     d.Yout = s.Yout;
     d.V = reinterpret_cast<const R*>(s.V);
     d.n1 = s.n1; d.n2 = s.n2; d.n3 = s.n3; d.ld = s.ld;
+    fill_coefficients<R>(s, d);
     for (int a = 0; a < 3; ++a) {
-        for (int p = 0; p < 6; ++p) d.w[a][p] = (R)(p < s.n0 ? s.w[a][p] : 0.0);
         d.ph[a][0] = s.phase[a][0];
         d.ph[a][1] = s.phase[a][1];
     }
-    d.center = (R)s.center;
-    d.alpha = (R)s.alpha;
-    d.beta = (R)s.beta;
     const int tiles = ((s.n1 + Cfg::TXP - 1) / Cfg::TXP) * ((s.n2 + TY - 1) / TY);
     const long want = 4L * h->num_sms;
     const long per = (long)tiles * s.ncol;
@@ -689,14 +729,11 @@ static int run_cfg(hub_t h, const StencilArgs& s) {
     d.Yout = s.Yout;
     d.V = reinterpret_cast<const R*>(s.V);
     d.n1 = s.n1; d.n2 = s.n2; d.n3 = s.n3; d.ld = s.ld;
+    fill_coefficients<R>(s, d);
     for (int a = 0; a < 3; ++a) {
-        for (int p = 0; p < 6; ++p) d.w[a][p] = (R)(p < s.n0 ? s.w[a][p] : 0.0);
         d.ph[a][0] = s.phase[a][0];
         d.ph[a][1] = s.phase[a][1];
     }
-    d.center = (R)s.center;
-    d.alpha = (R)s.alpha;
-    d.beta = (R)s.beta;
     const int tiles = ((s.n1 + TX - 1) / TX) * ((s.n2 + TY - 1) / TY);
     // enough CTAs to fill every SM several times, chunks long enough that the prologue of
     // 2*NH+P planes stays a modest overhead
