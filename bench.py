@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hub", choices=["hub", "reference"])
     ap.add_argument("--prec", default="f64", choices=list(PREC))
-    ap.add_argument("--workload", default="rutile", choices=["rutile", "tiny"])
+    ap.add_argument("--workload", default="rutile", choices=["rutile", "tiny", "batched"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--scf-tts", action="store_true",
@@ -320,10 +320,131 @@ def scf_compare(args):
     return 0
 
 
+def run_batched(args):
+    """16 perturbed rutile / anatase snapshots of 24-96 atoms with 1-4 k-points each (complex
+    float orbitals), all filtered (degree 24) in one graph; against the same systems filtered
+    one after another without the graph."""
+    import numpy as np
+    import torch
+    import workloads as w
+    from paper_2507_23612_gb300 import Hub, HUB_F32, batch_filter
+    dev = torch.device("cuda", 0)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1234)
+    snaps = w.snapshot_batch()
+    hubs, Xs, bounds, work = [], [], [], 0.0
+    t0 = time.perf_counter()
+    for sn in snaps:
+        for k, kpt in enumerate(sn.kpts):
+            hb = Hub(sn.n, sn.L, sn.fd_half_order, kpt=kpt, complex_=True, prec=HUB_F32)
+            hb.set_veff(torch.tensor(sn.veff, device=dev))
+            hb.set_atoms(sn.atoms)
+            hb.set_occupation_matrix(0, sn.D0[0])
+            X = torch.randn(sn.ncol, sn.Nd, dtype=torch.complex64, device=dev, generator=gen)
+            v0 = torch.randn(sn.Nd, dtype=torch.complex64, device=dev, generator=gen)
+            lo, up = hb.lanczos_bound(0, 10, v0)
+            hubs.append(hb)
+            Xs.append(X)
+            bounds.append((lo + 0.1 * (up - lo), up, lo))
+            work += sn.Nd * sn.ncol * sn.degree
+    setup_s = time.perf_counter() - t0
+    a = [bb[0] for bb in bounds]
+    b = [bb[1] for bb in bounds]
+    al = [bb[2] for bb in bounds]
+    degree = snaps[0].degree
+    t0 = time.perf_counter()
+    try:
+        batch_filter(hubs, [0] * len(hubs), Xs, degree, a, b, al)    # tune + capture + first run
+    except Exception:
+        free, total = torch.cuda.mem_get_info()
+        print(f"device memory free {free / 1e9:.1f} of {total / 1e9:.1f} GB; torch holds "
+              f"{torch.cuda.memory_allocated() / 1e9:.1f} GB", file=sys.stderr)
+        raise
+    first_s = time.perf_counter() - t0
+    for _ in range(max(1, args.warmup)):
+        batch_filter(hubs, [0] * len(hubs), Xs, degree, a, b, al)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    e0.record(stream)
+    for _ in range(args.steps):
+        batch_filter(hubs, [0] * len(hubs), Xs, degree, a, b, al)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_graph = e0.elapsed_time(e1) / args.steps
+    # the same work, one system after another, no graph
+    e0.record(stream)
+    for hb, X, bb in zip(hubs, Xs, bounds):
+        hb.chefsi_filter(0, X, degree, bb[0], bb[1], bb[2])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    grids = sorted(set(sn.n for sn in snaps), key=lambda n: n[0] * n[1] * n[2])
+    small = batched_small(args, dev, gen)
+    print(json.dumps({
+        "metric": "H·psi throughput, batched filter", "value": work / (ms_graph / 1e3) / 1e9,
+        "unit": "Gpt·orb/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64", "data": "synthetic",
+        "config": {"workload": "16 snapshots (rutile/anatase, 24-96 atoms, N(0,0.1 bohr)), 1-4 k-points, "
+                               "complex float, degree 24", "systems": len(hubs),
+                   "grids_min_max": [list(grids[0]), list(grids[-1])], "step": "one hub_batch_filter call"},
+        "sequential_no_graph": {"ms": ms_seq, "value": work / (ms_seq / 1e3) / 1e9},
+        "graph_speedup": ms_seq / ms_graph, "first_call_s": first_s, "setup_s": setup_s,
+        "stencil_variants": [hb.autotune(0, X) for hb, X in zip(hubs, Xs)][:8],
+        "small_systems": small}))
+    return 0
+
+
+def batched_small(args, dev, gen):
+    """Launch-bound case: 32 Bloch wavevectors of the 24^3 tiny cell (32 complex orbitals
+    each), filtered in one graph and one after another."""
+    import numpy as np
+    import torch
+    import workloads as w
+    from paper_2507_23612_gb300 import Hub, HUB_F32, batch_filter
+    wl = w.tiny()
+    hubs, Xs, a, b, al = [], [], [], [], []
+    for i in range(32):
+        kf = np.array([(i % 4) / 8.0, ((i // 4) % 4) / 8.0, (i // 16) / 8.0]) + 0.01
+        kpt = 2 * np.pi * kf / np.asarray(wl.L)
+        hb = Hub(wl.n, wl.L, wl.fd_half_order, kpt=tuple(kpt), complex_=True, prec=HUB_F32)
+        hb.set_veff(torch.tensor(wl.veff, device=dev))
+        hb.set_atoms(wl.atoms)
+        hb.set_occupation_matrix(0, wl.D0[0])
+        X = torch.randn(wl.ncol, wl.Nd, dtype=torch.complex64, device=dev, generator=gen)
+        v0 = torch.randn(wl.Nd, dtype=torch.complex64, device=dev, generator=gen)
+        lo, up = hb.lanczos_bound(0, 10, v0)
+        hubs.append(hb); Xs.append(X); a.append(lo + 0.1 * (up - lo)); b.append(up); al.append(lo)
+    work = 32 * wl.Nd * wl.ncol * wl.degree
+    batch_filter(hubs, [0] * 32, Xs, wl.degree, a, b, al)
+    batch_filter(hubs, [0] * 32, Xs, wl.degree, a, b, al)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(5):
+        batch_filter(hubs, [0] * 32, Xs, wl.degree, a, b, al)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_g = e0.elapsed_time(e1) / 5
+    e0.record(stream)
+    for hb, X, x1, x2, x3 in zip(hubs, Xs, a, b, al):
+        hb.chefsi_filter(0, X, wl.degree, x1, x2, x3)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1)
+    return {"systems": 32, "grid": list(wl.n), "orbitals": wl.ncol, "degree": wl.degree,
+            "graph_ms": ms_g, "sequential_ms": ms_s, "graph_speedup": ms_s / ms_g,
+            "graph_value": work / (ms_g / 1e3) / 1e9}
+
+
 def main():
     args = parse()
     if args.scf_compare:
         return scf_compare(args)
+    if args.workload == "batched":
+        return run_batched(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -245,6 +245,34 @@ int hub_scf_run(hub_t h, hub_scf_result* res);
 int hub_scf_get(hub_t h, double* eig, double* occ, double* D_out);
 
 /* ---------------------------------------------------------------------------------
+ * Batched filtering and tuning.
+ * --------------------------------------------------------------------------------- */
+
+/* Autotuner: times the candidate stencil tile shapes of this handle's kernel family on the
+ * block X (device, ncol columns, leading dimension ld; X is only read) and, for
+ * HUB_MIXED_BF16 handles, the split-K factor of the tensor-core Gram product; keeps the
+ * fastest for the handle and for every later handle of the same grid shape, precision and
+ * ncol (process-wide cache).  variant_out: NULL or the chosen stencil variant.
+ * Synchronises.  Errors: HUB_EINVAL. */
+int hub_autotune(hub_t h, int spin, const void* X, int ncol, int ld, int* variant_out);
+
+/* Chebyshev filter of nsys independent systems (snapshots, Bloch wavevectors, spins) in
+ * one CUDA graph (CheFSI, Sec. II.B): X_i <- p_m^(i)(H_i) X_i with the bounds
+ * (a[i], b[i], a_low[i]) of system i, each a_low < a < b, on handles sys[i] (distinct,
+ * same device, any grid, precision or k), spin[i], blocks X[i] (device, ncol[i] columns,
+ * leading dimension ld[i]).  The first call for a set of (handle, block) pairs autotunes
+ * every handle (hub_autotune), captures one chain of kernels per system on forked streams
+ * into a graph (the chains run concurrently) and instantiates it; later calls with the same
+ * handles, blocks and degree only copy the new filter coefficients to the device and
+ * replay the graph.  Every kernel reads its recurrence coefficients from a device table, so
+ * new bounds need no new capture.  A graph is rebuilt after a handle reallocates a
+ * workspace or its projector tables.  Work runs on cuda_stream; the call synchronises it.
+ * Errors: HUB_EINVAL, HUB_ENOMEM, HUB_ECUDA. */
+int hub_batch_filter(int nsys, const hub_t* sys, const int* spin, void* const* X,
+                     const int* ncol, const int* ld, int degree, const double* a,
+                     const double* b, const double* a_low, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------------
  * Measurement.  Every kernel launch of a handle is counted; with profiling on, each launch
  * is also bracketed by a pair of CUDA events recorded on the handle's stream (the stream
  * the kernel runs on), so per-kernel device time can be read back without a profiler.

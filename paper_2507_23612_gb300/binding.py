@@ -62,6 +62,8 @@ _SIGS = {
     "hub_scf_get": [_P, _PD, _PD, _PD],
     "hub_version": [C.c_char_p, _I],
     "hub_set_bf16_terms": [_P, _I],
+    "hub_autotune": [_P, _I, _P, _I, _I, _PI],
+    "hub_batch_filter": [_I, C.POINTER(C.c_void_p), _PI, C.POINTER(C.c_void_p), _PI, _PI, _I, _PD, _PD, _PD, _P],
     "hub_profile": [_P, _I],
     "hub_profile_read": [_P, _I, _PD, C.POINTER(C.c_longlong)],
     "hub_launch_count": [_P, C.POINTER(C.c_longlong)],
@@ -70,6 +72,25 @@ _SIGS = {
 KERNEL_KINDS = ["stencil", "gather", "transform", "scatter", "gram", "gram_reduce", "rotate",
                 "cholesky", "tri_inverse", "dgemm", "jacobi", "eig_misc", "occupation",
                 "lanczos", "copy", "table"]
+
+
+def batch_filter(hubs, spins, Xs, degree: int, a, b, a_low, stream=None):
+    """X_i <- p_m(H_i) X_i for every system i in one CUDA graph (hub_batch_filter)."""
+    import torch
+    lib = load_library()
+    n = len(hubs)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    hs = (C.c_void_p * n)(*[hb.h.value for hb in hubs])
+    xs = (C.c_void_p * n)(*[x.data_ptr() for x in Xs])
+    sp = np.ascontiguousarray(spins, dtype=np.int32)
+    nc = np.ascontiguousarray([x.shape[0] for x in Xs], dtype=np.int32)
+    ld = np.ascontiguousarray([x.shape[1] for x in Xs], dtype=np.int32)
+    av, bv, lv = (np.ascontiguousarray(v, dtype=np.float64) for v in (a, b, a_low))
+    rc = lib.hub_batch_filter(n, hs, _iptr(sp), xs, _iptr(nc), _iptr(ld), int(degree), _dptr(av), _dptr(bv),
+                              _dptr(lv), C.c_void_p(st.cuda_stream))
+    if rc != 0:
+        msg = lib.hub_last_error(hubs[0].h)
+        raise HubError(rc, f"hub_batch_filter: {msg.decode() if msg else ''}")
 
 
 def load_library(path: str | None = None) -> C.CDLL:
@@ -235,6 +256,12 @@ class Hub:
         self._check(self.lib.hub_lanczos_bound(self.h, spin, steps, _tptr(v0), C.byref(lo), C.byref(up)),
                     "hub_lanczos_bound")
         return lo.value, up.value
+
+    def autotune(self, spin: int, X) -> int:
+        ncol, ld = X.shape
+        v = C.c_int()
+        self._check(self.lib.hub_autotune(self.h, spin, _tptr(X), ncol, ld, C.byref(v)), "hub_autotune")
+        return v.value
 
     # ------------------------------------------------------------------ measurement
     def profile(self, enable: int):

@@ -19,6 +19,7 @@ int fail(hub_t h, int code, const std::string& msg) {
 
 int ensure(hub_t h, void** p, size_t* have, size_t need) {
     if (*have >= need && *p) return HUB_OK;
+    h->mem_gen++;
     if (*p) {
         cudaStreamSynchronize(h->stream);
         cudaFree(*p);
@@ -65,7 +66,7 @@ static void fd_weights(int n0, double* c0, double* c) {
 }
 
 int apply_H_internal(hub_t h, int spin, const void* X, int ld, void* Y, int ncol, double alpha,
-                     double shift, const void* Yprev, double beta) {
+                     double shift, const void* Yprev, double beta, const double* coef_dev) {
     int rc;
     if (h->proj.nsites > 0)
         if ((rc = launch_gather(h, X, ncol, ld, spin, true))) return rc;
@@ -82,16 +83,20 @@ int apply_H_internal(hub_t h, int spin, const void* X, int ld, void* Y, int ncol
     for (int ax = 0; ax < 3; ++ax) {
         const double ih2 = 1.0 / (h->h[ax] * h->h[ax]);
         inv2 += ih2;
-        for (int p = 0; p < h->n0; ++p) a.w[ax][p] = alpha * (-0.5) * c[p] * ih2;
+        for (int p = 0; p < h->n0; ++p) {
+            a.w[ax][p] = alpha * (-0.5) * c[p] * ih2;
+            a.wbase[ax][p] = (-0.5) * c[p] * ih2;
+        }
         a.phase[ax][0] = std::cos(h->kpt[ax] * h->L[ax]);
         a.phase[ax][1] = std::sin(h->kpt[ax] * h->L[ax]);
     }
     a.center = alpha * (-0.5 * c0 * inv2 - shift);
     a.alpha = alpha;
     a.beta = beta;
+    a.coef = coef_dev;
     if ((rc = launch_stencil(h, a))) return rc;
     if (h->proj.nsites > 0)
-        if ((rc = launch_scatter(h, Y, ncol, ld, alpha))) return rc;
+        if ((rc = launch_scatter(h, Y, ncol, ld, alpha, coef_dev))) return rc;
     return HUB_OK;
 }
 

@@ -399,7 +399,7 @@ int launch_gram_bf16(hub_t h, const void* A, int lda, const void* B, int ldb, in
     const int mtiles = (m + TM - 1) / TM, ntiles = (n + TN - 1) / TN;
     const int kchunks = (int)((Nd + TKC - 1) / TKC);
     const int tiles = mtiles * ntiles;
-    int splits = std::max(1, (2 * h->num_sms + tiles - 1) / tiles);
+    int splits = std::max(1, (h->gemm_split * h->num_sms + tiles - 1) / tiles);
     int per_split = (kchunks + splits - 1) / splits;
     splits = (kchunks + per_split - 1) / per_split;
     if ((rc = ensure(h, &h->d_gpart, &h->gpart_bytes, std::max(h->gpart_bytes, (size_t)splits * m * n * sizeof(float)))))

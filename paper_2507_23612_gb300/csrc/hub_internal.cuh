@@ -92,6 +92,10 @@ struct hub_ctx {
     int prec = HUB_F64;
     int esize = 8;                // bytes per real component of the working type
     int bf16_terms = 3;           // HUB_MIXED_BF16: 1 = bf16 x bf16, 3 = hi/lo split products
+    int stencil_variant = 0;      // tile shape chosen by the autotuner (stencil_variants)
+    int gemm_split = 2;           // tensor-core split-K: CTAs per SM of the Gram products
+    int capturing = 0;            // work is being captured into a CUDA graph
+    long long mem_gen = 0;        // bumped whenever a workspace or table is reallocated
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 0;
@@ -139,7 +143,7 @@ struct ProfScope {
     cudaEvent_t a = nullptr;
     ProfScope(hub_t h_, int k) : h(h_), kind(k) {
         h->launches++;
-        if (h->prof_on && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, h->stream);
+        if (h->prof_on && !h->capturing && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, h->stream);
     }
     ~ProfScope() {
         if (!a) return;
@@ -169,8 +173,11 @@ struct StencilArgs {
     double beta;
     int n0;
     double phase[3][2];     // exp(i k_a L_a) (re, im), complex only
+    const double* coef;     // device {alpha, beta, shift} or nullptr (then w/center/alpha/beta)
+    double wbase[3][kMaxHalf];  // (-1/2) c_p / h_a^2 (alpha = 1)
 };
 int launch_stencil(hub_t h, const StencilArgs& a);
+int stencil_variants(hub_t h);
 
 // projectors.cu
 int build_tables(hub_t h, int natoms, const double* pos, const int* kb_nchan, const int* kb_l,
@@ -181,8 +188,9 @@ void free_table(Table& t);
 // C[P x ncol] (double, x2 complex) = dV * <proj_p|x_n>; with want_W also W = transform(C)
 // in the working type (gamma .* C for KB rows, M_spin C for Hubbard rows).
 int launch_gather(hub_t h, const void* X, int ncol, int ld, int spin, bool want_W);
-// Y[g, n] += alpha * sum_e vals_e . W[rows_e, n]   (W from the last launch_gather)
-int launch_scatter(hub_t h, void* Y, int ncol, int ld, double alpha);
+// Y[g, n] += alpha * sum_e vals_e . W[rows_e, n]   (W from the last launch_gather); with
+// alpha_dev != nullptr alpha is read on the device
+int launch_scatter(hub_t h, void* Y, int ncol, int ld, double alpha, const double* alpha_dev = nullptr);
 // D per Hubbard atom (double, [nhub*50] re/im pairs) and E_U into d_scal[0] from the C of
 // the last launch_gather; f_dev [ncol] double.
 int launch_occupation(hub_t h, int ncol, const double* f_dev, double kweight, double* D_dev);
@@ -219,6 +227,6 @@ int launch_copy_block(hub_t h, const void* src, int lds, void* dst, int ldd, int
 // api: apply_H with explicit buffers (used by filter / RR / Lanczos)
 // Y = alpha (H X - shift X) + beta Yprev  (Yprev may alias Y; X, Y, Yprev share ld)
 int apply_H_internal(hub_t h, int spin, const void* X, int ld, void* Y, int ncol, double alpha,
-                     double shift, const void* Yprev, double beta);
+                     double shift, const void* Yprev, double beta, const double* coef_dev = nullptr);
 
 }  // namespace hub

@@ -257,8 +257,10 @@ __global__ void __launch_bounds__(256)
 k_scatter(typename VT<R, CPLX>::T* __restrict__ Y, int ld, int ncol, long Nd,
           const int* __restrict__ csr_off, const int2* __restrict__ csr_ent,
           const typename VT<R, CPLX>::T* __restrict__ vals,
-          const typename VT<R, CPLX>::T* __restrict__ W, R alpha, int vec_ok) {
+          const typename VT<R, CPLX>::T* __restrict__ W, R alpha, int vec_ok,
+          const double* __restrict__ alpha_dev) {
     using T = typename VT<R, CPLX>::T;
+    if (alpha_dev) alpha = (R)alpha_dev[0];
     constexpr int NC = 32 / sizeof(T);
     constexpr int PER16 = 16 / sizeof(T);
     const long g = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -588,6 +590,7 @@ int build_tables(hub_t h, int natoms, const double* pos, const int* kb_nchan, co
     HUB_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     free_table(h->proj);
     h->proj = std::move(t);
+    h->mem_gen++;
     return HUB_OK;
 }
 
@@ -624,7 +627,7 @@ int launch_gather(hub_t h, const void* X, int ncol, int ld, int spin, bool want_
 }
 
 template <typename R, bool CPLX>
-static int scatter_t(hub_t h, void* Y, int ncol, int ld, double alpha) {
+static int scatter_t(hub_t h, void* Y, int ncol, int ld, double alpha, const double* alpha_dev) {
     using T = typename VT<R, CPLX>::T;
     constexpr int NC = 32 / sizeof(T);
     Table& t = h->proj;
@@ -632,17 +635,18 @@ static int scatter_t(hub_t h, void* Y, int ncol, int ld, double alpha) {
     dim3 grid((unsigned)((h->Nd + 255) / 256), (ncol + NC - 1) / NC);
     ProfScope ps(h, HUB_K_SCATTER);
     k_scatter<R, CPLX><<<grid, 256, 0, h->stream>>>((T*)Y, ld, ncol, h->Nd, t.d_csr_off, t.d_csr_ent,
-                                                    (const T*)t.d_vals, (const T*)h->d_W, (R)alpha, vec_ok);
+                                                    (const T*)t.d_vals, (const T*)h->d_W, (R)alpha, vec_ok,
+                                                    alpha_dev);
     HUB_CUDA_TRY(h, cudaGetLastError());
     return HUB_OK;
 }
 
-int launch_scatter(hub_t h, void* Y, int ncol, int ld, double alpha) {
+int launch_scatter(hub_t h, void* Y, int ncol, int ld, double alpha, const double* alpha_dev) {
     if (ncol == 0 || h->proj.nsites == 0) return HUB_OK;
-    if (h->esize == 8) return h->cplx ? scatter_t<double, true>(h, Y, ncol, ld, alpha)
-                                      : scatter_t<double, false>(h, Y, ncol, ld, alpha);
-    return h->cplx ? scatter_t<float, true>(h, Y, ncol, ld, alpha)
-                   : scatter_t<float, false>(h, Y, ncol, ld, alpha);
+    if (h->esize == 8) return h->cplx ? scatter_t<double, true>(h, Y, ncol, ld, alpha, alpha_dev)
+                                      : scatter_t<double, false>(h, Y, ncol, ld, alpha, alpha_dev);
+    return h->cplx ? scatter_t<float, true>(h, Y, ncol, ld, alpha, alpha_dev)
+                   : scatter_t<float, false>(h, Y, ncol, ld, alpha, alpha_dev);
 }
 
 int launch_occupation(hub_t h, int ncol, const double* f_dev, double kweight, double* D_dev) {

@@ -31,7 +31,43 @@ struct StencilDev {
     R center, alpha, beta;    // float: centre without the kinetic part (difference form)
     double ph[3][2];
     int zchunk, nzc;
+    // batched / graph form: when coef != nullptr the recurrence coefficients are read on the
+    // device, coef = {alpha, beta, shift}, and w = alpha * wbase, centre = alpha * (cen_kin -
+    // shift) (double) or alpha * (-shift) (float)
+    const double* coef;
+    R wbase[3][6];
+    double cen_kin;
 };
+
+template <typename R>
+struct Coef {
+    R w[3][6];
+    R center, alpha, beta;
+};
+
+template <typename R>
+__device__ __forceinline__ Coef<R> resolve_coef(const StencilDev<R>& a) {
+    Coef<R> c;
+    if (a.coef) {
+        const double al = a.coef[0], be = a.coef[1], sh = a.coef[2];
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax)
+#pragma unroll
+            for (int p = 0; p < 6; ++p) c.w[ax][p] = (R)(al * (double)a.wbase[ax][p]);
+        c.center = (R)(sizeof(R) == 4 ? al * (-sh) : al * (a.cen_kin - sh));
+        c.alpha = (R)al;
+        c.beta = (R)be;
+    } else {
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax)
+#pragma unroll
+            for (int p = 0; p < 6; ++p) c.w[ax][p] = a.w[ax][p];
+        c.center = a.center;
+        c.alpha = a.alpha;
+        c.beta = a.beta;
+    }
+    return c;
+}
 
 // Rounded weights and the centre coefficient.  Double uses the summation form
 //   c f0 + sum_p w_p (f+p + f-p),   c = alpha(-1/2 c0 sum h^-2 - shift).
@@ -54,6 +90,15 @@ static void fill_coefficients(const StencilArgs& s, StencilDev<R>& d) {
     d.center = sizeof(R) == 4 ? (R)(s.center + 2.0 * wsum) : (R)s.center;
     d.alpha = (R)s.alpha;
     d.beta = (R)s.beta;
+    d.coef = s.coef;
+    double wb = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int p = 0; p < 6; ++p) {
+            const double w = p < s.n0 ? s.wbase[a][p] : 0.0;
+            d.wbase[a][p] = (R)w;
+            wb += w;
+        }
+    d.cen_kin = -2.0 * wb;
 }
 
 __device__ __forceinline__ int floordiv(int a, int n) {
@@ -93,6 +138,7 @@ struct StencilCfg {
 template <typename R, bool CPLX, int TX, int TY, int P>
 __global__ void __launch_bounds__(TX * TY)
 k_stencil(StencilDev<R> a) {
+    const Coef<R> cf = resolve_coef(a);
     using C = StencilCfg<R, CPLX, TX, TY, P>;
     using T = typename C::T;
     constexpr int NH = C::NH, SX = C::SX, S = C::S, NT = C::NT, PER = C::PER;
@@ -195,7 +241,7 @@ k_stencil(StencilDev<R> a) {
     for (int z = z0; z < z1; ++z) {
         if (active) {
             const T* ys = stage_Y(z);
-            T acc = mulr(a.center + a.alpha * stage_V(z)[tid], q[NH]);
+            T acc = mulr(cf.center + cf.alpha * stage_V(z)[tid], q[NH]);
             const T c0 = q[NH];
 #pragma unroll
             for (int p = 1; p <= NH; ++p) {
@@ -207,11 +253,11 @@ k_stencil(StencilDev<R> a) {
                     sx = fmar((R)-2, c0, sx);
                     sy = fmar((R)-2, c0, sy);
                 }
-                acc = fmar(a.w[2][p - 1], sz, acc);
-                acc = fmar(a.w[0][p - 1], sx, acc);
-                acc = fmar(a.w[1][p - 1], sy, acc);
+                acc = fmar(cf.w[2][p - 1], sz, acc);
+                acc = fmar(cf.w[0][p - 1], sx, acc);
+                acc = fmar(cf.w[1][p - 1], sy, acc);
             }
-            if (Yp) acc = fmar(a.beta, stage_P(z)[tid], acc);
+            if (Yp) acc = fmar(cf.beta, stage_P(z)[tid], acc);
             Yo[(long)z * plane + own] = acc;
         }
         if (z + 1 == z1) break;
@@ -266,6 +312,7 @@ struct VecCfg {
 template <typename R, bool CPLX, int VEC, int TXT, int TY, int P>
 __global__ void __launch_bounds__(TXT * TY)
 k_stencil_vec(StencilDev<R> a) {
+    const Coef<R> cf = resolve_coef(a);
     using C = VecCfg<R, CPLX, VEC, TXT, TY, P>;
     static_assert(sizeof(typename C::V) == 16, "Y vectors are 16-byte copies");
     static_assert(sizeof(typename C::VR) == sizeof(R) * VEC, "potential vectors are unpadded");
@@ -407,7 +454,7 @@ k_stencil_vec(StencilDev<R> a) {
             V out;
 #pragma unroll
             for (int e = 0; e < VEC; ++e) {
-                T acc = mulr(a.center + a.alpha * vv.v[e], q[NH].v[e]);
+                T acc = mulr(cf.center + cf.alpha * vv.v[e], q[NH].v[e]);
                 const T c0 = q[NH].v[e];
 #pragma unroll
                 for (int p = 1; p <= NH; ++p) {
@@ -417,8 +464,8 @@ k_stencil_vec(StencilDev<R> a) {
                         sz = fmar((R)-2, c0, sz);
                         sx = fmar((R)-2, c0, sx);
                     }
-                    acc = fmar(a.w[2][p - 1], sz, acc);
-                    acc = fmar(a.w[0][p - 1], sx, acc);
+                    acc = fmar(cf.w[2][p - 1], sz, acc);
+                    acc = fmar(cf.w[0][p - 1], sx, acc);
                 }
                 out.v[e] = acc;
             }
@@ -430,12 +477,12 @@ k_stencil_vec(StencilDev<R> a) {
                 for (int e = 0; e < VEC; ++e) {
                     T sy = add(up.v[e], dn.v[e]);
                     if constexpr (sizeof(R) == 4) sy = fmar((R)-2, q[NH].v[e], sy);
-                    out.v[e] = fmar(a.w[1][p - 1], sy, out.v[e]);
+                    out.v[e] = fmar(cf.w[1][p - 1], sy, out.v[e]);
                 }
             }
             if (Yp) {
 #pragma unroll
-                for (int e = 0; e < VEC; ++e) out.v[e] = fmar(a.beta, pv.v[e], out.v[e]);
+                for (int e = 0; e < VEC; ++e) out.v[e] = fmar(cf.beta, pv.v[e], out.v[e]);
             }
             *reinterpret_cast<V*>(Yo + (long)z * plane + own) = out;
         }
@@ -497,6 +544,7 @@ __device__ __forceinline__ u64 mul2(u64 a, u64 b) {
 template <int TXT, int TY, int P>
 __global__ void __launch_bounds__(TXT * TY)
 k_stencil_f32x4(StencilDev<float> a) {
+    const Coef<float> cf = resolve_coef(a);
     using C = VecCfg<float, false, 4, TXT, TY, P>;
     constexpr int NH = C::NH, HX = C::HX, SXV = C::SXV, S = C::S, NT = C::NT, PER = C::PER;
     constexpr int Q = 2 * NH + 1;
@@ -554,11 +602,11 @@ k_stencil_f32x4(StencilDev<float> a) {
     u64 wx[NH], wy[NH], wz[NH];
 #pragma unroll
     for (int p = 0; p < NH; ++p) {
-        wx[p] = pk2(a.w[0][p], a.w[0][p]);
-        wy[p] = pk2(a.w[1][p], a.w[1][p]);
-        wz[p] = pk2(a.w[2][p], a.w[2][p]);
+        wx[p] = pk2(cf.w[0][p], cf.w[0][p]);
+        wy[p] = pk2(cf.w[1][p], cf.w[1][p]);
+        wz[p] = pk2(cf.w[2][p], cf.w[2][p]);
     }
-    const u64 cen2 = pk2(a.center, a.center), alp2 = pk2(a.alpha, a.alpha), bet2 = pk2(a.beta, a.beta);
+    const u64 cen2 = pk2(cf.center, cf.center), alp2 = pk2(cf.alpha, cf.alpha), bet2 = pk2(cf.beta, cf.beta);
     const u64 m2 = pk2(-2.0f, -2.0f);
 
     const int last_needed = z1 + NH - 1;
@@ -756,6 +804,13 @@ static int run_cfg(hub_t h, const StencilArgs& s) {
     return HUB_OK;
 }
 
+// Tile shapes the autotuner chooses from, per kernel family (index 0 is the default).
+int stencil_variants(hub_t h) {
+    const int es = h->esize * (h->cplx ? 2 : 1);
+    if (h->esize == 4) return 4;          // float real (packed) and float complex (vector)
+    return es == 16 ? 2 : 3;              // double complex / double real (scalar pipeline)
+}
+
 int launch_stencil(hub_t h, const StencilArgs& a) {
     if (a.ncol == 0) return HUB_OK;
     const int es = h->esize * (h->cplx ? 2 : 1);
@@ -763,13 +818,33 @@ int launch_stencil(hub_t h, const StencilArgs& a) {
     const bool aligned = (a.n1 % vec == 0) && (a.ld % vec == 0) &&
                          ((uintptr_t)a.Y % 16 == 0) && ((uintptr_t)a.Yout % 16 == 0) &&
                          (!a.Yprev || (uintptr_t)a.Yprev % 16 == 0) && ((uintptr_t)a.V % 16 == 0);
+    const int v = h->stencil_variant;
     if (aligned && h->esize == 4) {
         // float streams from HBM: vector copies, packed pair arithmetic for real data
-        return h->cplx ? run_vec<float, true, 2, 16, 16, 2>(h, a) : run_f32x4<8, 16, 4>(h, a);
+        if (!h->cplx) {
+            switch (v) {
+                case 1: return run_f32x4<8, 8, 4>(h, a);
+                case 2: return run_f32x4<16, 8, 2>(h, a);
+                case 3: return run_f32x4<8, 16, 2>(h, a);
+                default: return run_f32x4<8, 16, 4>(h, a);
+            }
+        }
+        switch (v) {
+            case 1: return run_vec<float, true, 2, 16, 8, 2>(h, a);
+            case 2: return run_vec<float, true, 2, 8, 16, 2>(h, a);
+            case 3: return run_vec<float, true, 2, 8, 8, 4>(h, a);
+            default: return run_vec<float, true, 2, 16, 16, 2>(h, a);
+        }
     }
-    // FP64 is bound by the FP64 pipe: a short ring keeps two CTAs per SM; float streams from
-    // HBM: a deeper ring keeps more bytes in flight
-    if (h->esize == 8) return h->cplx ? run_cfg<double, true, 32, 8, 2>(h, a) : run_cfg<double, false, 32, 8, 2>(h, a);
+    // FP64 is bound by the FP64 pipe: a short ring keeps two CTAs per SM
+    if (h->esize == 8) {
+        if (h->cplx) return v == 1 ? run_cfg<double, true, 32, 4, 2>(h, a) : run_cfg<double, true, 32, 8, 2>(h, a);
+        switch (v) {
+            case 1: return run_cfg<double, false, 32, 4, 4>(h, a);
+            case 2: return run_cfg<double, false, 64, 4, 2>(h, a);
+            default: return run_cfg<double, false, 32, 8, 2>(h, a);
+        }
+    }
     return h->cplx ? run_cfg<float, true, 32, 8, 2>(h, a) : run_cfg<float, false, 32, 8, 4>(h, a);
 }
 
