@@ -45,7 +45,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hub", choices=["hub", "reference"])
     ap.add_argument("--prec", default="f64", choices=list(PREC))
-    ap.add_argument("--workload", default="rutile", choices=["rutile", "tiny", "batched"])
+    ap.add_argument("--workload", default="rutile", choices=["rutile", "tiny", "batched", "warm"])
+    ap.add_argument("--warm-train", type=int, default=8,
+                    help="warm workload: SCF solutions of displaced 2x2x3 cells to train on")
+    ap.add_argument("--warm-f64-iters", type=int, default=2,
+                    help="warm workload: FP64 iterations timed for the extrapolated cold FP64 time")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--scf-tts", action="store_true",
@@ -320,6 +324,101 @@ def scf_compare(args):
     return 0
 
 
+def run_warm(args):
+    """Warm-started SCF of the 3x3x4 rutile-shaped supercell (216 atoms, 72 Ti, 132x132x112
+    grid, 1044 orbitals per spin, two spins).  The occupation model (descriptors -> 3x256 SiLU
+    MLP with FP16 weights -> 15 D entries per spin) is trained on SCF solutions of displaced
+    2x2x3 cells computed by the library in mixed precision; the 216-atom cell is then solved
+    cold (atomic-guess D) and warm (predicted D), both in the mixed form with the precision
+    ladder, and its cold FP64 time is extrapolated from timed FP64 iterations."""
+    import numpy as np
+    import torch
+    import workloads as w
+    from paper_2507_23612_gb300 import HUB_F64, HUB_MIXED_BF16, Hub, scf_params
+    from paper_2507_23612_gb300.warmstart import OccupationModel, scf_solve
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    model = OccupationModel(nspin=2, seed=0)
+    gen = []
+    for i in range(args.warm_train):
+        wl = w.rutile_snapshot((2, 2, 3), 0.1, seed=i)
+        r = scf_solve(wl, HUB_MIXED_BF16)
+        model.add_solution(wl.atoms, wl.L, r["D"])
+        gen.append((r["iterations"], r["seconds"]))
+    t_gen = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    losses = model.fit(steps=2000)
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t1
+
+    big = w.rutile_snapshot((3, 3, 4), 0.1, seed=1000)
+    nat = len(big.atoms)
+    t2 = time.perf_counter()
+    D_pred = model.predict(big.atoms, big.L)
+    t_pred = time.perf_counter() - t2
+    cold = scf_solve(big, HUB_MIXED_BF16)
+    torch.cuda.empty_cache()
+    warm = scf_solve(big, HUB_MIXED_BF16, D0=D_pred)
+    torch.cuda.empty_cache()
+
+    # cold FP64: the first iteration (first passes) and the following ones timed, then
+    # extrapolated with the cold mixed run's iteration count
+    f64 = None
+    if args.warm_f64_iters > 0:
+        hub = Hub(big.n, big.L, big.fd_half_order, prec=HUB_F64)
+        hub.set_veff(torch.tensor(big.veff, device=dev))
+        hub.set_atoms(big.atoms)
+        Xs = [torch.tensor(big.orbitals(s), device=dev).contiguous() for s in range(big.nspin)]
+        v0s = [torch.tensor(big.lanczos_start(s), device=dev).contiguous() for s in range(big.nspin)]
+        p = scf_params(nspin=2, ncol=big.ncol, ld=big.Nd, degree=big.degree, max_iter=200, first_passes=3,
+                       lanczos_steps=10, pulay_history=7, natoms=nat, pulay_beta=0.3, kT=big.kT,
+                       n_elec=big.n_elec, tol_e_atom=1e-5, tol_D=1e-4)
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        hub.scf_begin(p, Xs, v0s, big.D0)
+        times = []
+        for _ in range(args.warm_f64_iters):
+            hub.scf_iterate()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - ts)
+            ts = time.perf_counter()
+        hub.close()
+        del Xs, v0s
+        torch.cuda.empty_cache()
+        later = float(np.mean(times[1:])) if len(times) > 1 else times[0] / 3
+        est = times[0] + (cold["iterations"] - 1) * later
+        f64 = {"first_iteration_s": round(times[0], 3), "later_iteration_s": round(later, 3),
+               "time_to_solution_s_extrapolated": round(est, 2),
+               "extrapolation": "first FP64 iteration + (cold mixed iteration count - 1) x timed later FP64 iteration"}
+    err0 = float(np.max(np.abs(big.D0 - cold["D"])))
+    errp = float(np.max(np.abs(D_pred - cold["D"])))
+    line = {
+        "metric": "SCF time to solution at 1e-5 Ha/atom (warm start)",
+        "value": round(warm["seconds"], 3), "unit": "s", "higher_is_better": False, "n_gpus": 1,
+        "dtype": "f32+bf16 (FP64 dense steps)", "data": "synthetic",
+        "config": {"workload": big.name, "grid": list(big.n), "orbitals_per_spin": big.ncol, "spins": 2,
+                   "atoms": nat, "hubbard_atoms": D_pred.shape[1], "chebyshev_degree": big.degree,
+                   "criterion": "|dE|/atom < 1e-5 Ha twice and max|dD| < 1e-4",
+                   "model": "descriptors(48) -> 3x256 SiLU -> 30, FP16 weights, FP32 accumulate"},
+        "training": {"scf_solutions": args.warm_train, "cells": "displaced 2x2x3 rutile (72 atoms, 24 Ti), mixed",
+                     "samples": model.n_samples, "generation_s": round(t_gen, 2),
+                     "scf_iterations": [g[0] for g in gen], "fit_s": round(t_fit, 3), "adam_steps": 2000,
+                     "loss_first_last": [losses[0], losses[-1]], "predict_s": round(t_pred, 4)},
+        "cold_mixed": {"iterations": cold["iterations"], "seconds": round(cold["seconds"], 3),
+                       "E_Ha": cold["E"], "converged": cold["converged"]},
+        "warm_mixed": {"iterations": warm["iterations"], "seconds": round(warm["seconds"], 3),
+                       "E_Ha": warm["E"], "converged": warm["converged"]},
+        "fixed_point": {"dE_Ha_per_atom": abs(warm["E"] - cold["E"]) / nat,
+                        "max_abs_dD": float(np.max(np.abs(warm["D"] - cold["D"])))},
+        "initial_D_error": {"atomic_guess": err0, "model": errp},
+        "cold_f64": f64,
+    }
+    if f64:
+        line["speedup_warm_mixed_vs_cold_f64"] = round(f64["time_to_solution_s_extrapolated"] / warm["seconds"], 2)
+    print(json.dumps(line))
+    return 0
+
+
 def run_batched(args):
     """16 perturbed rutile / anatase snapshots of 24-96 atoms with 1-4 k-points each (complex
     float orbitals), all filtered (degree 24) in one graph; against the same systems filtered
@@ -445,6 +544,8 @@ def main():
         return scf_compare(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "warm":
+        return run_warm(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

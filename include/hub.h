@@ -273,6 +273,49 @@ int hub_batch_filter(int nsys, const hub_t* sys, const int* spin, void* const* X
                      const double* b, const double* a_low, void* cuda_stream);
 
 /* ---------------------------------------------------------------------------------
+ * Warm start.  The paper has no learned component; this model only proposes the starting
+ * occupation matrices D of an SCF (Sec. II.B starts from a diagonal D), and the SCF still
+ * converges to its own fixed point.  Descriptors of a Hubbard atom (per neighbour species,
+ * over periodic images within rc, cosine cutoff fc(r) = (cos(pi r/rc) + 1)/2):
+ *   nrad radial Gaussians exp(-(r - mu_k)^2/(2 eta^2)) fc(r), mu_k = linspace(0.5, rc-0.5),
+ *   then the sums of Y_1m(r/|r|) fc(r) (m = -1..1) and Y_2m(r/|r|) fc(r) (m = -2..2).
+ * Model: n_in -> n_layers hidden layers of n_hidden (SiLU) -> n_out, with input and output
+ * standardisation; FP32 master weights, an FP16 weight copy for the products when
+ * weight_fp16, FP32 accumulation; loss = mean of ((y - t)/sd_out)^2; Adam (0.9, 0.999,
+ * 1e-8).  Parameters are flat: for every layer W (out x in, row-major) then b (out).
+ * All X / T / Y arrays are device float, row-major [batch x features].
+ * --------------------------------------------------------------------------------- */
+typedef struct hub_mlp_ctx* hub_mlp_t;
+
+/* Descriptors of the centre atoms (host pos [natoms*3] bohr, species [natoms] in
+ * 0..nspecies-1 (nspecies <= 2), L [3] orthogonal cell, centers [ncenter]) into out_dev
+ * [ncenter x nspecies*(nrad+8)] float.  nrad <= 32.  Synchronises cuda_stream. */
+int hub_descriptors(int natoms, const double* pos, const int* species, const double* L, int ncenter,
+                    const int* centers, int nspecies, double rc, int nrad, double eta, float* out_dev,
+                    void* cuda_stream);
+/* Model with seeded initialisation U(-1/sqrt(in), 1/sqrt(in)) (SplitMix64 of seed + index). */
+int hub_mlp_create(hub_mlp_t* out, int n_in, int n_hidden, int n_layers, int n_out, int weight_fp16,
+                   unsigned long long seed, void* cuda_stream);
+int hub_mlp_destroy(hub_mlp_t m);
+const char* hub_mlp_last_error(hub_mlp_t m);
+int hub_mlp_num_params(hub_mlp_t m, long long* n);
+/* Host float [n_params] in / out; set also resets the Adam state. */
+int hub_mlp_set_params(hub_mlp_t m, const float* host);
+int hub_mlp_get_params(hub_mlp_t m, float* host);
+/* Standardisation from host arrays, or fitted on the device to the columns of X and T. */
+int hub_mlp_set_normalization(hub_mlp_t m, const float* mu_in, const float* sd_in,
+                              const float* mu_out, const float* sd_out);
+int hub_mlp_fit_normalization(hub_mlp_t m, const float* X_dev, const float* T_dev, int batch);
+/* Y = model(X). */
+int hub_mlp_forward(hub_mlp_t m, const float* X_dev, int batch, float* Y_dev);
+/* Loss and gradient (host float [n_params], NULL to skip) of the batch.  Synchronises. */
+int hub_mlp_loss_grad(hub_mlp_t m, const float* X_dev, const float* T_dev, int batch, float* loss_host,
+                      float* grad_host);
+/* One Adam step on the batch; loss_host NULL or the loss before the step (synchronises). */
+int hub_mlp_train_step(hub_mlp_t m, const float* X_dev, const float* T_dev, int batch, float lr,
+                       float* loss_host);
+
+/* ---------------------------------------------------------------------------------
  * Measurement.  Every kernel launch of a handle is counted; with profiling on, each launch
  * is also bracketed by a pair of CUDA events recorded on the handle's stream (the stream
  * the kernel runs on), so per-kernel device time can be read back without a profiler.

@@ -9,5 +9,5 @@ binding's entry points raises.
 """
 from .binding import (  # noqa: F401
     HubError, Hub, load_library, library_path, HUB_F64, HUB_F32, HUB_MIXED_BF16, KERNEL_KINDS,
-    scf_params, STATUS_NAMES, batch_filter,
+    scf_params, STATUS_NAMES, batch_filter, MLP, descriptors,
 )

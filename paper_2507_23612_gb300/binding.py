@@ -64,6 +64,18 @@ _SIGS = {
     "hub_set_bf16_terms": [_P, _I],
     "hub_autotune": [_P, _I, _P, _I, _I, _PI],
     "hub_batch_filter": [_I, C.POINTER(C.c_void_p), _PI, C.POINTER(C.c_void_p), _PI, _PI, _I, _PD, _PD, _PD, _P],
+    "hub_descriptors": [_I, _PD, _PI, _PD, _I, _PI, _I, _D, _I, _D, _P, _P],
+    "hub_mlp_create": [C.POINTER(C.c_void_p), _I, _I, _I, _I, _I, C.c_ulonglong, _P],
+    "hub_mlp_destroy": [_P],
+    "hub_mlp_last_error": [_P],
+    "hub_mlp_num_params": [_P, C.POINTER(C.c_longlong)],
+    "hub_mlp_set_params": [_P, C.POINTER(C.c_float)],
+    "hub_mlp_get_params": [_P, C.POINTER(C.c_float)],
+    "hub_mlp_set_normalization": [_P, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_float)],
+    "hub_mlp_fit_normalization": [_P, _P, _P, _I],
+    "hub_mlp_forward": [_P, _P, _I, _P],
+    "hub_mlp_loss_grad": [_P, _P, _P, _I, C.POINTER(C.c_float), C.POINTER(C.c_float)],
+    "hub_mlp_train_step": [_P, _P, _P, _I, C.c_float, C.POINTER(C.c_float)],
     "hub_profile": [_P, _I],
     "hub_profile_read": [_P, _I, _PD, C.POINTER(C.c_longlong)],
     "hub_launch_count": [_P, C.POINTER(C.c_longlong)],
@@ -106,7 +118,7 @@ def load_library(path: str | None = None) -> C.CDLL:
     for name, args in _SIGS.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = C.c_char_p if name == "hub_last_error" else C.c_int
+        fn.restype = C.c_char_p if name in ("hub_last_error", "hub_mlp_last_error") else C.c_int
     if path is None:
         _LIB = lib
     return lib
@@ -313,3 +325,86 @@ class Hub:
         self._check(self.lib.hub_scf_get(self.h, _dptr(eig), _dptr(occ), _dptr(D)), "hub_scf_get")
         return (eig.reshape(p.nspin, p.ncol), occ.reshape(p.nspin, p.ncol),
                 D[:p.nspin * self.nhub * 25].reshape(p.nspin, self.nhub, 5, 5))
+
+
+def descriptors(pos, species, L, centers, out, nspecies=2, rc=6.0, nrad=16, eta=0.4, stream=None):
+    """Per-atom local-environment descriptors into the device float tensor `out`."""
+    import torch
+    lib = load_library()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1)
+    sp = np.ascontiguousarray(species, dtype=np.int32)
+    Lv = np.ascontiguousarray(L, dtype=np.float64)
+    ce = np.ascontiguousarray(centers, dtype=np.int32)
+    rc_ = lib.hub_descriptors(len(sp), _dptr(pos), _iptr(sp), _dptr(Lv), len(ce), _iptr(ce), nspecies,
+                              float(rc), nrad, float(eta), _tptr(out), C.c_void_p(st.cuda_stream))
+    if rc_ != 0:
+        raise HubError(rc_, "hub_descriptors")
+
+
+class MLP:
+    """Warm-start model handle (hub_mlp_*)."""
+
+    def __init__(self, n_in, n_hidden=256, n_layers=3, n_out=30, fp16=True, seed=0, stream=None):
+        import torch
+        self.lib = load_library()
+        st = stream if stream is not None else torch.cuda.current_stream()
+        m = C.c_void_p()
+        rc = self.lib.hub_mlp_create(C.byref(m), n_in, n_hidden, n_layers, n_out, int(fp16), seed,
+                                     C.c_void_p(st.cuda_stream))
+        if rc != 0:
+            raise HubError(rc, "hub_mlp_create")
+        self.m = m
+        n = C.c_longlong()
+        self.lib.hub_mlp_num_params(self.m, C.byref(n))
+        self.nparams = n.value
+        self.sizes = [n_in] + [n_hidden] * n_layers + [n_out]
+
+    def _check(self, rc, what):
+        if rc != 0:
+            msg = self.lib.hub_mlp_last_error(self.m)
+            raise HubError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "m", None):
+            self.lib.hub_mlp_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        self._check(self.lib.hub_mlp_set_params(self.m, a.ctypes.data_as(C.POINTER(C.c_float))), "set_params")
+
+    def get_params(self):
+        a = np.zeros(self.nparams, dtype=np.float32)
+        self._check(self.lib.hub_mlp_get_params(self.m, a.ctypes.data_as(C.POINTER(C.c_float))), "get_params")
+        return a
+
+    def set_normalization(self, mu_in, sd_in, mu_out, sd_out):
+        arrs = [np.ascontiguousarray(v, dtype=np.float32) for v in (mu_in, sd_in, mu_out, sd_out)]
+        self._check(self.lib.hub_mlp_set_normalization(self.m, *[v.ctypes.data_as(C.POINTER(C.c_float)) for v in arrs]),
+                    "set_normalization")
+
+    def fit_normalization(self, X, T):
+        self._check(self.lib.hub_mlp_fit_normalization(self.m, _tptr(X), _tptr(T), X.shape[0]), "fit_normalization")
+
+    def forward(self, X, Y):
+        self._check(self.lib.hub_mlp_forward(self.m, _tptr(X), X.shape[0], _tptr(Y)), "forward")
+
+    def loss_grad(self, X, T):
+        loss = C.c_float()
+        g = np.zeros(self.nparams, dtype=np.float32)
+        self._check(self.lib.hub_mlp_loss_grad(self.m, _tptr(X), _tptr(T), X.shape[0], C.byref(loss),
+                                               g.ctypes.data_as(C.POINTER(C.c_float))), "loss_grad")
+        return loss.value, g
+
+    def train_step(self, X, T, lr):
+        loss = C.c_float()
+        self._check(self.lib.hub_mlp_train_step(self.m, _tptr(X), _tptr(T), X.shape[0], float(lr), C.byref(loss)),
+                    "train_step")
+        return loss.value

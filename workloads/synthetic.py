@@ -186,17 +186,24 @@ def displaced(positions, sigma: float, seed: int):
 
 
 def _tio2_atoms(pos_ti, pos_o, U_ev: float, seed_gamma: int, kb_rc: float = 2.5,
-                hub_rc: float = 5.0):
+                hub_rc: float = 5.0, species_gamma: bool = False):
+    """Ti (KB s/p/d + Hubbard d) and O (KB s/p/d) atoms.  KB strengths are drawn per atom,
+    or, with species_gamma, once per species (the same pseudopotential for every atom of a
+    species, as transferable models across cells need)."""
     g = _rng(seed_gamma)
+    if species_gamma:
+        g_ti, g_o = tuple(g.uniform(0.5, 2.0, 3)), tuple(g.uniform(0.5, 2.0, 3))
     atoms = []
     for p in pos_ti:
         atoms.append(Atom("Ti", np.asarray(p, dtype=np.float64), kb_l=(0, 1, 2),
-                          kb_rs=(0.8, 0.8, 1.0), kb_gamma=tuple(g.uniform(0.5, 2.0, 3)),
+                          kb_rs=(0.8, 0.8, 1.0),
+                          kb_gamma=g_ti if species_gamma else tuple(g.uniform(0.5, 2.0, 3)),
                           kb_rc=kb_rc, hub_l=2, hub_rs=1.0, hub_rc=hub_rc,
                           hub_U=U_ev / HARTREE_EV))
     for p in pos_o:
         atoms.append(Atom("O", np.asarray(p, dtype=np.float64), kb_l=(0, 1, 2),
-                          kb_rs=(0.8, 0.8, 1.0), kb_gamma=tuple(g.uniform(0.5, 2.0, 3)),
+                          kb_rs=(0.8, 0.8, 1.0),
+                          kb_gamma=g_o if species_gamma else tuple(g.uniform(0.5, 2.0, 3)),
                           kb_rc=kb_rc))
     return atoms
 
@@ -252,6 +259,29 @@ def rutile(reps=(2, 2, 3), grid=(88, 88, 84), n_occ=290, n_extra=58, degree=24,
                     tuple(grid), tuple(L), veff, atoms, ncol=n_occ + n_extra, degree=degree,
                     nspin=nspin, n_elec=float(2 * n_occ), kT=0.005,
                     D0=_spin_split_D0(nhub, nspin), seed_orbitals=20, seed_lanczos=30)
+
+
+def rutile_snapshot(reps=(2, 2, 3), sigma: float = 0.1, seed: int = 0, h_target: float = 0.2,
+                    degree: int = 24, U_ev: float = 3.5, nspin: int = 2,
+                    occ_per_atom: float = 290 / 72, extra: float = 0.2) -> Workload:
+    """A displaced rutile-shaped supercell (atoms moved by N(0, sigma) bohr) with one KB
+    pseudopotential per species, grid spacing about h_target, occ_per_atom occupied orbitals
+    per atom plus a fraction `extra` of buffer orbitals, spin-polarised: a member of the
+    family whose SCF solutions train the warm-start model (3x3x4: 216 atoms, 132x132x112
+    grid, 1044 orbitals)."""
+    L, pti, po = _supercell(rutile_cell(), reps)
+    pti = displaced(pti, sigma, 50_000 + seed)
+    po = displaced(po, sigma, 60_000 + seed)
+    atoms = _tio2_atoms(pti, po, U_ev, 4, species_gamma=True)
+    grid = scaled_grid_for(L, h_target)
+    veff = _tio2_potential(grid, L, atoms)
+    n_occ = int(round(occ_per_atom * len(atoms)))
+    ncol = n_occ + int(round(extra * n_occ))
+    return Workload(f"rutile-snap{seed}-{reps[0]}x{reps[1]}x{reps[2]}-{len(atoms)}atoms-"
+                    f"{grid[0]}x{grid[1]}x{grid[2]}-{ncol}orb",
+                    tuple(grid), tuple(L), veff, atoms, ncol=ncol, degree=degree, nspin=nspin,
+                    n_elec=float(2 * n_occ), kT=0.005, D0=_spin_split_D0(len(pti), nspin),
+                    seed_orbitals=70_000 + seed, seed_lanczos=80_000 + seed)
 
 
 def small_test_system(n=(20, 24, 28), L=None, ncol=37, natoms=3, nspin=1, seed=7,
