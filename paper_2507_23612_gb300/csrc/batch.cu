@@ -116,6 +116,23 @@ using namespace hub;
 
 extern "C" {
 
+int hub_set_tuning(hub_t h, int stencil_variant, int gemm_split) {
+    if (!h) return HUB_EINVAL;
+    if (stencil_variant >= hub::stencil_variants(h) || stencil_variant < -1 || gemm_split == 0 || gemm_split < -1)
+        return hub::fail(h, HUB_EINVAL, "bad tuning");
+    if (stencil_variant >= 0) h->stencil_variant = stencil_variant;
+    if (gemm_split > 0) h->gemm_split = gemm_split;
+    return HUB_OK;
+}
+
+int hub_get_tuning(hub_t h, int* stencil_variant, int* n_variants, int* gemm_split) {
+    if (!h) return HUB_EINVAL;
+    if (stencil_variant) *stencil_variant = h->stencil_variant;
+    if (n_variants) *n_variants = hub::stencil_variants(h);
+    if (gemm_split) *gemm_split = h->gemm_split;
+    return HUB_OK;
+}
+
 int hub_autotune(hub_t h, int spin, const void* X, int ncol, int ld, int* variant_out) {
     if (!h || !X || ncol < 1 || (long)ld < h->Nd) return hub::fail(h, HUB_EINVAL, "bad autotune arguments");
     if (!h->veff_set || !h->atoms_set) return hub::fail(h, HUB_EINVAL, "handle not set up");

@@ -86,10 +86,6 @@ __global__ void k_table_values(const SiteDev* __restrict__ sites, const int* __r
 }
 
 // ---------------------------------------------------------------------------- gather
-// One warp per (work item, NC columns): lanes stride over the item's points, each lane keeps
-// the NP x NC partial inner products in registers, and one warp-shuffle reduction per item
-// produces the partial sums (no shared memory, no block barriers).  NP (the site's number
-// of projectors) is a template argument so no lane multiplies padding.
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -107,7 +103,12 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-template <typename T, typename D, int NP, int NC>
+// One warp per (work item, NC columns), GW warps per CTA on neighbouring column groups:
+// lanes stride over the item's points, each lane keeps the NP x NC partial inner products in
+// registers, and one warp-shuffle reduction per item produces the partial sums (no shared
+// memory, no block barriers).  NP (the site's number of projectors) is a template argument so no lane
+// multiplies padding.
+template <typename T, typename D, int NP, int NC, int PTS>
 __device__ __forceinline__ void gather_body(const T* __restrict__ X, int ld, int nc, int c0,
                                             const int* __restrict__ idx, const T* __restrict__ vp0,
                                             int first, int cnt, int lane, D* __restrict__ part,
@@ -117,27 +118,39 @@ __device__ __forceinline__ void gather_body(const T* __restrict__ X, int ld, int
     for (int p = 0; p < NP; ++p)
 #pragma unroll
         for (int j = 0; j < NC; ++j) acc[p][j] = zero_of(T());
-    // two points per lane and iteration: twice the independent loads in flight
+    // PTS points per lane and iteration (PTS times the independent loads in flight); the
+    // grid indices of the next iteration are fetched one iteration ahead
     int l = lane;
-    for (; l + 32 < cnt; l += 64) {
-        const long g0 = idx[first + l], g1 = idx[first + l + 32];
-        const T* va = vp0 + (size_t)l * NP;
-        const T* vb = va + (size_t)32 * NP;
-        T pa[NP], pb[NP], xa[NC], xb[NC];
+    if (l + 32 * (PTS - 1) < cnt) {
+        long gn[PTS];
 #pragma unroll
-        for (int p = 0; p < NP; ++p) { pa[p] = va[p]; pb[p] = vb[p]; }
+        for (int q = 0; q < PTS; ++q) gn[q] = idx[first + l + 32 * q];
+        for (; l + 32 * (PTS - 1) < cnt; l += 32 * PTS) {
+            long gq[PTS];
 #pragma unroll
-        for (int j = 0; j < NC; ++j) {
-            xa[j] = j < nc ? X[g0 + (size_t)(c0 + j) * ld] : zero_of(T());
-            xb[j] = j < nc ? X[g1 + (size_t)(c0 + j) * ld] : zero_of(T());
-        }
+            for (int q = 0; q < PTS; ++q) gq[q] = gn[q];
+            if (l + 32 * PTS + 32 * (PTS - 1) < cnt) {
 #pragma unroll
-        for (int j = 0; j < NC; ++j)
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                acc[p][j] = cfma_conj(pa[p], xa[j], acc[p][j]);
-                acc[p][j] = cfma_conj(pb[p], xb[j], acc[p][j]);
+                for (int q = 0; q < PTS; ++q) gn[q] = idx[first + l + 32 * PTS + 32 * q];
             }
+            T xq[PTS][NC];
+#pragma unroll
+            for (int q = 0; q < PTS; ++q)
+#pragma unroll
+                for (int j = 0; j < NC; ++j)
+                    xq[q][j] = j < nc ? X[gq[q] + (size_t)(c0 + j) * ld] : zero_of(T());
+#pragma unroll
+            for (int q = 0; q < PTS; ++q) {
+                const T* vq = vp0 + (size_t)(l + 32 * q) * NP;
+                T pq[NP];
+#pragma unroll
+                for (int p = 0; p < NP; ++p) pq[p] = vq[p];
+#pragma unroll
+                for (int j = 0; j < NC; ++j)
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) acc[p][j] = cfma_conj(pq[p], xq[q][j], acc[p][j]);
+            }
+        }
     }
     for (; l < cnt; l += 32) {
         const long g = idx[first + l];
@@ -169,8 +182,8 @@ __device__ __forceinline__ void gather_body(const T* __restrict__ X, int ld, int
         }
 }
 
-template <typename R, bool CPLX>
-__global__ void __launch_bounds__(128)
+template <typename R, bool CPLX, int GW, int PTS>
+__global__ void __launch_bounds__(GW * 32)
 k_gather(const typename VT<R, CPLX>::T* __restrict__ X, int ld, int ncol,
          const SiteDev* __restrict__ sites, const int* __restrict__ items,
          const int* __restrict__ idx, const typename VT<R, CPLX>::T* __restrict__ vals,
@@ -182,21 +195,21 @@ k_gather(const typename VT<R, CPLX>::T* __restrict__ X, int ld, int ncol,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int s = items[3 * it], first = items[3 * it + 1], cnt = items[3 * it + 2];
     const int np = sites[s].nproj;
-    const int c0 = (blockIdx.y * 4 + warp) * NC;
+    const int c0 = (blockIdx.y * GW + warp) * NC;
     if (c0 >= ncol) return;
     const int nc = min(NC, ncol - c0);
     const T* vp0 = vals + (size_t)sites[s].val_off + (size_t)(first - sites[s].pt_off) * np;
     const size_t pbase = (size_t)it * kMaxProj * ncol;
     switch (np) {
-        case 1: gather_body<T, D, 1, NC>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
-        case 2: gather_body<T, D, 2, NC>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
-        case 3: gather_body<T, D, 3, NC>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
-        case 4: gather_body<T, D, 4, NC>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
-        case 5: gather_body<T, D, 5, NC>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
-        case 6: gather_body<T, D, 6, NC>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
-        case 7: gather_body<T, D, 7, NC>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
-        case 8: gather_body<T, D, 8, NC>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
-        case 9: gather_body<T, D, 9, NC>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
+        case 1: gather_body<T, D, 1, NC, PTS>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
+        case 2: gather_body<T, D, 2, NC, PTS>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
+        case 3: gather_body<T, D, 3, NC, PTS>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
+        case 4: gather_body<T, D, 4, NC, PTS>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
+        case 5: gather_body<T, D, 5, NC, PTS>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
+        case 6: gather_body<T, D, 6, NC, PTS>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
+        case 7: gather_body<T, D, 7, NC, PTS>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
+        case 8: gather_body<T, D, 8, NC, PTS>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
+        case 9: gather_body<T, D, 9, NC, PTS>(X, ld, nc, c0, idx, vp0, first, cnt, lane, part, pbase, ncol); break;
         default: break;   // build_tables rejects sites with more than kMaxProj functions
     }
 }
@@ -249,11 +262,12 @@ __global__ void k_reduce_transform(int nsites, int ncol, double dV, const SiteDe
 }
 
 // ---------------------------------------------------------------------------- scatter
-// One thread per grid point and NC columns: walks the point's CSR entries (one 8-byte
-// metadata load each), multiplies the site's values into W rows (16-byte vector loads when
-// the rows are aligned) and updates Y once per column.
+// One thread per grid point, looping over all columns NC at a time: the point's CSR entries
+// and values are fetched from HBM once and re-read from L1 for the later column groups.  Per
+// entry, the site's values multiply W rows (16-byte vector loads when the rows are aligned);
+// Y is updated once per column.
 template <typename R, bool CPLX>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 k_scatter(typename VT<R, CPLX>::T* __restrict__ Y, int ld, int ncol, long Nd,
           const int* __restrict__ csr_off, const int2* __restrict__ csr_ent,
           const typename VT<R, CPLX>::T* __restrict__ vals,
@@ -261,48 +275,49 @@ k_scatter(typename VT<R, CPLX>::T* __restrict__ Y, int ld, int ncol, long Nd,
           const double* __restrict__ alpha_dev) {
     using T = typename VT<R, CPLX>::T;
     if (alpha_dev) alpha = (R)alpha_dev[0];
-    constexpr int NC = 32 / sizeof(T);
+    constexpr int NC = 64 / sizeof(T);
     constexpr int PER16 = 16 / sizeof(T);
     const long g = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= Nd) return;
     const int e0 = csr_off[g], e1 = csr_off[g + 1];
     if (e0 == e1) return;
-    const int c0 = blockIdx.y * NC;
-    const int nc = min(NC, ncol - c0);
-    T acc[NC];
+    for (int c0 = 0; c0 < ncol; c0 += NC) {
+        const int nc = min(NC, ncol - c0);
+        T acc[NC];
 #pragma unroll
-    for (int j = 0; j < NC; ++j) acc[j] = zero_of(T());
-    int2 m = csr_ent[e0];
-    for (int e = e0; e < e1; ++e) {
-        const int2 mn = (e + 1 < e1) ? csr_ent[e + 1] : m;      // next entry, in flight early
-        const int np = m.y & 15;
-        const T* wrow = W + (size_t)(m.y >> 4) * ncol + c0;
-        const T* vrow = vals + m.x;
-        for (int p = 0; p < np; ++p, wrow += ncol) {
-            const T v = vrow[p];
-            if (vec_ok && nc == NC) {
-                float4 q4[NC / PER16];
+        for (int j = 0; j < NC; ++j) acc[j] = zero_of(T());
+        int2 m = csr_ent[e0];
+        for (int e = e0; e < e1; ++e) {
+            const int2 mn = (e + 1 < e1) ? csr_ent[e + 1] : m;      // next entry, in flight early
+            const int np = m.y & 15;
+            const T* wrow = W + (size_t)(m.y >> 4) * ncol + c0;
+            const T* vrow = vals + m.x;
+            for (int p = 0; p < np; ++p, wrow += ncol) {
+                const T v = vrow[p];
+                if (vec_ok && nc == NC) {
+                    float4 q4[NC / PER16];
 #pragma unroll
-                for (int k = 0; k < NC / PER16; ++k) q4[k] = reinterpret_cast<const float4*>(wrow)[k];
+                    for (int k = 0; k < NC / PER16; ++k) q4[k] = reinterpret_cast<const float4*>(wrow)[k];
 #pragma unroll
-                for (int k = 0; k < NC / PER16; ++k) {
-                    const T* w = reinterpret_cast<const T*>(&q4[k]);
+                    for (int k = 0; k < NC / PER16; ++k) {
+                        const T* w = reinterpret_cast<const T*>(&q4[k]);
 #pragma unroll
-                    for (int i = 0; i < PER16; ++i) acc[k * PER16 + i] = cfma(v, w[i], acc[k * PER16 + i]);
+                        for (int i = 0; i < PER16; ++i) acc[k * PER16 + i] = cfma(v, w[i], acc[k * PER16 + i]);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < NC; ++j)
+                        if (j < nc) acc[j] = cfma(v, wrow[j], acc[j]);
                 }
-            } else {
-#pragma unroll
-                for (int j = 0; j < NC; ++j)
-                    if (j < nc) acc[j] = cfma(v, wrow[j], acc[j]);
             }
+            m = mn;
         }
-        m = mn;
-    }
 #pragma unroll
-    for (int j = 0; j < NC; ++j) {
-        if (j < nc) {
-            T* y = Y + (size_t)(c0 + j) * ld + g;
-            *y = fmar(alpha, acc[j], *y);
+        for (int j = 0; j < NC; ++j) {
+            if (j < nc) {
+                T* y = Y + (size_t)(c0 + j) * ld + g;
+                *y = fmar(alpha, acc[j], *y);
+            }
         }
     }
 }
@@ -604,10 +619,14 @@ static int gather_t(hub_t h, const void* X, int ncol, int ld, int spin, bool wan
     if ((rc = ensure(h, &h->d_C, &h->C_bytes, (size_t)t.nproj * ncol * sizeof(D)))) return rc;
     if ((rc = ensure(h, &h->d_W, &h->W_bytes, (size_t)t.nproj * ncol * sizeof(T)))) return rc;
     constexpr int NC = 16 / sizeof(T);
-    dim3 g1(t.nitems, (ncol + 4 * NC - 1) / (4 * NC));
     { ProfScope ps(h, HUB_K_GATHER);
-    k_gather<R, CPLX><<<g1, 128, 0, h->stream>>>((const T*)X, ld, ncol, t.d_sites, t.d_items, t.d_idx,
-                                                 (const T*)t.d_vals, (D*)h->d_part); }
+    // one warp per CTA and four points per lane and iteration: the fastest of the shapes
+    // measured on the rutile workload (1, 2, 4, 8 warps x 2, 4 points)
+    constexpr int GW = 1, PTS = 4;
+    dim3 g1(t.nitems, (ncol + GW * NC - 1) / (GW * NC));
+    k_gather<R, CPLX, GW, PTS><<<g1, GW * 32, 0, h->stream>>>((const T*)X, ld, ncol, t.d_sites, t.d_items,
+                                                            t.d_idx, (const T*)t.d_vals, (D*)h->d_part);
+    }
     HUB_CUDA_TRY(h, cudaGetLastError());
     const long nthr = (long)t.nsites * ncol;
     { ProfScope ps(h, HUB_K_TRANSFORM);
@@ -629,12 +648,11 @@ int launch_gather(hub_t h, const void* X, int ncol, int ld, int spin, bool want_
 template <typename R, bool CPLX>
 static int scatter_t(hub_t h, void* Y, int ncol, int ld, double alpha, const double* alpha_dev) {
     using T = typename VT<R, CPLX>::T;
-    constexpr int NC = 32 / sizeof(T);
     Table& t = h->proj;
     const int vec_ok = ((ncol * sizeof(T)) % 16 == 0) && ((uintptr_t)h->d_W % 16 == 0);
-    dim3 grid((unsigned)((h->Nd + 255) / 256), (ncol + NC - 1) / NC);
+    dim3 grid((unsigned)((h->Nd + 127) / 128));
     ProfScope ps(h, HUB_K_SCATTER);
-    k_scatter<R, CPLX><<<grid, 256, 0, h->stream>>>((T*)Y, ld, ncol, h->Nd, t.d_csr_off, t.d_csr_ent,
+    k_scatter<R, CPLX><<<grid, 128, 0, h->stream>>>((T*)Y, ld, ncol, h->Nd, t.d_csr_off, t.d_csr_ent,
                                                     (const T*)t.d_vals, (const T*)h->d_W, (R)alpha, vec_ok,
                                                     alpha_dev);
     HUB_CUDA_TRY(h, cudaGetLastError());

@@ -504,11 +504,9 @@ k_stencil_vec(StencilDev<R> a) {
     cp_async_wait<0>();
 }
 
-// ---------------------------------------------------------------------------- float x4 form
-// Real float, 4 consecutive x-points per thread, held as two packed pairs so that every
-// add / FMA is one Blackwell f32x2 instruction (add.rn.f32x2, fma.rn.f32x2: two lanes of
-// ordinary IEEE float arithmetic, the same rounding as scalar code).  The z-loop is
-// unrolled 2*NH+1 times so the register queue rotates by static indexing instead of moves.
+// ---------------------------------------------------------------------------- packed float pairs
+// Blackwell f32x2 instructions (add.rn.f32x2, fma.rn.f32x2, mul.rn.f32x2): two lanes of
+// ordinary IEEE float arithmetic per instruction, the same rounding as scalar code.
 typedef unsigned long long u64;
 __device__ __forceinline__ u64 pk2(float a, float b) {
     u64 r;
@@ -541,14 +539,40 @@ __device__ __forceinline__ u64 mul2(u64 a, u64 b) {
     return d;
 }
 
-template <int TXT, int TY, int P>
+// ---------------------------------------------------------------------------- float x4 form
+// Real float, 4 consecutive x-points per thread held as two packed pairs, so that every add
+// and FMA is one f32x2 instruction; the z-loop is unrolled 2*NH+1 times so that the
+// register queue rotates by static indexing.  A stage holds the halo'd plane z only (the x/y
+// neighbours), plus three per-thread interior slots: the plane z + NH + 1 that enters the
+// z register queue after plane z, and V and Yprev of plane z.  Stages are filled PH planes
+// ahead; with RS = PH + 2 stages the copy into a stage starts two planes after its last
+// reader, so one barrier per plane suffices (the interior slots are written and read by the
+// same thread and need none).  The three axes accumulate in separate registers (six
+// independent FMA chains per thread instead of two).
+template <int TXT, int TY, int PH>
+struct SplitCfg {
+    static constexpr int NH = 6, HX = 8;
+    static constexpr int TXP = TXT * 4;
+    static constexpr int SXV = (TXP + 2 * HX) / 4;     // float4 vectors per halo row
+    static constexpr int SY = TY + 2 * NH;
+    static constexpr int NT = TXT * TY;
+    static constexpr int RS = PH + 2;
+    static constexpr int NVS = SXV * SY;
+    static constexpr int PER = (NVS + NT - 1) / NT;
+    static constexpr size_t YB = 16 * (size_t)NVS;     // halo plane
+    static constexpr size_t IB = 16 * (size_t)NT;      // one float4 per thread
+    static constexpr size_t STAGE = YB + 3 * IB;       // halo | feed | V | Yprev
+    static constexpr size_t SMEM = STAGE * RS;
+};
+
+template <int TXT, int TY, int PH>
 __global__ void __launch_bounds__(TXT * TY)
-k_stencil_f32x4(StencilDev<float> a) {
+k_stencil_f32s(StencilDev<float> a) {
     const Coef<float> cf = resolve_coef(a);
-    using C = VecCfg<float, false, 4, TXT, TY, P>;
-    constexpr int NH = C::NH, HX = C::HX, SXV = C::SXV, S = C::S, NT = C::NT, PER = C::PER;
+    using C = SplitCfg<TXT, TY, PH>;
+    constexpr int NH = C::NH, HX = C::HX, SXV = C::SXV, RS = C::RS, NT = C::NT, PER = C::PER;
     constexpr int Q = 2 * NH + 1;
-    static_assert(HX == 8, "x halo of two float4 vectors");
+    static_assert(C::YB % 16 == 0 && C::STAGE % 16 == 0, "stage regions stay 16-byte aligned");
     extern __shared__ __align__(128) unsigned char smem[];
 
     const int tid = threadIdx.x;
@@ -584,21 +608,29 @@ k_stencil_f32x4(StencilDev<float> a) {
     const long own = (long)(gy0 + ty) * n1 + (gx0 + tx * 4);
 
     auto stY = [&](int st) { return reinterpret_cast<ulonglong2*>(smem + C::STAGE * (size_t)st); };
-    auto stV = [&](int st) { return reinterpret_cast<ulonglong2*>(smem + C::STAGE * (size_t)st + C::YB); };
-    auto stP = [&](int st) { return reinterpret_cast<ulonglong2*>(smem + C::STAGE * (size_t)st + C::YB + C::VB); };
-    auto issue = [&](int st, int zw, bool interior) {
-        const long zoff = (long)zw * plane;
-        ulonglong2* ys = stY(st);
+    auto stI = [&](int st, int k) {            // k = 0 feed, 1 V, 2 Yprev
+        return reinterpret_cast<ulonglong2*>(smem + C::STAGE * (size_t)st + C::YB + C::IB * (size_t)k);
+    };
+    // copy group j: halo, V and Yprev of plane z0 + j, and the queue feed plane z0 + j + NH + 1
+    auto issue = [&](int j, int st) {
+        const int p = z0 + j;
+        if (p < z1) {
+            const long zoff = (long)p * plane;          // p < z1 <= n3: no wrap
+            ulonglong2* ys = stY(st);
 #pragma unroll
-        for (int k = 0; k < PER; ++k)
-            if (s_idx[k] >= 0) cp_async<16>(ys + s_idx[k], s_src[k] + zoff);
-        if (active && interior) {
-            cp_async<16>(stV(st) + tid, a.V + zoff + own);
-            if (Yp) cp_async<16>(stP(st) + tid, Yp + zoff + own);
+            for (int k = 0; k < PER; ++k)
+                if (s_idx[k] >= 0) cp_async<16>(ys + s_idx[k], s_src[k] + zoff);
+            if (active) {
+                cp_async<16>(stI(st, 1) + tid, a.V + zoff + own);
+                if (Yp) cp_async<16>(stI(st, 2) + tid, Yp + zoff + own);
+            }
+        }
+        if (active && p + 1 < z1) {
+            const int pf = (p + NH + 1) % n3;
+            cp_async<16>(stI(st, 0) + tid, Y + (long)pf * plane + own);
         }
     };
 
-    // packed coefficients
     u64 wx[NH], wy[NH], wz[NH];
 #pragma unroll
     for (int p = 0; p < NH; ++p) {
@@ -609,8 +641,7 @@ k_stencil_f32x4(StencilDev<float> a) {
     const u64 cen2 = pk2(cf.center, cf.center), alp2 = pk2(cf.alpha, cf.alpha), bet2 = pk2(cf.beta, cf.beta);
     const u64 m2 = pk2(-2.0f, -2.0f);
 
-    const int last_needed = z1 + NH - 1;
-    u64 ql[Q], qh[Q];                 // points (0,1) and (2,3) of planes in the queue
+    u64 ql[Q], qh[Q];
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         ql[j] = 0ull;
@@ -623,16 +654,12 @@ k_stencil_f32x4(StencilDev<float> a) {
             qh[j] = v.y;
         }
     }
-    int ist = 0, izw = z0 % n3, ip = z0;
 #pragma unroll 1
-    for (int j = 0; j <= NH + P; ++j) {
-        if (ip <= last_needed) issue(ist, izw, ip < z1);
+    for (int j = 0; j < PH; ++j) {
+        issue(j, j % RS);
         cp_async_commit();
-        ++ip; if (++ist == S) ist = 0; if (++izw == n3) izw = 0;
     }
-    cp_async_wait<P>();
-    __syncthreads();
-    int sz = 0, sf = (NH + 1) % S;
+    int sz = 0, si = PH % RS;                   // stage of plane z, stage of the next issue
     const int rbase = (ty + NH) * SXV;
 #pragma unroll 1
     for (int zb = z0; zb < z1; zb += Q) {
@@ -640,9 +667,12 @@ k_stencil_f32x4(StencilDev<float> a) {
         for (int st = 0; st < Q; ++st) {
             const int z = zb + st;
             if (z >= z1) break;
+            issue(z - z0 + PH, si);
+            cp_async_commit();
+            cp_async_wait<PH>();
+            __syncthreads();
             if (active) {
                 const ulonglong2* ys = stY(sz);
-                // own row: floats x-8 .. x+11 as ten packed pairs r[0..9] (r[k] = floats 2k, 2k+1)
                 u64 r[10];
 #pragma unroll
                 for (int j = 0; j < 5; ++j) {
@@ -650,59 +680,62 @@ k_stencil_f32x4(StencilDev<float> a) {
                     r[2 * j] = v.x;
                     r[2 * j + 1] = v.y;
                 }
-                // odd-aligned pairs u[k] = floats (2k+1, 2k+2), k = 1..7
                 u64 u[8];
 #pragma unroll
                 for (int k = 1; k <= 7; ++k) u[k] = pk2(hi2(r[k]), lo2(r[k + 1]));
-                const ulonglong2 vv = stV(sz)[tid];
-                // points 0,1 sit at floats 8,9 (pair r[4]); points 2,3 at floats 10,11 (r[5])
+                const ulonglong2 vv = stI(sz, 1)[tid];
                 const u64 cl = ql[(st + NH) % Q], ch = qh[(st + NH) % Q];
-                u64 al = mul2(fma2(alp2, vv.x, cen2), cl);
-                u64 ah = mul2(fma2(alp2, vv.y, cen2), ch);
+                u64 xl = 0ull, xh = 0ull, yl = 0ull, yh = 0ull, zl = 0ull, zh = 0ull;
 #pragma unroll
                 for (int p = 1; p <= NH; ++p) {
-                    // difference form: w ((f+p + f-p) - 2 f0)
-                    al = fma2(wz[p - 1], fma2(m2, cl, add2(ql[(st + NH + p) % Q], ql[(st + NH - p) % Q])), al);
-                    ah = fma2(wz[p - 1], fma2(m2, ch, add2(qh[(st + NH + p) % Q], qh[(st + NH - p) % Q])), ah);
-                    // x +- p of floats (8,9) and (10,11)
+                    const u64 dzl = fma2(m2, cl, add2(ql[(st + NH + p) % Q], ql[(st + NH - p) % Q]));
+                    const u64 dzh = fma2(m2, ch, add2(qh[(st + NH + p) % Q], qh[(st + NH - p) % Q]));
                     const u64 lp = (p & 1) ? u[(8 + p - 1) / 2] : r[(8 + p) / 2];
                     const u64 lm = (p & 1) ? u[(8 - p - 1) / 2] : r[(8 - p) / 2];
                     const u64 hp = (p & 1) ? u[(10 + p - 1) / 2] : r[(10 + p) / 2];
                     const u64 hm = (p & 1) ? u[(10 - p - 1) / 2] : r[(10 - p) / 2];
-                    al = fma2(wx[p - 1], fma2(m2, cl, add2(lp, lm)), al);
-                    ah = fma2(wx[p - 1], fma2(m2, ch, add2(hp, hm)), ah);
+                    const u64 dxl = fma2(m2, cl, add2(lp, lm));
+                    const u64 dxh = fma2(m2, ch, add2(hp, hm));
                     const ulonglong2 up = ys[rbase + p * SXV + tx + 2];
                     const ulonglong2 dn = ys[rbase - p * SXV + tx + 2];
-                    al = fma2(wy[p - 1], fma2(m2, cl, add2(up.x, dn.x)), al);
-                    ah = fma2(wy[p - 1], fma2(m2, ch, add2(up.y, dn.y)), ah);
+                    const u64 dyl = fma2(m2, cl, add2(up.x, dn.x));
+                    const u64 dyh = fma2(m2, ch, add2(up.y, dn.y));
+                    if (p == 1) {
+                        zl = mul2(wz[0], dzl); zh = mul2(wz[0], dzh);
+                        xl = mul2(wx[0], dxl); xh = mul2(wx[0], dxh);
+                        yl = mul2(wy[0], dyl); yh = mul2(wy[0], dyh);
+                    } else {
+                        zl = fma2(wz[p - 1], dzl, zl); zh = fma2(wz[p - 1], dzh, zh);
+                        xl = fma2(wx[p - 1], dxl, xl); xh = fma2(wx[p - 1], dxh, xh);
+                        yl = fma2(wy[p - 1], dyl, yl); yh = fma2(wy[p - 1], dyh, yh);
+                    }
                 }
+                u64 al = mul2(fma2(alp2, vv.x, cen2), cl);
+                u64 ah = mul2(fma2(alp2, vv.y, cen2), ch);
+                al = add2(al, add2(add2(xl, yl), zl));
+                ah = add2(ah, add2(add2(xh, yh), zh));
                 if (Yp) {
-                    const ulonglong2 pv = stP(sz)[tid];
+                    const ulonglong2 pv = stI(sz, 2)[tid];
                     al = fma2(bet2, pv.x, al);
                     ah = fma2(bet2, pv.y, ah);
                 }
                 *reinterpret_cast<ulonglong2*>(Yo + (long)z * plane + own) = make_ulonglong2(al, ah);
+                if (z + 1 < z1) {
+                    const ulonglong2 f = stI(sz, 0)[tid];
+                    ql[st] = f.x;                 // slot of plane z - NH takes plane z + NH + 1
+                    qh[st] = f.y;
+                }
             }
-            if (z + 1 == z1) break;
-            __syncthreads();
-            if (ip <= last_needed) issue(ist, izw, ip < z1);
-            cp_async_commit();
-            ++ip; if (++ist == S) ist = 0; if (++izw == n3) izw = 0;
-            cp_async_wait<P>();
-            __syncthreads();
-            const ulonglong2 f = stY(sf)[rbase + tx + 2];
-            ql[st] = f.x;                     // slot of plane z - NH takes plane z + NH + 1
-            qh[st] = f.y;
-            if (++sz == S) sz = 0;
-            if (++sf == S) sf = 0;
+            if (++sz == RS) sz = 0;
+            if (++si == RS) si = 0;
         }
     }
     cp_async_wait<0>();
 }
 
-template <int TXT, int TY, int P>
-static int run_f32x4(hub_t h, const StencilArgs& s) {
-    using Cfg = VecCfg<float, false, 4, TXT, TY, P>;
+template <int TXT, int TY, int PH>
+static int run_f32s(hub_t h, const StencilArgs& s) {
+    using Cfg = SplitCfg<TXT, TY, PH>;
     StencilDev<float> d;
     d.Y = s.Y;
     d.Yprev = s.Yprev;
@@ -715,7 +748,7 @@ static int run_f32x4(hub_t h, const StencilArgs& s) {
         d.ph[a][1] = 0.0;
     }
     const int tiles = ((s.n1 + Cfg::TXP - 1) / Cfg::TXP) * ((s.n2 + TY - 1) / TY);
-    const long want = 4L * h->num_sms;
+    const long want = 8L * h->num_sms;
     const long per = (long)tiles * s.ncol;
     int nzc = 1;
     if (per < want) nzc = (int)((want + per - 1) / per);
@@ -725,11 +758,11 @@ static int run_f32x4(hub_t h, const StencilArgs& s) {
     while ((long)s.ncol * nzc > 65535) { zchunk *= 2; nzc = (s.n3 + zchunk - 1) / zchunk; }
     d.zchunk = zchunk;
     d.nzc = nzc;
-    HUB_CUDA_TRY(h, cudaFuncSetAttribute(k_stencil_f32x4<TXT, TY, P>,
+    HUB_CUDA_TRY(h, cudaFuncSetAttribute(k_stencil_f32s<TXT, TY, PH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
     dim3 grid((s.n1 + Cfg::TXP - 1) / Cfg::TXP, (s.n2 + TY - 1) / TY, s.ncol * nzc);
     ProfScope ps(h, HUB_K_STENCIL);
-    k_stencil_f32x4<TXT, TY, P><<<grid, TXT * TY, Cfg::SMEM, h->stream>>>(d);
+    k_stencil_f32s<TXT, TY, PH><<<grid, TXT * TY, Cfg::SMEM, h->stream>>>(d);
     HUB_CUDA_TRY(h, cudaGetLastError());
     return HUB_OK;
 }
@@ -807,7 +840,7 @@ static int run_cfg(hub_t h, const StencilArgs& s) {
 // Tile shapes the autotuner chooses from, per kernel family (index 0 is the default).
 int stencil_variants(hub_t h) {
     const int es = h->esize * (h->cplx ? 2 : 1);
-    if (h->esize == 4) return 4;          // float real (packed) and float complex (vector)
+    if (h->esize == 4) return h->cplx ? 4 : 6;   // float real (packed) / float complex (vector)
     return es == 16 ? 2 : 3;              // double complex / double real (scalar pipeline)
 }
 
@@ -823,10 +856,12 @@ int launch_stencil(hub_t h, const StencilArgs& a) {
         // float streams from HBM: vector copies, packed pair arithmetic for real data
         if (!h->cplx) {
             switch (v) {
-                case 1: return run_f32x4<8, 8, 4>(h, a);
-                case 2: return run_f32x4<16, 8, 2>(h, a);
-                case 3: return run_f32x4<8, 16, 2>(h, a);
-                default: return run_f32x4<8, 16, 4>(h, a);
+                case 1: return run_f32s<8, 8, 3>(h, a);
+                case 2: return run_f32s<8, 32, 2>(h, a);
+                case 3: return run_f32s<8, 16, 3>(h, a);
+                case 4: return run_f32s<16, 8, 2>(h, a);
+                case 5: return run_f32s<8, 8, 2>(h, a);
+                default: return run_f32s<8, 16, 2>(h, a);
             }
         }
         switch (v) {

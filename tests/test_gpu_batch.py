@@ -72,7 +72,7 @@ def test_autotune_keeps_results_identical():
     Y0 = torch.empty_like(X)
     hb.apply_H(0, X, Y0)
     v = hb.autotune(0, X)
-    assert 0 <= v < 4
+    assert 0 <= v < hb.get_tuning()["n_variants"]
     Y1 = torch.empty_like(X)
     hb.apply_H(0, X, Y1)
     # every tile shape evaluates the same arithmetic in the same order per point

@@ -67,6 +67,28 @@ def test_apply_H_padded_leading_dimension_and_spin_channels():
         assert torch.all(Yd[:, wl.Nd:] == 7.0)            # padding untouched
 
 
+@pytest.mark.parametrize("prec", [HUB_F32, HUB_F64])
+def test_apply_H_every_stencil_variant(prec):
+    """Every tile shape the autotuner may choose, on a ragged grid with chunked z and on a
+    grid thinner in z than the stencil's half-width (each plane wraps several times)."""
+    cases = [systems()["ragged"],
+             w.small_test_system(n=(8, 12, 3), ncol=5, natoms=2, hub_rc=2.0, kb_rc=1.5, seed=5)]
+    for wl in cases:
+        X = wl.orbitals()
+        ref = oracle_ham(wl, D=wl.D0[0]).apply(X.T).T
+        hb = make_hub(wl, prec)
+        hb.set_occupation_matrix(0, wl.D0[0])
+        Xd = to_dev(X, hb.dtype)
+        for v in range(hb.get_tuning()["n_variants"]):
+            hb.set_tuning(v)
+            Yd = torch.empty_like(Xd)
+            hb.apply_H(0, Xd, Yd)
+            err = rel(Yd.cpu().numpy().astype(np.float64), ref)
+            assert err < (5e-6 if prec == HUB_F32 else TOL64), (wl.name, v, err)
+        with pytest.raises(HubError):
+            hb.set_tuning(hb.get_tuning()["n_variants"])
+
+
 @pytest.mark.parametrize("name", ["ragged", "bloch"])
 def test_apply_H_fp32(name):
     wl = systems()[name]
