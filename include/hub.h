@@ -249,20 +249,22 @@ int hub_scf_get(hub_t h, double* eig, double* occ, double* D_out);
  * --------------------------------------------------------------------------------- */
 
 /* Autotuner: times the candidate stencil tile shapes of this handle's kernel family on the
- * block X (device, ncol columns, leading dimension ld; X is only read) and, for
- * HUB_MIXED_BF16 handles, the split-K factor of the tensor-core Gram product; keeps the
- * fastest for the handle and for every later handle of the same grid shape, precision and
- * ncol (process-wide cache).  variant_out: NULL or the chosen stencil variant.
+ * block X (device, ncol columns, leading dimension ld; X is only read), for
+ * HUB_MIXED_BF16 handles the split-K factor of the tensor-core Gram product, and for real
+ * float handles the projector gather form (point-major or 8x8x4 bricks); keeps the fastest
+ * for the handle and for every later handle of the same grid shape, precision and ncol
+ * (process-wide cache).  variant_out: NULL or the chosen stencil variant.
  * Synchronises.  Errors: HUB_EINVAL. */
 int hub_autotune(hub_t h, int spin, const void* X, int ncol, int ld, int* variant_out);
 /* Tuning of this handle without timing: stencil_variant in 0 .. n_variants-1 (the tile
  * shapes the autotuner chooses from; 0 is the default), gemm_split >= 1 (split-K factor of
- * the tensor-core Gram product, in units of one wave of tiles).  Pass -1 to keep either.
- * Errors: HUB_EINVAL. */
-int hub_set_tuning(hub_t h, int stencil_variant, int gemm_split);
+ * the tensor-core Gram product, in units of one wave of tiles), gather_form 0 (point-major
+ * projector gather) or 1 (8x8x4 brick form; real float handles only).  Pass -1 to keep
+ * any of them.  Errors: HUB_EINVAL. */
+int hub_set_tuning(hub_t h, int stencil_variant, int gemm_split, int gather_form);
 /* Current tuning of the handle and the number of stencil variants of its kernel family
  * (any pointer may be NULL). */
-int hub_get_tuning(hub_t h, int* stencil_variant, int* n_variants, int* gemm_split);
+int hub_get_tuning(hub_t h, int* stencil_variant, int* n_variants, int* gemm_split, int* gather_form);
 
 /* Chebyshev filter of nsys independent systems (snapshots, Bloch wavevectors, spins) in
  * one CUDA graph (CheFSI, Sec. II.B): X_i <- p_m^(i)(H_i) X_i with the bounds

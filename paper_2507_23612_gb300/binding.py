@@ -76,8 +76,8 @@ _SIGS = {
     "hub_mlp_forward": [_P, _P, _I, _P],
     "hub_mlp_loss_grad": [_P, _P, _P, _I, C.POINTER(C.c_float), C.POINTER(C.c_float)],
     "hub_mlp_train_step": [_P, _P, _P, _I, C.c_float, C.POINTER(C.c_float)],
-    "hub_set_tuning": [_P, _I, _I],
-    "hub_get_tuning": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
+    "hub_set_tuning": [_P, _I, _I, _I],
+    "hub_get_tuning": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "hub_profile": [_P, _I],
     "hub_profile_read": [_P, _I, _PD, C.POINTER(C.c_longlong)],
     "hub_launch_count": [_P, C.POINTER(C.c_longlong)],
@@ -277,13 +277,15 @@ class Hub:
         self._check(self.lib.hub_autotune(self.h, spin, _tptr(X), ncol, ld, C.byref(v)), "hub_autotune")
         return v.value
 
-    def set_tuning(self, stencil_variant: int = -1, gemm_split: int = -1):
-        self._check(self.lib.hub_set_tuning(self.h, int(stencil_variant), int(gemm_split)), "hub_set_tuning")
+    def set_tuning(self, stencil_variant: int = -1, gemm_split: int = -1, gather_form: int = -1):
+        self._check(self.lib.hub_set_tuning(self.h, int(stencil_variant), int(gemm_split), int(gather_form)),
+                    "hub_set_tuning")
 
     def get_tuning(self) -> dict:
-        v, n, g = C.c_int(), C.c_int(), C.c_int()
-        self._check(self.lib.hub_get_tuning(self.h, C.byref(v), C.byref(n), C.byref(g)), "hub_get_tuning")
-        return {"stencil_variant": v.value, "n_variants": n.value, "gemm_split": g.value}
+        v, n, g, f = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        self._check(self.lib.hub_get_tuning(self.h, C.byref(v), C.byref(n), C.byref(g), C.byref(f)),
+                    "hub_get_tuning")
+        return {"stencil_variant": v.value, "n_variants": n.value, "gemm_split": g.value, "gather_form": f.value}
 
     # ------------------------------------------------------------------ measurement
     def profile(self, enable: int):

@@ -27,7 +27,10 @@ struct TuneKey {
     }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int>> g_tuned;   // shape -> (stencil variant, gemm split)
+struct TuneVal {
+    int variant, split, gather_form;
+};
+std::map<TuneKey, TuneVal> g_tuned;   // shape -> stencil variant, gemm split, gather form
 
 struct BatchGraph {
     std::vector<hub_t> sys;
@@ -116,20 +119,23 @@ using namespace hub;
 
 extern "C" {
 
-int hub_set_tuning(hub_t h, int stencil_variant, int gemm_split) {
+int hub_set_tuning(hub_t h, int stencil_variant, int gemm_split, int gather_form) {
     if (!h) return HUB_EINVAL;
-    if (stencil_variant >= hub::stencil_variants(h) || stencil_variant < -1 || gemm_split == 0 || gemm_split < -1)
+    if (stencil_variant >= hub::stencil_variants(h) || stencil_variant < -1 || gemm_split == 0 || gemm_split < -1 ||
+        gather_form < -1 || gather_form > 1 || (gather_form == 1 && (h->esize != 4 || h->cplx)))
         return hub::fail(h, HUB_EINVAL, "bad tuning");
     if (stencil_variant >= 0) h->stencil_variant = stencil_variant;
     if (gemm_split > 0) h->gemm_split = gemm_split;
+    if (gather_form >= 0) h->gather_dense = gather_form;
     return HUB_OK;
 }
 
-int hub_get_tuning(hub_t h, int* stencil_variant, int* n_variants, int* gemm_split) {
+int hub_get_tuning(hub_t h, int* stencil_variant, int* n_variants, int* gemm_split, int* gather_form) {
     if (!h) return HUB_EINVAL;
     if (stencil_variant) *stencil_variant = h->stencil_variant;
     if (n_variants) *n_variants = hub::stencil_variants(h);
     if (gemm_split) *gemm_split = h->gemm_split;
+    if (gather_form) *gather_form = h->gather_dense;
     return HUB_OK;
 }
 
@@ -141,8 +147,9 @@ int hub_autotune(hub_t h, int spin, const void* X, int ncol, int ld, int* varian
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) {
-            h->stencil_variant = it->second.first;
-            h->gemm_split = it->second.second;
+            h->stencil_variant = it->second.variant;
+            h->gemm_split = it->second.split;
+            h->gather_dense = (h->proj.dense && h->esize == 4 && !h->cplx) ? it->second.gather_form : 0;
             if (variant_out) *variant_out = h->stencil_variant;
             return HUB_OK;
         }
@@ -228,12 +235,33 @@ int hub_autotune(hub_t h, int spin, const void* X, int ncol, int ld, int* varian
         if (rc) { h->prof_on = saved_prof; return rc; }
     }
     h->gemm_split = best_split;
+    // projector gather form (real float handles with brick tables): point-major or bricks
+    int best_form = 0;
+    if (h->proj.dense && h->esize == 4 && !h->cplx) {
+        float fms[2] = {1e30f, 1e30f};
+        for (int form = 0; form < 2 && !rc; ++form) {
+            h->gather_dense = form;
+            if ((rc = launch_gather(h, X, ncol, ld, spin, true))) break;       // warm-up
+            for (int r = 0; r < 3 && !rc; ++r) {
+                HUB_CUDA_TRY(h, cudaEventRecord(e0, h->stream));
+                rc = launch_gather(h, X, ncol, ld, spin, true);
+                HUB_CUDA_TRY(h, cudaEventRecord(e1, h->stream));
+                HUB_CUDA_TRY(h, cudaEventSynchronize(e1));
+                float ms = 0.f;
+                HUB_CUDA_TRY(h, cudaEventElapsedTime(&ms, e0, e1));
+                fms[form] = std::min(fms[form], ms);
+            }
+        }
+        if (rc) { h->prof_on = saved_prof; return rc; }
+        best_form = fms[1] < fms[0] ? 1 : 0;
+    }
+    h->gather_dense = best_form;
     h->prof_on = saved_prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[key] = {best, best_split};
+        g_tuned[key] = {best, best_split, best_form};
     }
     if (variant_out) *variant_out = best;
     return check_flags(h);

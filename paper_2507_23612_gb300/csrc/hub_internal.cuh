@@ -66,6 +66,18 @@ struct Table {
     double* d_U = nullptr;
     double* d_M[2] = {nullptr, nullptr};  // per spin [nhub*25] (x2 complex), row p, col m
     std::vector<double> h_M[2];
+    // dense brick form (real float only): the grid in 8x8x4 bricks; per brick, entries of at
+    // most 64 functions with their values as a dense [256 points][fp] block
+    int dense = 0;                    // 1 when the brick tables below are built
+    int nbx = 0, nby = 0, nbz = 0;
+    int nbent = 0, nbused = 0;        // entries, bricks with at least one entry
+    long npart_rows = 0;              // sum of fp over entries (gather partial rows)
+    int4* d_bent = nullptr;           // per entry: brick, fp, value offset, partial row base
+    int* d_bfirst = nullptr;          // [nbused + 1] first entry of each used brick
+    float* d_phi = nullptr;           // dense values
+    int* d_frow = nullptr;            // [npart_rows] global projector row (-1: padding)
+    int* d_roff = nullptr;            // [nproj + 1] partial rows of each projector row (CSR)
+    int* d_rent = nullptr;
 };
 
 // ---------------------------------------------------------------------------- profiling
@@ -93,6 +105,7 @@ struct hub_ctx {
     int esize = 8;                // bytes per real component of the working type
     int bf16_terms = 3;           // HUB_MIXED_BF16: 1 = bf16 x bf16, 3 = hi/lo split products
     int stencil_variant = 0;      // tile shape chosen by the autotuner (stencil_variants)
+    int gather_dense = 0;         // real float: gather in the brick form (else point-major)
     int gemm_split = 2;           // tensor-core split-K: CTAs per SM of the Gram products
     int capturing = 0;            // work is being captured into a CUDA graph
     long long mem_gen = 0;        // bumped whenever a workspace or table is reallocated

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <numeric>
 #include <type_traits>
+#include <unordered_map>
 
 #include "hub_internal.cuh"
 #include "cplx.cuh"
@@ -214,6 +215,58 @@ k_gather(const typename VT<R, CPLX>::T* __restrict__ X, int ld, int ncol,
     }
 }
 
+// W row of a site from its inner products c (KB: gamma C; Hubbard: M C, Eq. DerED)
+template <typename R, bool CPLX>
+__device__ __forceinline__ void site_transform(const SiteDev& S, const typename VT<double, CPLX>::T* c,
+                                               const double* __restrict__ gamma, const double* __restrict__ M,
+                                               typename VT<R, CPLX>::T* __restrict__ W, int n, int ncol) {
+    using D = typename VT<double, CPLX>::T;
+    using T = typename VT<R, CPLX>::T;
+    for (int p = 0; p < S.nproj; ++p) {
+        D w = zero_of(D());
+        if (S.kind == 0) {
+            w = mulr(gamma[S.proj_off + p], c[p]);
+        } else {
+            // coefficient of phi_p: sum_m M[p][m] C_m  (M = (U/2)(I - 2D))
+            for (int m = 0; m < S.nproj; ++m) {
+                D mm;
+                if constexpr (CPLX) {
+                    const double* Mi = M + (size_t)S.hub_index * 50;
+                    mm = make_double2(Mi[2 * (p * 5 + m)], Mi[2 * (p * 5 + m) + 1]);
+                } else {
+                    mm = M[(size_t)S.hub_index * 25 + p * 5 + m];
+                }
+                w = cfma(mm, c[m], w);
+            }
+        }
+        T wv;
+        if constexpr (CPLX) wv = T{(R)w.x, (R)w.y};
+        else wv = (R)w;
+        W[(size_t)(S.proj_off + p) * ncol + n] = wv;
+    }
+}
+
+// brick form: C of each projector row from its float partials over bricks, then W
+__global__ void k_reduce_transform_dense(int nsites, int ncol, double dV, const SiteDev* __restrict__ sites,
+                                         const int* __restrict__ roff, const int* __restrict__ rent,
+                                         const float* __restrict__ part, const double* __restrict__ gamma,
+                                         const double* __restrict__ M, double* __restrict__ C,
+                                         float* __restrict__ W, int want_W) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)nsites * ncol) return;
+    const int s = (int)(t / ncol), n = (int)(t - (long)s * ncol);
+    const SiteDev S = sites[s];
+    double c[kMaxProj];
+    for (int p = 0; p < S.nproj; ++p) {
+        const int r = S.proj_off + p;
+        double acc = 0.0;
+        for (int e = roff[r]; e < roff[r + 1]; ++e) acc += (double)part[(size_t)rent[e] * ncol + n];
+        c[p] = dV * acc;
+        C[(size_t)r * ncol + n] = c[p];
+    }
+    if (want_W) site_transform<float, false>(S, c, gamma, M, W, n, ncol);
+}
+
 // reduce partials of each site and apply the coefficient transform
 template <typename R, bool CPLX>
 __global__ void k_reduce_transform(int nsites, int ncol, double dV, const SiteDev* __restrict__ sites,
@@ -236,29 +289,7 @@ __global__ void k_reduce_transform(int nsites, int ncol, double dV, const SiteDe
         c[p] = mulr(dV, acc);
         C[(size_t)(S.proj_off + p) * ncol + n] = c[p];
     }
-    if (!want_W) return;
-    for (int p = 0; p < S.nproj; ++p) {
-        D w = zero_of(D());
-        if (S.kind == 0) {
-            w = mulr(gamma[S.proj_off + p], c[p]);
-        } else {
-            // coefficient of phi_p: sum_m M[p][m] C_m  (M = (U/2)(I - 2D), Eq. DerED)
-            for (int m = 0; m < S.nproj; ++m) {
-                D mm;
-                if constexpr (CPLX) {
-                    const double* Mi = M + (size_t)S.hub_index * 50;
-                    mm = make_double2(Mi[2 * (p * 5 + m)], Mi[2 * (p * 5 + m) + 1]);
-                } else {
-                    mm = M[(size_t)S.hub_index * 25 + p * 5 + m];
-                }
-                w = cfma(mm, c[m], w);
-            }
-        }
-        T wv;
-        if constexpr (CPLX) wv = T{(R)w.x, (R)w.y};
-        else wv = (R)w;
-        W[(size_t)(S.proj_off + p) * ncol + n] = wv;
-    }
+    if (want_W) site_transform<R, CPLX>(S, c, gamma, M, W, n, ncol);
 }
 
 // ---------------------------------------------------------------------------- scatter
@@ -317,6 +348,164 @@ k_scatter(typename VT<R, CPLX>::T* __restrict__ Y, int ld, int ncol, long Nd,
             if (j < nc) {
                 T* y = Y + (size_t)(c0 + j) * ld + g;
                 *y = fmar(alpha, acc[j], *y);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------- brick form
+// Real float only.  The grid is cut into bricks of 8 x 8 x 4 points (32 rows of 8 along x;
+// point p = x + 8 row, row = y + 8 z inside the brick).  Every brick lists the functions of
+// the sites that touch it, in entries of at most 64 (a site's functions stay together, fp =
+// their count rounded up to 4), and keeps their values as a dense block [fp][256]
+// (function-major), zero where a function vanishes.  Both directions then become small dense products per brick:
+//   gather:  part[prow + f, n] = sum_p phi[p, f] X[g(p), n]    (partial inner products,
+//            summed per function over its bricks by k_reduce_transform_dense)
+//   scatter: Y[g(p), n] += alpha sum_f phi[p, f] W[frow[f], n]
+// with every X and Y element read once per brick and pass, in 16-byte rows.
+constexpr int BRX = 8, BRY = 8, BRZ = 4, BRP = BRX * BRY * BRZ, BRF = 64;
+constexpr int GD_COLS = 32, GD_XS = GD_COLS + 4;     // gather: columns per pass, smem row stride
+constexpr int SD_COLS = 32;                          // scatter: columns per pass
+
+__global__ void k_brick_fill(int npts, const int2* __restrict__ rowinfo, const SiteDev* __restrict__ sites,
+                             const float* __restrict__ vals, float* __restrict__ phi) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= npts) return;
+    const int2 ri = rowinfo[r];
+    const int np = sites[ri.y].nproj;
+    const size_t v0 = (size_t)sites[ri.y].val_off + (size_t)(r - sites[ri.y].pt_off) * np;
+    for (int p = 0; p < np; ++p) phi[ri.x + (size_t)p * BRP] = vals[v0 + p];
+}
+
+__device__ __forceinline__ long brick_point(int b, int nbx, int nby, int p, int n1, int n2, int n3, bool* ok) {
+    const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
+    const int row = p >> 3;
+    const int x = bx * BRX + (p & 7), y = by * BRY + (row & 7), z = bz * BRZ + (row >> 3);
+    *ok = x < n1 && y < n2 && z < n3;
+    return x + (long)n1 * (y + (long)n2 * z);
+}
+
+// one CTA per (entry, 32 columns): 128 threads = 16 function groups of 4 x 8 column groups
+// of 4.  The X tile is staged point-major in shared memory; values are read as float4 rows
+// from L1 (the entry's block is shared by the CTA's warps).
+__global__ void __launch_bounds__(128)
+k_gather_dense(const float* __restrict__ X, int ld, int ncol, int n1, int n2, int n3, int nbx, int nby,
+               const int4* __restrict__ bent, const float* __restrict__ phi, float* __restrict__ part) {
+    __shared__ __align__(16) float xs[BRP * GD_XS];
+    const int4 E = bent[blockIdx.x];
+    const int fp = E.y;
+    const int c0 = blockIdx.y * GD_COLS;
+    // X tile: 32 columns x 32 rows of 8 points (two 16-byte loads, one whole sector, per
+    // thread; consecutive threads take consecutive columns, so the transposing stores into
+    // the point-major tile hit distinct banks)
+    for (int i = threadIdx.x; i < GD_COLS * 32; i += blockDim.x) {
+        const int c = i & (GD_COLS - 1), row = i / GD_COLS;
+        const int p = row * 8;
+        bool ok0, ok1;
+        const long g = brick_point(E.x, nbx, nby, p, n1, n2, n3, &ok0);
+        brick_point(E.x, nbx, nby, p + 4, n1, n2, n3, &ok1);
+        float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = va;
+        if (c0 + c < ncol) {
+            const float* src = X + (size_t)(c0 + c) * ld + g;
+            if (ok0) va = *reinterpret_cast<const float4*>(src);
+            if (ok1) vb = *reinterpret_cast<const float4*>(src + 4);
+        }
+        const float v[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) xs[(p + k) * GD_XS + c] = v[k];
+    }
+    __syncthreads();
+    const int fg = threadIdx.x >> 3, cg = threadIdx.x & 7;
+    if (fg * 4 >= fp) return;
+    const float* ph = phi + E.z + (size_t)fg * 4 * BRP;
+    float acc[4][4] = {};
+#pragma unroll 4
+    for (int p = 0; p < BRP; ++p) {
+        const float4 x = *reinterpret_cast<const float4*>(xs + p * GD_XS + cg * 4);
+        const float fv[4] = {ph[p], ph[BRP + p], ph[2 * BRP + p], ph[3 * BRP + p]}, xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[k][j] = fmaf(fv[k], xv[j], acc[k][j]);
+    }
+    const int cb = c0 + cg * 4;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float* out = part + (size_t)(E.w + fg * 4 + k) * ncol;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (cb + j < ncol) out[cb + j] = acc[k][j];
+    }
+}
+
+// one CTA per brick, looping over the columns SD_COLS at a time: 256 threads = 8 column
+// groups (of 4) x 32 rows (of 8 points).  Values are read from global memory function-major
+// (a row's 8 points are 32 contiguous bytes; the entry's block stays in L1/L2 over the
+// passes), W rows of the pass are staged in shared memory and read as one broadcast per warp.
+// (Measured on the rutile workload, this beat packed f32x2 FMAs, a 4-row x 8-group warp
+// mapping, and staging the values in shared memory.)
+__global__ void __launch_bounds__(256, 3)
+k_scatter_dense(float* __restrict__ Y, int ld, int ncol, int n1, int n2, int n3, int nbx, int nby,
+                const int4* __restrict__ bent, const int* __restrict__ bfirst, const float* __restrict__ phi,
+                const int* __restrict__ frow, const float* __restrict__ W, float alpha,
+                const double* __restrict__ alpha_dev) {
+    __shared__ __align__(16) float ws[BRF * SD_COLS];
+    if (alpha_dev) alpha = (float)alpha_dev[0];
+    const int e0 = bfirst[blockIdx.x], e1 = bfirst[blockIdx.x + 1];
+    const int b = bent[e0].x;
+    const int cg = threadIdx.x >> 5, row = threadIdx.x & 31;
+    bool ok0, ok1;
+    const long g0 = brick_point(b, nbx, nby, row * 8, n1, n2, n3, &ok0);
+    brick_point(b, nbx, nby, row * 8 + 4, n1, n2, n3, &ok1);
+    for (int c0 = 0; c0 < ncol; c0 += SD_COLS) {
+        float acc[8][4] = {};
+        for (int e = e0; e < e1; ++e) {
+            const int4 E = bent[e];
+            const int fp = E.y;
+            __syncthreads();                       // previous pass / entry fully read
+            for (int i = threadIdx.x; i < fp * SD_COLS; i += blockDim.x) {
+                const int f = i / SD_COLS, c = i - f * SD_COLS;
+                const int r = frow[E.w + f];
+                ws[i] = (r >= 0 && c0 + c < ncol) ? W[(size_t)r * ncol + c0 + c] : 0.f;
+            }
+            __syncthreads();
+            const float* ph = phi + E.z + row * 8;
+#pragma unroll 4
+            for (int f = 0; f < fp; ++f) {
+                const float4 pa = __ldg(reinterpret_cast<const float4*>(ph + (size_t)f * BRP));
+                const float4 pb = __ldg(reinterpret_cast<const float4*>(ph + (size_t)f * BRP + 4));
+                const float4 w4 = *reinterpret_cast<const float4*>(ws + f * SD_COLS + cg * 4);
+                const float pv[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
+                const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(pv[i], wv[j], acc[i][j]);
+            }
+        }
+        float4 ya[4], yb[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = c0 + cg * 4 + j;
+            const float* y = Y + (size_t)c * ld + g0;
+            ya[j] = (ok0 && c < ncol) ? *reinterpret_cast<const float4*>(y) : make_float4(0.f, 0.f, 0.f, 0.f);
+            yb[j] = (ok1 && c < ncol) ? *reinterpret_cast<const float4*>(y + 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = c0 + cg * 4 + j;
+            float* y = Y + (size_t)c * ld + g0;
+            if (ok0 && c < ncol) {
+                float4 v = ya[j];
+                v.x = fmaf(alpha, acc[0][j], v.x); v.y = fmaf(alpha, acc[1][j], v.y);
+                v.z = fmaf(alpha, acc[2][j], v.z); v.w = fmaf(alpha, acc[3][j], v.w);
+                *reinterpret_cast<float4*>(y) = v;
+            }
+            if (ok1 && c < ncol) {
+                float4 v = yb[j];
+                v.x = fmaf(alpha, acc[4][j], v.x); v.y = fmaf(alpha, acc[5][j], v.y);
+                v.z = fmaf(alpha, acc[6][j], v.z); v.w = fmaf(alpha, acc[7][j], v.w);
+                *reinterpret_cast<float4*>(y + 4) = v;
             }
         }
     }
@@ -410,13 +599,113 @@ int upload(hub_t h, Tp** dptr, const std::vector<Tp>& v) {
 void free_table(Table& t) {
     void* ptrs[] = {t.d_sites, t.d_items, t.d_item_first, t.d_idx, t.d_vals, t.d_csr_off,
                     t.d_csr_ent, t.d_gamma, t.d_hub_sites, t.d_U,
-                    t.d_M[0], t.d_M[1]};
+                    t.d_M[0], t.d_M[1], t.d_bent, t.d_bfirst, t.d_phi, t.d_frow, t.d_roff,
+                    t.d_rent};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     t = Table();
 }
 
 static int floordiv_host(double a) { return (int)std::floor(a); }
+
+// Brick form of the tables (real float working type, n1 a multiple of 4): entries, dense
+// values copied from the point-major table, and the reduction lists of the gather.
+static int build_bricks(hub_t h, Table& t, const std::vector<std::vector<int>>& site_pts) {
+    const int n1 = h->n1, n2 = h->n2;
+    t.nbx = (h->n1 + BRX - 1) / BRX;
+    t.nby = (h->n2 + BRY - 1) / BRY;
+    t.nbz = (h->n3 + BRZ - 1) / BRZ;
+    const long nb = (long)t.nbx * t.nby * t.nbz;
+    auto brick_of = [&](int g) -> long {
+        const int x = g % n1, y = (g / n1) % n2, z = g / (n1 * n2);
+        return x / BRX + t.nbx * (y / BRY + (long)t.nby * (z / BRZ));
+    };
+    auto point_in = [&](int g) -> int {
+        const int x = g % n1, y = (g / n1) % n2, z = g / (n1 * n2);
+        return (x % BRX) + BRX * ((y % BRY) + BRY * (z % BRZ));
+    };
+    std::vector<std::vector<int>> bs(nb);           // sites touching each brick, ascending
+    for (int s = 0; s < t.nsites; ++s) {
+        std::vector<long> bl;
+        bl.reserve(site_pts[s].size());
+        for (int g : site_pts[s]) bl.push_back(brick_of(g));
+        std::sort(bl.begin(), bl.end());
+        bl.erase(std::unique(bl.begin(), bl.end()), bl.end());
+        for (long b : bl) bs[b].push_back(s);
+    }
+    std::vector<int4> bent;
+    std::vector<int> bfirst, frow;
+    std::unordered_map<long long, std::pair<int, int>> where;   // (site, brick) -> entry, offset
+    long phi_off = 0, prow = 0;
+    for (long b = 0; b < nb; ++b) {
+        const std::vector<int>& L = bs[b];
+        if (L.empty()) continue;
+        bfirst.push_back((int)bent.size());
+        size_t i = 0;
+        while (i < L.size()) {
+            int f = 0;
+            size_t j = i;
+            const int e = (int)bent.size();
+            while (j < L.size() && f + t.h_sites[L[j]].nproj <= BRF) {
+                where[(long long)L[j] * nb + b] = {e, f};
+                f += t.h_sites[L[j]].nproj;
+                ++j;
+            }
+            const int fp = (f + 3) & ~3;
+            bent.push_back(make_int4((int)b, fp, (int)phi_off, (int)prow));
+            for (size_t k = i; k < j; ++k)
+                for (int q = 0; q < t.h_sites[L[k]].nproj; ++q) frow.push_back(t.h_sites[L[k]].proj_off + q);
+            for (int q = f; q < fp; ++q) frow.push_back(-1);
+            phi_off += (long)fp * BRP;
+            prow += fp;
+            if (phi_off >= (1L << 31) || prow >= (1L << 31)) return HUB_OK;    // stay point-major
+            i = j;
+        }
+    }
+    bfirst.push_back((int)bent.size());
+    std::vector<int2> rowinfo(t.npts);
+    for (int s = 0; s < t.nsites; ++s) {
+        const SiteDev& S = t.h_sites[s];
+        for (int l = 0; l < S.npts; ++l) {
+            const int g = site_pts[s][l];
+            const auto& w = where.at((long long)s * nb + brick_of(g));
+            const int4& E = bent[w.first];
+            rowinfo[S.pt_off + l] = make_int2(E.z + w.second * BRP + point_in(g), s);
+        }
+    }
+    std::vector<int> roff(t.nproj + 1, 0), rent(prow);
+    for (long r = 0; r < prow; ++r)
+        if (frow[r] >= 0) roff[frow[r] + 1]++;
+    for (int r = 0; r < t.nproj; ++r) roff[r + 1] += roff[r];
+    {
+        std::vector<int> fill(roff.begin(), roff.end() - 1);
+        for (long r = 0; r < prow; ++r)
+            if (frow[r] >= 0) rent[fill[frow[r]]++] = (int)r;
+    }
+    int rc;
+    int2* d_rowinfo = nullptr;
+    if ((rc = upload(h, &t.d_bent, bent))) return rc;
+    if ((rc = upload(h, &t.d_bfirst, bfirst))) return rc;
+    if ((rc = upload(h, &t.d_frow, frow))) return rc;
+    if ((rc = upload(h, &t.d_roff, roff))) return rc;
+    if ((rc = upload(h, &t.d_rent, rent))) return rc;
+    if ((rc = upload(h, &d_rowinfo, rowinfo))) return rc;
+    HUB_CUDA_TRY(h, cudaMalloc((void**)&t.d_phi, (size_t)phi_off * sizeof(float)));
+    HUB_CUDA_TRY(h, cudaMemsetAsync(t.d_phi, 0, (size_t)phi_off * sizeof(float), h->stream));
+    {
+        ProfScope ps(h, HUB_K_TABLE);
+        k_brick_fill<<<(t.npts + 255) / 256, 256, 0, h->stream>>>(t.npts, d_rowinfo, t.d_sites,
+                                                                (const float*)t.d_vals, t.d_phi);
+    }
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    HUB_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    cudaFree(d_rowinfo);
+    t.nbent = (int)bent.size();
+    t.nbused = (int)bfirst.size() - 1;
+    t.npart_rows = prow;
+    t.dense = 1;
+    return HUB_OK;
+}
 
 int build_tables(hub_t h, int natoms, const double* pos, const int* kb_nchan, const int* kb_l,
                  const double* kb_rs, const double* kb_gamma, const double* kb_rc,
@@ -589,6 +878,10 @@ int build_tables(hub_t h, int natoms, const double* pos, const int* kb_nchan, co
         }
         HUB_CUDA_TRY(h, cudaGetLastError());
     }
+    if (h->esize == 4 && !h->cplx && h->n1 % 4 == 0 && t.nsites > 0) {
+        HUB_CUDA_TRY(h, cudaStreamSynchronize(h->stream));     // values are ready
+        if ((rc = build_bricks(h, t, site_pts))) return rc;
+    }
     const size_t mbytes = (size_t)std::max(t.nhub, 1) * 25 * sizeof(double) * (h->cplx ? 2 : 1);
     for (int s = 0; s < 2; ++s) {
         HUB_CUDA_TRY(h, cudaMalloc((void**)&t.d_M[s], mbytes));
@@ -607,6 +900,45 @@ int build_tables(hub_t h, int natoms, const double* pos, const int* kb_nchan, co
     h->proj = std::move(t);
     h->mem_gen++;
     return HUB_OK;
+}
+
+static int gather_dense(hub_t h, const void* X, int ncol, int ld, int spin, bool want_W) {
+    Table& t = h->proj;
+    int rc;
+    if ((rc = ensure(h, &h->d_part, &h->part_bytes, (size_t)t.npart_rows * ncol * sizeof(float)))) return rc;
+    if ((rc = ensure(h, &h->d_C, &h->C_bytes, (size_t)t.nproj * ncol * sizeof(double)))) return rc;
+    if ((rc = ensure(h, &h->d_W, &h->W_bytes, (size_t)t.nproj * ncol * sizeof(float)))) return rc;
+    {
+        ProfScope ps(h, HUB_K_GATHER);
+        dim3 g(t.nbent, (ncol + GD_COLS - 1) / GD_COLS);
+        k_gather_dense<<<g, 128, 0, h->stream>>>((const float*)X, ld, ncol, h->n1, h->n2, h->n3, t.nbx, t.nby,
+                                                 t.d_bent, t.d_phi, (float*)h->d_part);
+    }
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    const long nthr = (long)t.nsites * ncol;
+    {
+        ProfScope ps(h, HUB_K_TRANSFORM);
+        k_reduce_transform_dense<<<(unsigned)((nthr + 127) / 128), 128, 0, h->stream>>>(
+            t.nsites, ncol, h->dV, t.d_sites, t.d_roff, t.d_rent, (const float*)h->d_part, t.d_gamma,
+            t.d_M[spin], (double*)h->d_C, (float*)h->d_W, want_W ? 1 : 0);
+    }
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    return HUB_OK;
+}
+
+static int scatter_dense(hub_t h, void* Y, int ncol, int ld, double alpha, const double* alpha_dev) {
+    Table& t = h->proj;
+    ProfScope ps(h, HUB_K_SCATTER);
+    k_scatter_dense<<<t.nbused, 256, 0, h->stream>>>((float*)Y, ld, ncol, h->n1, h->n2, h->n3, t.nbx, t.nby,
+                                                        t.d_bent, t.d_bfirst, t.d_phi, t.d_frow,
+                                                        (const float*)h->d_W, (float)alpha, alpha_dev);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    return HUB_OK;
+}
+
+// the brick form applies to real float blocks whose columns start on 16-byte boundaries
+static bool use_dense(hub_t h, const void* A, int ld) {
+    return h->proj.dense && h->esize == 4 && !h->cplx && ld % 4 == 0 && (uintptr_t)A % 16 == 0;
 }
 
 template <typename R, bool CPLX>
@@ -639,6 +971,7 @@ static int gather_t(hub_t h, const void* X, int ncol, int ld, int spin, bool wan
 
 int launch_gather(hub_t h, const void* X, int ncol, int ld, int spin, bool want_W) {
     if (ncol == 0 || h->proj.nsites == 0) return HUB_OK;
+    if (h->gather_dense && use_dense(h, X, ld)) return gather_dense(h, X, ncol, ld, spin, want_W);
     if (h->esize == 8) return h->cplx ? gather_t<double, true>(h, X, ncol, ld, spin, want_W)
                                       : gather_t<double, false>(h, X, ncol, ld, spin, want_W);
     return h->cplx ? gather_t<float, true>(h, X, ncol, ld, spin, want_W)
@@ -661,6 +994,7 @@ static int scatter_t(hub_t h, void* Y, int ncol, int ld, double alpha, const dou
 
 int launch_scatter(hub_t h, void* Y, int ncol, int ld, double alpha, const double* alpha_dev) {
     if (ncol == 0 || h->proj.nsites == 0) return HUB_OK;
+    if (use_dense(h, Y, ld)) return scatter_dense(h, Y, ncol, ld, alpha, alpha_dev);
     if (h->esize == 8) return h->cplx ? scatter_t<double, true>(h, Y, ncol, ld, alpha, alpha_dev)
                                       : scatter_t<double, false>(h, Y, ncol, ld, alpha, alpha_dev);
     return h->cplx ? scatter_t<float, true>(h, Y, ncol, ld, alpha, alpha_dev)

@@ -89,6 +89,26 @@ def test_apply_H_every_stencil_variant(prec):
             hb.set_tuning(hb.get_tuning()["n_variants"])
 
 
+@pytest.mark.parametrize("n,natoms", [((12, 10, 9), 3), ((16, 16, 16), 12)])
+def test_apply_H_fp32_brick_edges_and_crowded_bricks(n, natoms):
+    """Real float blocks use the 8x8x4 brick form of the projectors: a grid that ends inside
+    bricks in x, y and z, and a cell so crowded that bricks carry more than 64 functions
+    (several entries per brick)."""
+    wl = w.small_test_system(n=n, ncol=19, natoms=natoms, seed=21, hub_rc=2.5, kb_rc=2.5)
+    X = wl.orbitals()
+    ref = oracle_ham(wl, D=wl.D0[0]).apply(X.T).T
+    hb = make_hub(wl, HUB_F32)
+    hb.set_occupation_matrix(0, wl.D0[0])
+    Xd = to_dev(X, torch.float32)
+    for form in (0, 1):                     # point-major and brick-form gather
+        hb.set_tuning(gather_form=form)
+        Yd = torch.empty_like(Xd)
+        hb.apply_H(0, Xd, Yd)
+        err = rel(Yd.cpu().numpy().astype(np.float64), ref)
+        print(n, natoms, form, "fp32 rel err", err)
+        assert err < 5e-6
+
+
 @pytest.mark.parametrize("name", ["ragged", "bloch"])
 def test_apply_H_fp32(name):
     wl = systems()[name]
