@@ -154,6 +154,38 @@ def cpu_oracle_sample(workload: str, seconds: float, cols: int = 2):
 
 
 # ------------------------------------------------------------------------------ hub arm
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path))["hbm_gbs"], "measured (MEASURED_PEAKS.json hbm_gbs)"
+    return 6800.0, "fallback 6.8 TB/s"
+
+
+def kernel_roofline(name, t_n, wl, prec, function_points):
+    """Roofline of one hot kernel from its summed event time and launch count (every timed
+    launch processes the whole ncol-column block).  Algorithmic work per launch:
+      stencil  FP64: 59 flop per point-orbital against the FP64 pipe; float: 12 B per
+               point-orbital (read Y and Yprev, write Yout) against HBM
+      gather   FP64: 2 flop per function-point and column against the FP64 pipe; float: one
+               read of the block (4 B per point-orbital) against HBM
+      scatter  FP64: as the gather; float: read and write of the block (8 B per point-orbital)"""
+    t_ms, n = t_n
+    per_launch_s = t_ms / n / 1e3
+    pts_orb = wl.Nd * wl.ncol
+    if prec == "f64":
+        flops = (STENCIL_FLOP * pts_orb) if name == "stencil" else 2.0 * function_points * wl.ncol
+        achieved = flops / per_launch_s / 1e12
+        peak = FP64_PEAK_GFLOPS / 1e3
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": name,
+                "peak_source": "FP64 pipe: 152 SM x 2 FMA/clk x 2.07 GHz (probe: 1.196)"}
+    per_pt = {"stencil": 12.0, "gather": 4.0, "scatter": 8.0}[name]
+    gbs = per_pt * pts_orb / per_launch_s / 1e9
+    peak, src = hbm_peak()
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak, "traffic": None,
+            "kernel": name, "peak_source": src}
+
+
 def run_hub(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -252,28 +284,17 @@ def run_hub(args, rank, world, local_rank):
                "converged": bool(res["converged"]), "E_Ha": res["E"], "E_U_Ha": res["E_U"],
                "criterion": "|dE|/atom < 1e-5 Ha twice and max|dD| < 1e-4"}
 
-    # dominant kernel and its roofline
+    # rooflines of the three hot kernels, and the dominant kernel's
+    fpts = hub.projector_stats()["function_points"]
+    rooflines = {k: kernel_roofline(k, prof[k], wl, args.prec, fpts) for k in ("stencil", "gather", "scatter")
+                 if k in prof}
     dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 0))
-    roof = None
-    if dom[0] == "stencil":
-        flops = STENCIL_FLOP * wl.Nd * wl.ncol * dom[1][1]      # every timed launch: ncol columns
-        achieved = flops / (dom[1][0] / 1e3) / 1e12
-        if args.prec == "f64":
-            peak = FP64_PEAK_GFLOPS / 1e3
-            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "kernel": "k_stencil<double>",
-                    "peak_source": "FP64 pipe: 152 SM x 2 FMA/clk x 2.07 GHz (probe: 1.196)"}
-        else:
-            bytes_ = 12.0 * wl.Nd * wl.ncol * dom[1][1]
-            gbs = bytes_ / (dom[1][0] / 1e3) / 1e9
-            peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
-                if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
-            roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
-                    "frac": gbs / peak, "traffic": None, "kernel": "k_stencil<float>"}
+    roof = rooflines.get(dom[0])
     breakdown = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / ms, 4)}
                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
     return {"value": value, "ms": ms, "launches": launches, "e2e": e2e, "tts": tts,
-            "roofline": roof, "kernels": breakdown, "clocks": clocks, "last": last, "wl": wl}
+            "roofline": roof, "rooflines": rooflines, "kernels": breakdown, "clocks": clocks, "last": last,
+            "wl": wl}
 
 
 def scf_compare(args):
@@ -605,7 +626,7 @@ def main():
                        "step": "one SCF iteration (filter + Rayleigh-Ritz per spin, occupations, D, E_U, Pulay)",
                        "l2": "inputs larger than L2 (each orbital block %.2f GB)" % (wl.Nd * wl.ncol * (8 if args.prec == 'f64' else 4) / 1e9),
                        "parallelism": f"replicas x{world}"},
-            "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"],
+            "roofline": r["roofline"], "rooflines": r["rooflines"], "cpu_baseline": cpu, "e2e": r["e2e"],
             "gpu_launches": r["launches"], "clocks": r["clocks"],
             "kernels": r["kernels"],
         }

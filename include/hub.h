@@ -358,6 +358,12 @@ int hub_profile_read(hub_t h, int kind, double* total_ms, long long* launches);
 /* Kernels launched by this handle since it was created. */
 int hub_launch_count(hub_t h, long long* launches);
 
+/* Size of the projector tables of the handle (after hub_set_atoms_projectors):
+ * function_points = sum over sites of (grid points in the site's support) x (functions),
+ * the number of multiply-adds per column of one gather or scatter; site_points = sum of the
+ * supports.  Either pointer may be NULL. */
+int hub_projector_stats(hub_t h, long long* function_points, long long* site_points);
+
 /* Library build information: writes a short string (arch, version) into buf. */
 int hub_version(char* buf, int len);
 

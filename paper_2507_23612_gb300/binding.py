@@ -78,6 +78,7 @@ _SIGS = {
     "hub_mlp_train_step": [_P, _P, _P, _I, C.c_float, C.POINTER(C.c_float)],
     "hub_set_tuning": [_P, _I, _I, _I],
     "hub_get_tuning": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
+    "hub_projector_stats": [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)],
     "hub_profile": [_P, _I],
     "hub_profile_read": [_P, _I, _PD, C.POINTER(C.c_longlong)],
     "hub_launch_count": [_P, C.POINTER(C.c_longlong)],
@@ -299,6 +300,11 @@ class Hub:
             if n.value:
                 out[name] = (t.value, n.value)
         return out
+
+    def projector_stats(self) -> dict:
+        fp, sp = C.c_longlong(), C.c_longlong()
+        self._check(self.lib.hub_projector_stats(self.h, C.byref(fp), C.byref(sp)), "hub_projector_stats")
+        return {"function_points": fp.value, "site_points": sp.value}
 
     def launch_count(self) -> int:
         n = C.c_longlong()

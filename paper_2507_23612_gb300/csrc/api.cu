@@ -409,6 +409,13 @@ int hub_occupation(hub_t h, int spin, const void* X, int ncol, int ld, const dou
     return HUB_OK;
 }
 
+int hub_projector_stats(hub_t h, long long* function_points, long long* site_points) {
+    if (!h) return HUB_EINVAL;
+    if (function_points) *function_points = h->proj.nvals;
+    if (site_points) *site_points = h->proj.npts;
+    return HUB_OK;
+}
+
 int hub_lanczos_bound(hub_t h, int spin, int steps, const void* v0, double* lo_out, double* up_out) {
     int rc = check_block(h, spin, v0, 1, (int)h->Nd);
     if (rc) return rc;

@@ -171,12 +171,21 @@ __device__ __forceinline__ void pair_of(int step, int k, int N, int& p, int& q) 
     if (p > q) { const int t = p; p = q; q = t; }
 }
 
-__global__ void k_jacobi(double* A, double* V, int n, int N, double* rot, int max_sweeps, double tol,
+// Parallel cyclic Jacobi with the round-robin pair schedule.  Each step applies n/2
+// disjoint rotations.  Every CTA computes all rotation angles of a step itself from the
+// current matrix (identical inputs and operations, so all copies agree), and the step
+// writes the rotated matrix into the other of two buffers: nothing the step reads is
+// written during it, so one grid barrier per step suffices.  V is rotated in place (only
+// the step's own rotations touch a given V element).
+__global__ void k_jacobi(double* A, double* Ab, double* V, int n, int N, int max_sweeps, double tol,
                          unsigned int* bar, int* flags, unsigned long long* red, int* sweeps_out) {
+    extern __shared__ double rot[];               // [N]: cosine and sine of each pair
     const unsigned int nb = gridDim.x;
     const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const long nthr = (long)gridDim.x * blockDim.x;
     const int H = N / 2;
+    double* cur = A;
+    double* nxt = Ab;
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         // convergence: max |a_ij| (i != j) against max |a_ii|
@@ -184,7 +193,7 @@ __global__ void k_jacobi(double* A, double* V, int n, int N, double* rot, int ma
         double off = 0.0, dia = 0.0;
         for (long e = tid; e < (long)n * n; e += nthr) {
             const int i = (int)(e / n), j = (int)(e % n);
-            const double v = fabs(A[e]);
+            const double v = fabs(cur[e]);
             if (i == j) dia = fmax(dia, v); else off = fmax(off, v);
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -211,15 +220,15 @@ __global__ void k_jacobi(double* A, double* V, int n, int N, double* rot, int ma
         // pairs whose coupling is below this are left alone (threshold Jacobi)
         const double skip = 1e-3 * tol * fmax(gdia, 1e-300);
         for (int step = 0; step < N - 1; ++step) {
-            // phase 1: the n/2 disjoint rotations of this step
-            for (long k = tid; k < H; k += nthr) {
+            // phase 1 (per CTA): the n/2 disjoint rotations of this step
+            for (int k = threadIdx.x; k < H; k += blockDim.x) {
                 int p, q;
-                pair_of(step, (int)k, N, p, q);
+                pair_of(step, k, N, p, q);
                 double c = 1.0, s = 0.0;
                 if (q < n) {
-                    const double apq = A[(size_t)p * n + q];
+                    const double apq = cur[(size_t)p * n + q];
                     if (fabs(apq) > skip) {
-                        const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+                        const double app = cur[(size_t)p * n + p], aqq = cur[(size_t)q * n + q];
                         const double theta = (aqq - app) / (2.0 * apq);
                         double t;
                         if (fabs(theta) > 1e150) t = 0.5 / theta;
@@ -231,37 +240,39 @@ __global__ void k_jacobi(double* A, double* V, int n, int N, double* rot, int ma
                 rot[2 * k] = c;
                 rot[2 * k + 1] = s;
             }
-            if (!grid_barrier(bar, nb, flags)) return;
-            // phase 2, in place: every 2x2 block (P, Q) <- J_P^T B J_Q (each block is read and
-            // written by one thread), and V <- V J; blocks with two identity rotations are skipped
+            __syncthreads();
+            // phase 2: every 2x2 block (P, Q) of the next matrix <- J_P^T B J_Q (blocks of two
+            // identity rotations are copied), and V <- V J in place
             const long nblk = (long)H * H;
             for (long e = tid; e < nblk + (long)n * H; e += nthr) {
                 if (e < nblk) {
                     const int P = (int)(e / H), Q = (int)(e % H);
                     const double s1 = rot[2 * P + 1], s2 = rot[2 * Q + 1];
-                    if (s1 == 0.0 && s2 == 0.0) continue;
                     const double c1 = rot[2 * P], c2 = rot[2 * Q];
                     int p1, q1, p2, q2;
                     pair_of(step, P, N, p1, q1);
                     pair_of(step, Q, N, p2, q2);
-                    auto ld = [&](int i, int j) { return (i < n && j < n) ? A[(size_t)i * n + j] : 0.0; };
+                    auto ld = [&](int i, int j) { return (i < n && j < n) ? cur[(size_t)i * n + j] : 0.0; };
                     const double b00 = ld(p1, p2), b01 = ld(p1, q2), b10 = ld(q1, p2), b11 = ld(q1, q2);
-                    const double r00 = c1 * b00 - s1 * b10, r01 = c1 * b01 - s1 * b11;
-                    const double r10 = s1 * b00 + c1 * b10, r11 = s1 * b01 + c1 * b11;
-                    double n00 = c2 * r00 - s2 * r01, n01 = s2 * r00 + c2 * r01;
-                    double n10 = c2 * r10 - s2 * r11, n11 = s2 * r10 + c2 * r11;
-                    if (P == Q && q1 < n) {
-                        // the rotated pair: exact zero off-diagonal, diagonal by the t-update
-                        const double t = s1 / c1;
-                        n00 = b00 - t * b01;
-                        n11 = b11 + t * b01;
-                        n01 = 0.0;
-                        n10 = 0.0;
+                    double n00 = b00, n01 = b01, n10 = b10, n11 = b11;
+                    if (s1 != 0.0 || s2 != 0.0) {
+                        const double r00 = c1 * b00 - s1 * b10, r01 = c1 * b01 - s1 * b11;
+                        const double r10 = s1 * b00 + c1 * b10, r11 = s1 * b01 + c1 * b11;
+                        n00 = c2 * r00 - s2 * r01; n01 = s2 * r00 + c2 * r01;
+                        n10 = c2 * r10 - s2 * r11; n11 = s2 * r10 + c2 * r11;
+                        if (P == Q && q1 < n) {
+                            // the rotated pair: exact zero off-diagonal, diagonal by the t-update
+                            const double t = s1 / c1;
+                            n00 = b00 - t * b01;
+                            n11 = b11 + t * b01;
+                            n01 = 0.0;
+                            n10 = 0.0;
+                        }
                     }
-                    if (p1 < n && p2 < n) A[(size_t)p1 * n + p2] = n00;
-                    if (p1 < n && q2 < n) A[(size_t)p1 * n + q2] = n01;
-                    if (q1 < n && p2 < n) A[(size_t)q1 * n + p2] = n10;
-                    if (q1 < n && q2 < n) A[(size_t)q1 * n + q2] = n11;
+                    if (p1 < n && p2 < n) nxt[(size_t)p1 * n + p2] = n00;
+                    if (p1 < n && q2 < n) nxt[(size_t)p1 * n + q2] = n01;
+                    if (q1 < n && p2 < n) nxt[(size_t)q1 * n + p2] = n10;
+                    if (q1 < n && q2 < n) nxt[(size_t)q1 * n + q2] = n11;
                 } else {
                     const long f = e - nblk;
                     const int r = (int)(f / H), P = (int)(f % H);
@@ -277,8 +288,11 @@ __global__ void k_jacobi(double* A, double* V, int n, int N, double* rot, int ma
                 }
             }
             if (!grid_barrier(bar, nb, flags)) return;
+            double* t = cur; cur = nxt; nxt = t;
         }
     }
+    if (cur != A)
+        for (long e = tid; e < (long)n * n; e += nthr) A[e] = cur[e];
     if (tid == 0) *sweeps_out = sweep;
 }
 
@@ -356,11 +370,11 @@ int dense_jacobi_eigh(hub_t h, double* A, double* V, double* eig, int n) {
     const int N = n + (n & 1);
     const size_t nn = (size_t)n * n;
     int rc;
-    size_t need = (nn + (size_t)N + 8) * sizeof(double);
+    size_t need = (2 * nn + 8) * sizeof(double);
     if ((rc = ensure(h, &h->d_work2, &h->work2_bytes, std::max(need, h->work2_bytes)))) return rc;
     double* Vt = (double*)h->d_work2;
-    double* rot = Vt + nn;
-    unsigned long long* red = (unsigned long long*)(rot + N);   // 4 slots
+    double* Ab = Vt + nn;                                        // second matrix buffer
+    unsigned long long* red = (unsigned long long*)(Ab + nn);   // 4 slots
     int* sweeps = h->d_flags + 6;
     {
         ProfScope ps(h, HUB_K_EIG_MISC);
@@ -370,7 +384,9 @@ int dense_jacobi_eigh(hub_t h, double* A, double* V, double* eig, int n) {
     HUB_CUDA_TRY(h, cudaMemsetAsync(red, 0, 4 * sizeof(unsigned long long), h->stream));
     HUB_CUDA_TRY(h, cudaMemsetAsync(h->d_bar, 0, 4 * sizeof(unsigned int), h->stream));
     int per_sm = 0;
-    HUB_CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, 256, 0));
+    const size_t rot_bytes = (size_t)N * sizeof(double);
+    if (rot_bytes > 48 * 1024) return fail(h, HUB_EINVAL, "subspace too large for the Jacobi solver");
+    HUB_CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, 256, rot_bytes));
     int blocks = std::max(1, std::min(per_sm, 1)) * h->num_sms;
     const long work = (long)(N / 2) * (N / 2) + (long)n * (N / 2);
     blocks = (int)std::min<long>(blocks, std::max<long>(1, (work + 255) / 256));
@@ -378,10 +394,10 @@ int dense_jacobi_eigh(hub_t h, double* A, double* V, double* eig, int n) {
     double tol = 1e-13;
     unsigned int* bar = h->d_bar;
     int* flags = h->d_flags;
-    void* args[] = {&A, &Vt, &n, (void*)&N, &rot, &max_sweeps, &tol, &bar, &flags, &red, &sweeps};
+    void* args[] = {&A, &Ab, &Vt, &n, (void*)&N, &max_sweeps, &tol, &bar, &flags, &red, &sweeps};
     {
         ProfScope ps(h, HUB_K_JACOBI);
-        HUB_CUDA_TRY(h, cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(blocks), dim3(256), args, 0,
+        HUB_CUDA_TRY(h, cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(blocks), dim3(256), args, rot_bytes,
                                                     h->stream));
     }
     {
