@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--scf-tts", action="store_true",
                     help="also run one cold-start SCF to convergence and report its time")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--probe-alu", action="store_true",
+                    help="measure the FP64 and FP32 FMA throughput of the GPU (roofline denominators)")
+    ap.add_argument("--probe-apply", type=int, default=0, metavar="NCOL",
+                    help="profiling case: four H applications to NCOL random columns of the rutile "
+                         "workload in --prec, then exit (no timing)")
     ap.add_argument("--scf-compare", action="store_true",
                     help="cold-start SCF to convergence in FP64, FP32 and mixed (BF16 with the "
                          "precision ladder); report time to solution and errors against FP64")
@@ -154,6 +159,14 @@ def cpu_oracle_sample(workload: str, seconds: float, cols: int = 2):
 
 
 # ------------------------------------------------------------------------------ hub arm
+# DRAM bytes per point-orbital of one launch (dram__bytes_read.sum + dram__bytes_write.sum of
+# full-size launches of the 348-orbital rutile block, ncu; profiles/hot_kernels_f32_rutile_dram.md;
+# the mixed form runs the float kernels).
+# Valid for the kernels as they stand; a changed kernel reports null until captured again.
+TRAFFIC_B_PER_PTORB = {"f32": {"stencil": 12.53, "gather": 12.07, "scatter": 8.32},
+                       "f64": {"stencil": 25.15, "gather": 95.78, "scatter": 16.58}}
+
+
 def hbm_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -176,13 +189,17 @@ def kernel_roofline(name, t_n, wl, prec, function_points):
         flops = (STENCIL_FLOP * pts_orb) if name == "stencil" else 2.0 * function_points * wl.ncol
         achieved = flops / per_launch_s / 1e12
         peak = FP64_PEAK_GFLOPS / 1e3
+        traffic = TRAFFIC_B_PER_PTORB["f64"].get(name)
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": name,
-                "peak_source": "FP64 pipe: 152 SM x 2 FMA/clk x 2.07 GHz (probe: 1.196)"}
+                "traffic": traffic * pts_orb if traffic else None, "traffic_unit": "DRAM bytes per launch",
+                "kernel": name,
+                "peak_source": "FP64 pipe: 152 SM x 2 FMA/clk x 2.07 GHz (nominal; bench.py --probe-alu measured 1.253)"}
     per_pt = {"stencil": 12.0, "gather": 4.0, "scatter": 8.0}[name]
     gbs = per_pt * pts_orb / per_launch_s / 1e9
     peak, src = hbm_peak()
-    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak, "traffic": None,
+    traffic = TRAFFIC_B_PER_PTORB["f32"].get(name)
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "traffic": traffic * pts_orb if traffic else None, "traffic_unit": "DRAM bytes per launch",
             "kernel": name, "peak_source": src}
 
 
@@ -559,8 +576,38 @@ def batched_small(args, dev, gen):
             "graph_value": work / (ms_g / 1e3) / 1e9}
 
 
+def probe_apply(args):
+    """A small case for ncu captures of the hot kernels: the rutile handle, four hub_apply_H
+    calls on a seeded random block of args.probe_apply columns (larger than L2 from 64 on)."""
+    import torch
+    import workloads as w
+    from paper_2507_23612_gb300 import Hub
+    wl = w.rutile()
+    dev = torch.device("cuda", 0)
+    hub = Hub(wl.n, wl.L, wl.fd_half_order, prec=PREC[args.prec])
+    hub.set_veff(torch.tensor(wl.veff, device=dev))
+    hub.set_atoms(wl.atoms)
+    hub.set_occupation_matrix(0, wl.D0[0])
+    g = torch.Generator(device=dev).manual_seed(5)
+    X = torch.randn(args.probe_apply, wl.Nd, device=dev, dtype=torch.float64, generator=g).to(hub.dtype).contiguous()
+    Y = torch.empty_like(X)
+    for _ in range(4):
+        hub.apply_H(0, X, Y)
+    torch.cuda.synchronize()
+    print(json.dumps({"probe": "apply_H", "columns": args.probe_apply, "prec": args.prec,
+                      "max_abs": float(Y.abs().max())}))
+    hub.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.probe_apply:
+        return probe_apply(args)
+    if args.probe_alu:
+        from paper_2507_23612_gb300.binding import alu_peaks
+        print(json.dumps({"probe": "alu_peaks", **alu_peaks()}))
+        return 0
     if args.scf_compare:
         return scf_compare(args)
     if args.workload == "batched":

@@ -364,6 +364,12 @@ int hub_launch_count(hub_t h, long long* launches);
  * supports.  Either pointer may be NULL. */
 int hub_projector_stats(hub_t h, long long* function_points, long long* site_points);
 
+/* Measured FMA throughput of the device (GFLOP/s, multiply-add = 2 flop) in FP64 and FP32:
+ * eight independent FMA chains per thread over a full grid, best of five timed launches on
+ * cuda_stream.  The denominators of ALU-bound rooflines; the paper has no counterpart.
+ * Synchronises.  Errors: HUB_ECUDA, HUB_ENOMEM. */
+int hub_alu_peaks(double* fp64_gflops, double* fp32_gflops, void* cuda_stream);
+
 /* Library build information: writes a short string (arch, version) into buf. */
 int hub_version(char* buf, int len);
 

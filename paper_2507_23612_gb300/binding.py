@@ -79,6 +79,7 @@ _SIGS = {
     "hub_set_tuning": [_P, _I, _I, _I],
     "hub_get_tuning": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "hub_projector_stats": [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)],
+    "hub_alu_peaks": [_PD, _PD, _P],
     "hub_profile": [_P, _I],
     "hub_profile_read": [_P, _I, _PD, C.POINTER(C.c_longlong)],
     "hub_launch_count": [_P, C.POINTER(C.c_longlong)],
@@ -426,3 +427,15 @@ class MLP:
         self._check(self.lib.hub_mlp_train_step(self.m, _tptr(X), _tptr(T), X.shape[0], float(lr), C.byref(loss)),
                     "train_step")
         return loss.value
+
+
+def alu_peaks(stream=None) -> dict:
+    """Measured FP64 and FP32 FMA throughput of the current device (GFLOP/s)."""
+    import torch
+    lib = load_library()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    f64, f32 = C.c_double(), C.c_double()
+    rc = lib.hub_alu_peaks(C.byref(f64), C.byref(f32), C.c_void_p(st.cuda_stream))
+    if rc != 0:
+        raise HubError(rc, "hub_alu_peaks")
+    return {"fp64_gflops": f64.value, "fp32_gflops": f32.value}

@@ -204,3 +204,60 @@ int launch_lanczos(hub_t h, int spin, int steps, const void* v0, double* lo, dou
 }
 
 }  // namespace hub
+
+// ---------------------------------------------------------------------------- ALU peaks
+// Throughput probe for the roofline denominators of ALU-bound kernels: eight independent
+// FMA chains per thread (enough to cover the pipe latency), a full grid of 256-thread CTAs.
+namespace {
+template <typename T>
+__global__ void k_fma_probe(T* out, int iters, T a, T b) {
+    T x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = (T)(threadIdx.x & 7) * (T)1e-3 + (T)i;
+    for (int it = 0; it < iters; ++it)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = fma(x[i], a, b);
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += x[i];
+    if (s == (T)-1.2345) out[0] = s;          // keeps the chains alive; never true
+}
+}  // namespace
+
+extern "C" int hub_alu_peaks(double* fp64_gflops, double* fp32_gflops, void* cuda_stream) {
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HUB_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return HUB_ECUDA;
+    double* buf = nullptr;
+    if (cudaMalloc(&buf, 16) != cudaSuccess) return HUB_ENOMEM;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int blocks = sms * 8, threads = 256;
+    int rc = HUB_OK;
+    for (int kind = 0; kind < 2 && rc == HUB_OK; ++kind) {
+        const int iters = kind == 0 ? 2048 : 65536;
+        float best = 1e30f;
+        for (int r = 0; r < 6; ++r) {
+            cudaEventRecord(e0, st);
+            if (kind == 0) k_fma_probe<double><<<blocks, threads, 0, st>>>(buf, iters, 0.9999999, 1e-9);
+            else k_fma_probe<float><<<blocks, threads, 0, st>>>((float*)buf, iters, 0.9999999f, 1e-9f);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = HUB_ECUDA; break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r > 0) best = std::min(best, ms);              // first launch is the warm-up
+        }
+        const double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
+        if (rc == HUB_OK) {
+            if (kind == 0 && fp64_gflops) *fp64_gflops = flops / (best * 1e-3) / 1e9;
+            if (kind == 1 && fp32_gflops) *fp32_gflops = flops / (best * 1e-3) / 1e9;
+        }
+    }
+    if (cudaGetLastError() != cudaSuccess) rc = HUB_ECUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    return rc;
+}
