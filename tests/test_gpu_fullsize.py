@@ -1,0 +1,171 @@
+"""Parity at the full size of the benchmarked workload: the rutile-shaped 2x2x3 supercell
+(88x88x84 grid, 348 orbitals, 24 Ti + 48 O), in the launch configuration bench.py times
+(whole 348-column blocks, degree 24).  The GPU processes the whole block; the FP64 oracle
+checks sampled outputs it can compute column by column (H applications and filters act on
+each column independently), and properties that hold at any size (Ritz values are the
+Rayleigh quotients of orthonormal Ritz vectors; D and E_U of the whole block)."""
+import numpy as np
+import pytest
+
+import workloads as w
+from oracle import hubbard as o
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2507_23612_gb300 import HUB_F32, HUB_F64, HUB_MIXED_BF16, Hub  # noqa: E402
+
+DEV = torch.device("cuda:0")
+COLS = [0, 57, 173, 289, 347]          # sampled orbital columns (first, last, occupied edge)
+
+
+@pytest.fixture(scope="module")
+def rutile():
+    wl = w.rutile()
+    X0 = wl.orbitals(0)                                      # (348, Nd) seeded
+    g = o.Grid(wl.n, wl.L, wl.kpts[0], wl.fd_half_order)
+    H = o.Hamiltonian(g, wl.veff, wl.atoms, wl.D0[0])
+    return wl, X0, H
+
+
+def _hub(wl, prec):
+    hb = Hub(wl.n, wl.L, wl.fd_half_order, prec=prec)
+    hb.set_veff(torch.tensor(wl.veff, device=DEV))
+    hb.set_atoms(wl.atoms)
+    hb.set_occupation_matrix(0, wl.D0[0])
+    return hb
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("prec,tol", [(HUB_F64, 1e-10), (HUB_F32, 5e-6)])
+def test_full_size_H_application(rutile, prec, tol):
+    wl, X0, H = rutile
+    hb = _hub(wl, prec)
+    hb.autotune(0, torch.tensor(X0, device=DEV).to(hb.dtype).contiguous())
+    X = torch.tensor(X0, device=DEV).to(hb.dtype).contiguous()
+    Y = torch.empty_like(X)
+    hb.apply_H(0, X, Y)
+    got = Y[COLS].double().cpu().numpy()
+    Xs = X[COLS].double().cpu().numpy()              # the block as the GPU saw it
+    ref = H.apply(Xs.T).T
+    err = _rel(got, ref)
+    print("H application, prec", prec, "rel err", err)
+    assert err < tol
+    hb.close()
+
+
+def _bounds(hb, wl):
+    v0 = torch.tensor(wl.lanczos_start(0), device=DEV).to(hb.dtype).contiguous()
+    lo, up = hb.lanczos_bound(0, 10, v0)
+    return lo, lo + 0.1 * (up - lo), up
+
+
+@pytest.mark.parametrize("prec,tol", [(HUB_F64, 1e-10), (HUB_F32, 2e-4)])
+def test_full_size_chebyshev_filter(rutile, prec, tol):
+    """Degree 24 on the whole block with the first-iteration bounds of the SCF.  Float
+    tolerance: the per-application float error (5e-6) accumulates over 24 recurrence steps."""
+    wl, X0, H = rutile
+    hb = _hub(wl, prec)
+    a_low, a, b = _bounds(hb, wl)
+    X = torch.tensor(X0, device=DEV).to(hb.dtype).contiguous()
+    Xs = X[COLS].double().cpu().numpy()
+    hb.chefsi_filter(0, X, wl.degree, a, b, a_low)
+    got = X[COLS].double().cpu().numpy()
+    ref = o.chebyshev_filter(H, Xs.T, wl.degree, a, b, a_low).T
+    err = _rel(got, ref)
+    print("filter, prec", prec, "bounds", (a_low, a, b), "rel err", err)
+    assert err < tol
+    hb.close()
+
+
+@pytest.fixture(scope="module")
+def filtered_rr(rutile):
+    """FP64: one filter + Rayleigh-Ritz pass of the whole block (the SCF's first pass)."""
+    wl, X0, H = rutile
+    hb = _hub(wl, HUB_F64)
+    a_low, a, b = _bounds(hb, wl)
+    X = torch.tensor(X0, device=DEV).contiguous()
+    hb.chefsi_filter(0, X, wl.degree, a, b, a_low)
+    Xf = X.clone()
+    eig = hb.rayleigh_ritz(0, X)
+    return hb, Xf, X, eig
+
+
+def test_full_size_rayleigh_ritz_fp64(rutile, filtered_rr):
+    wl, _, H = rutile
+    _, _, X, eig = filtered_rr
+    assert np.all(np.diff(eig) >= 0)
+    Xs = X[COLS].cpu().numpy()
+    dV = H.grid.dV
+    G = dV * Xs @ Xs.T
+    assert np.max(np.abs(G - np.eye(len(COLS)))) < 1e-10
+    rq = dV * np.einsum("ij,ij->i", Xs, H.apply(Xs.T).T)
+    print("Ritz values", eig[COLS], "Rayleigh quotients", rq)
+    assert np.max(np.abs(rq - eig[COLS])) < 1e-10 * np.max(np.abs(eig))
+
+
+def test_full_size_occupation_fp64(rutile, filtered_rr):
+    wl, _, H = rutile
+    hb, _, X, eig = filtered_rr
+    f = np.zeros(wl.ncol)
+    f[:290] = 1.0
+    D, _, eu = hb.occupation(0, X, f)
+    Xh = X.cpu().numpy().T                              # (Nd, ncol)
+    Dref = o.occupation_matrices(H, Xh, f)
+    U = [a.hub_U for a in wl.atoms if a.hub_l >= 0]
+    euref = o.hubbard_energy(Dref, U)
+    print("max |dD|", np.max(np.abs(D - Dref)), "E_U", eu, euref)
+    assert np.max(np.abs(D - Dref)) < 1e-10
+    assert abs(eu - euref) < 1e-10 * max(1.0, abs(euref))
+
+
+def test_full_size_mixed_rayleigh_ritz_error(rutile, filtered_rr):
+    """One Rayleigh-Ritz pass of the mixed form (BF16 tcgen05 Gram and projected-H products
+    with the hi/lo split and FP32 accumulation, FP64 dense steps) against the FP64 pass on
+    the same block, for the SCF's first pass and for a later one.  A BF16 hi/lo product
+    carries ~16 significand bits and FP32 accumulation over ~2e4 grid points per split, so a
+    single pass is accurate to ~1e-5 relative in the eigenvalues (~1e-4 Ha/atom in their sum
+    here), not to 1e-5 Ha/atom: the SCF reaches that only through its precision ladder (next
+    test).  Bound: 1e-3 Ha/atom in the occupied sum, 1e-3 Ha in any occupied eigenvalue."""
+    wl, _, _ = rutile
+    hb64, Xf, Xr, _ = filtered_rr
+    nat = len(wl.atoms)
+    hbm = _hub(wl, HUB_MIXED_BF16)
+    e64 = hb64.rayleigh_ritz(0, Xf.clone())
+    em = hbm.rayleigh_ritz(0, Xf.float().contiguous())
+    d1 = abs(np.sum(em[:290]) - np.sum(e64[:290])) / nat
+    a_low, a, b = float(e64[0]), float(e64[-1]), _bounds(hb64, wl)[2]
+    X2 = Xr.clone()
+    hb64.chefsi_filter(0, X2, wl.degree, a, b, a_low)
+    X2m = X2.float().contiguous()
+    eig64 = hb64.rayleigh_ritz(0, X2)
+    eigm = hbm.rayleigh_ritz(0, X2m)
+    d2 = abs(np.sum(eigm[:290]) - np.sum(eig64[:290])) / nat
+    print("mixed vs FP64 occupied eigenvalue sum, Ha/atom: first pass", d1, "later pass", d2,
+          "max |d eig| (occupied)", np.max(np.abs(eigm[:290] - eig64[:290])))
+    assert d1 < 1e-3 and d2 < 1e-3
+    assert np.max(np.abs(eigm[:290] - eig64[:290])) < 1e-3
+    hbm.close()
+
+
+def test_full_size_mixed_scf_reaches_the_fp64_fixed_point(rutile):
+    """The benchmarked SCF (both spins, degree 24, |dE|/atom < 1e-5 Ha twice and
+    max|dD| < 1e-4) in FP64 and in the mixed form with the precision ladder: energy, E_U and
+    band energy within 1e-5 Ha/atom of the FP64 fixed point (spec tolerance)."""
+    from paper_2507_23612_gb300.warmstart import scf_solve
+    wl, _, _ = rutile
+    nat = len(wl.atoms)
+    r64 = scf_solve(wl, HUB_F64)
+    rm = scf_solve(wl, HUB_MIXED_BF16)
+    print("FP64", r64["iterations"], r64["seconds"], "mixed", rm["iterations"], rm["seconds"],
+          "dE/atom", abs(rm["E"] - r64["E"]) / nat, "dE_U/atom", abs(rm["E_U"] - r64["E_U"]) / nat,
+          "d band/atom", abs(rm["band"] - r64["band"]) / nat, "max dD", np.max(np.abs(rm["D"] - r64["D"])))
+    assert r64["converged"] and rm["converged"]
+    assert abs(rm["E"] - r64["E"]) / nat < 1e-5
+    assert abs(rm["E_U"] - r64["E_U"]) / nat < 1e-5
+    assert abs(rm["band"] - r64["band"]) / nat < 1e-5
