@@ -611,24 +611,32 @@ k_stencil_f32s(StencilDev<float> a) {
     auto stI = [&](int st, int k) {            // k = 0 feed, 1 V, 2 Yprev
         return reinterpret_cast<ulonglong2*>(smem + C::STAGE * (size_t)st + C::YB + C::IB * (size_t)k);
     };
-    // copy group j: halo, V and Yprev of plane z0 + j, and the queue feed plane z0 + j + NH + 1
-    auto issue = [&](int j, int st) {
-        const int p = z0 + j;
-        if (p < z1) {
-            const long zoff = (long)p * plane;          // p < z1 <= n3: no wrap
+    // copy group j: halo, V and Yprev of plane z0 + j, and the queue feed plane z0 + j + NH + 1.
+    // Groups are issued in order; the plane of the next group and the offsets of its planes
+    // advance by additions (no multiply or modulo per plane).
+    int ip = z0;                                // plane of the next group
+    long ioff = (long)z0 * plane;               // its offset (ip < z1 <= n3: no wrap)
+    int fz = z0 + NH + 1;                       // its feed plane, wrapped into the cell
+    while (fz >= n3) fz -= n3;
+    long foff = (long)fz * plane;
+    const float* Yown = Y + own;
+    const float* Vown = a.V + own;
+    const float* Pown = Yp ? Yp + own : nullptr;
+    auto issue = [&](int st) {
+        if (ip < z1) {
             ulonglong2* ys = stY(st);
 #pragma unroll
             for (int k = 0; k < PER; ++k)
-                if (s_idx[k] >= 0) cp_async<16>(ys + s_idx[k], s_src[k] + zoff);
+                if (s_idx[k] >= 0) cp_async<16>(ys + s_idx[k], s_src[k] + ioff);
             if (active) {
-                cp_async<16>(stI(st, 1) + tid, a.V + zoff + own);
-                if (Yp) cp_async<16>(stI(st, 2) + tid, Yp + zoff + own);
+                cp_async<16>(stI(st, 1) + tid, Vown + ioff);
+                if (Pown) cp_async<16>(stI(st, 2) + tid, Pown + ioff);
             }
         }
-        if (active && p + 1 < z1) {
-            const int pf = (p + NH + 1) % n3;
-            cp_async<16>(stI(st, 0) + tid, Y + (long)pf * plane + own);
-        }
+        if (active && ip + 1 < z1) cp_async<16>(stI(st, 0) + tid, Yown + foff);
+        ++ip;
+        ioff += plane;
+        if (++fz == n3) { fz = 0; foff = 0; } else foff += plane;
     };
 
     u64 wx[NH], wy[NH], wz[NH];
@@ -656,7 +664,7 @@ k_stencil_f32s(StencilDev<float> a) {
     }
 #pragma unroll 1
     for (int j = 0; j < PH; ++j) {
-        issue(j, j % RS);
+        issue(j % RS);
         cp_async_commit();
     }
     int sz = 0, si = PH % RS;                   // stage of plane z, stage of the next issue
@@ -667,7 +675,7 @@ k_stencil_f32s(StencilDev<float> a) {
         for (int st = 0; st < Q; ++st) {
             const int z = zb + st;
             if (z >= z1) break;
-            issue(z - z0 + PH, si);
+            issue(si);
             cp_async_commit();
             cp_async_wait<PH>();
             __syncthreads();
