@@ -358,7 +358,8 @@ k_scatter(typename VT<R, CPLX>::T* __restrict__ Y, int ld, int ncol, long Nd,
 // point p = x + 8 row, row = y + 8 z inside the brick).  Every brick lists the functions of
 // the sites that touch it, in entries of at most 64 (a site's functions stay together, fp =
 // their count rounded up to 4), and keeps their values as a dense block [fp][256]
-// (function-major), zero where a function vanishes.  Both directions then become small dense products per brick:
+// (function-major, points in brick_slot order), zero where a function vanishes.
+// Both directions then become small dense products per brick:
 //   gather:  part[prow + f, n] = sum_p phi[p, f] X[g(p), n]    (partial inner products,
 //            summed per function over its bricks by k_reduce_transform_dense)
 //   scatter: Y[g(p), n] += alpha sum_f phi[p, f] W[frow[f], n]
@@ -366,6 +367,13 @@ k_scatter(typename VT<R, CPLX>::T* __restrict__ Y, int ld, int ncol, long Nd,
 constexpr int BRX = 8, BRY = 8, BRZ = 4, BRP = BRX * BRY * BRZ, BRF = 64;
 constexpr int GD_COLS = 32, GD_XS = GD_COLS + 4;     // gather: columns per pass, smem row stride
 constexpr int SD_COLS = 32;                          // scatter: columns per pass
+
+// position of point p = x + 8 row of a brick inside a function's 256 values: the two
+// 4-point halves of the 32 rows are stored as two planes, [half][row][4], so that a warp
+// reading one half of 32 consecutive rows touches 512 contiguous bytes
+__host__ __device__ __forceinline__ int brick_slot(int p) {
+    return ((p >> 2) & 1) * 128 + (p >> 3) * 4 + (p & 3);
+}
 
 __global__ void k_brick_fill(int npts, const int2* __restrict__ rowinfo, const SiteDev* __restrict__ sites,
                              const float* __restrict__ vals, float* __restrict__ phi) {
@@ -422,7 +430,8 @@ k_gather_dense(const float* __restrict__ X, int ld, int ncol, int n1, int n2, in
 #pragma unroll 4
     for (int p = 0; p < BRP; ++p) {
         const float4 x = *reinterpret_cast<const float4*>(xs + p * GD_XS + cg * 4);
-        const float fv[4] = {ph[p], ph[BRP + p], ph[2 * BRP + p], ph[3 * BRP + p]}, xv[4] = {x.x, x.y, x.z, x.w};
+        const int q = brick_slot(p);
+        const float fv[4] = {ph[q], ph[BRP + q], ph[2 * BRP + q], ph[3 * BRP + q]}, xv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k)
 #pragma unroll
@@ -440,8 +449,9 @@ k_gather_dense(const float* __restrict__ X, int ld, int ncol, int n1, int n2, in
 
 // one CTA per brick, looping over the columns SD_COLS at a time: 256 threads = 8 column
 // groups (of 4) x 32 rows (of 8 points).  Values are read from global memory function-major
-// (a row's 8 points are 32 contiguous bytes; the entry's block stays in L1/L2 over the
-// passes), W rows of the pass are staged in shared memory and read as one broadcast per warp.
+// (each half row is 16 bytes, and a warp's 32 rows of one half are 512 contiguous bytes; the
+// entry's block stays in L1/L2 over the passes), W rows of the pass are staged in shared
+// memory and read as one broadcast per warp.
 // (Measured on the rutile workload, this beat packed f32x2 FMAs, a 4-row x 8-group warp
 // mapping, and staging the values in shared memory.)
 __global__ void __launch_bounds__(256, 3)
@@ -469,11 +479,11 @@ k_scatter_dense(float* __restrict__ Y, int ld, int ncol, int n1, int n2, int n3,
                 ws[i] = (r >= 0 && c0 + c < ncol) ? W[(size_t)r * ncol + c0 + c] : 0.f;
             }
             __syncthreads();
-            const float* ph = phi + E.z + row * 8;
+            const float* ph = phi + E.z + row * 4;
 #pragma unroll 4
             for (int f = 0; f < fp; ++f) {
                 const float4 pa = __ldg(reinterpret_cast<const float4*>(ph + (size_t)f * BRP));
-                const float4 pb = __ldg(reinterpret_cast<const float4*>(ph + (size_t)f * BRP + 4));
+                const float4 pb = __ldg(reinterpret_cast<const float4*>(ph + (size_t)f * BRP + 128));
                 const float4 w4 = *reinterpret_cast<const float4*>(ws + f * SD_COLS + cg * 4);
                 const float pv[8] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
                 const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
@@ -670,7 +680,7 @@ static int build_bricks(hub_t h, Table& t, const std::vector<std::vector<int>>& 
             const int g = site_pts[s][l];
             const auto& w = where.at((long long)s * nb + brick_of(g));
             const int4& E = bent[w.first];
-            rowinfo[S.pt_off + l] = make_int2(E.z + w.second * BRP + point_in(g), s);
+            rowinfo[S.pt_off + l] = make_int2(E.z + w.second * BRP + brick_slot(point_in(g)), s);
         }
     }
     std::vector<int> roff(t.nproj + 1, 0), rent(prow);
