@@ -203,6 +203,30 @@ def kernel_roofline(name, t_n, wl, prec, function_points):
             "kernel": name, "peak_source": src}
 
 
+# ------------------------------------------------------------------------------ ranks
+def replica_spin_index(spin: int, rank: int) -> int:
+    """Seed index of the starting orbitals of one spin channel on one rank: every rank is an
+    independent replica with its own seeded orbitals (indices 0, 1 on rank 0; 2, 3 on rank 1 ...)."""
+    return spin + 2 * rank
+
+
+def max_over_ranks(x: float, device) -> float:
+    """The largest value of x over the ranks of the default process group (x itself without
+    one): the job's time is the slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: float, steps: int, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank_step * steps * world / seconds
+
+
 def run_hub(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -218,7 +242,7 @@ def run_hub(args, rank, world, local_rank):
     hub.set_atoms(wl.atoms)
     dt = hub.dtype
     # each rank is an independent replica: its own seeded starting orbitals
-    X0 = [wl.orbitals(s + 2 * rank) for s in range(nspin)]
+    X0 = [wl.orbitals(replica_spin_index(s, rank)) for s in range(nspin)]
     Xs = [torch.tensor(x, device=dev).to(dt).contiguous() for x in X0]
     v0s = [torch.tensor(wl.lanczos_start(s), device=dev).to(dt).contiguous() for s in range(nspin)]
     p = scf_params(nspin=nspin, ncol=wl.ncol, ld=wl.Nd, degree=wl.degree, max_iter=1000,
@@ -252,12 +276,9 @@ def run_hub(args, rank, world, local_rank):
     hub.profile(0)
     prof = hub.profile_read()
     clocks = sampler.stop()
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     ptorb_step = nspin * (wl.degree + 1) * wl.Nd * wl.ncol
-    value = ptorb_step * args.steps * world / (ms / 1e3) / 1e9
+    value = whole_job_rate(ptorb_step, args.steps, world, ms / 1e3) / 1e9
 
     # e2e: the same step through the public API with the orbitals on the host (pinned):
     # every step copies the blocks host->device, iterates, and copies the blocks, the
@@ -279,13 +300,9 @@ def run_hub(args, rank, world, local_rank):
                 hx.copy_(x, non_blocking=True)
             eig, occ, D = hub.scf_get()
             torch.cuda.synchronize()
-        t_e2e = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = max_over_ranks(time.perf_counter() - t0, dev)
         bx = sum(x.numel() * x.element_size() for x in Xs)
-        e2e = {"value": ptorb_step * args.steps * world / t_e2e / 1e9, "unit": "Gpt·orb/s",
+        e2e = {"value": whole_job_rate(ptorb_step, args.steps, world, t_e2e) / 1e9, "unit": "Gpt·orb/s",
                "h2d_bytes_per_step": bx,
                "d2h_bytes_per_step": bx + 8 * (eig.size + occ.size + D.size)}
 

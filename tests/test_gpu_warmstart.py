@@ -19,13 +19,6 @@ from paper_2507_23612_gb300.warmstart import (OccupationModel, pack_occupations,
 REPS = (1, 1, 2)      # 12 atoms (4 Ti), 44x44x56 grid, 58 orbitals per spin
 
 
-def test_pack_roundtrip():
-    g = np.random.Generator(np.random.PCG64(0))
-    A = g.normal(size=(2, 3, 5, 5))
-    D = A + A.transpose(0, 1, 3, 2)
-    np.testing.assert_array_equal(unpack_occupations(pack_occupations(D), 2), D)
-
-
 def test_warm_start_reaches_the_cold_fixed_point_from_a_better_guess():
     model = OccupationModel(nspin=2, seed=0)
     train = []
