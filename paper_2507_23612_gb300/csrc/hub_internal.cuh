@@ -61,6 +61,8 @@ struct Table {
     int* d_csr_off = nullptr;         // [Nd+1] entries per grid point
     int2* d_csr_ent = nullptr;        // per entry: x = value index of its first projector,
                                       // y = (projector row of its site << 4) | nproj
+    int* d_order = nullptr;           // [norder] grid points with entries, grouped by the
+    int norder = 0;                   // list of sites that touch them (scatter order)
     double* d_gamma = nullptr;        // [nproj] KB energy per projector row (0 for Hubbard)
     int* d_hub_sites = nullptr;
     double* d_U = nullptr;

@@ -293,14 +293,16 @@ __global__ void k_reduce_transform(int nsites, int ncol, double dV, const SiteDe
 }
 
 // ---------------------------------------------------------------------------- scatter
-// One thread per grid point, looping over all columns NC at a time: the point's CSR entries
-// and values are fetched from HBM once and re-read from L1 for the later column groups.  Per
-// entry, the site's values multiply W rows (16-byte vector loads when the rows are aligned);
-// Y is updated once per column.
+// One thread per grid point that carries entries, taken in the scatter order (points grouped
+// by the list of sites touching them, so that a warp's lanes run the same loops and read the
+// same W rows), looping over all columns NC at a time: the point's CSR entries and values are
+// fetched from HBM once and re-read from L1 for the later column groups.  Per entry, the
+// site's values multiply W rows (16-byte vector loads when the rows are aligned); Y is
+// updated once per column.
 template <typename R, bool CPLX>
 __global__ void __launch_bounds__(128)
-k_scatter(typename VT<R, CPLX>::T* __restrict__ Y, int ld, int ncol, long Nd,
-          const int* __restrict__ csr_off, const int2* __restrict__ csr_ent,
+k_scatter(typename VT<R, CPLX>::T* __restrict__ Y, int ld, int ncol, int norder,
+          const int* __restrict__ order, const int* __restrict__ csr_off, const int2* __restrict__ csr_ent,
           const typename VT<R, CPLX>::T* __restrict__ vals,
           const typename VT<R, CPLX>::T* __restrict__ W, R alpha, int vec_ok,
           const double* __restrict__ alpha_dev) {
@@ -308,10 +310,10 @@ k_scatter(typename VT<R, CPLX>::T* __restrict__ Y, int ld, int ncol, long Nd,
     if (alpha_dev) alpha = (R)alpha_dev[0];
     constexpr int NC = 64 / sizeof(T);
     constexpr int PER16 = 16 / sizeof(T);
-    const long g = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= Nd) return;
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= norder) return;
+    const long g = order[i];
     const int e0 = csr_off[g], e1 = csr_off[g + 1];
-    if (e0 == e1) return;
     for (int c0 = 0; c0 < ncol; c0 += NC) {
         const int nc = min(NC, ncol - c0);
         T acc[NC];
@@ -608,7 +610,7 @@ int upload(hub_t h, Tp** dptr, const std::vector<Tp>& v) {
 
 void free_table(Table& t) {
     void* ptrs[] = {t.d_sites, t.d_items, t.d_item_first, t.d_idx, t.d_vals, t.d_csr_off,
-                    t.d_csr_ent, t.d_gamma, t.d_hub_sites, t.d_U,
+                    t.d_csr_ent, t.d_order, t.d_gamma, t.d_hub_sites, t.d_U,
                     t.d_M[0], t.d_M[1], t.d_bent, t.d_bfirst, t.d_phi, t.d_frow, t.d_roff,
                     t.d_rent};
     for (void* p : ptrs)
@@ -858,12 +860,29 @@ int build_tables(hub_t h, int natoms, const double* pos, const int* kb_nchan, co
             csr_ent[e] = make_int2(S.val_off + l * S.nproj, (S.proj_off << 4) | S.nproj);
         }
     }
+    // scatter order: the points that carry entries, grouped by the list of sites touching
+    // them (then by grid index), so that the lanes of a warp walk the same entry list (same
+    // trip counts, one W row per site for the whole warp)
+    std::vector<int> order;
+    for (long g = 0; g < h->Nd; ++g)
+        if (csr_off[g + 1] > csr_off[g]) order.push_back((int)g);
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        const int na = csr_off[a + 1] - csr_off[a], nb = csr_off[b + 1] - csr_off[b];
+        if (na != nb) return na < nb;
+        for (int k = 0; k < na; ++k) {
+            const int sa = csr_ent[csr_off[a] + k].y, sb = csr_ent[csr_off[b] + k].y;
+            if (sa != sb) return sa < sb;
+        }
+        return a < b;
+    });
+    t.norder = (int)order.size();
 
     int rc;
     if ((rc = upload(h, &t.d_sites, t.h_sites))) return rc;
     if ((rc = upload(h, &t.d_items, items))) return rc;
     if ((rc = upload(h, &t.d_item_first, t.h_item_first))) return rc;
     if ((rc = upload(h, &t.d_idx, idx))) return rc;
+    if ((rc = upload(h, &t.d_order, order))) return rc;
     if ((rc = upload(h, &t.d_csr_off, csr_off))) return rc;
     if ((rc = upload(h, &t.d_csr_ent, csr_ent))) return rc;
     if ((rc = upload(h, &t.d_gamma, gamma_rows))) return rc;
@@ -993,9 +1012,10 @@ static int scatter_t(hub_t h, void* Y, int ncol, int ld, double alpha, const dou
     using T = typename VT<R, CPLX>::T;
     Table& t = h->proj;
     const int vec_ok = ((ncol * sizeof(T)) % 16 == 0) && ((uintptr_t)h->d_W % 16 == 0);
-    dim3 grid((unsigned)((h->Nd + 127) / 128));
+    if (t.norder == 0) return HUB_OK;
+    dim3 grid((unsigned)((t.norder + 127) / 128));
     ProfScope ps(h, HUB_K_SCATTER);
-    k_scatter<R, CPLX><<<grid, 128, 0, h->stream>>>((T*)Y, ld, ncol, h->Nd, t.d_csr_off, t.d_csr_ent,
+    k_scatter<R, CPLX><<<grid, 128, 0, h->stream>>>((T*)Y, ld, ncol, t.norder, t.d_order, t.d_csr_off, t.d_csr_ent,
                                                     (const T*)t.d_vals, (const T*)h->d_W, (R)alpha, vec_ok,
                                                     alpha_dev);
     HUB_CUDA_TRY(h, cudaGetLastError());
