@@ -860,13 +860,15 @@ int build_tables(hub_t h, int natoms, const double* pos, const int* kb_nchan, co
             csr_ent[e] = make_int2(S.val_off + l * S.nproj, (S.proj_off << 4) | S.nproj);
         }
     }
-    // scatter order: the points that carry entries, grouped by the list of sites touching
-    // them (then by grid index), so that the lanes of a warp walk the same entry list (same
-    // trip counts, one W row per site for the whole warp)
+    // scatter order: the points that carry entries.  Double working types group them by the
+    // list of sites touching them (then by grid index), so that the lanes of a warp walk the
+    // same entry list (same trip counts, one W row per site for the whole warp): a masked
+    // lane still costs FP64 pipe time.  Float types keep grid order, where neighbouring
+    // lanes update neighbouring elements of Y (measured faster for complex float).
     std::vector<int> order;
     for (long g = 0; g < h->Nd; ++g)
         if (csr_off[g + 1] > csr_off[g]) order.push_back((int)g);
-    std::sort(order.begin(), order.end(), [&](int a, int b) {
+    if (h->esize == 8) std::sort(order.begin(), order.end(), [&](int a, int b) {
         const int na = csr_off[a + 1] - csr_off[a], nb = csr_off[b + 1] - csr_off[b];
         if (na != nb) return na < nb;
         for (int k = 0; k < na; ++k) {
