@@ -163,8 +163,8 @@ def cpu_oracle_sample(workload: str, seconds: float, cols: int = 2):
 # full-size launches of the 348-orbital rutile block, ncu; profiles/hot_kernels_f32_rutile_dram.md;
 # the mixed form runs the float kernels).
 # Valid for the kernels as they stand; a changed kernel reports null until captured again.
-TRAFFIC_B_PER_PTORB = {"f32": {"stencil": 12.53, "gather": 12.07, "scatter": 8.32},
-                       "f64": {"stencil": 25.15, "gather": 95.78, "scatter": 16.58}}
+TRAFFIC_B_PER_PTORB = {"f32": {"stencil": 12.53, "gather": 11.73, "scatter": 8.32},
+                       "f64": {"stencil": 25.29, "gather": 95.70, "scatter": 51.01}}
 
 
 def hbm_peak():
