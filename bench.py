@@ -144,6 +144,18 @@ print(json.dumps({{"applications": n, "seconds": dt, "cols": {cols}, "Nd": wl.Nd
 """
 
 
+def run_config(args, wl_name, wl, world):
+    """The workload description shared by both arms of the bench line."""
+    block = wl.Nd * wl.ncol * (8 if args.prec == "f64" else 4) / 1e9
+    return {"workload": wl_name, "grid": list(wl.n), "orbitals_per_spin": wl.ncol,
+            "spins": wl.nspin, "chebyshev_degree": wl.degree,
+            "h_applications_per_step": wl.nspin * (wl.degree + 1),
+            "step": "one SCF iteration (filter + Rayleigh-Ritz per spin, occupations, D, E_U, Pulay)",
+            "l2": ("inputs larger than L2" if block > 0.129 else "inputs smaller than L2 (not flushed)")
+                  + " (each orbital block %.3f GB)" % block,
+            "parallelism": f"replicas x{world}"}
+
+
 def cpu_oracle_sample(workload: str, seconds: float, cols: int = 2):
     """Time the oracle's H application on a bounded sample, single-threaded numpy."""
     make = "w.rutile()" if workload == "rutile" else "w.tiny()"
@@ -658,7 +670,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": wl_name, "sample": "bounded oracle sample"},
+            "config": run_config(args, wl_name, make_workload(args.workload), world),
             "cpu_baseline": {"value": value, "unit": "Gpt·orb/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "Gpt·orb/s", "h2d_bytes_per_step": 0,
@@ -684,12 +696,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE_NAME[args.prec], "data": "synthetic",
-            "config": {"workload": wl_name, "grid": list(wl.n), "orbitals_per_spin": wl.ncol,
-                       "spins": wl.nspin, "chebyshev_degree": wl.degree,
-                       "h_applications_per_step": wl.nspin * (wl.degree + 1),
-                       "step": "one SCF iteration (filter + Rayleigh-Ritz per spin, occupations, D, E_U, Pulay)",
-                       "l2": "inputs larger than L2 (each orbital block %.2f GB)" % (wl.Nd * wl.ncol * (8 if args.prec == 'f64' else 4) / 1e9),
-                       "parallelism": f"replicas x{world}"},
+            "config": run_config(args, wl_name, wl, world),
             "roofline": r["roofline"], "rooflines": r["rooflines"], "cpu_baseline": cpu, "e2e": r["e2e"],
             "gpu_launches": r["launches"], "clocks": r["clocks"],
             "kernels": r["kernels"],
