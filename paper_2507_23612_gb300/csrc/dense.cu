@@ -243,10 +243,21 @@ __global__ void k_jacobi(double* A, double* Ab, double* V, int n, int N, int max
             __syncthreads();
             // phase 2: every 2x2 block (P, Q) of the next matrix <- J_P^T B J_Q (blocks of two
             // identity rotations are copied), and V <- V J in place
-            const long nblk = (long)H * H;
+            // the matrix stays symmetric: only the blocks P <= Q are computed, and each
+            // writes its transpose too
+            const long nblk = (long)H * (H + 1) / 2;
             for (long e = tid; e < nblk + (long)n * H; e += nthr) {
                 if (e < nblk) {
-                    const int P = (int)(e / H), Q = (int)(e % H);
+                    // row P of the upper triangle holds H - P blocks; S(P) = P (2H - P + 1) / 2
+                    // (estimate in float arithmetic: the FP64 pipe is the scarce one; the two
+                    // loops below correct the estimate)
+                    const float h2 = 2.0f * H + 1.0f;
+                    int P = (int)((h2 - sqrtf(fmaxf(h2 * h2 - 8.0f * (float)e, 0.0f))) * 0.5f);
+                    P = max(0, min(P, H - 1));
+                    auto S = [&](long r) { return r * (2L * H - r + 1) / 2; };
+                    while (P > 0 && S(P) > e) --P;
+                    while (P < H - 1 && S(P + 1) <= e) ++P;
+                    const int Q = P + (int)(e - S(P));
                     const double s1 = rot[2 * P + 1], s2 = rot[2 * Q + 1];
                     const double c1 = rot[2 * P], c2 = rot[2 * Q];
                     int p1, q1, p2, q2;
@@ -269,10 +280,10 @@ __global__ void k_jacobi(double* A, double* Ab, double* V, int n, int N, int max
                             n10 = 0.0;
                         }
                     }
-                    if (p1 < n && p2 < n) nxt[(size_t)p1 * n + p2] = n00;
-                    if (p1 < n && q2 < n) nxt[(size_t)p1 * n + q2] = n01;
-                    if (q1 < n && p2 < n) nxt[(size_t)q1 * n + p2] = n10;
-                    if (q1 < n && q2 < n) nxt[(size_t)q1 * n + q2] = n11;
+                    if (p1 < n && p2 < n) { nxt[(size_t)p1 * n + p2] = n00; nxt[(size_t)p2 * n + p1] = n00; }
+                    if (p1 < n && q2 < n) { nxt[(size_t)p1 * n + q2] = n01; nxt[(size_t)q2 * n + p1] = n01; }
+                    if (q1 < n && p2 < n) { nxt[(size_t)q1 * n + p2] = n10; nxt[(size_t)p2 * n + q1] = n10; }
+                    if (q1 < n && q2 < n) { nxt[(size_t)q1 * n + q2] = n11; nxt[(size_t)q2 * n + q1] = n11; }
                 } else {
                     const long f = e - nblk;
                     const int r = (int)(f / H), P = (int)(f % H);

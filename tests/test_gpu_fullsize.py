@@ -169,3 +169,42 @@ def test_full_size_mixed_scf_reaches_the_fp64_fixed_point(rutile):
     assert abs(rm["E"] - r64["E"]) / nat < 1e-5
     assert abs(rm["E_U"] - r64["E_U"]) / nat < 1e-5
     assert abs(rm["band"] - r64["band"]) / nat < 1e-5
+
+
+def test_full_size_batched_snapshots_complex():
+    """The batched form at the size the bench runs it: whole complex-float blocks of two
+    seeded snapshots (24-atom rutile- and anatase-shaped cells, 1 and 2 Monkhorst-Pack
+    k-points, 115 orbitals, degree 24) filtered in one graph by hub_batch_filter; two sampled
+    columns of every system checked against the oracle's complex filter with the same
+    bounds.  Float tolerance as for the real block (24 recurrence steps of float rounding)."""
+    from paper_2507_23612_gb300 import batch_filter
+    snaps = w.snapshot_batch()
+    chosen = [snaps[0], snaps[5]]
+    hubs, Xs, X0s, a, b, al, refs = [], [], [], [], [], [], []
+    for sn in chosen:
+        for k, kpt in enumerate(sn.kpts):
+            hb = Hub(sn.n, sn.L, sn.fd_half_order, kpt=kpt, complex_=True, prec=HUB_F32)
+            hb.set_veff(torch.tensor(sn.veff, device=DEV))
+            hb.set_atoms(sn.atoms)
+            hb.set_occupation_matrix(0, sn.D0[0])
+            X0 = sn.orbitals(0, k, complex_=True)
+            v0 = torch.tensor(sn.lanczos_start(0, k, complex_=True), device=DEV).to(torch.complex64).contiguous()
+            lo, up = hb.lanczos_bound(0, 10, v0)
+            hubs.append(hb)
+            X = torch.tensor(X0, device=DEV).to(torch.complex64).contiguous()
+            Xs.append(X)
+            X0s.append(X[[0, sn.ncol - 1]].to(torch.complex128).cpu().numpy())
+            a.append(lo + 0.1 * (up - lo)); b.append(up); al.append(lo)
+            refs.append((sn, k))
+    batch_filter(hubs, [0] * len(hubs), Xs, chosen[0].degree, a, b, al)
+    torch.cuda.synchronize()
+    for i, ((sn, k), X) in enumerate(zip(refs, Xs)):
+        g = o.Grid(sn.n, sn.L, sn.kpts[k], sn.fd_half_order)
+        H = o.Hamiltonian(g, sn.veff, sn.atoms, sn.D0[0])
+        ref = o.chebyshev_filter(H, X0s[i].T, sn.degree, a[i], b[i], al[i]).T
+        got = X[[0, sn.ncol - 1]].to(torch.complex128).cpu().numpy()
+        err = _rel(got, ref)
+        print(sn.name, "k", k, "batched complex filter rel err", err)
+        assert err < 2e-4
+    for hb in hubs:
+        hb.close()
