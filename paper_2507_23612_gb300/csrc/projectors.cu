@@ -10,6 +10,8 @@
 //   transform: W = gamma .* C (KB) or W = M C with M = (U/2)(I - 2 D) (Hubbard, Eq. DerED)
 //   scatter:   Y[g, n] += alpha * sum_{entries e at g} vals_e . W[rows_e, n]
 // The scatter walks a per-grid-point CSR so that no two threads write the same element.
+// Real float handles also keep a brick form of the tables (dense values per 8x8x4 brick,
+// see "brick form" below) for a dense scatter and an alternative gather.
 #include <algorithm>
 #include <cmath>
 #include <numeric>
