@@ -1,7 +1,7 @@
 // Warm-start model: per-atom local-environment descriptors and a SiLU multilayer
 // perceptron that maps them to occupation matrices D, with hand-written forward, backward
 // and Adam kernels.  (The paper has no learned component; its SCF, with D updated and mixed
-// every iteration, stays the judge: the model only supplies the starting D.)
+// every iteration, stays the arbiter: the model only supplies the starting D.)
 //
 // Layers: h0 = (x - mu_in) / sd_in; h_l = silu(W_l h_{l-1} + b_l) for the hidden layers;
 // y = (W_L h_{L-1} + b_L) * sd_out + mu_out.  Weights are kept in FP32 (master, Adam state)

@@ -7,7 +7,7 @@ kernels) maps descriptors of each Hubbard atom's neighbourhood (hub_descriptors)
 unique entries of its 5x5 D per spin, and is trained on SCF solutions that the library
 itself computes on displaced cells.  The SCF started from the predicted D converges to its
 own fixed point: the model only saves iterations, and the plain SCF remains the fallback
-and the judge of its error.  (The paper has no learned component.)
+and the arbiter of its error.  (The paper has no learned component.)
 
 This module is argument marshalling and orchestration: descriptors, training, inference and
 the SCF all run in the library's kernels.

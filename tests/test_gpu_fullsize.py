@@ -156,7 +156,7 @@ def test_full_size_mixed_rayleigh_ritz_error(rutile, filtered_rr):
 def test_full_size_mixed_scf_reaches_the_fp64_fixed_point(rutile):
     """The benchmarked SCF (both spins, degree 24, |dE|/atom < 1e-5 Ha twice and
     max|dD| < 1e-4) in FP64 and in the mixed form with the precision ladder: energy, E_U and
-    band energy within 1e-5 Ha/atom of the FP64 fixed point (spec tolerance)."""
+    band energy within 1e-5 Ha/atom of the FP64 fixed point (the target tolerance of the mixed form)."""
     from paper_2507_23612_gb300.warmstart import scf_solve
     wl, _, _ = rutile
     nat = len(wl.atoms)

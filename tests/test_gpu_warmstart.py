@@ -1,7 +1,7 @@
 """Warm start of the SCF from the trained occupation model, end to end on the GPU: SCF
 solutions of displaced rutile-shaped cells (computed by the library), training by the
 library's MLP kernels, prediction for a cell it has not seen, and the SCF started from the
-prediction.  The SCF stays the judge: it must reach the cold start's fixed point."""
+prediction.  The SCF stays the arbiter: it must reach the cold start's fixed point."""
 import numpy as np
 import pytest
 
