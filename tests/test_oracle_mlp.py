@@ -77,3 +77,28 @@ def test_pack_unpack_roundtrip():
     A = g.standard_normal((2, 3, 5, 5))
     D = A + np.transpose(A, (0, 1, 3, 2))
     np.testing.assert_allclose(m.unpack_D(m.pack_D(D), 2), D)
+
+
+def test_descriptor_rotation_covariance():
+    """Rotating an environment by 90 degrees about z, (x, y, z) -> (-y, x, z), leaves the
+    radial values unchanged and maps the harmonic sums in the fixed way the real Y_1m and
+    Y_2m do: Y_1 (y, z, x) -> (x, z, -y); Y_2 (xy, yz, 2z^2-x^2-y^2, xz, x^2-y^2) ->
+    (-xy, xz, 2z^2-x^2-y^2, -yz, -(x^2-y^2)).  A swapped or mis-signed component fails."""
+    g = np.random.default_rng(7)
+    L = np.array([30.0, 30.0, 30.0])
+    c = L / 2
+    rel = g.uniform(-4.0, 4.0, (7, 3))
+    sp = [0] + list(g.integers(0, 2, 6))
+    pos = np.vstack([c, c + rel[1:]])
+    R = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    pos_r = np.vstack([c, c + rel[1:] @ R.T])
+    d = m.descriptors(pos, sp, L, [0])[0]
+    dr = m.descriptors(pos_r, sp, L, [0])[0]
+    for s in range(2):
+        b = 24 * s
+        np.testing.assert_allclose(dr[b:b + 16], d[b:b + 16], atol=1e-12)
+        y1 = d[b + 16:b + 19]
+        np.testing.assert_allclose(dr[b + 16:b + 19], [y1[2], y1[1], -y1[0]], atol=1e-12)
+        y2 = d[b + 19:b + 24]
+        np.testing.assert_allclose(dr[b + 19:b + 24], [-y2[0], y2[3], y2[2], -y2[1], -y2[4]], atol=1e-12)
+    assert np.abs(d[16:24]).max() > 1e-3 and np.abs(d[40:48]).max() > 1e-3   # not a trivial case
