@@ -1,0 +1,78 @@
+"""Argument checks of the C ABI that happen on the host, before any device work: bad sizes,
+orders, precisions and NULL handles come back as HUB_EINVAL (no GPU needed, no launch)."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+EINVAL = -1
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2507_23612_gb300 import build as b
+    b.build()
+    from paper_2507_23612_gb300 import binding
+    return binding.load_library()
+
+
+def _create(lib, n=(8, 8, 8), L=(2.0, 2.0, 2.0), order=6, prec=0):
+    h = C.c_void_p()
+    k = (C.c_double * 3)(0.0, 0.0, 0.0)
+    rc = lib.hub_create_grid(C.byref(h), n[0], n[1], n[2], L[0], L[1], L[2], order, 0, k, prec, None)
+    return rc, h
+
+
+@pytest.mark.parametrize("kw", [dict(n=(0, 8, 8)), dict(n=(8, -1, 8)), dict(L=(2.0, 0.0, 2.0)),
+                                dict(L=(float("nan"), 2.0, 2.0)), dict(order=0), dict(order=7),
+                                dict(prec=3), dict(prec=-1), dict(n=(2000, 2000, 1000))])
+def test_create_grid_rejects_bad_arguments(lib, kw):
+    rc, h = _create(lib, **kw)
+    assert rc == EINVAL and not h.value
+
+
+def test_null_handles(lib):
+    assert lib.hub_destroy(None) == 0
+    assert lib.hub_last_error(None)                         # a message, not a crash
+    assert lib.hub_set_tuning(None, 0, 1, 0) == EINVAL
+    n = C.c_int()
+    assert lib.hub_get_tuning(None, C.byref(n), None, None, None) == EINVAL
+    assert lib.hub_mlp_destroy(None) == 0
+
+
+def test_batch_filter_rejects_empty_batch(lib):
+    assert lib.hub_batch_filter(0, None, None, None, None, None, 24, None, None, None, None) == EINVAL
+
+
+def test_mlp_create_rejects_bad_shapes(lib):
+    m = C.c_void_p()
+    for args in [(0, 256, 3, 30), (48, 0, 3, 30), (48, 256, 0, 30), (48, 256, 3, 0)]:
+        assert lib.hub_mlp_create(C.byref(m), *args, 1, 0, None) == EINVAL
+
+
+def test_descriptors_reject_bad_inputs(lib):
+    pos = np.zeros(6)
+    L = np.array([10.0, 10.0, 10.0])
+    out = C.c_void_p(0)
+
+    def call(species, centers, nspecies=2, nrad=16, rc=6.0, eta=0.4):
+        sp = np.ascontiguousarray(species, dtype=np.int32)
+        ce = np.ascontiguousarray(centers, dtype=np.int32)
+        return lib.hub_descriptors(2, pos.ctypes.data_as(C.POINTER(C.c_double)),
+                                   sp.ctypes.data_as(C.POINTER(C.c_int)),
+                                   L.ctypes.data_as(C.POINTER(C.c_double)), len(ce),
+                                   ce.ctypes.data_as(C.POINTER(C.c_int)), nspecies, rc, nrad, eta,
+                                   out, None)
+    assert call([0, 2], [0]) == EINVAL                     # species out of range
+    assert call([0, 1], [2]) == EINVAL                     # centre out of range
+    assert call([0, 1], [0], nspecies=3) == EINVAL          # at most two species
+    assert call([0, 1], [0], nrad=33) == EINVAL             # at most 32 radial values
+    assert call([0, 1], [0], rc=0.0) == EINVAL
+    assert call([0, 1], [0], eta=-1.0) == EINVAL
+
+
+def test_gram_noalloc_rejects_bad_arguments_before_any_device_work(lib):
+    assert lib.hub_gram_noalloc(None, 4, None, 4, 1024, 1024, 0, 1.0, None, None) == EINVAL   # NULL operands
+    assert lib.hub_gram_noalloc(None, 4, None, 4, 1024, 1000, 0, 1.0, None, None) == EINVAL   # ld < nrows
+    assert lib.hub_gram_noalloc(None, 4, None, 4, 1024, 1024, 2, 1.0, None, None) == EINVAL   # precision
+    assert lib.hub_gram_noalloc(None, 0, None, 4, 1024, 1024, 0, 1.0, None, None) == 0        # empty: no work
