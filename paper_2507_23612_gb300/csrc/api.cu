@@ -40,7 +40,7 @@ int check_flags(hub_t h) {
     int f[8];
     HUB_CUDA_TRY(h, cudaMemcpyAsync(f, h->d_flags, sizeof(f), cudaMemcpyDeviceToHost, h->stream));
     HUB_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    h->last_sweeps = f[6];
+    h->last_sweeps = std::max(f[6], f[7]);
     bool any = false;
     for (int i = 0; i < 6; ++i) any |= f[i] != 0;
     if (!any) return HUB_OK;
@@ -305,28 +305,18 @@ int hub_chefsi_filter(hub_t h, int spin, void* X, int ncol, int ld, int degree, 
     return HUB_OK;
 }
 
-int hub_rayleigh_ritz(hub_t h, int spin, void* X, int ncol, int ld, double* eig_host, void* work) {
-    int rc = check_block(h, spin, X, ncol, ld);
-    if (rc) return rc;
-    if (h->cplx) return fail(h, HUB_EINVAL, "Rayleigh-Ritz supports real orbitals only");
-    if (ncol > 0 && !eig_host) return fail(h, HUB_EINVAL, "NULL eigenvalue output");
-    if (ncol == 0) return HUB_OK;
-    const int n = ncol;
-    void* HX = work;
-    if (!HX) {
-        if ((rc = ensure(h, &h->d_work, &h->work_bytes, (size_t)ld * ncol * elem_bytes(h)))) return rc;
-        HX = h->d_work;
-    }
+namespace hub {
+// Rayleigh-Ritz in two halves around the subspace eigensolve, so that the SCF can solve the
+// two spin channels' eigenproblems in one launch.  ws: 6 n^2 + n doubles (S, Hs, Linv, T, Vs,
+// Q, eig); HX: a block like X.
+static int rr_prepare(hub_t h, int spin, void* X, int n, int ld, void* HX, double* ws) {
     const size_t nn = (size_t)n * n;
-    if ((rc = ensure(h, &h->d_small, &h->small_bytes, (6 * nn + n) * sizeof(double)))) return rc;
-    double* S = (double*)h->d_small;
+    double* S = ws;
     double* Hs = S + nn;
     double* Linv = Hs + nn;
     double* T = Linv + nn;
-    double* Vs = T + nn;
-    double* Q = Vs + nn;
-    double* eig = Q + nn;
-    if ((rc = apply_H_internal(h, spin, X, ld, HX, ncol, 1.0, 0.0, nullptr, 0.0))) return rc;
+    int rc;
+    if ((rc = apply_H_internal(h, spin, X, ld, HX, n, 1.0, 0.0, nullptr, 0.0))) return rc;
     const bool tensor = (h->prec == HUB_MIXED_BF16) && h->bf16_terms > 0;
     if (tensor) {
         // the Gram matrix feeds the Cholesky factor: always the hi/lo split (about 16
@@ -346,20 +336,71 @@ int hub_rayleigh_ritz(hub_t h, int spin, void* X, int ncol, int ld, double* eig_
     if ((rc = dense_tri_inverse(h, S, Linv, n))) return rc;
     if ((rc = dense_gemm(h, false, false, n, n, n, 1.0, Linv, n, Hs, n, 0.0, T, n))) return rc;
     if ((rc = dense_gemm(h, false, true, n, n, n, 1.0, T, n, Linv, n, 0.0, Hs, n))) return rc;
-    if ((rc = dense_symmetrize(h, Hs, n))) return rc;
-    if ((rc = dense_jacobi_eigh(h, Hs, Vs, eig, n))) return rc;
+    return dense_symmetrize(h, Hs, n);
+}
+
+static int rr_finish(hub_t h, void* X, int n, int ld, void* HX, double* ws, double* eig_host) {
+    const size_t nn = (size_t)n * n;
+    double* Linv = ws + 2 * nn;
+    double* Vs = ws + 4 * nn;
+    double* Q = ws + 5 * nn;
+    double* eig = ws + 6 * nn;
+    int rc;
     if ((rc = dense_gemm(h, true, false, n, n, n, 1.0, Linv, n, Vs, n, 0.0, Q, n))) return rc;
-    if (tensor) {
+    if ((h->prec == HUB_MIXED_BF16) && h->bf16_terms > 0) {
         if ((rc = launch_rotate_bf16(h, X, ld, Q, n, n, HX, ld))) return rc;
     } else {
         if ((rc = launch_rotate(h, X, ld, Q, n, n, HX, ld))) return rc;
     }
-    if ((rc = launch_copy_block(h, HX, ld, X, ld, ncol))) return rc;
+    if ((rc = launch_copy_block(h, HX, ld, X, ld, n))) return rc;
     HUB_CUDA_TRY(h, cudaMemcpyAsync(eig_host, eig, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     if ((rc = check_flags(h))) return rc;
     for (int i = 0; i < n; ++i)
         if (!std::isfinite(eig_host[i])) return fail(h, HUB_ENONFINITE, "non-finite Ritz value");
     return HUB_OK;
+}
+
+// Rayleigh-Ritz of both spin channels (blocks X[0], X[1] of the same shape): the two
+// subspace eigenproblems are solved in one cooperative launch, half the SMs each.
+static int rr_two_spins(hub_t h, void* const* X, int n, int ld, double* const* eig_host) {
+    const size_t nn = (size_t)n * n, wsz = 6 * nn + n;
+    const size_t blk = (size_t)ld * n * elem_bytes(h);
+    int rc;
+    if ((rc = ensure(h, &h->d_work, &h->work_bytes, std::max(2 * blk, h->work_bytes)))) return rc;
+    if ((rc = ensure(h, &h->d_small, &h->small_bytes, std::max(2 * wsz * sizeof(double), h->small_bytes))))
+        return rc;
+    void* HX[2] = {h->d_work, (char*)h->d_work + blk};
+    double* ws[2] = {(double*)h->d_small, (double*)h->d_small + wsz};
+    for (int s = 0; s < 2; ++s)
+        if ((rc = rr_prepare(h, s, X[s], n, ld, HX[s], ws[s]))) return rc;
+    double* Hs[2] = {ws[0] + nn, ws[1] + nn};
+    double* Vs[2] = {ws[0] + 4 * nn, ws[1] + 4 * nn};
+    double* eig[2] = {ws[0] + 6 * nn, ws[1] + 6 * nn};
+    if ((rc = dense_jacobi_eigh_multi(h, 2, Hs, Vs, eig, n))) return rc;
+    for (int s = 0; s < 2; ++s)
+        if ((rc = rr_finish(h, X[s], n, ld, HX[s], ws[s], eig_host[s]))) return rc;
+    return HUB_OK;
+}
+}  // namespace hub
+
+int hub_rayleigh_ritz(hub_t h, int spin, void* X, int ncol, int ld, double* eig_host, void* work) {
+    int rc = check_block(h, spin, X, ncol, ld);
+    if (rc) return rc;
+    if (h->cplx) return fail(h, HUB_EINVAL, "Rayleigh-Ritz supports real orbitals only");
+    if (ncol > 0 && !eig_host) return fail(h, HUB_EINVAL, "NULL eigenvalue output");
+    if (ncol == 0) return HUB_OK;
+    const int n = ncol;
+    void* HX = work;
+    if (!HX) {
+        if ((rc = ensure(h, &h->d_work, &h->work_bytes, (size_t)ld * ncol * elem_bytes(h)))) return rc;
+        HX = h->d_work;
+    }
+    const size_t nn = (size_t)n * n;
+    if ((rc = ensure(h, &h->d_small, &h->small_bytes, (6 * nn + n) * sizeof(double)))) return rc;
+    double* ws = (double*)h->d_small;
+    if ((rc = rr_prepare(h, spin, X, n, ld, HX, ws))) return rc;
+    if ((rc = dense_jacobi_eigh(h, ws + nn, ws + 4 * nn, ws + 6 * nn, n))) return rc;
+    return rr_finish(h, X, n, ld, HX, ws, eig_host);
 }
 
 int hub_gram(hub_t h, const void* A, int ncol_a, const void* B, int ncol_b, int ld, double alpha,
@@ -569,10 +610,13 @@ int hub_scf_iterate(hub_t h, hub_scf_result* res) {
     const double deg = ns == 1 ? 2.0 : 1.0;
     int rc;
     if (p.ladder && h->prec == HUB_MIXED_BF16) h->bf16_terms = st.laddered ? 0 : 1;
-    for (int s = 0; s < ns; ++s) {
+    // per spin channel: filter + Rayleigh-Ritz passes; with two channels both are filtered
+    // first and their Rayleigh-Ritz projections share one eigensolver launch
+    const int passes = st.iter == 0 ? std::max(1, p.first_passes) : 1;
+    for (int s = 0; s < ns; ++s)
         if ((rc = hub_set_occupation_matrix(h, s, st.D_in.data() + (size_t)s * nh * 25, nullptr))) return rc;
-        const int passes = st.iter == 0 ? std::max(1, p.first_passes) : 1;
-        for (int pass = 0; pass < passes; ++pass) {
+    for (int pass = 0; pass < passes; ++pass) {
+        for (int s = 0; s < ns; ++s) {
             if (!st.have_bounds[s]) {
                 double lo, up;
                 if ((rc = hub_lanczos_bound(h, s, p.lanczos_steps, st.v0[s], &lo, &up))) return rc;
@@ -583,8 +627,17 @@ int hub_scf_iterate(hub_t h, hub_scf_result* res) {
             }
             if ((rc = hub_chefsi_filter(h, s, st.X[s], p.ncol, p.ld, p.degree, st.bounds[s][1],
                                         st.bounds[s][2], st.bounds[s][0], nullptr))) return rc;
-            double* eg = st.eig.data() + (size_t)s * p.ncol;
-            if ((rc = hub_rayleigh_ritz(h, s, st.X[s], p.ncol, p.ld, eg, nullptr))) return rc;
+            if (ns == 1) {
+                double* eg = st.eig.data();
+                if ((rc = hub_rayleigh_ritz(h, s, st.X[s], p.ncol, p.ld, eg, nullptr))) return rc;
+            }
+        }
+        if (ns == 2) {
+            double* eg[2] = {st.eig.data(), st.eig.data() + p.ncol};
+            if ((rc = rr_two_spins(h, st.X.data(), p.ncol, p.ld, eg))) return rc;
+        }
+        for (int s = 0; s < ns; ++s) {
+            const double* eg = st.eig.data() + (size_t)s * p.ncol;
             st.bounds[s][0] = eg[0];
             st.bounds[s][1] = eg[p.ncol - 1];
         }

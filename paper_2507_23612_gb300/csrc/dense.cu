@@ -177,12 +177,23 @@ __device__ __forceinline__ void pair_of(int step, int k, int N, int& p, int& q) 
 // writes the rotated matrix into the other of two buffers: nothing the step reads is
 // written during it, so one grid barrier per step suffices.  V is rotated in place (only
 // the step's own rotations touch a given V element).
-__global__ void k_jacobi(double* A, double* Ab, double* V, int n, int N, int max_sweeps, double tol,
-                         unsigned int* bar, int* flags, unsigned long long* red, int* sweeps_out) {
+// With nmat = 2 the grid solves two independent matrices of the same size at once: each
+// half of the CTAs owns one matrix, its buffers, its barrier counters and its reduction
+// slots, and only the error flags are shared (a timeout in one half ends both).
+__global__ void k_jacobi(double* A0, double* Ab0, double* V0, double* A1, double* Ab1, double* V1, int nmat,
+                         int n, int N, int max_sweeps, double tol, unsigned int* bar, int* flags,
+                         unsigned long long* red0, unsigned long long* red1, int* sweeps_out) {
     extern __shared__ double rot[];               // [N]: cosine and sine of each pair
-    const unsigned int nb = gridDim.x;
-    const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long nthr = (long)gridDim.x * blockDim.x;
+    const int grp = (nmat == 2 && blockIdx.x >= gridDim.x / 2) ? 1 : 0;
+    const unsigned int nb = nmat == 2 ? gridDim.x / 2 : gridDim.x;
+    double* A = grp ? A1 : A0;
+    double* Ab = grp ? Ab1 : Ab0;
+    double* V = grp ? V1 : V0;
+    unsigned long long* red = grp ? red1 : red0;
+    bar += 2 * grp;
+    sweeps_out += grp;
+    const long tid = (long)(blockIdx.x - grp * nb) * blockDim.x + threadIdx.x;
+    const long nthr = (long)nb * blockDim.x;
     const int H = N / 2;
     double* cur = A;
     double* nxt = Ab;
@@ -207,7 +218,7 @@ __global__ void k_jacobi(double* A, double* Ab, double* V, int n, int N, int max
         if (!grid_barrier(bar, nb, flags)) return;
         const double goff = __longlong_as_double((long long)*((volatile unsigned long long*)acc));
         const double gdia = __longlong_as_double((long long)*((volatile unsigned long long*)(acc + 1)));
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (tid == 0) {                          // the group's first thread
             unsigned long long* other = red + 2 * ((sweep + 1) & 1);
             other[0] = 0ull;
             other[1] = 0ull;
@@ -376,47 +387,66 @@ int dense_symmetrize(hub_t h, double* A, int n) {
 
 // A (n x n symmetric, destroyed) -> eig ascending (device [n]) and V (device n x n row-major,
 // column j = eigenvector j).  Uses 2 n x n + n scratch from the handle.
-int dense_jacobi_eigh(hub_t h, double* A, double* V, double* eig, int n) {
+int dense_jacobi_eigh_multi(hub_t h, int nmat, double* const* A, double* const* V, double* const* eig, int n) {
     if (n == 0) return HUB_OK;
+    if (nmat < 1 || nmat > 2) return fail(h, HUB_EINVAL, "one or two matrices per Jacobi launch");
     const int N = n + (n & 1);
     const size_t nn = (size_t)n * n;
+    const size_t per = 2 * nn + 8;                               // doubles of workspace per matrix
     int rc;
-    size_t need = (2 * nn + 8) * sizeof(double);
-    if ((rc = ensure(h, &h->d_work2, &h->work2_bytes, std::max(need, h->work2_bytes)))) return rc;
-    double* Vt = (double*)h->d_work2;
-    double* Ab = Vt + nn;                                        // second matrix buffer
-    unsigned long long* red = (unsigned long long*)(Ab + nn);   // 4 slots
-    int* sweeps = h->d_flags + 6;
-    {
-        ProfScope ps(h, HUB_K_EIG_MISC);
-        k_eye<<<(unsigned)((nn + 255) / 256), 256, 0, h->stream>>>(Vt, n);
+    if ((rc = ensure(h, &h->d_work2, &h->work2_bytes, std::max(nmat * per * sizeof(double), h->work2_bytes))))
+        return rc;
+    double* Vt[2];
+    double* Ab[2];
+    unsigned long long* red[2];
+    for (int g = 0; g < 2; ++g) {
+        const int m = g < nmat ? g : 0;
+        Vt[g] = (double*)h->d_work2 + m * per;
+        Ab[g] = Vt[g] + nn;                                     // second matrix buffer
+        red[g] = (unsigned long long*)(Ab[g] + nn);             // 4 slots
     }
-    HUB_CUDA_TRY(h, cudaGetLastError());
-    HUB_CUDA_TRY(h, cudaMemsetAsync(red, 0, 4 * sizeof(unsigned long long), h->stream));
+    int* sweeps = h->d_flags + 6;                               // slots 6 and 7
+    for (int g = 0; g < nmat; ++g) {
+        {
+            ProfScope ps(h, HUB_K_EIG_MISC);
+            k_eye<<<(unsigned)((nn + 255) / 256), 256, 0, h->stream>>>(Vt[g], n);
+        }
+        HUB_CUDA_TRY(h, cudaGetLastError());
+        HUB_CUDA_TRY(h, cudaMemsetAsync(red[g], 0, 4 * sizeof(unsigned long long), h->stream));
+    }
     HUB_CUDA_TRY(h, cudaMemsetAsync(h->d_bar, 0, 4 * sizeof(unsigned int), h->stream));
+    HUB_CUDA_TRY(h, cudaMemsetAsync(sweeps, 0, 2 * sizeof(int), h->stream));
     int per_sm = 0;
     const size_t rot_bytes = (size_t)N * sizeof(double);
     if (rot_bytes > 48 * 1024) return fail(h, HUB_EINVAL, "subspace too large for the Jacobi solver");
     HUB_CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, 256, rot_bytes));
-    int blocks = std::max(1, std::min(per_sm, 1)) * h->num_sms;
-    const long work = (long)(N / 2) * (N / 2) + (long)n * (N / 2);
+    int blocks = std::max(1, std::min(per_sm, 1)) * h->num_sms / nmat;   // per matrix
+    const long work = (long)(N / 2) * (N / 2 + 1) / 2 + (long)n * (N / 2);
     blocks = (int)std::min<long>(blocks, std::max<long>(1, (work + 255) / 256));
+    blocks = std::max(1, blocks) * nmat;
     int max_sweeps = 60;
     double tol = 1e-13;
     unsigned int* bar = h->d_bar;
     int* flags = h->d_flags;
-    void* args[] = {&A, &Ab, &Vt, &n, (void*)&N, &max_sweeps, &tol, &bar, &flags, &red, &sweeps};
+    double* A0 = A[0];
+    double* A1 = nmat > 1 ? A[1] : A[0];
+    void* args[] = {&A0, &Ab[0], &Vt[0], &A1, &Ab[1], &Vt[1], &nmat, &n, (void*)&N, &max_sweeps, &tol, &bar,
+                    &flags, &red[0], &red[1], &sweeps};
     {
         ProfScope ps(h, HUB_K_JACOBI);
         HUB_CUDA_TRY(h, cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(blocks), dim3(256), args, rot_bytes,
                                                     h->stream));
     }
-    {
+    for (int g = 0; g < nmat; ++g) {
         ProfScope ps(h, HUB_K_EIG_MISC);
-        k_sort_eig<<<(n + 127) / 128, 128, 0, h->stream>>>(A, Vt, n, eig, V);
+        k_sort_eig<<<(n + 127) / 128, 128, 0, h->stream>>>(A[g], Vt[g], n, eig[g], V[g]);
     }
     HUB_CUDA_TRY(h, cudaGetLastError());
     return HUB_OK;
+}
+
+int dense_jacobi_eigh(hub_t h, double* A, double* V, double* eig, int n) {
+    return dense_jacobi_eigh_multi(h, 1, &A, &V, &eig, n);
 }
 
 }  // namespace hub

@@ -231,6 +231,8 @@ int dense_tri_inverse(hub_t h, const double* L, double* Linv, int n);
 int dense_gemm(hub_t h, bool ta, bool tb, int m, int n, int k, double alpha, const double* A,
                int lda, const double* B, int ldb, double beta, double* C, int ldc);
 int dense_jacobi_eigh(hub_t h, double* A, double* V, double* eig, int n);  // ascending
+// one or two independent n x n problems in one cooperative launch (half the SMs each)
+int dense_jacobi_eigh_multi(hub_t h, int nmat, double* const* A, double* const* V, double* const* eig, int n);
 int dense_symmetrize(hub_t h, double* A, int n);
 
 // misc.cu
