@@ -15,6 +15,7 @@ Paper: "Real-space Hubbard-corrected density functional theory" (arXiv 2507.2361
   * Sec. II.A.1, Eq. (orbital_occup_ext) ...... occupation matrix D
   * Sec. II.A.1, Bloch-mapped atomic orbitals . image sum with Bloch phase
   * Sec. II.A.2, Eqs. (DerED) and V_U ......... Hubbard potential applied to orbitals
+  * Sec. II.A.3, final force equation ......... Hubbard atomic forces (FD gradient form)
   * Sec. II.B, gradient weights equation ...... FD weights family, index wrap, quadrature
   * Sec. II.B, last paragraph ................. CheFSI + Pulay mixing, diagonal initial D
 Readings where the paper is silent (Laplacian weights, filter recurrence, Rayleigh-Ritz
@@ -417,6 +418,41 @@ def occupation_matrices(ham: Hamiltonian, X, f, kweight: float = 1.0):
                 D[m, mp] = kweight * np.sum(np.asarray(f) * np.conj(C[mp]) * C[m])
         out.append(D)
     return np.array(out)
+
+
+def hubbard_forces(ham: Hamiltonian, X, f, kweight: float = 1.0, D=None):
+    """Hubbard atomic forces from one (spin, k-point) set of orbitals (Sec. II.A.3, final
+    force equation, with the derivative moved from the atomic orbitals onto the FD
+    gradient of the orbitals):
+
+        F_J = Re sum_{mm'} U_J (2 D_J,m'm - delta_mm') sum_n w_k f_n
+                 <grad psi_n|phi_Jm'> <phi_Jm|psi_n>
+
+    Reading: the chain rule through dE_U/dD_mm' = (U/2)(delta_mm' - 2 D_m'm) puts D_m'm
+    inside the real part; the printed equation carries D_mm' outside it.  The two agree for
+    the real symmetric D of the Gamma point; only this form is the derivative of E_U for a
+    Hermitian complex D.  D defaults to the occupation matrices the Hamiltonian carries
+    (the self-consistent D at convergence).  X: (Nd, ncol), f: (ncol,).
+    Returns (nhub, 3) for the Hubbard atoms in order; the force on E_U of this term only
+    (the caller sums spins and k-points, and doubles a spin-unpolarized channel)."""
+    D = ham.D if D is None else np.asarray(D)
+    f = np.asarray(f, dtype=np.float64)
+    grads = [gradient(X, ham.grid, a) for a in range(3)]
+    out = np.zeros((len(ham.hub), 3))
+    for I, (idx, vals, U) in enumerate(ham.hub):
+        C = ham.grid.dV * (vals.conj().T @ X[idx])               # <phi_m|psi_n>
+        nm = C.shape[0]
+        for a in range(3):
+            G = ham.grid.dV * (vals.conj().T @ grads[a][idx])     # <phi_m|d_a psi_n>
+            acc = 0.0
+            for m in range(nm):
+                for mp in range(nm):
+                    coef = U * (2.0 * D[I][mp, m] - (1.0 if m == mp else 0.0))
+                    # <grad psi_n|phi_m'> = conj(<phi_m'|grad psi_n>)
+                    s = np.sum(f * np.conj(G[mp]) * C[m])
+                    acc += np.real(coef * kweight * s)
+            out[I, a] = acc
+    return out
 
 
 def hubbard_energy(D, U):

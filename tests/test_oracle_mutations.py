@@ -82,3 +82,40 @@ def test_wrong_filter_recurrence_is_caught(monkeypatch):
     monkeypatch.setattr(o, "chebyshev_filter", bad_filter)
     with pytest.raises(AssertionError):
         tc.test_filter_equals_chebyshev_polynomial_of_dense_H((0.0, 0.0, 0.0))
+
+
+def _force_variant(coef_fn, grad_sign=1.0):
+    """A copy of the oracle's Hubbard force with one planted change: the coefficient of the
+    (m, m') term and the sign of the orbital gradient."""
+    def forces(ham, X, f, kweight=1.0, D=None):
+        D = ham.D if D is None else np.asarray(D)
+        f = np.asarray(f, dtype=np.float64)
+        out = np.zeros((len(ham.hub), 3))
+        for I, (idx, vals, U) in enumerate(ham.hub):
+            C = ham.grid.dV * (vals.conj().T @ X[idx])
+            for a in range(3):
+                G = grad_sign * ham.grid.dV * (vals.conj().T @ o.gradient(X, ham.grid, a)[idx])
+                s = np.einsum("n,pn,mn->mp", f, np.conj(G), C)        # s[m, m']
+                out[I, a] = np.real(np.sum(coef_fn(U, D[I]) * kweight * s))
+        return out
+    return forces
+
+
+@pytest.mark.parametrize("name,coef,sign", [
+    ("dropped delta term", lambda U, D: U * 2.0 * D.T, 1.0),
+    ("D_mm' in the chain-rule slot", lambda U, D: U * (2.0 * D - np.eye(5)), 1.0),
+    ("U/2 instead of U", lambda U, D: 0.5 * U * (2.0 * D.T - np.eye(5)), 1.0),
+    ("gradient sign", lambda U, D: U * (2.0 * D.T - np.eye(5)), -1.0)])
+def test_planted_force_mistakes_are_caught(monkeypatch, name, coef, sign):
+    import test_oracle_forces as tf
+    monkeypatch.setattr(o, "hubbard_forces", _force_variant(coef, sign))
+    F, Ffd = tf.fd_and_formula(tf.K_POINT, n=28)
+    assert np.max(np.abs(F - Ffd)) / np.max(np.abs(Ffd)) > 1e-2, name
+
+
+def test_unplanted_force_variant_passes(monkeypatch):
+    # the einsum rewrite used by the mutations is itself the oracle's formula
+    import test_oracle_forces as tf
+    monkeypatch.setattr(o, "hubbard_forces", _force_variant(lambda U, D: U * (2.0 * D.T - np.eye(5))))
+    F, Ffd = tf.fd_and_formula(tf.K_POINT, n=28)
+    assert np.max(np.abs(F - Ffd)) / np.max(np.abs(Ffd)) < 1e-3
