@@ -6,6 +6,7 @@
  *   Sec. II.A.1  Dudarev energy E_U (Eq. E_U), occupation matrix D (Eq. orbital_occup_ext),
  *                Bloch-periodically mapped atomic orbitals.
  *   Sec. II.A.2  Hubbard potential V_U (Eq. DerED and the V_U equation).
+ *   Sec. II.A.3  Hubbard atomic forces (final force equation, FD gradient form).
  *   Sec. II.B    uniform grid, 2*n0-th order centred finite differences, Bloch-periodic
  *                index wrap, trapezoidal quadrature, atom-by-atom projector integrals
  *                "computed simultaneously", CheFSI with Pulay mixing of D.
@@ -186,6 +187,22 @@ int hub_gram_noalloc(const void* A, int ncol_a, const void* B, int ncol_b, long 
 int hub_occupation(hub_t h, int spin, const void* X, int ncol, int ld, const double* f_host,
                    double kweight, double* D_re_out, double* D_im_out, double* EU_out);
 
+/* Hubbard atomic forces of one (spin, k) block (Sec. II.A.3, final force equation, with
+ * the derivative carried by the FD gradient of the orbitals of Sec. II.B):
+ *   F_J,a = Re sum_mm' U_J (2 D_J,m'm - delta_mm') kweight sum_n f_n
+ *             conj(<phi_Jm'|d_a x_n>) <phi_Jm|x_n>
+ * with D the occupation matrices last set for `spin` (hub_set_occupation_matrix; the
+ * self-consistent D).  This is -dE_U/dR_J of this block alone: the caller sums spins and
+ * k-points and folds a spin degeneracy into kweight.
+ * X: device block [ld x ncol] (handle element type).  f_host: host double [ncol].
+ * F_host: host double [natoms * 3] (the atoms of hub_set_atoms_projectors, x, y, z),
+ * overwritten; atoms without a Hubbard shell get 0.  work: NULL (internal workspace) or a
+ * device buffer of at least ld * ncol elements of the handle type, which receives the
+ * gradient blocks.  Synchronises.  Errors: HUB_EINVAL (bad arguments, NULL pointers),
+ * HUB_ECUDA. */
+int hub_hubbard_forces(hub_t h, int spin, const void* X, int ncol, int ld, const double* f_host,
+                       double kweight, double* F_host, void* work);
+
 /* k-step Lanczos from the device vector v0 [Nd] (handle element type): returns the
  * smallest Ritz value and the largest Ritz value plus |beta_k| (the CheFSI bound
  * estimate).  1 <= steps <= 64.  Synchronises. */
@@ -347,6 +364,7 @@ typedef enum {
     HUB_K_LANCZOS,        /* Lanczos vector updates and dot products */
     HUB_K_COPY,           /* block copies and conversions */
     HUB_K_TABLE,          /* projector table values */
+    HUB_K_FORCE,          /* FD gradient of the orbitals and the Hubbard force reduction */
     HUB_K_COUNT
 } hub_kernel_kind;
 

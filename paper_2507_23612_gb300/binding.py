@@ -53,6 +53,7 @@ _SIGS = {
     "hub_chefsi_filter": [_P, _I, _P, _I, _I, _I, _D, _D, _D, _P],
     "hub_rayleigh_ritz": [_P, _I, _P, _I, _I, _PD, _P],
     "hub_occupation": [_P, _I, _P, _I, _I, _PD, _D, _PD, _PD, _PD],
+    "hub_hubbard_forces": [_P, _I, _P, _I, _I, _PD, _D, _PD, _P],
     "hub_gram": [_P, _P, _I, _P, _I, _I, _D, _P],
     "hub_gram_noalloc": [_P, _I, _P, _I, C.c_longlong, _I, _I, _D, _P, _P],
     "hub_lanczos_bound": [_P, _I, _I, _P, _PD, _PD],
@@ -87,7 +88,7 @@ _SIGS = {
 
 KERNEL_KINDS = ["stencil", "gather", "transform", "scatter", "gram", "gram_reduce", "rotate",
                 "cholesky", "tri_inverse", "dgemm", "jacobi", "eig_misc", "occupation",
-                "lanczos", "copy", "table"]
+                "lanczos", "copy", "table", "force"]
 
 
 def batch_filter(hubs, spins, Xs, degree: int, a, b, a_low, stream=None):
@@ -221,6 +222,7 @@ class Hub:
         n = C.c_int()
         self._check(self.lib.hub_num_hubbard_atoms(self.h, C.byref(n)), "hub_num_hubbard_atoms")
         self.nhub = n.value
+        self.natoms = nat
 
     def set_occupation_matrix(self, spin: int, D, D_im=None):
         Dr = np.ascontiguousarray(np.real(D), dtype=np.float64).reshape(-1)
@@ -266,6 +268,15 @@ class Hub:
         self._check(self.lib.hub_occupation(self.h, spin, _tptr(X), ncol, ld, _dptr(f), kweight,
                                             _dptr(Dr), _dptr(Di), C.byref(eu)), "hub_occupation")
         return Dr[:self.nhub], Di[:self.nhub], eu.value
+
+    def hubbard_forces(self, spin: int, X, f, kweight: float = 1.0, work=None) -> np.ndarray:
+        """Hubbard forces (natoms, 3) of one (spin, k) block with the D last set for `spin`."""
+        ncol, ld = X.shape
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        F = np.zeros((max(self.natoms, 1), 3))
+        self._check(self.lib.hub_hubbard_forces(self.h, spin, _tptr(X), ncol, ld, _dptr(f), kweight,
+                                                _dptr(F), _tptr(work)), "hub_hubbard_forces")
+        return F[:self.natoms]
 
     def lanczos_bound(self, spin: int, steps: int, v0):
         lo, up = C.c_double(), C.c_double()

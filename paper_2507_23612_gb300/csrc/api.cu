@@ -450,6 +450,51 @@ int hub_occupation(hub_t h, int spin, const void* X, int ncol, int ld, const dou
     return HUB_OK;
 }
 
+int hub_hubbard_forces(hub_t h, int spin, const void* X, int ncol, int ld, const double* f_host,
+                       double kweight, double* F_host, void* work) {
+    int rc = check_block(h, spin, X, ncol, ld);
+    if (rc) return rc;
+    if (!F_host) return fail(h, HUB_EINVAL, "NULL force output");
+    if (ncol > 0 && !f_host) return fail(h, HUB_EINVAL, "NULL occupations");
+    const Table& t = h->proj;
+    std::fill(F_host, F_host + (size_t)t.natoms * 3, 0.0);
+    if (t.nhub == 0 || ncol == 0) return HUB_OK;
+    // first-derivative weights of Sec. II.B per axis (1/h_a included)
+    auto fact = [](int k) { double r = 1.0; for (int i = 2; i <= k; ++i) r *= i; return r; };
+    double w[3][kMaxHalf];
+    for (int ax = 0; ax < 3; ++ax)
+        for (int p = 1; p <= h->n0; ++p)
+            w[ax][p - 1] = ((p % 2) ? 1.0 : -1.0) * fact(h->n0) * fact(h->n0) /
+                           (h->h[ax] * p * fact(h->n0 - p) * fact(h->n0 + p));
+    void* G = work;
+    if (!G) {
+        if ((rc = ensure(h, &h->d_work, &h->work_bytes, (size_t)ld * ncol * elem_bytes(h)))) return rc;
+        G = h->d_work;
+    }
+    // C of X set aside, then one gather of each gradient component
+    if ((rc = launch_gather(h, X, ncol, ld, spin, false))) return rc;
+    const int cw = h->cplx ? 2 : 1;
+    const size_t nC = (size_t)t.nproj * ncol * cw;
+    const size_t need = (nC + ncol + (size_t)t.nhub * 3) * sizeof(double);
+    if ((rc = ensure(h, &h->d_aux, &h->aux_bytes, std::max(need, h->aux_bytes)))) return rc;
+    double* C0 = (double*)h->d_aux;
+    double* f_dev = C0 + nC;
+    double* F_dev = f_dev + ncol;
+    HUB_CUDA_TRY(h, cudaMemcpyAsync(C0, h->d_C, nC * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    HUB_CUDA_TRY(h, cudaMemcpyAsync(f_dev, f_host, ncol * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    for (int ax = 0; ax < 3; ++ax) {
+        if ((rc = launch_fd_gradient(h, X, ld, ncol, ax, w[ax], G))) return rc;
+        if ((rc = launch_gather(h, G, ncol, ld, spin, false))) return rc;
+        if ((rc = launch_hub_force(h, spin, ncol, f_dev, kweight, C0, ax, F_dev))) return rc;
+    }
+    std::vector<double> F((size_t)t.nhub * 3);
+    HUB_CUDA_TRY(h, cudaMemcpyAsync(F.data(), F_dev, F.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if ((rc = check_flags(h))) return rc;
+    for (int i = 0; i < t.nhub; ++i)
+        for (int ax = 0; ax < 3; ++ax) F_host[(size_t)t.h_hub_atom[i] * 3 + ax] = F[(size_t)i * 3 + ax];
+    return HUB_OK;
+}
+
 int hub_projector_stats(hub_t h, long long* function_points, long long* site_points) {
     if (!h) return HUB_EINVAL;
     if (function_points) *function_points = h->proj.nvals;

@@ -51,6 +51,8 @@ struct Table {
     int nsites = 0, nproj = 0, npts = 0, nvals = 0, nhub = 0, nitems = 0;
     std::vector<SiteDev> h_sites;
     std::vector<int> h_hub_sites;     // site index of each Hubbard atom
+    std::vector<int> h_hub_atom;      // atom index of each Hubbard atom
+    int natoms = 0;
     std::vector<double> h_U;          // U per Hubbard atom (Ha)
     std::vector<int> h_item_first;    // first gather item of each site, size nsites + 1
     SiteDev* d_sites = nullptr;
@@ -209,6 +211,16 @@ int launch_scatter(hub_t h, void* Y, int ncol, int ld, double alpha, const doubl
 // D per Hubbard atom (double, [nhub*50] re/im pairs) and E_U into d_scal[0] from the C of
 // the last launch_gather; f_dev [ncol] double.
 int launch_occupation(hub_t h, int ncol, const double* f_dev, double kweight, double* D_dev);
+// F_dev[hsite*3 + axis] = -2 kweight Re sum_n f_n sum_m' conj(G_m'n) (M_spin C)_m'n per
+// Hubbard atom, from C0 (the C of a gather of X, copied aside) and the C of the last
+// launch_gather (a gather of d_axis X)
+int launch_hub_force(hub_t h, int spin, int ncol, const double* f_dev, double kweight,
+                     const void* C0, int axis, double* F_dev);
+
+// stencil.cu: G = d_axis X by the FD gradient of Sec. II.B (weights w[p-1] include 1/h),
+// Bloch factor exp(i k_a L_a) per wrap (complex only); X, G share ld
+int launch_fd_gradient(hub_t h, const void* X, int ld, int ncol, int axis, const double* w,
+                       void* G);
 
 // gemm.cu
 // G[m x n] = alpha * A^H B, A: [K x m] (lda), B: [K x n] (ldb); K = Nd. Out double, row-major

@@ -585,6 +585,66 @@ __global__ void k_occupation(int ncol, const SiteDev* __restrict__ sites, const 
     }
 }
 
+// ---------------------------------------------------------------------------- forces
+// Hubbard force component `axis` of each Hubbard atom (Sec. II.A.3, final force equation):
+//   F = Re sum_mm' U (2 D_m'm - delta_mm') kweight sum_n f_n conj(G_m'n) C_mn
+//     = -2 kweight Re sum_n f_n sum_m' conj(G_m'n) W_m'n,   W = M C,  M = (U/2)(I - 2D)
+// with C_mn = <phi_m|x_n> and G_m'n = <phi_m'|d_axis x_n>.  One CTA per Hubbard atom, a
+// deterministic reduction over the columns.
+template <bool CPLX>
+__global__ void k_hub_force(int ncol, const SiteDev* __restrict__ sites, const int* __restrict__ hub_sites,
+                            const typename VT<double, CPLX>::T* __restrict__ C,
+                            const typename VT<double, CPLX>::T* __restrict__ G,
+                            const double* __restrict__ f, double kweight, const double* __restrict__ M,
+                            int axis, double* __restrict__ F) {
+    using Dt = typename VT<double, CPLX>::T;
+    const int hsite = blockIdx.x;
+    const SiteDev S = sites[hub_sites[hsite]];
+    __shared__ double Ms[25][2];
+    __shared__ double red[32];
+    if (threadIdx.x < 25) {
+        if constexpr (CPLX) {
+            Ms[threadIdx.x][0] = M[((size_t)hsite * 25 + threadIdx.x) * 2];
+            Ms[threadIdx.x][1] = M[((size_t)hsite * 25 + threadIdx.x) * 2 + 1];
+        } else {
+            Ms[threadIdx.x][0] = M[(size_t)hsite * 25 + threadIdx.x];
+            Ms[threadIdx.x][1] = 0.0;
+        }
+    }
+    __syncthreads();
+    double acc = 0.0;
+    for (int n = threadIdx.x; n < ncol; n += blockDim.x) {
+        Dt c[5];
+        for (int m = 0; m < 5; ++m) c[m] = C[(size_t)(S.proj_off + m) * ncol + n];
+        double s = 0.0;
+        for (int p = 0; p < 5; ++p) {
+            const Dt g = G[(size_t)(S.proj_off + p) * ncol + n];
+            if constexpr (CPLX) {
+                double wr = 0.0, wi = 0.0;       // W_p = sum_m M_pm C_m
+                for (int m = 0; m < 5; ++m) {
+                    wr += Ms[p * 5 + m][0] * c[m].x - Ms[p * 5 + m][1] * c[m].y;
+                    wi += Ms[p * 5 + m][0] * c[m].y + Ms[p * 5 + m][1] * c[m].x;
+                }
+                s += g.x * wr + g.y * wi;        // Re(conj(g) W)
+            } else {
+                double w = 0.0;
+                for (int m = 0; m < 5; ++m) w += Ms[p * 5 + m][0] * c[m];
+                s += g * w;
+            }
+        }
+        acc += f[n] * s;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) red[wid] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += red[w];
+        F[(size_t)hsite * 3 + axis] = -2.0 * kweight * t;
+    }
+}
+
 __global__ void k_sum_serial(const double* __restrict__ x, int n, double* __restrict__ out) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         double s = 0.0;
@@ -762,6 +822,7 @@ int build_tables(hub_t h, int natoms, const double* pos, const int* kb_nchan, co
                 S.hub_index = (int)t.h_U.size();
                 t.h_U.push_back(hub_U[a]);
                 t.h_hub_sites.push_back((int)t.h_sites.size());
+                t.h_hub_atom.push_back(a);
             }
             if (!(S.rc > 0)) return fail(h, HUB_EINVAL, "cutoff radius must be > 0");
             int np = 0;
@@ -832,6 +893,7 @@ int build_tables(hub_t h, int natoms, const double* pos, const int* kb_nchan, co
     }
     t.nsites = (int)t.h_sites.size();
     t.nhub = (int)t.h_U.size();
+    t.natoms = natoms;
 
     // flat row -> grid index, gather items, CSR of entries per grid point
     std::vector<int> idx(t.npts);
@@ -1055,6 +1117,23 @@ int launch_occupation(hub_t h, int ncol, const double* f_dev, double kweight, do
     HUB_CUDA_TRY(h, cudaGetLastError());
     ProfScope ps2(h, HUB_K_OCCUPATION);
     k_sum_serial<<<1, 32, 0, h->stream>>>(eu, t.nhub, h->d_scal);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    return HUB_OK;
+}
+
+int launch_hub_force(hub_t h, int spin, int ncol, const double* f_dev, double kweight,
+                     const void* C0, int axis, double* F_dev) {
+    Table& t = h->proj;
+    if (t.nhub == 0 || ncol == 0) return HUB_OK;
+    ProfScope ps(h, HUB_K_FORCE);
+    if (h->cplx)
+        k_hub_force<true><<<t.nhub, 256, 0, h->stream>>>(ncol, t.d_sites, t.d_hub_sites, (const double2*)C0,
+                                                        (const double2*)h->d_C, f_dev, kweight, t.d_M[spin],
+                                                        axis, F_dev);
+    else
+        k_hub_force<false><<<t.nhub, 256, 0, h->stream>>>(ncol, t.d_sites, t.d_hub_sites, (const double*)C0,
+                                                         (const double*)h->d_C, f_dev, kweight, t.d_M[spin],
+                                                         axis, F_dev);
     HUB_CUDA_TRY(h, cudaGetLastError());
     return HUB_OK;
 }

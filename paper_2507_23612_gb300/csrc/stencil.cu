@@ -15,6 +15,9 @@
 // Slots that wrapped across a cell face get the Bloch factor exp(i k_a L_a)^wraps (only
 // for complex elements; real Gamma-point data is copied untouched).  Yprev may alias Yout:
 // each element is read (through the ring) before the same thread writes it.
+#include <algorithm>
+#include <cmath>
+
 #include "hub_internal.cuh"
 #include "cplx.cuh"
 
@@ -841,6 +844,79 @@ static int run_cfg(hub_t h, const StencilArgs& s) {
     dim3 grid((s.n1 + TX - 1) / TX, (s.n2 + TY - 1) / TY, s.ncol * nzc);
     ProfScope ps(h, HUB_K_STENCIL);
     k_stencil<R, CPLX, TX, TY, P><<<grid, TX * TY, Cfg::SMEM, h->stream>>>(d);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    return HUB_OK;
+}
+
+// ---------------------------------------------------------------------------- gradient
+// G = d_axis X by the 2*n0-th order centred first derivative of Sec. II.B:
+//   G_i = sum_p w_p (X_{i+p} - X_{i-p}),  w_p = (-1)^{p+1} (n0!)^2 / (h p (n0-p)! (n0+p)!)
+// An index past a cell face maps back with exp(i k_a L_a) per crossing (complex only).
+// One thread per element, grid-stride; the sums run in double.  Used once per force
+// evaluation, outside the filter, so it is a plain gather form rather than a staged tile.
+struct GradArgs {
+    double w[kMaxHalf];
+    double ph_re, ph_im;
+    int n0, axis;
+};
+
+template <typename R, bool CPLX>
+__global__ void k_fd_gradient(const typename VT<R, CPLX>::T* __restrict__ X, int ld, int ncol, int n1, int n2,
+                              int n3, GradArgs a, typename VT<R, CPLX>::T* __restrict__ G) {
+    using T = typename VT<R, CPLX>::T;
+    using D = typename VT<double, CPLX>::T;
+    const long Nd = (long)n1 * n2 * n3;
+    const long total = Nd * ncol;
+    const int n = a.axis == 0 ? n1 : (a.axis == 1 ? n2 : n3);
+    const long stride = a.axis == 0 ? 1 : (a.axis == 1 ? (long)n1 : (long)n1 * n2);
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const long col = e / Nd;
+        const long g = e - col * Nd;
+        const int c = (int)((a.axis == 0) ? g % n1 : (a.axis == 1 ? (g / n1) % n2 : g / ((long)n1 * n2)));
+        const T* xc = X + col * ld + (g - (long)c * stride);   // start of this point's line
+        D acc = zero_of(D{});
+        for (int p = 1; p <= a.n0; ++p) {
+            int cf = c + p, wf = 0;
+            while (cf >= n) { cf -= n; ++wf; }
+            int cb = c - p, wb = 0;
+            while (cb < 0) { cb += n; --wb; }
+            const T xf = xc[(long)cf * stride], xb = xc[(long)cb * stride];
+            if constexpr (CPLX) {
+                const double2 pf = phase_pow<double2>(a.ph_re, a.ph_im, wf);
+                const double2 pb = phase_pow<double2>(a.ph_re, a.ph_im, wb);
+                const double2 vf = cmul(pf, make_double2(xf.x, xf.y));
+                const double2 vb = cmul(pb, make_double2(xb.x, xb.y));
+                acc.x = fma(a.w[p - 1], vf.x - vb.x, acc.x);
+                acc.y = fma(a.w[p - 1], vf.y - vb.y, acc.y);
+            } else {
+                acc = fma(a.w[p - 1], (double)xf - (double)xb, acc);
+            }
+        }
+        if constexpr (CPLX) G[col * ld + g] = T{(R)acc.x, (R)acc.y};
+        else G[col * ld + g] = (T)acc;
+    }
+}
+
+int launch_fd_gradient(hub_t h, const void* X, int ld, int ncol, int axis, const double* w, void* G) {
+    if (ncol == 0) return HUB_OK;
+    GradArgs a{};
+    for (int p = 0; p < h->n0; ++p) a.w[p] = w[p];
+    a.n0 = h->n0;
+    a.axis = axis;
+    const double th = h->kpt[axis] * h->L[axis];
+    a.ph_re = std::cos(th);
+    a.ph_im = std::sin(th);
+    const long total = h->Nd * (long)ncol;
+    const long want = (total + 255) / 256;
+    const unsigned blocks = (unsigned)std::min<long>(want, (long)h->num_sms * 16);
+    ProfScope ps(h, HUB_K_FORCE);
+    if (h->esize == 8) {
+        if (h->cplx) k_fd_gradient<double, true><<<blocks, 256, 0, h->stream>>>((const double2*)X, ld, ncol, h->n1, h->n2, h->n3, a, (double2*)G);
+        else k_fd_gradient<double, false><<<blocks, 256, 0, h->stream>>>((const double*)X, ld, ncol, h->n1, h->n2, h->n3, a, (double*)G);
+    } else {
+        if (h->cplx) k_fd_gradient<float, true><<<blocks, 256, 0, h->stream>>>((const float2*)X, ld, ncol, h->n1, h->n2, h->n3, a, (float2*)G);
+        else k_fd_gradient<float, false><<<blocks, 256, 0, h->stream>>>((const float*)X, ld, ncol, h->n1, h->n2, h->n3, a, (float*)G);
+    }
     HUB_CUDA_TRY(h, cudaGetLastError());
     return HUB_OK;
 }

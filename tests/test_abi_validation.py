@@ -76,3 +76,8 @@ def test_gram_noalloc_rejects_bad_arguments_before_any_device_work(lib):
     assert lib.hub_gram_noalloc(None, 4, None, 4, 1024, 1000, 0, 1.0, None, None) == EINVAL   # ld < nrows
     assert lib.hub_gram_noalloc(None, 4, None, 4, 1024, 1024, 2, 1.0, None, None) == EINVAL   # precision
     assert lib.hub_gram_noalloc(None, 0, None, 4, 1024, 1024, 0, 1.0, None, None) == 0        # empty: no work
+
+
+def test_hubbard_forces_rejects_a_null_handle(lib):
+    F = (C.c_double * 3)()
+    assert lib.hub_hubbard_forces(None, 0, None, 0, 0, None, 1.0, F, None) == EINVAL
