@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--probe-apply", type=int, default=0, metavar="NCOL",
                     help="profiling case: four H applications to NCOL random columns of the rutile "
                          "workload in --prec, then exit (no timing)")
+    ap.add_argument("--forces", action="store_true",
+                    help="time hub_hubbard_forces on the rutile workload (348 orbitals, one spin) "
+                         "in --prec and report the FD-gradient kernel against the HBM roofline")
     ap.add_argument("--scf-compare", action="store_true",
                     help="cold-start SCF to convergence in FP64, FP32 and mixed (BF16 with the "
                          "precision ladder); report time to solution and errors against FP64")
@@ -629,8 +632,57 @@ def probe_apply(args):
     return 0
 
 
+def run_forces(args):
+    """Hubbard forces of one (spin, k) block of the rutile workload: three FD gradients of
+    the 348-orbital block, four projector gathers and the per-atom reductions per call.
+    The gradient kernel reads X and writes d_a X once each (16 B per point-orbital in FP64,
+    8 B in float), so its roofline is HBM.  Times with CUDA events on the library's stream."""
+    import math
+    import numpy as np
+    import torch
+    import workloads as w
+    from paper_2507_23612_gb300 import Hub
+    wl = w.rutile()
+    dev = torch.device("cuda", 0)
+    hub = Hub(wl.n, wl.L, wl.fd_half_order, prec=PREC[args.prec])
+    hub.set_veff(torch.tensor(wl.veff, device=dev))
+    hub.set_atoms(wl.atoms)
+    hub.set_occupation_matrix(0, wl.D0[0])
+    g = torch.Generator(device=dev).manual_seed(5)
+    X = torch.randn(wl.ncol, wl.Nd, device=dev, dtype=torch.float64, generator=g).to(hub.dtype).contiguous()
+    X /= (X.double().norm(dim=1, keepdim=True) * math.sqrt(wl.dV)).to(X.dtype)
+    f = np.linspace(1.0, 0.0, wl.ncol)
+    work = torch.empty_like(X)
+    for _ in range(max(args.warmup, 1)):
+        F = hub.hubbard_forces(0, X, f, 1.0, work=work)
+    torch.cuda.synchronize()
+    hub.profile(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        F = hub.hubbard_forces(0, X, f, 1.0, work=work)
+    wall_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    prof = hub.profile_read()
+    hub.profile(0)
+    grad_ms, grad_n = prof.get("force", (0.0, 0))
+    per_launch = grad_ms / max(grad_n, 1)
+    bytes_per = (16 if hub.dtype == torch.float64 else 8) * wl.Nd * wl.ncol
+    peak = hbm_peak()[0]
+    achieved = bytes_per / (per_launch * 1e-3) / 1e9 if per_launch > 0 else None
+    print(json.dumps({"probe": "hubbard_forces", "prec": args.prec, "grid": list(wl.n),
+                      "orbitals": wl.ncol, "hubbard_atoms": hub.nhub, "ms_per_call": wall_ms,
+                      "gradient": {"ms_per_launch": per_launch, "launches": grad_n,
+                                   "achieved_gbs": achieved, "peak_gbs": peak,
+                                   "frac": achieved / peak if achieved and peak else None},
+                      "kernels": {k: v for k, v in prof.items() if v[1]},
+                      "max_abs_force": float(np.max(np.abs(F)))}))
+    hub.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.forces:
+        return run_forces(args)
     if args.probe_apply:
         return probe_apply(args)
     if args.probe_alu:

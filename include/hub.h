@@ -360,11 +360,11 @@ typedef enum {
     HUB_K_DGEMM,          /* small n x n products */
     HUB_K_JACOBI,         /* subspace eigensolver */
     HUB_K_EIG_MISC,       /* symmetrise, identity, sort */
-    HUB_K_OCCUPATION,     /* D and E_U reduction */
+    HUB_K_OCCUPATION,     /* D and E_U reduction; per-atom Hubbard force reduction */
     HUB_K_LANCZOS,        /* Lanczos vector updates and dot products */
     HUB_K_COPY,           /* block copies and conversions */
     HUB_K_TABLE,          /* projector table values */
-    HUB_K_FORCE,          /* FD gradient of the orbitals and the Hubbard force reduction */
+    HUB_K_FORCE,          /* FD gradient of the orbitals (Hubbard forces) */
     HUB_K_COUNT
 } hub_kernel_kind;
 

@@ -1125,7 +1125,7 @@ int launch_hub_force(hub_t h, int spin, int ncol, const double* f_dev, double kw
                      const void* C0, int axis, double* F_dev) {
     Table& t = h->proj;
     if (t.nhub == 0 || ncol == 0) return HUB_OK;
-    ProfScope ps(h, HUB_K_FORCE);
+    ProfScope ps(h, HUB_K_OCCUPATION);
     if (h->cplx)
         k_hub_force<true><<<t.nhub, 256, 0, h->stream>>>(ncol, t.d_sites, t.d_hub_sites, (const double2*)C0,
                                                         (const double2*)h->d_C, f_dev, kweight, t.d_M[spin],

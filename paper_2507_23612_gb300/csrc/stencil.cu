@@ -852,48 +852,71 @@ static int run_cfg(hub_t h, const StencilArgs& s) {
 // G = d_axis X by the 2*n0-th order centred first derivative of Sec. II.B:
 //   G_i = sum_p w_p (X_{i+p} - X_{i-p}),  w_p = (-1)^{p+1} (n0!)^2 / (h p (n0-p)! (n0+p)!)
 // An index past a cell face maps back with exp(i k_a L_a) per crossing (complex only).
-// One thread per element, grid-stride; the sums run in double.  Used once per force
-// evaluation, outside the filter, so it is a plain gather form rather than a staged tile.
+// One warp per grid row (fixed y, z) of one column, lanes along x: no per-element index
+// division, coalesced loads; the neighbours along y and z are rows of the same column that
+// neighbouring warps also read, so they come from L1/L2.  Sums in the working type (float
+// blocks stay on the float pipe; FP64 is bound by the FP64 pipe: 12 operations per element).
 struct GradArgs {
     double w[kMaxHalf];
     double ph_re, ph_im;
     int n0, axis;
 };
 
+constexpr int kGradRows = 8;   // warps (rows) per CTA
+
+template <typename T>
+__device__ __forceinline__ T sub(T a, T b);
+template <> __device__ __forceinline__ double sub(double a, double b) { return a - b; }
+template <> __device__ __forceinline__ float sub(float a, float b) { return a - b; }
+template <> __device__ __forceinline__ double2 sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+template <> __device__ __forceinline__ float2 sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
 template <typename R, bool CPLX>
-__global__ void k_fd_gradient(const typename VT<R, CPLX>::T* __restrict__ X, int ld, int ncol, int n1, int n2,
-                              int n3, GradArgs a, typename VT<R, CPLX>::T* __restrict__ G) {
+__global__ void __launch_bounds__(32 * kGradRows)
+k_fd_gradient(const typename VT<R, CPLX>::T* __restrict__ X, int ld, int n1, int n2, int n3, GradArgs a,
+              typename VT<R, CPLX>::T* __restrict__ G) {
     using T = typename VT<R, CPLX>::T;
-    using D = typename VT<double, CPLX>::T;
-    const long Nd = (long)n1 * n2 * n3;
-    const long total = Nd * ncol;
-    const int n = a.axis == 0 ? n1 : (a.axis == 1 ? n2 : n3);
-    const long stride = a.axis == 0 ? 1 : (a.axis == 1 ? (long)n1 : (long)n1 * n2);
-    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
-        const long col = e / Nd;
-        const long g = e - col * Nd;
-        const int c = (int)((a.axis == 0) ? g % n1 : (a.axis == 1 ? (g / n1) % n2 : g / ((long)n1 * n2)));
-        const T* xc = X + col * ld + (g - (long)c * stride);   // start of this point's line
-        D acc = zero_of(D{});
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * kGradRows + (threadIdx.x >> 5);   // row = y + n2 * z
+    if (row >= n2 * n3) return;
+    const int y = row % n2, z = row / n2;
+    const T* xc = X + (long)blockIdx.y * ld;
+    T* gc = G + (long)blockIdx.y * ld;
+    const long own = (long)row * n1;
+    R w[kMaxHalf];
+    for (int p = 0; p < kMaxHalf; ++p) w[p] = (R)a.w[p];
+    for (int x = lane; x < n1; x += 32) {
+        T acc = zero_of(T{});
         for (int p = 1; p <= a.n0; ++p) {
-            int cf = c + p, wf = 0;
-            while (cf >= n) { cf -= n; ++wf; }
-            int cb = c - p, wb = 0;
-            while (cb < 0) { cb += n; --wb; }
-            const T xf = xc[(long)cf * stride], xb = xc[(long)cb * stride];
-            if constexpr (CPLX) {
-                const double2 pf = phase_pow<double2>(a.ph_re, a.ph_im, wf);
-                const double2 pb = phase_pow<double2>(a.ph_re, a.ph_im, wb);
-                const double2 vf = cmul(pf, make_double2(xf.x, xf.y));
-                const double2 vb = cmul(pb, make_double2(xb.x, xb.y));
-                acc.x = fma(a.w[p - 1], vf.x - vb.x, acc.x);
-                acc.y = fma(a.w[p - 1], vf.y - vb.y, acc.y);
+            long of, ob;       // offsets of the +p and -p neighbours in the column
+            int wf = 0, wb = 0;
+            if (a.axis == 0) {
+                int xf = x + p, xb = x - p;
+                while (xf >= n1) { xf -= n1; ++wf; }
+                while (xb < 0) { xb += n1; --wb; }
+                of = own + xf;
+                ob = own + xb;
+            } else if (a.axis == 1) {
+                int yf = y + p, yb = y - p;
+                while (yf >= n2) { yf -= n2; ++wf; }
+                while (yb < 0) { yb += n2; --wb; }
+                of = ((long)z * n2 + yf) * n1 + x;
+                ob = ((long)z * n2 + yb) * n1 + x;
             } else {
-                acc = fma(a.w[p - 1], (double)xf - (double)xb, acc);
+                int zf = z + p, zb = z - p;
+                while (zf >= n3) { zf -= n3; ++wf; }
+                while (zb < 0) { zb += n3; --wb; }
+                of = ((long)zf * n2 + y) * n1 + x;
+                ob = ((long)zb * n2 + y) * n1 + x;
             }
+            T vf = xc[of], vb = xc[ob];
+            if constexpr (CPLX) {
+                if (wf) vf = cmul(phase_pow<T>(a.ph_re, a.ph_im, wf), vf);
+                if (wb) vb = cmul(phase_pow<T>(a.ph_re, a.ph_im, wb), vb);
+            }
+            acc = fmar(w[p - 1], sub(vf, vb), acc);
         }
-        if constexpr (CPLX) G[col * ld + g] = T{(R)acc.x, (R)acc.y};
-        else G[col * ld + g] = (T)acc;
+        gc[own + x] = acc;
     }
 }
 
@@ -906,16 +929,16 @@ int launch_fd_gradient(hub_t h, const void* X, int ld, int ncol, int axis, const
     const double th = h->kpt[axis] * h->L[axis];
     a.ph_re = std::cos(th);
     a.ph_im = std::sin(th);
-    const long total = h->Nd * (long)ncol;
-    const long want = (total + 255) / 256;
-    const unsigned blocks = (unsigned)std::min<long>(want, (long)h->num_sms * 16);
+    if (ncol > 65535) return fail(h, HUB_EINVAL, "at most 65535 columns per gradient launch");
+    const dim3 grid((unsigned)((h->n2 * h->n3 + kGradRows - 1) / kGradRows), (unsigned)ncol);
+    const int threads = 32 * kGradRows;
     ProfScope ps(h, HUB_K_FORCE);
     if (h->esize == 8) {
-        if (h->cplx) k_fd_gradient<double, true><<<blocks, 256, 0, h->stream>>>((const double2*)X, ld, ncol, h->n1, h->n2, h->n3, a, (double2*)G);
-        else k_fd_gradient<double, false><<<blocks, 256, 0, h->stream>>>((const double*)X, ld, ncol, h->n1, h->n2, h->n3, a, (double*)G);
+        if (h->cplx) k_fd_gradient<double, true><<<grid, threads, 0, h->stream>>>((const double2*)X, ld, h->n1, h->n2, h->n3, a, (double2*)G);
+        else k_fd_gradient<double, false><<<grid, threads, 0, h->stream>>>((const double*)X, ld, h->n1, h->n2, h->n3, a, (double*)G);
     } else {
-        if (h->cplx) k_fd_gradient<float, true><<<blocks, 256, 0, h->stream>>>((const float2*)X, ld, ncol, h->n1, h->n2, h->n3, a, (float2*)G);
-        else k_fd_gradient<float, false><<<blocks, 256, 0, h->stream>>>((const float*)X, ld, ncol, h->n1, h->n2, h->n3, a, (float*)G);
+        if (h->cplx) k_fd_gradient<float, true><<<grid, threads, 0, h->stream>>>((const float2*)X, ld, h->n1, h->n2, h->n3, a, (float2*)G);
+        else k_fd_gradient<float, false><<<grid, threads, 0, h->stream>>>((const float*)X, ld, h->n1, h->n2, h->n3, a, (float*)G);
     }
     HUB_CUDA_TRY(h, cudaGetLastError());
     return HUB_OK;
