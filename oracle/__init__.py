@@ -4,4 +4,4 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py`` (its CPU-baseline 
 reference legs) may import this package.  The CUDA library never imports, links or calls
 it, and it imports nothing from the library.
 """
-from . import hubbard, mlp  # noqa: F401
+from . import density_scf, hubbard, mlp  # noqa: F401

@@ -119,3 +119,42 @@ def test_unplanted_force_variant_passes(monkeypatch):
     monkeypatch.setattr(o, "hubbard_forces", _force_variant(lambda U, D: U * (2.0 * D.T - np.eye(5))))
     F, Ffd = tf.fd_and_formula(tf.K_POINT, n=28)
     assert np.max(np.abs(F - Ffd)) / np.max(np.abs(Ffd)) < 1e-3
+
+
+def test_planted_density_scf_mistakes_are_caught(monkeypatch):
+    import test_oracle_density_scf as tds
+    from oracle import density_scf as ds
+    good_h = ds.hartree_potential
+    good_x = ds.lda_exchange
+    # Hartree with the wrong sign
+    monkeypatch.setattr(ds, "hartree_potential", lambda rho, g: -good_h(rho, g))
+    with pytest.raises(AssertionError):
+        tds.test_hartree_solves_the_fd_poisson_problem()
+    monkeypatch.setattr(ds, "hartree_potential", good_h)
+
+    # exchange potential without the 4/3 of the derivative
+    def bad_x(rhos, g):
+        v, E = good_x(rhos, g)
+        return [0.75 * vv for vv in v], E
+    monkeypatch.setattr(ds, "lda_exchange", bad_x)
+    with pytest.raises(AssertionError):
+        tds.test_exchange_potential_is_the_derivative_of_the_energy(1)
+    monkeypatch.setattr(ds, "lda_exchange", good_x)
+
+    # two channels without the spin-scaling factor 2^(1/3)
+    def bad_spin(rhos, g):
+        v, E = good_x(rhos, g)
+        if len(rhos) == 2:
+            f = 2.0 ** (-1.0 / 3.0)
+            return [f * vv for vv in v], f * E
+        return v, E
+    monkeypatch.setattr(ds, "lda_exchange", bad_spin)
+    with pytest.raises(AssertionError):
+        tds.test_spin_scaling_relation()
+    monkeypatch.setattr(ds, "lda_exchange", good_x)
+
+    # the band-structure energy without the Hubbard double counting: the identity with the
+    # directly evaluated functional breaks
+    monkeypatch.setattr(ds, "hubbard_double_counting", lambda ham, D: 0.0)
+    with pytest.raises(AssertionError):
+        tds.test_model_b_scf_spin_polarized()
