@@ -239,6 +239,21 @@ typedef struct {
                              products (hub_set_bf16_terms 0) for the remaining iterations;
                              0 = keep the handle's setting */
     double ladder_tol;    /* Ha/atom */
+    /* self-consistent density (appended; zero-initialised parameters keep the fixed-V_eff
+     * SCF).  density = 1: V_eff^s = V_loc + V_H[rho_in] + v_x^s[rho_in], V_loc the potential
+     * last set by hub_set_veff; V_H from -Lap_h V_H = 4 pi (rho - mean rho) (mean zero, the
+     * kinetic term's FD Laplacian); v_x local-density (Dirac-Slater) exchange, spin-scaled
+     * for two channels; rho_in starts uniform (n_elec / volume); the upper filter bound is
+     * re-estimated by Lanczos every iteration; Pulay (pulay_history, pulay_beta) on the
+     * joint vector [rho, D] with the Kerker preconditioner (-Lap)(-Lap + kappa^2)^-1 on the
+     * density block (Sec. II.B: preconditioned Pulay whose coefficients also mix D); energy
+     *   E = sum f eig - sum_s int rho_out^s (V_H + v_x^s)[rho_in] + E_H[rho_out] + E_x[rho_out]
+     *       - sum_I Tr(M_in D_out) + E_U(D_out) - kT S;
+     * converged when, in addition, int |rho_out - rho_in| / n_elec < tol_rho. */
+    int density;
+    double kerker_kappa;  /* bohr^-1 (0.5 when 0) */
+    double tol_rho;       /* (1e-4 when 0) */
+    double cg_tol;        /* relative residual of the Poisson and Kerker CG solves (1e-10 when 0) */
 } hub_scf_params;
 
 typedef struct {
@@ -247,6 +262,10 @@ typedef struct {
     double E, E_band, E_U, dE, dD, mu;
     int bf16_terms;       /* products used in this iteration on mixed handles (1, 3, 0) */
     int jacobi_sweeps;    /* sweeps of the last subspace eigensolve */
+    /* self-consistent density only (appended): Hartree and exchange energies of rho_out,
+     * int |rho_out - rho_in| / n_elec, and the CG iterations of this iteration's solves */
+    double E_H, E_x, drho;
+    int cg_iters;
 } hub_scf_result;
 
 /* Start an SCF: X[nspin] device blocks (ld*ncol each; updated in place every iteration),
@@ -260,6 +279,38 @@ int hub_scf_run(hub_t h, hub_scf_result* res);
 /* Results of the last iteration: eig/occ host [nspin*ncol] (may be NULL),
  * D_out host [nspin*nhub*25] (may be NULL). */
 int hub_scf_get(hub_t h, double* eig, double* occ, double* D_out);
+/* Self-consistent density SCF: the output density of the last iteration, summed over the
+ * spin channels, into rho_dev (device double [Nd]).  HUB_EINVAL when the SCF is not in
+ * density mode.  Synchronises. */
+int hub_scf_density(hub_t h, double* rho_dev);
+
+/* ---------------------------------------------------------------------------------
+ * Grid-sized steps of the self-consistent density SCF (Sec. II.B, last paragraph: CheFSI
+ * with preconditioned Pulay mixing; the functional pieces are readings, the paper does not
+ * print E_DFT).  All vectors are device double [Nd], cell-periodic; the FD Laplacian is the
+ * kinetic term's (order 2 n0, periodic).
+ * --------------------------------------------------------------------------------- */
+/* rho[g] += scale * sum_n f_n |x_n(g)|^2 for one (spin, k) block X (handle element type,
+ * [ld x ncol]); scale = spin degeneracy * k weight.  f_host host [ncol].  Accumulates:
+ * the caller zeroes rho.  Asynchronous. */
+int hub_density(hub_t h, const void* X, int ncol, int ld, const double* f_host, double scale,
+                double* rho_dev);
+/* Hartree potential: -Lap_h V = 4 pi (rho - mean rho), mean V = 0, by conjugate gradients
+ * (FP64) from the V given (warm start) to |r| <= tol |b|.  iters_out, EH_out (= 1/2 dV sum
+ * rho V) may be NULL.  Synchronises.  HUB_ENOCONV when max_iter is reached. */
+int hub_hartree(hub_t h, const double* rho_dev, double* V_dev, double tol, int max_iter,
+                int* iters_out, double* EH_out);
+/* Local-density exchange of one channel (rho1, vx1 NULL: the total density) or two spin
+ * channels: v_x = -(4/3) k rho^(1/3), E_x = -k dV sum rho^(4/3), k = (3/4)(3/pi)^(1/3),
+ * times 2^(1/3) for each channel of a spin-polarized pair.  Negative densities count as 0.
+ * Ex_out (host) may be NULL.  Synchronises. */
+int hub_lda_exchange(hub_t h, int nchan, const double* rho0, const double* rho1, double* vx0,
+                     double* vx1, double* Ex_out);
+/* Kerker preconditioner z = (-Lap_h)(-Lap_h + kappa^2)^-1 r by conjugate gradients on
+ * (-Lap_h + kappa^2) z = -Lap_h r from z = 0 (the constant part of r is removed).
+ * Synchronises.  HUB_ENOCONV when max_iter is reached. */
+int hub_kerker(hub_t h, const double* r_dev, double* z_dev, double kappa, double tol, int max_iter,
+               int* iters_out);
 
 /* ---------------------------------------------------------------------------------
  * Batched filtering and tuning.
@@ -365,6 +416,7 @@ typedef enum {
     HUB_K_COPY,           /* block copies and conversions */
     HUB_K_TABLE,          /* projector table values */
     HUB_K_FORCE,          /* FD gradient of the orbitals (Hubbard forces) */
+    HUB_K_DENSITY,        /* density SCF: density, Poisson / Kerker CG, exchange */
     HUB_K_COUNT
 } hub_kernel_kind;
 

@@ -29,14 +29,17 @@ class scf_params(C.Structure):
                 ("max_iter", C.c_int), ("first_passes", C.c_int), ("lanczos_steps", C.c_int),
                 ("pulay_history", C.c_int), ("natoms", C.c_int), ("pulay_beta", C.c_double),
                 ("kT", C.c_double), ("n_elec", C.c_double), ("tol_e_atom", C.c_double),
-                ("tol_D", C.c_double), ("ladder", C.c_int), ("ladder_tol", C.c_double)]
+                ("tol_D", C.c_double), ("ladder", C.c_int), ("ladder_tol", C.c_double),
+                ("density", C.c_int), ("kerker_kappa", C.c_double), ("tol_rho", C.c_double),
+                ("cg_tol", C.c_double)]
 
 
 class scf_result(C.Structure):
     _fields_ = [("iter", C.c_int), ("converged", C.c_int), ("E", C.c_double),
                 ("E_band", C.c_double), ("E_U", C.c_double), ("dE", C.c_double),
                 ("dD", C.c_double), ("mu", C.c_double), ("bf16_terms", C.c_int),
-                ("jacobi_sweeps", C.c_int)]
+                ("jacobi_sweeps", C.c_int), ("E_H", C.c_double), ("E_x", C.c_double),
+                ("drho", C.c_double), ("cg_iters", C.c_int)]
 
 
 _P, _I, _D = C.c_void_p, C.c_int, C.c_double
@@ -61,6 +64,11 @@ _SIGS = {
     "hub_scf_iterate": [_P, C.POINTER(scf_result)],
     "hub_scf_run": [_P, C.POINTER(scf_result)],
     "hub_scf_get": [_P, _PD, _PD, _PD],
+    "hub_scf_density": [_P, _P],
+    "hub_density": [_P, _P, _I, _I, _PD, _D, _P],
+    "hub_hartree": [_P, _P, _P, _D, _I, _PI, _PD],
+    "hub_lda_exchange": [_P, _I, _P, _P, _P, _P, _PD],
+    "hub_kerker": [_P, _P, _P, _D, _D, _I, _PI],
     "hub_version": [C.c_char_p, _I],
     "hub_set_bf16_terms": [_P, _I],
     "hub_autotune": [_P, _I, _P, _I, _I, _PI],
@@ -88,7 +96,7 @@ _SIGS = {
 
 KERNEL_KINDS = ["stencil", "gather", "transform", "scatter", "gram", "gram_reduce", "rotate",
                 "cholesky", "tri_inverse", "dgemm", "jacobi", "eig_misc", "occupation",
-                "lanczos", "copy", "table", "force"]
+                "lanczos", "copy", "table", "force", "density"]
 
 
 def batch_filter(hubs, spins, Xs, degree: int, a, b, a_low, stream=None):
@@ -355,6 +363,40 @@ class Hub:
         self._check(self.lib.hub_scf_get(self.h, _dptr(eig), _dptr(occ), _dptr(D)), "hub_scf_get")
         return (eig.reshape(p.nspin, p.ncol), occ.reshape(p.nspin, p.ncol),
                 D[:p.nspin * self.nhub * 25].reshape(p.nspin, self.nhub, 5, 5))
+
+
+    def scf_density(self, rho):
+        """Output density of the last density-SCF iteration (summed over spins) into rho."""
+        self._check(self.lib.hub_scf_density(self.h, _tptr(rho)), "hub_scf_density")
+
+    # ------------------------------------------------------------------ density SCF steps
+    def density(self, X, f, scale, rho):
+        """rho += scale * sum_n f_n |x_n|^2 (rho: device double [Nd])."""
+        ncol, ld = X.shape
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        self._check(self.lib.hub_density(self.h, _tptr(X), ncol, ld, _dptr(f), float(scale), _tptr(rho)),
+                    "hub_density")
+
+    def hartree(self, rho, V, tol=1e-10, max_iter=20000):
+        """V (warm start in, solution out) and (CG iterations, E_H)."""
+        it, eh = C.c_int(), C.c_double()
+        self._check(self.lib.hub_hartree(self.h, _tptr(rho), _tptr(V), tol, max_iter, C.byref(it),
+                                         C.byref(eh)), "hub_hartree")
+        return it.value, eh.value
+
+    def lda_exchange(self, rhos, vxs) -> float:
+        ex = C.c_double()
+        two = len(rhos) == 2
+        self._check(self.lib.hub_lda_exchange(self.h, len(rhos), _tptr(rhos[0]), _tptr(rhos[1]) if two else None,
+                                              _tptr(vxs[0]), _tptr(vxs[1]) if two else None, C.byref(ex)),
+                    "hub_lda_exchange")
+        return ex.value
+
+    def kerker(self, r, z, kappa, tol=1e-10, max_iter=20000) -> int:
+        it = C.c_int()
+        self._check(self.lib.hub_kerker(self.h, _tptr(r), _tptr(z), kappa, tol, max_iter, C.byref(it)),
+                    "hub_kerker")
+        return it.value
 
 
 def descriptors(pos, species, L, centers, out, nspecies=2, rc=6.0, nrad=16, eta=0.4, stream=None):

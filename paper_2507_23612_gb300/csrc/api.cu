@@ -53,7 +53,7 @@ int check_flags(hub_t h) {
     return HUB_OK;
 }
 
-static void fd_weights(int n0, double* c0, double* c) {
+void fd_laplacian_weights(int n0, double* c0, double* c) {
     // centred second-derivative weights of order 2 n0:
     // c_p = 2 (-1)^{p+1} (n0!)^2 / (p^2 (n0-p)! (n0+p)!),  c_0 = -2 sum 1/p^2
     auto fact = [](int k) { double r = 1.0; for (int i = 2; i <= k; ++i) r *= i; return r; };
@@ -74,11 +74,11 @@ int apply_H_internal(hub_t h, int spin, const void* X, int ld, void* Y, int ncol
     a.Y = X;
     a.Yprev = Yprev;
     a.Yout = Y;
-    a.V = h->d_veff;
+    a.V = (h->veff_per_spin && h->d_veff_spin[spin]) ? h->d_veff_spin[spin] : h->d_veff;
     a.n1 = h->n1; a.n2 = h->n2; a.n3 = h->n3; a.ld = ld; a.ncol = ncol;
     a.n0 = h->n0;
     double c0, c[kMaxHalf];
-    fd_weights(h->n0, &c0, c);
+    fd_laplacian_weights(h->n0, &c0, c);
     double inv2 = 0.0;
     for (int ax = 0; ax < 3; ++ax) {
         const double ih2 = 1.0 / (h->h[ax] * h->h[ax]);
@@ -128,6 +128,13 @@ struct ScfState {
     bool have_prev = false;
     double E_prev = 0.0;
     hub_scf_result last{};
+    // self-consistent density: device vectors [Nd] inside hub_ctx::d_rho_ws
+    bool density = false;
+    double *vh = nullptr, *vh_out = nullptr, *tmp = nullptr, *rbar = nullptr, *z = nullptr;
+    double *vx[2] = {nullptr, nullptr}, *vx_out[2] = {nullptr, nullptr};
+    double *rho_in[2] = {nullptr, nullptr}, *rho_out[2] = {nullptr, nullptr};
+    std::vector<double*> hist_x, hist_r;   // per history slot: nspin vectors each
+    std::vector<int> slots;               // history slot of each entry of hx / hr
 };
 
 }  // namespace hub
@@ -187,7 +194,8 @@ int hub_destroy(hub_t h) {
     for (auto& e : h->prof) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     free_table(h->proj);
     void* ptrs[] = {h->d_veff, h->d_work, h->d_work2, h->d_part, h->d_C, h->d_W, h->d_small,
-                    h->d_gpart, h->d_bf16, h->d_aux, h->d_flags, h->d_bar, h->d_scal};
+                    h->d_gpart, h->d_bf16, h->d_aux, h->d_flags, h->d_bar, h->d_scal, h->d_dens,
+                    h->d_veff_spin[0], h->d_veff_spin[1], h->d_rho_ws, h->d_vloc};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete h->scf;
@@ -205,6 +213,11 @@ int hub_set_veff(hub_t h, const double* veff_dev) {
     if (!veff_dev) return fail(h, HUB_EINVAL, "NULL potential");
     int rc = launch_copy_convert_veff(h, veff_dev, h->d_veff);
     if (rc) return rc;
+    // the double copy is the local potential of a self-consistent density SCF
+    if ((rc = ensure(h, (void**)&h->d_vloc, &h->vloc_bytes, (size_t)h->Nd * sizeof(double)))) return rc;
+    HUB_CUDA_TRY(h, cudaMemcpyAsync(h->d_vloc, veff_dev, (size_t)h->Nd * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, h->stream));
+    h->veff_per_spin = 0;
     h->veff_set = true;
     return HUB_OK;
 }
@@ -552,9 +565,47 @@ static double fd_entropy(const std::vector<double>& f) {
     return s;
 }
 
-// Pulay / DIIS: minimise |sum c_i r_i| with sum c_i = 1, then x = sum c_i (x_i + beta r_i)
-static std::vector<double> pulay_mix(ScfState& st, const std::vector<double>& xin,
-                                     const std::vector<double>& xout) {
+// Pulay / DIIS coefficients: minimise |sum c_i r_i| subject to sum c_i = 1, from the k x k
+// Gram matrix A (row-major) of the residuals.  false when the bordered system is singular.
+static bool pulay_solve(const std::vector<double>& G, int k, std::vector<double>& coef) {
+    coef.assign(k, 0.0);
+    if (k < 2) return false;
+    const int m = k + 1;
+    std::vector<double> A((size_t)m * m, 0.0), b(m, 0.0);
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) A[(size_t)i * m + j] = G[(size_t)i * k + j];
+    for (int i = 0; i < k; ++i) { A[(size_t)i * m + k] = 1.0; A[(size_t)k * m + i] = 1.0; }
+    b[k] = 1.0;
+    // Gaussian elimination with partial pivoting
+    double scale = 0.0;
+    for (double v : A) scale = std::max(scale, std::fabs(v));
+    for (int c = 0; c < m; ++c) {
+        int piv = c;
+        for (int r2 = c + 1; r2 < m; ++r2)
+            if (std::fabs(A[(size_t)r2 * m + c]) > std::fabs(A[(size_t)piv * m + c])) piv = r2;
+        if (std::fabs(A[(size_t)piv * m + c]) <= 1e-14 * scale) return false;
+        if (piv != c) {
+            for (int q = 0; q < m; ++q) std::swap(A[(size_t)c * m + q], A[(size_t)piv * m + q]);
+            std::swap(b[c], b[piv]);
+        }
+        for (int r2 = c + 1; r2 < m; ++r2) {
+            const double fct = A[(size_t)r2 * m + c] / A[(size_t)c * m + c];
+            for (int q = c; q < m; ++q) A[(size_t)r2 * m + q] -= fct * A[(size_t)c * m + q];
+            b[r2] -= fct * b[c];
+        }
+    }
+    std::vector<double> x(m);
+    for (int c = m - 1; c >= 0; --c) {
+        double sm = b[c];
+        for (int q = c + 1; q < m; ++q) sm -= A[(size_t)c * m + q] * x[q];
+        x[c] = sm / A[(size_t)c * m + c];
+    }
+    for (int i = 0; i < k; ++i) coef[i] = x[i];
+    return true;
+}
+
+// pushes (xin, xout - xin) into the D history (at most pulay_history entries)
+static void pulay_push(ScfState& st, const std::vector<double>& xin, const std::vector<double>& xout) {
     const size_t n = xin.size();
     std::vector<double> r(n);
     for (size_t i = 0; i < n; ++i) r[i] = xout[i] - xin[i];
@@ -562,51 +613,32 @@ static std::vector<double> pulay_mix(ScfState& st, const std::vector<double>& xi
     st.hr.push_back(r);
     const int hist = std::max(1, st.p.pulay_history);
     while ((int)st.hx.size() > hist) { st.hx.erase(st.hx.begin()); st.hr.erase(st.hr.begin()); }
+}
+
+// Gram matrix of the stored D residuals
+static std::vector<double> pulay_gram_D(const ScfState& st) {
+    const int k = (int)st.hr.size();
+    std::vector<double> G((size_t)k * k, 0.0);
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) {
+            double sm = 0.0;
+            for (size_t q = 0; q < st.hr[i].size(); ++q) sm += st.hr[i][q] * st.hr[j][q];
+            G[(size_t)i * k + j] = sm;
+        }
+    return G;
+}
+
+// Pulay / DIIS on D alone: x = sum c_i (x_i + beta r_i); linear mixing while the history is
+// one entry long or its system is singular
+static std::vector<double> pulay_mix(ScfState& st, const std::vector<double>& xin,
+                                     const std::vector<double>& xout) {
+    pulay_push(st, xin, xout);
     const int k = (int)st.hr.size();
     const double beta = st.p.pulay_beta;
-    std::vector<double> out(n);
-    std::vector<double> coef(k, 0.0);
-    bool ok = k > 1;
-    if (ok) {
-        const int m = k + 1;
-        std::vector<double> A((size_t)m * m, 0.0), b(m, 0.0);
-        for (int i = 0; i < k; ++i)
-            for (int j = 0; j < k; ++j) {
-                double s = 0.0;
-                for (size_t q = 0; q < n; ++q) s += st.hr[i][q] * st.hr[j][q];
-                A[(size_t)i * m + j] = s;
-            }
-        for (int i = 0; i < k; ++i) { A[(size_t)i * m + k] = 1.0; A[(size_t)k * m + i] = 1.0; }
-        b[k] = 1.0;
-        // Gaussian elimination with partial pivoting
-        double scale = 0.0;
-        for (double v : A) scale = std::max(scale, std::fabs(v));
-        for (int c = 0; c < m && ok; ++c) {
-            int piv = c;
-            for (int r2 = c + 1; r2 < m; ++r2)
-                if (std::fabs(A[(size_t)r2 * m + c]) > std::fabs(A[(size_t)piv * m + c])) piv = r2;
-            if (std::fabs(A[(size_t)piv * m + c]) <= 1e-14 * scale) { ok = false; break; }
-            if (piv != c) {
-                for (int q = 0; q < m; ++q) std::swap(A[(size_t)c * m + q], A[(size_t)piv * m + q]);
-                std::swap(b[c], b[piv]);
-            }
-            for (int r2 = c + 1; r2 < m; ++r2) {
-                const double fct = A[(size_t)r2 * m + c] / A[(size_t)c * m + c];
-                for (int q = c; q < m; ++q) A[(size_t)r2 * m + q] -= fct * A[(size_t)c * m + q];
-                b[r2] -= fct * b[c];
-            }
-        }
-        if (ok) {
-            std::vector<double> x(m);
-            for (int c = m - 1; c >= 0; --c) {
-                double s = b[c];
-                for (int q = c + 1; q < m; ++q) s -= A[(size_t)c * m + q] * x[q];
-                x[c] = s / A[(size_t)c * m + c];
-            }
-            for (int i = 0; i < k; ++i) coef[i] = x[i];
-        }
-    }
-    if (!ok) {
+    const size_t n = xin.size();
+    std::vector<double> out(n), coef;
+    if (!pulay_solve(pulay_gram_D(st), k, coef)) {
+        const std::vector<double>& r = st.hr.back();
         for (size_t q = 0; q < n; ++q) out[q] = xin[q] + beta * r[q];
         return out;
     }
@@ -616,6 +648,171 @@ static std::vector<double> pulay_mix(ScfState& st, const std::vector<double>& xi
         out[q] = xs + beta * rs;
     }
     return out;
+}
+
+// ---------------------------------------------------------------------------- density SCF
+constexpr int kCgMaxIter = 20000;
+static double dens_kappa(const hub_scf_params& p) { return p.kerker_kappa > 0 ? p.kerker_kappa : 0.5; }
+static double dens_tol_rho(const hub_scf_params& p) { return p.tol_rho > 0 ? p.tol_rho : 1e-4; }
+static double dens_cg_tol(const hub_scf_params& p) { return p.cg_tol > 0 ? p.cg_tol : 1e-10; }
+
+// device vectors of the density model: V_H, V_H of rho_out, scratch, Pulay combination,
+// preconditioned residual, v_x of rho_in and of rho_out, rho_in, rho_out, and the Pulay
+// history of densities and residuals; per-spin V_eff in the working type
+static int density_setup(hub_t h, ScfState& st) {
+    const int ns = st.p.nspin;
+    const int H = std::max(1, st.p.pulay_history);
+    const size_t Nd = (size_t)h->Nd;
+    const size_t nvec = 5 + 4 * (size_t)ns + 2 * (size_t)H * ns;
+    int rc;
+    if ((rc = ensure(h, (void**)&h->d_rho_ws, &h->rho_ws_bytes, nvec * Nd * sizeof(double)))) return rc;
+    HUB_CUDA_TRY(h, cudaMemsetAsync(h->d_rho_ws, 0, nvec * Nd * sizeof(double), h->stream));
+    double* v = h->d_rho_ws;
+    auto take = [&]() { double* q = v; v += Nd; return q; };
+    st.vh = take(); st.vh_out = take(); st.tmp = take(); st.rbar = take(); st.z = take();
+    for (int s = 0; s < ns; ++s) { st.vx[s] = take(); st.vx_out[s] = take(); st.rho_in[s] = take(); st.rho_out[s] = take(); }
+    st.hist_x.assign(H, nullptr);
+    st.hist_r.assign(H, nullptr);
+    for (int i = 0; i < H; ++i) {
+        st.hist_x[i] = v; v += ns * Nd;
+        st.hist_r[i] = v; v += ns * Nd;
+    }
+    for (int s = 0; s < ns; ++s)
+        if (!h->d_veff_spin[s])
+            HUB_CUDA_TRY(h, cudaMalloc(&h->d_veff_spin[s], Nd * h->esize));
+    const double vol = h->dV * (double)h->Nd;
+    for (int s = 0; s < ns; ++s)
+        if ((rc = density_fill(h, st.rho_in[s], st.p.n_elec / ns / vol))) return rc;
+    st.density = true;
+    return HUB_OK;
+}
+
+// total density of the channels into st.tmp (or the one channel itself)
+static int density_total(hub_t h, ScfState& st, double* const* rho, const double** out) {
+    if (st.p.nspin == 1) { *out = rho[0]; return HUB_OK; }
+    const double* v[2] = {rho[0], rho[1]};
+    const double c[2] = {1.0, 1.0};
+    *out = st.tmp;
+    return density_lincomb(h, st.tmp, 2, v, c, nullptr, 0.0);
+}
+
+// V_eff^s = V_loc + V_H[rho_in] + v_x^s[rho_in] for every channel; fresh upper bounds
+static int density_potentials(hub_t h, ScfState& st, int* cg_iters) {
+    const hub_scf_params& p = st.p;
+    const int ns = p.nspin;
+    int rc, it = 0;
+    const double* rho_tot;
+    if ((rc = density_total(h, st, st.rho_in, &rho_tot))) return rc;
+    if ((rc = hub_hartree(h, rho_tot, st.vh, dens_cg_tol(p), kCgMaxIter, &it, nullptr))) return rc;
+    *cg_iters += it;
+    if ((rc = hub_lda_exchange(h, ns, st.rho_in[0], ns == 2 ? st.rho_in[1] : nullptr, st.vx[0],
+                               ns == 2 ? st.vx[1] : nullptr, nullptr))) return rc;
+    for (int s = 0; s < ns; ++s) {
+        if ((rc = density_add3(h, st.tmp, h->d_vloc, st.vh, st.vx[s]))) return rc;
+        if ((rc = launch_copy_convert_veff(h, st.tmp, h->d_veff_spin[s]))) return rc;
+    }
+    h->veff_per_spin = 1;
+    for (int s = 0; s < ns; ++s) {
+        double lo, up;
+        if ((rc = hub_lanczos_bound(h, s, p.lanczos_steps, st.v0[s], &lo, &up))) return rc;
+        if (!st.have_bounds[s]) {
+            st.bounds[s][0] = lo;
+            st.bounds[s][1] = lo + 0.1 * (up - lo);
+            st.have_bounds[s] = true;
+        }
+        st.bounds[s][2] = up;
+    }
+    return HUB_OK;
+}
+
+// rho_out of the iteration and the density terms of the energy
+static int density_terms(hub_t h, ScfState& st, double deg, double* e_dc_hx, double* e_h, double* e_x,
+                         double* drho, int* cg_iters) {
+    const hub_scf_params& p = st.p;
+    const int ns = p.nspin;
+    int rc;
+    *e_dc_hx = 0.0;
+    *drho = 0.0;
+    for (int s = 0; s < ns; ++s) {
+        HUB_CUDA_TRY(h, cudaMemsetAsync(st.rho_out[s], 0, (size_t)h->Nd * sizeof(double), h->stream));
+        if ((rc = hub_density(h, st.X[s], p.ncol, p.ld, st.occ.data() + (size_t)s * p.ncol, deg,
+                              st.rho_out[s]))) return rc;
+        double a = 0.0, b = 0.0, d = 0.0;
+        if ((rc = density_dot(h, st.rho_out[s], st.vh, 0, &a))) return rc;
+        if ((rc = density_dot(h, st.rho_out[s], st.vx[s], 0, &b))) return rc;
+        if ((rc = density_dot(h, st.rho_out[s], st.rho_in[s], 1, &d))) return rc;
+        *e_dc_hx += h->dV * (a + b);
+        *drho += h->dV * d;
+    }
+    *drho /= std::max(p.n_elec, 1e-300);
+    const double* rho_tot;
+    if ((rc = density_total(h, st, st.rho_out, &rho_tot))) return rc;
+    HUB_CUDA_TRY(h, cudaMemcpyAsync(st.vh_out, st.vh, (size_t)h->Nd * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    int it = 0;
+    if ((rc = hub_hartree(h, rho_tot, st.vh_out, dens_cg_tol(p), kCgMaxIter, &it, e_h))) return rc;
+    *cg_iters += it;
+    return hub_lda_exchange(h, ns, st.rho_out[0], ns == 2 ? st.rho_out[1] : nullptr, st.vx_out[0],
+                            ns == 2 ? st.vx_out[1] : nullptr, e_x);
+}
+
+// Pulay on [rho, D] with one set of coefficients; the density block of the combined
+// residual goes through the Kerker preconditioner
+static int density_mix(hub_t h, ScfState& st, int* cg_iters) {
+    const hub_scf_params& p = st.p;
+    const int ns = p.nspin;
+    const int H = std::max(1, p.pulay_history);
+    const size_t Nd = (size_t)h->Nd;
+    int rc;
+    int slot;
+    if ((int)st.slots.size() < H) slot = (int)st.slots.size();
+    else { slot = st.slots.front(); st.slots.erase(st.slots.begin()); }
+    pulay_push(st, st.D_in, st.D_out);
+    st.slots.push_back(slot);
+    for (int s = 0; s < ns; ++s) {
+        HUB_CUDA_TRY(h, cudaMemcpyAsync(st.hist_x[slot] + s * Nd, st.rho_in[s], Nd * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, h->stream));
+        const double* v[2] = {st.rho_out[s], st.rho_in[s]};
+        const double c[2] = {1.0, -1.0};
+        if ((rc = density_lincomb(h, st.hist_r[slot] + s * Nd, 2, v, c, nullptr, 0.0))) return rc;
+    }
+    const int k = (int)st.slots.size();
+    std::vector<double> G = pulay_gram_D(st);
+    for (int i = 0; i < k; ++i)
+        for (int j = i; j < k; ++j) {
+            double d = 0.0;
+            for (int s = 0; s < ns; ++s) {
+                double ds = 0.0;
+                if ((rc = density_dot(h, st.hist_r[st.slots[i]] + s * Nd, st.hist_r[st.slots[j]] + s * Nd, 0, &ds))) return rc;
+                d += ds;
+            }
+            G[(size_t)i * k + j] += d;
+            if (j != i) G[(size_t)j * k + i] += d;
+        }
+    std::vector<double> coef;
+    if (!pulay_solve(G, k, coef)) { coef.assign(k, 0.0); coef[k - 1] = 1.0; }   // linear mixing
+    const double beta = p.pulay_beta;
+    for (int s = 0; s < ns; ++s) {
+        const double* vr[8];
+        const double* vx[8];
+        for (int i = 0; i < k; ++i) {
+            vr[i] = st.hist_r[st.slots[i]] + s * Nd;
+            vx[i] = st.hist_x[st.slots[i]] + s * Nd;
+        }
+        if ((rc = density_lincomb(h, st.rbar, k, vr, coef.data(), nullptr, 0.0))) return rc;
+        int it = 0;
+        if ((rc = hub_kerker(h, st.rbar, st.z, dens_kappa(p), dens_cg_tol(p), kCgMaxIter, &it))) return rc;
+        *cg_iters += it;
+        if ((rc = density_lincomb(h, st.rho_in[s], k, vx, coef.data(), st.z, beta))) return rc;
+    }
+    const size_t n = st.D_in.size();
+    std::vector<double> out(n);
+    for (size_t q = 0; q < n; ++q) {
+        double xs = 0.0, rs = 0.0;
+        for (int i = 0; i < k; ++i) { xs += coef[i] * st.hx[i][q]; rs += coef[i] * st.hr[i][q]; }
+        out[q] = xs + beta * rs;
+    }
+    st.D_in = out;
+    return HUB_OK;
 }
 
 int hub_scf_begin(hub_t h, const hub_scf_params* p, void* const* X, const void* const* v0,
@@ -643,6 +840,32 @@ int hub_scf_begin(hub_t h, const hub_scf_params* p, void* const* X, const void* 
     st.D_out.assign(st.D_in.size(), 0.0);
     st.eig.assign((size_t)p->nspin * p->ncol, 0.0);
     st.occ.assign(st.eig.size(), 0.0);
+    h->veff_per_spin = 0;
+    if (p->density) {
+        if (p->pulay_history > 8) return fail(h, HUB_EINVAL, "density SCF: pulay_history <= 8");
+        if (!(p->n_elec > 0)) return fail(h, HUB_EINVAL, "density SCF: n_elec must be > 0");
+        if (!h->d_vloc) return fail(h, HUB_EINVAL, "density SCF: no local potential");
+        int rc = density_setup(h, st);
+        if (rc) return rc;
+    }
+    return HUB_OK;
+}
+
+int hub_scf_density(hub_t h, double* rho_dev) {
+    if (!h || !h->scf) return fail(h, HUB_EINVAL, "hub_scf_begin has not been called");
+    ScfState& st = *h->scf;
+    if (!st.density) return fail(h, HUB_EINVAL, "the SCF is not in density mode");
+    if (!rho_dev) return fail(h, HUB_EINVAL, "NULL density");
+    const size_t bytes = (size_t)h->Nd * sizeof(double);
+    if (st.p.nspin == 1) {
+        HUB_CUDA_TRY(h, cudaMemcpyAsync(rho_dev, st.rho_out[0], bytes, cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+        const double* v[2] = {st.rho_out[0], st.rho_out[1]};
+        const double c[2] = {1.0, 1.0};
+        int rc = density_lincomb(h, rho_dev, 2, v, c, nullptr, 0.0);
+        if (rc) return rc;
+    }
+    HUB_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return HUB_OK;
 }
 
@@ -660,6 +883,9 @@ int hub_scf_iterate(hub_t h, hub_scf_result* res) {
     const int passes = st.iter == 0 ? std::max(1, p.first_passes) : 1;
     for (int s = 0; s < ns; ++s)
         if ((rc = hub_set_occupation_matrix(h, s, st.D_in.data() + (size_t)s * nh * 25, nullptr))) return rc;
+    int cg_iters = 0;
+    if (st.density)
+        if ((rc = density_potentials(h, st, &cg_iters))) return rc;
     for (int pass = 0; pass < passes; ++pass) {
         for (int s = 0; s < ns; ++s) {
             if (!st.have_bounds[s]) {
@@ -713,7 +939,10 @@ int hub_scf_iterate(hub_t h, hub_scf_result* res) {
             ent += deg * fd_entropy(f);
         }
     }
-    const double E = e_band - e_dc + e_u - p.kT * ent;
+    double e_dc_hx = 0.0, e_h = 0.0, e_x = 0.0, drho = 0.0;
+    if (st.density)
+        if ((rc = density_terms(h, st, deg, &e_dc_hx, &e_h, &e_x, &drho, &cg_iters))) return rc;
+    const double E = e_band - e_dc + e_u - p.kT * ent - e_dc_hx + e_h + e_x;
     double dD = 0.0;
     for (size_t q = 0; q < st.D_in.size(); ++q) dD = std::max(dD, std::fabs(st.D_out[q] - st.D_in[q]));
     const double dE = st.have_prev ? E - st.E_prev : 0.0;
@@ -724,7 +953,8 @@ int hub_scf_iterate(hub_t h, hub_scf_result* res) {
     st.iter++;
     hub_scf_result r{};
     r.iter = st.iter;
-    r.converged = (st.small >= 2 && dD < p.tol_D) ? 1 : 0;
+    r.converged = (st.small >= 2 && dD < p.tol_D && (!st.density || drho < dens_tol_rho(p))) ? 1 : 0;
+    r.E_H = e_h; r.E_x = e_x; r.drho = drho; r.cg_iters = cg_iters;
     r.E = E; r.E_band = e_band; r.E_U = e_u; r.dE = dE; r.dD = dD; r.mu = mu;
     r.bf16_terms = h->prec == HUB_MIXED_BF16 ? h->bf16_terms : 0;
     r.jacobi_sweeps = h->last_sweeps;
@@ -733,8 +963,14 @@ int hub_scf_iterate(hub_t h, hub_scf_result* res) {
         st.small = 0;       // the converged-energy count restarts at the finer precision
         r.converged = 0;
     }
+    if (!r.converged) {
+        if (st.density) {
+            if ((rc = density_mix(h, st, &r.cg_iters))) return rc;
+        } else {
+            st.D_in = pulay_mix(st, st.D_in, st.D_out);
+        }
+    }
     st.last = r;
-    if (!r.converged) st.D_in = pulay_mix(st, st.D_in, st.D_out);
     if (res) *res = r;
     return HUB_OK;
 }

@@ -134,6 +134,13 @@ struct hub_ctx {
     void* d_gpart = nullptr;      size_t gpart_bytes = 0;   // split-K GEMM partials
     void* d_bf16 = nullptr;       size_t bf16_bytes = 0;    // bf16 operand copies
     void* d_aux = nullptr;        size_t aux_bytes = 0;     // occupations and D output
+    void* d_dens = nullptr;       size_t dens_bytes = 0;    // density SCF: CG vectors, partials
+    // density SCF: per-spin V_eff in the working type (used by apply_H when veff_per_spin),
+    // and the double buffers of the density model (V_loc, rho, V_H, v_x, Pulay history)
+    void* d_veff_spin[2] = {nullptr, nullptr};
+    int veff_per_spin = 0;
+    double* d_rho_ws = nullptr;   size_t rho_ws_bytes = 0;
+    double* d_vloc = nullptr;     size_t vloc_bytes = 0;    // double copy of the set V_eff
     int* d_flags = nullptr;       // [8] device error flags (0..5), Jacobi sweep count (6)
     unsigned int* d_bar = nullptr;  // [4] grid-barrier state
     double* d_scal = nullptr;     // [256] device scalars (Lanczos, reductions)
@@ -246,6 +253,18 @@ int dense_jacobi_eigh(hub_t h, double* A, double* V, double* eig, int n);  // as
 // one or two independent n x n problems in one cooperative launch (half the SMs each)
 int dense_jacobi_eigh_multi(hub_t h, int nmat, double* const* A, double* const* V, double* const* eig, int n);
 int dense_symmetrize(hub_t h, double* A, int n);
+
+// api.cu: centred second-derivative weights of order 2 n0 (c0 and c_1..c_n0)
+void fd_laplacian_weights(int n0, double* c0, double* c);
+
+// density.cu: reductions and vector algebra of the density SCF on [Nd] double vectors
+int density_sum(hub_t h, const double* x, double* out_host);
+int density_dot(hub_t h, const double* x, const double* y, int absdiff, double* out_host);
+// y = sum_i c_i v_i + beta z (z may be nullptr); k <= 8; y may alias a v_i
+int density_lincomb(hub_t h, double* y, int k, const double* const* v, const double* c,
+                    const double* z, double beta);
+int density_add3(hub_t h, double* y, const double* a, const double* b, const double* c);
+int density_fill(hub_t h, double* y, double value);
 
 // misc.cu
 int launch_copy_convert_veff(hub_t h, const double* src, void* dst);

@@ -11,3 +11,5 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+    config.addinivalue_line("markers", "gpu_pending: GPU test of code that has not run on a GPU yet; "
+                                       "kept out of -m gpu until its first run (-m gpu_pending)")

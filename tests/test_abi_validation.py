@@ -81,3 +81,29 @@ def test_gram_noalloc_rejects_bad_arguments_before_any_device_work(lib):
 def test_hubbard_forces_rejects_a_null_handle(lib):
     F = (C.c_double * 3)()
     assert lib.hub_hubbard_forces(None, 0, None, 0, 0, None, 1.0, F, None) == EINVAL
+
+
+def test_density_steps_reject_a_null_handle(lib):
+    assert lib.hub_density(None, None, 0, 0, None, 1.0, None) == EINVAL
+    assert lib.hub_hartree(None, None, None, 1e-10, 10, None, None) == EINVAL
+    assert lib.hub_lda_exchange(None, 1, None, None, None, None, None) == EINVAL
+    assert lib.hub_kerker(None, None, None, 0.5, 1e-10, 10, None) == EINVAL
+    assert lib.hub_scf_density(None, None) == EINVAL
+
+
+def test_scf_structs_match_the_header(lib):
+    # the binding's ctypes layouts carry every field the header declares, in order
+    import re
+    from paper_2507_23612_gb300.binding import scf_params, scf_result
+    import os
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "hub.h")).read()
+    for struct, name in ((scf_params, "hub_scf_params"), (scf_result, "hub_scf_result")):
+        body = hdr[:hdr.index("} " + name + ";")]
+        body = body[body.rindex("typedef struct {"):]
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        fields = []
+        for decl in body.split(";")[:-1]:
+            decl = decl.replace("typedef struct {", "").strip()
+            names = decl.split(None, 1)[1]
+            fields += [n.strip() for n in names.split(",")]
+        assert [f for f, _ in struct._fields_] == fields, name

@@ -1,0 +1,124 @@
+"""Parity of the self-consistent density SCF steps and driver (CUDA, through the C ABI)
+with the CPU oracle: the density of a block, the FD Poisson solve of the Hartree potential,
+local-density exchange, the Kerker preconditioner, and the SCF's fixed point (energy,
+eigenvalues, D, density) for one and two spin channels.
+
+Marked gpu_pending: this code has not run on a GPU yet; the marker moves to gpu after its
+first GPU run.  Tolerances: density and exchange are elementwise FP64 sums (1e-13
+relative); the CG solves stop at a 1e-12 relative residual, so V_H and the Kerker output
+agree with the oracle's exact Fourier solution to 1e-9 relative; the SCF fixed points agree
+to the SCF's own tolerances (the two sides mix with different Pulay solvers, so their
+trajectories differ at rounding level)."""
+import numpy as np
+import pytest
+
+import workloads as w
+from oracle import hubbard as o
+from oracle import density_scf as ds
+from hubtest import make_hub, to_dev, rel
+
+pytestmark = pytest.mark.gpu_pending
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2507_23612_gb300 import HUB_F32, HUB_F64, scf_params  # noqa: E402
+
+DEV = torch.device("cuda", 0)
+
+
+def _dev64(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+@pytest.mark.parametrize("prec,cplx", [(HUB_F64, False), (HUB_F64, True), (HUB_F32, False), (HUB_F32, True)])
+def test_density_of_a_block(prec, cplx):
+    wl = w.small_test_system(n=(20, 24, 28), ncol=37, natoms=3,
+                             kpt=(0.21, -0.13, 0.34) if cplx else (0.0, 0.0, 0.0))
+    X = wl.orbitals(complex_=cplx)
+    if prec == HUB_F32:
+        X = X.astype(np.complex64 if cplx else np.float32).astype(np.complex128 if cplx else np.float64)
+    f = np.linspace(1.0, 0.0, X.shape[0])
+    g = o.Grid(wl.n, wl.L, wl.kpts[0])
+    ref = 0.5 + ds.electron_density(X.T, f, g, degeneracy=2.0, kweight=0.7)
+    hb = make_hub(wl, prec)
+    rho = _dev64(np.full(wl.Nd, 0.5))
+    hb.density(to_dev(X, hb.dtype), f, 1.4, rho)
+    assert rel(rho.cpu().numpy(), ref) < 1e-13
+
+
+@pytest.mark.parametrize("n", [(20, 24, 28), (5, 7, 4), (33, 9, 17)])
+def test_hartree_potential(n):
+    wl = w.small_test_system(n=n, ncol=2, natoms=1)
+    g = o.Grid(wl.n, wl.L)
+    rng = np.random.default_rng(3)
+    rho = rng.uniform(0.0, 1.0, wl.Nd)
+    ref = ds.hartree_potential(rho, g)
+    hb = make_hub(wl, HUB_F64)
+    V = torch.zeros(wl.Nd, dtype=torch.float64, device=DEV)
+    it, eh = hb.hartree(_dev64(rho), V, tol=1e-12)
+    print(n, "CG iterations", it)
+    assert rel(V.cpu().numpy(), ref) < 1e-9
+    assert abs(eh - ds.hartree_energy(rho, g)) < 1e-9 * abs(ds.hartree_energy(rho, g))
+    # a warm start from the solution converges at once
+    it2, _ = hb.hartree(_dev64(rho), V, tol=1e-9)
+    assert it2 <= 16
+
+
+@pytest.mark.parametrize("nchan", [1, 2])
+def test_lda_exchange(nchan):
+    wl = w.small_test_system(n=(20, 24, 28), ncol=2, natoms=1)
+    g = o.Grid(wl.n, wl.L)
+    rng = np.random.default_rng(4)
+    rhos = [rng.uniform(-0.01, 1.0, wl.Nd) for _ in range(nchan)]      # a few negatives clip to 0
+    v_ref, E_ref = ds.lda_exchange(rhos, g)
+    hb = make_hub(wl, HUB_F64)
+    vx = [torch.empty(wl.Nd, dtype=torch.float64, device=DEV) for _ in range(nchan)]
+    E = hb.lda_exchange([_dev64(r) for r in rhos], vx)
+    assert abs(E - E_ref) < 1e-12 * abs(E_ref)
+    for s in range(nchan):
+        assert rel(vx[s].cpu().numpy(), v_ref[s]) < 1e-13
+
+
+def test_kerker_preconditioner():
+    wl = w.small_test_system(n=(20, 24, 28), ncol=2, natoms=1)
+    g = o.Grid(wl.n, wl.L)
+    rng = np.random.default_rng(5)
+    r = rng.standard_normal(wl.Nd)
+    ref = ds.kerker(r, g, 0.5)
+    hb = make_hub(wl, HUB_F64)
+    z = torch.empty(wl.Nd, dtype=torch.float64, device=DEV)
+    it = hb.kerker(_dev64(r), z, 0.5, tol=1e-12)
+    print("CG iterations", it)
+    assert rel(z.cpu().numpy(), ref) < 1e-9
+
+
+@pytest.mark.parametrize("nspin", [1, 2])
+def test_density_scf_reaches_the_oracle_fixed_point(nspin):
+    wl = w.small_test_system(n=(10, 10, 12), ncol=8, natoms=2, seed=11, nspin=nspin)
+    X0s = [wl.orbitals(spin=s) for s in range(nspin)]
+    v0s = [wl.lanczos_start(spin=s) for s in range(nspin)]
+    kw = dict(n_elec=6.0, kT=0.01, degree=12, max_iter=80, tol_e_atom=1e-8, tol_D=1e-6, tol_rho=1e-6)
+    ref = ds.scf_model_b((wl.n, wl.L, (0, 0, 0), 6), wl.veff, wl.atoms, wl.D0, [x.T for x in X0s],
+                         lanczos_v0s=v0s, **kw)
+    assert ref["converged"]
+    hb = make_hub(wl, HUB_F64)
+    p = scf_params(nspin=nspin, ncol=wl.ncol, ld=wl.Nd, degree=kw["degree"], max_iter=kw["max_iter"],
+                   first_passes=3, lanczos_steps=10, pulay_history=7, natoms=len(wl.atoms),
+                   pulay_beta=0.3, kT=kw["kT"], n_elec=kw["n_elec"], tol_e_atom=kw["tol_e_atom"],
+                   tol_D=kw["tol_D"], density=1, kerker_kappa=0.5, tol_rho=kw["tol_rho"], cg_tol=1e-12)
+    Xs = [to_dev(x, torch.float64) for x in X0s]
+    vs = [to_dev(v, torch.float64) for v in v0s]
+    hb.scf_begin(p, Xs, vs, wl.D0)
+    res = hb.scf_run()
+    eig, occ, D = hb.scf_get()
+    rho = torch.empty(wl.Nd, dtype=torch.float64, device=DEV)
+    hb.scf_density(rho)
+    print("gpu", res, "oracle", ref["iterations"], ref["E"])
+    assert res["converged"] == 1
+    nat = len(wl.atoms)
+    assert abs(res["E"] - ref["E"]) / nat < 1e-7
+    assert abs(res["E_H"] - ref["E_H"]) < 1e-6 and abs(res["E_x"] - ref["E_x"]) < 1e-6
+    np.testing.assert_allclose(D, ref["D"], atol=1e-5)
+    np.testing.assert_allclose(eig[:, :5], np.array(ref["eig"])[:, :5], atol=1e-6)
+    assert wl.dV * np.sum(np.abs(rho.cpu().numpy() - sum(ref["rho"]))) < 1e-4
