@@ -586,3 +586,50 @@ def build_hamiltonian(workload, spin: int = 0, kidx: int = 0):
     grid = Grid(workload.n, workload.L, workload.kpts[kidx], workload.fd_half_order)
     D = None if workload.D0 is None else workload.D0[spin]
     return Hamiltonian(grid, workload.veff, workload.atoms, D)
+
+
+# ----------------------------------------------------------------------------------------
+# Sec. II.B, last paragraph: occupation matrices across MD steps
+# ----------------------------------------------------------------------------------------
+
+
+def alfe_coefficients(R_hist):
+    """(alpha, beta) of the second-order extrapolation, fitted to the atomic positions.
+    R_hist: positions (natoms, 3) at t - 2dt, t - dt, t and t + dt (oldest first; the last
+    are the positions of the step about to be solved).  Least squares over all coordinates:
+        R(t+dt) - R(t) ~ alpha (R(t) - R(t-dt)) + beta (R(t-dt) - R(t-2dt)).
+    Reading: the paper extrapolates the residual of D "to second order" as it does the
+    density, citing Alfe's scheme; this is that scheme's fit.  With three position sets
+    beta = 0 and alpha is fitted alone; with fewer, alpha = beta = 0."""
+    R = [np.asarray(r, dtype=np.float64).ravel() for r in R_hist]
+    if len(R) < 3:
+        return 0.0, 0.0
+    target = R[-1] - R[-2]
+    d1 = R[-2] - R[-3]
+    if len(R) == 3:
+        den = float(np.dot(d1, d1))
+        return (float(np.dot(d1, target)) / den if den > 0 else 0.0), 0.0
+    d2 = R[-3] - R[-4]
+    g11, g12, g22 = float(np.dot(d1, d1)), float(np.dot(d1, d2)), float(np.dot(d2, d2))
+    det = g11 * g22 - g12 * g12
+    if det <= 1e-12 * g11 * g22:       # parallel steps: the one-coefficient fit
+        return (float(np.dot(d1, target)) / g11 if g11 > 0 else 0.0), 0.0
+    b1, b2 = float(np.dot(d1, target)), float(np.dot(d2, target))
+    return (g22 * b1 - g12 * b2) / det, (g11 * b2 - g12 * b1) / det
+
+
+def extrapolate_occupations(D_hist, D_atomic, alpha: float, beta: float):
+    """Starting D of the next MD step (Sec. II.B): the atomic guess plus the extrapolated
+    residual Delta = D - D_atomic of the converged D of the previous steps (oldest first):
+        Delta(t+dt) = Delta(t) + alpha (Delta(t) - Delta(t-dt)) + beta (Delta(t-dt) - Delta(t-2dt)).
+    Terms whose history is missing are dropped (no history: the atomic guess)."""
+    Da = np.asarray(D_atomic, dtype=np.float64)
+    d = [np.asarray(D, dtype=np.float64) - Da for D in D_hist]
+    if not d:
+        return Da.copy()
+    out = d[-1].copy()
+    if len(d) >= 2:
+        out += alpha * (d[-1] - d[-2])
+    if len(d) >= 3:
+        out += beta * (d[-2] - d[-3])
+    return Da + out

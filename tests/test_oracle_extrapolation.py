@@ -1,0 +1,74 @@
+"""Pins for the MD extrapolation of the occupation matrices (Sec. II.B, last paragraph):
+the fitted coefficients of constant-velocity and constant-acceleration trajectories, exact
+extrapolation when D depends linearly on the positions along such trajectories, the atomic
+guess without history, and the library's host implementation against the oracle."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from oracle import hubbard as o
+
+
+def _traj(kind, n=4, natoms=5, seed=0):
+    rng = np.random.default_rng(seed)
+    a, b, c = (rng.standard_normal((natoms, 3)) for _ in range(3))
+    t = np.arange(n, dtype=np.float64)
+    if kind == "linear":
+        return [a + b * ti for ti in t]
+    return [a + b * ti + 0.3 * c * ti * ti for ti in t]
+
+
+def test_constant_velocity_gives_alpha_one_beta_zero():
+    al, be = o.alfe_coefficients(_traj("linear"))
+    # d1 = d2 = target: the two-coefficient system is singular; the one-coefficient fit
+    assert abs(al - 1.0) < 1e-12 and be == 0.0
+    al3, be3 = o.alfe_coefficients(_traj("linear")[1:])
+    assert abs(al3 - 1.0) < 1e-12 and be3 == 0.0
+
+
+def test_constant_acceleration_gives_two_and_minus_one():
+    al, be = o.alfe_coefficients(_traj("quadratic"))
+    assert abs(al - 2.0) < 1e-10 and abs(be + 1.0) < 1e-10
+
+
+def test_linear_response_along_a_quadratic_trajectory_is_extrapolated_exactly():
+    R = _traj("quadratic", n=4, natoms=3, seed=2)
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((2 * 2 * 25, 9))                   # D depends linearly on R
+    Da = np.tile(0.2 * np.eye(5), (2, 2, 1, 1))
+    D_of = [Da + (A @ r.ravel()).reshape(2, 2, 5, 5) for r in R]
+    al, be = o.alfe_coefficients(R)
+    D_next = o.extrapolate_occupations(D_of[:3], Da, al, be)
+    np.testing.assert_allclose(D_next, D_of[3], atol=1e-10)
+
+
+def test_history_shorter_than_the_scheme():
+    Da = 0.2 * np.eye(5)[None]
+    np.testing.assert_array_equal(o.extrapolate_occupations([], Da, 2.0, -1.0), Da)
+    D1 = Da + 0.01
+    np.testing.assert_allclose(o.extrapolate_occupations([D1], Da, 2.0, -1.0), D1)
+    assert o.alfe_coefficients(_traj("linear")[:2]) == (0.0, 0.0)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2507_23612_gb300 import build as b
+    b.build()
+    from paper_2507_23612_gb300 import binding
+    return binding.load_library()
+
+
+@pytest.mark.parametrize("nhist", [0, 1, 2, 3])
+def test_library_extrapolation_matches_the_oracle(lib, nhist):
+    from paper_2507_23612_gb300.binding import extrapolate_occupations
+    rng = np.random.default_rng(7 + nhist)
+    R = _traj("quadratic", n=nhist + 1, natoms=4, seed=nhist)
+    R = [r + 0.01 * rng.standard_normal(r.shape) for r in R]    # not exactly quadratic
+    Da = np.tile(0.2 * np.eye(5), (2, 3, 1, 1))
+    D_hist = [Da + 0.05 * rng.standard_normal(Da.shape) for _ in range(nhist)]
+    al, be = o.alfe_coefficients(R)
+    ref = o.extrapolate_occupations(D_hist, Da, al, be)
+    D_next, (al2, be2) = extrapolate_occupations(D_hist, Da, R)
+    assert abs(al2 - al) < 1e-12 and abs(be2 - be) < 1e-12
+    np.testing.assert_allclose(D_next, ref, atol=1e-13)
