@@ -284,6 +284,24 @@ int hub_scf_get(hub_t h, double* eig, double* occ, double* D_out);
  * density mode.  Synchronises. */
 int hub_scf_density(hub_t h, double* rho_dev);
 
+/* Starting occupation matrices of the next MD step (Sec. II.B, last paragraph: D split into
+ * the atomic guess and a residual extrapolated to second order, as for the density):
+ *   Delta = D - D_atomic,
+ *   Delta(t+dt) = Delta(t) + alpha (Delta(t) - Delta(t-dt)) + beta (Delta(t-dt) - Delta(t-2dt)),
+ * (alpha, beta) the least-squares fit R(t+dt) - R(t) ~ alpha (R(t) - R(t-dt))
+ * + beta (R(t-dt) - R(t-2dt)) over all coordinates (beta = 0 with alpha fitted alone when
+ * the two steps are parallel or only three position sets are given; terms without history
+ * are dropped; no history gives D_atomic).  Host arithmetic only, no handle, no GPU.
+ *   n         numbers per D set (e.g. nspin * nhub * 25)
+ *   nhist     converged D sets given, 0..3, oldest first: D_hist host [nhist * n]
+ *   D_atomic  host [n]
+ *   natoms, R_hist  host [(nhist + 1) * natoms * 3]: the positions of those steps and, last,
+ *             of the step to be solved
+ *   coef_out  NULL or host [2]: alpha, beta.   D_out host [n].
+ * Errors: HUB_EINVAL (nhist outside 0..3, NULL arrays with nonzero sizes). */
+int hub_extrapolate_occupations(int n, int nhist, const double* D_hist, const double* D_atomic,
+                                int natoms, const double* R_hist, double* coef_out, double* D_out);
+
 /* ---------------------------------------------------------------------------------
  * Grid-sized steps of the self-consistent density SCF (Sec. II.B, last paragraph: CheFSI
  * with preconditioned Pulay mixing; the functional pieces are readings, the paper does not

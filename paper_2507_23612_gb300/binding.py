@@ -65,6 +65,7 @@ _SIGS = {
     "hub_scf_run": [_P, C.POINTER(scf_result)],
     "hub_scf_get": [_P, _PD, _PD, _PD],
     "hub_scf_density": [_P, _P],
+    "hub_extrapolate_occupations": [_I, _I, _PD, _PD, _I, _PD, _PD, _PD],
     "hub_density": [_P, _P, _I, _I, _PD, _D, _P],
     "hub_hartree": [_P, _P, _P, _D, _I, _PI, _PD],
     "hub_lda_exchange": [_P, _I, _P, _P, _P, _P, _PD],
@@ -397,6 +398,28 @@ class Hub:
         self._check(self.lib.hub_kerker(self.h, _tptr(r), _tptr(z), kappa, tol, max_iter, C.byref(it)),
                     "hub_kerker")
         return it.value
+
+
+def extrapolate_occupations(D_hist, D_atomic, R_hist):
+    """Starting D of the next MD step from up to three converged D sets (oldest first) and
+    the positions of those steps plus the new one (hub_extrapolate_occupations).
+    Returns (D, (alpha, beta))."""
+    lib = load_library()
+    Da = np.ascontiguousarray(D_atomic, dtype=np.float64)
+    n = Da.size
+    nh = len(D_hist)
+    Dh = np.ascontiguousarray(np.stack([np.asarray(d, dtype=np.float64).reshape(-1) for d in D_hist])
+                              if nh else np.zeros(1), dtype=np.float64)
+    R = [np.asarray(r, dtype=np.float64).reshape(-1) for r in R_hist]
+    natoms = R[0].size // 3 if R else 0
+    Rh = np.ascontiguousarray(np.concatenate(R) if R else np.zeros(1), dtype=np.float64)
+    coef = np.zeros(2)
+    out = np.zeros(n)
+    rc = lib.hub_extrapolate_occupations(n, nh, _dptr(Dh), _dptr(Da.reshape(-1)), natoms, _dptr(Rh),
+                                         _dptr(coef), _dptr(out))
+    if rc:
+        raise HubError(rc, "hub_extrapolate_occupations: bad arguments")
+    return out.reshape(Da.shape), (float(coef[0]), float(coef[1]))
 
 
 def descriptors(pos, species, L, centers, out, nspecies=2, rc=6.0, nrad=16, eta=0.4, stream=None):

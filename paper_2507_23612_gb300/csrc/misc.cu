@@ -261,3 +261,51 @@ extern "C" int hub_alu_peaks(double* fp64_gflops, double* fp32_gflops, void* cud
     cudaFree(buf);
     return rc;
 }
+
+// ---------------------------------------------------------------------------- MD extrapolation
+extern "C" int hub_extrapolate_occupations(int n, int nhist, const double* D_hist, const double* D_atomic,
+                                           int natoms, const double* R_hist, double* coef_out, double* D_out) {
+    if (n < 0 || nhist < 0 || nhist > 3 || natoms < 0) return HUB_EINVAL;
+    if (n > 0 && (!D_atomic || !D_out || (nhist > 0 && !D_hist))) return HUB_EINVAL;
+    if (natoms > 0 && nhist >= 2 && !R_hist) return HUB_EINVAL;
+    // coefficients from the positions: nhist + 1 sets, the last one the new step
+    double alpha = 0.0, beta = 0.0;
+    const long m = (long)natoms * 3;
+    const int npos = nhist + 1;
+    if (npos >= 3 && m > 0) {
+        const double* Rn = R_hist + (long)(npos - 1) * m;    // t + dt
+        const double* R0 = R_hist + (long)(npos - 2) * m;    // t
+        const double* R1 = R_hist + (long)(npos - 3) * m;    // t - dt
+        double g11 = 0.0, g12 = 0.0, g22 = 0.0, b1 = 0.0, b2 = 0.0;
+        for (long i = 0; i < m; ++i) {
+            const double t = Rn[i] - R0[i], d1 = R0[i] - R1[i];
+            g11 += d1 * d1;
+            b1 += d1 * t;
+            if (npos >= 4) {
+                const double d2 = R1[i] - R_hist[(long)(npos - 4) * m + i];
+                g12 += d1 * d2;
+                g22 += d2 * d2;
+                b2 += d2 * t;
+            }
+        }
+        const double det = g11 * g22 - g12 * g12;
+        if (npos >= 4 && det > 1e-12 * g11 * g22) {
+            alpha = (g22 * b1 - g12 * b2) / det;
+            beta = (g11 * b2 - g12 * b1) / det;
+        } else {
+            alpha = g11 > 0.0 ? b1 / g11 : 0.0;
+            beta = 0.0;
+        }
+    }
+    if (coef_out) { coef_out[0] = alpha; coef_out[1] = beta; }
+    for (long q = 0; q < n; ++q) {
+        const double da = D_atomic[q];
+        if (nhist == 0) { D_out[q] = da; continue; }
+        const double d0 = D_hist[(long)(nhist - 1) * n + q] - da;
+        double v = d0;
+        if (nhist >= 2) v += alpha * (d0 - (D_hist[(long)(nhist - 2) * n + q] - da));
+        if (nhist >= 3) v += beta * ((D_hist[(long)(nhist - 2) * n + q] - da) - (D_hist[(long)(nhist - 3) * n + q] - da));
+        D_out[q] = da + v;
+    }
+    return HUB_OK;
+}
