@@ -16,6 +16,7 @@ Paper: "Real-space Hubbard-corrected density functional theory" (arXiv 2507.2361
   * Sec. II.A.1, Bloch-mapped atomic orbitals . image sum with Bloch phase
   * Sec. II.A.2, Eqs. (DerED) and V_U ......... Hubbard potential applied to orbitals
   * Sec. II.A.3, final force equation ......... Hubbard atomic forces (FD gradient form)
+  * Sec. II.A.4, stress definition and result . Hubbard stress tensor (FD gradient form)
   * Sec. II.B, gradient weights equation ...... FD weights family, index wrap, quadrature
   * Sec. II.B, last paragraph ................. CheFSI + Pulay mixing, diagonal initial D
 Readings where the paper is silent (Laplacian weights, filter recurrence, Rayleigh-Ritz
@@ -165,7 +166,7 @@ def radial_norm(l: int, rs: float) -> float:
     return sqrt(2.0 / (_gamma_fn(l + 1.5) * rs ** (2 * l + 3)))
 
 
-def atom_function_table(grid: Grid, R, channels, rc: float):
+def atom_function_table(grid: Grid, R, channels, rc: float, moments: bool = False):
     """Grid table of one atom's localized functions, Bloch-periodically mapped.
 
     Sec. II.A.1: phi_{Ilm}(x, k) = sum_{images I~} phi^(|x - R_I~|) exp(-i k.(R_I - R_I~)).
@@ -174,11 +175,15 @@ def atom_function_table(grid: Grid, R, channels, rc: float):
     by a value threshold, Sec. II.B; the workloads fix rc).
     channels: list of (l, rs).  Returns (idx, vals): idx = sorted grid indices touched by
     any image, vals = (len(idx), nproj) with projector order channel by channel, m = -l..l.
+    With moments=True also mom (3, len(idx), nproj): the same image sum with each image's
+    term multiplied by (x - R_I~)_b, the displacement from that image's centre (the moment
+    integrals of the stress, Sec. II.A.4).
     """
     R = np.asarray(R, dtype=np.float64)
     nproj = sum(2 * l + 1 for l, _ in channels)
     dtype = np.complex128 if grid.is_complex else np.float64
     acc = np.zeros((grid.Nd, nproj), dtype=dtype)
+    mom = np.zeros((3, grid.Nd, nproj), dtype=dtype) if moments else None
     touched = np.zeros(grid.Nd, dtype=bool)
     n = np.asarray(grid.n)
     # lattice translations whose sphere can meet the cell [0, L)
@@ -209,9 +214,14 @@ def atom_function_table(grid: Grid, R, channels, rc: float):
                     vals = radial_norm(l, rs) * np.exp(-r2 / (2.0 * rs * rs)) * \
                         real_solid_harmonics(l, d)
                     acc[g, col:col + 2 * l + 1] += (phase * vals).T
+                    if moments:
+                        for b_ in range(3):
+                            mom[b_, g, col:col + 2 * l + 1] += (phase * vals * d[:, b_]).T
                     col += 2 * l + 1
                 touched[g] = True
     idx = np.nonzero(touched)[0]
+    if moments:
+        return idx, acc[idx], mom[:, idx]
     return idx, acc[idx]
 
 
@@ -453,6 +463,48 @@ def hubbard_forces(ham: Hamiltonian, X, f, kweight: float = 1.0, D=None):
                     acc += np.real(coef * kweight * s)
             out[I, a] = acc
     return out
+
+
+def hubbard_stress(ham: Hamiltonian, atoms, X, f, kweight: float = 1.0, D=None):
+    """Hubbard stress tensor of one (spin, k-point) set of orbitals (Sec. II.A.4), in
+    Ha/bohr^3, from the definition sigma_ab = (1/|Omega|) dE_U/dF_ab at fixed orbitals
+    (carried along by the deformation) and the chain rule through D:
+      sigma_ab = (1/|Omega|) sum_J (U_J/2) [ -delta_ab sum_mm' (delta_mm' - 2 D_m'm) D_mm'
+                  - 2 Re sum_mm' (delta_mm' - 2 D_m'm) kweight sum_n f_n
+                        conj(<phi_m'|psi_n>) <(x - R)_b phi_m|d_a psi_n> ]
+    with the moment (x - R_I~)_b taken from each periodic image's own centre.
+    Readings: the index order of D as for the force; the moment about the image centre
+    (the printed (S^T x - S^T R_I') with a sum over images and Bloch phases; only the image
+    centre makes the result independent of which image is called the atom); the 1/|Omega|
+    of the definition (the printed final expression is dE_U/dF).  Orthogonal cell (S = I).
+    atoms: the Hamiltonian's atoms (positions and Hubbard shells).  Returns (3, 3)."""
+    D = ham.D if D is None else np.asarray(D)
+    f = np.asarray(f, dtype=np.float64)
+    g = ham.grid
+    grads = [gradient(X, g, a) for a in range(3)]
+    omega = g.Nd * g.dV
+    sig = np.zeros((3, 3))
+    J = 0
+    for at in atoms:
+        if at.hub_l < 0:
+            continue
+        idx, vals, mom = atom_function_table(g, at.pos, [(at.hub_l, at.hub_rs)], at.hub_rc, moments=True)
+        U = at.hub_U
+        C = g.dV * (vals.conj().T @ X[idx])                      # <phi_m|psi_n>
+        nm = C.shape[0]
+        A = np.array([[(1.0 if m == mp else 0.0) - 2.0 * D[J][mp, m] for mp in range(nm)]
+                      for m in range(nm)])                      # A[m, m'] = delta - 2 D_m'm
+        trace_term = float(np.real(np.sum(A * D[J])))            # sum_mm' A_mm' D_mm'
+        for a in range(3):
+            for b_ in range(3):
+                Gm = g.dV * (mom[b_].conj().T @ grads[a][idx])   # <(x-R)_b phi_m|d_a psi_n>
+                s = 0.0
+                for m in range(nm):
+                    for mp in range(nm):
+                        s += np.real(A[m, mp] * kweight * np.sum(f * np.conj(C[mp]) * Gm[m]))
+                sig[a, b_] += 0.5 * U * (-(1.0 if a == b_ else 0.0) * trace_term - 2.0 * s) / omega
+        J += 1
+    return sig
 
 
 def hubbard_energy(D, U):

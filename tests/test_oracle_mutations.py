@@ -158,3 +158,40 @@ def test_planted_density_scf_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(ds, "hubbard_double_counting", lambda ham, D: 0.0)
     with pytest.raises(AssertionError):
         tds.test_model_b_scf_spin_polarized()
+
+
+def test_planted_stress_mistakes_are_caught(monkeypatch):
+    import test_oracle_stress as ts
+    good_table = o.atom_function_table
+
+    # moments about the atom with in-cell coordinates instead of about each image
+    def bad_table(grid, R, channels, rc, moments=False):
+        idx, vals = good_table(grid, R, channels, rc)
+        if not moments:
+            return idx, vals
+        x = grid.coords()[idx]
+        mom = np.stack([vals * (x[:, b] - np.asarray(R)[b])[:, None] for b in range(3)])
+        return idx, vals, mom
+    monkeypatch.setattr(o, "atom_function_table", bad_table)
+    with pytest.raises(AssertionError):
+        ts.test_lattice_translation_of_an_atom_leaves_the_stress_unchanged()
+    monkeypatch.setattr(o, "atom_function_table", good_table)
+
+    # without the delta_ab term of the volume change, or without 1/|Omega|
+    good_stress = o.hubbard_stress
+
+    def no_delta(ham, atoms, X, f, kweight=1.0, D=None):
+        sig = good_stress(ham, atoms, X, f, kweight, D)
+        Dm = ham.D if D is None else np.asarray(D)
+        omega = ham.grid.Nd * ham.grid.dV
+        tr = sum(0.5 * a.hub_U * float(np.real(np.trace(Dm[J]) - 2 * np.trace(Dm[J] @ Dm[J])))
+                 for J, a in enumerate([a for a in atoms if a.hub_l >= 0]))
+        return sig + np.eye(3) * tr / omega            # removes the -delta_ab term
+    monkeypatch.setattr(o, "hubbard_stress", no_delta)
+    with pytest.raises(AssertionError):
+        ts.test_diagonal_stress_is_the_strain_derivative_of_EU((0.0, 0.0, 0.0))
+    monkeypatch.setattr(o, "hubbard_stress",
+                        lambda ham, atoms, X, f, kweight=1.0, D=None:
+                        good_stress(ham, atoms, X, f, kweight, D) * ham.grid.Nd * ham.grid.dV)
+    with pytest.raises(AssertionError):
+        ts.test_diagonal_stress_is_the_strain_derivative_of_EU((0.0, 0.0, 0.0))
