@@ -472,7 +472,11 @@ def hubbard_stress(ham: Hamiltonian, atoms, X, f, kweight: float = 1.0, D=None):
       sigma_ab = (1/|Omega|) sum_J (U_J/2) [ -delta_ab sum_mm' (delta_mm' - 2 D_m'm) D_mm'
                   - 2 Re sum_mm' (delta_mm' - 2 D_m'm) kweight sum_n f_n
                         conj(<phi_m'|psi_n>) <(x - R)_b phi_m|d_a psi_n> ]
-    with the moment (x - R_I~)_b taken from each periodic image's own centre.
+    with the moment (x - R_I~)_b taken from each periodic image's own centre; in the
+    delta_ab term (the volume change of the orbitals' normalisation) D_mm' is this block's
+    own contribution kweight sum_n f_n <psi_n|phi_m'><phi_m|psi_n>, so that summing the
+    blocks of all spins and k-points gives the stress of the full D (for one k-point with
+    its weight it is the full D).
     Readings: the index order of D as for the force; the moment about the image centre
     (the printed (S^T x - S^T R_I') with a sum over images and Bloch phases; only the image
     centre makes the result independent of which image is called the atom); the 1/|Omega|
@@ -494,7 +498,8 @@ def hubbard_stress(ham: Hamiltonian, atoms, X, f, kweight: float = 1.0, D=None):
         nm = C.shape[0]
         A = np.array([[(1.0 if m == mp else 0.0) - 2.0 * D[J][mp, m] for mp in range(nm)]
                       for m in range(nm)])                      # A[m, m'] = delta - 2 D_m'm
-        trace_term = float(np.real(np.sum(A * D[J])))            # sum_mm' A_mm' D_mm'
+        D_blk = kweight * np.einsum("n,mn,pn->mp", f, C, np.conj(C))   # this block's D_mm'
+        trace_term = float(np.real(np.sum(A * D_blk)))            # sum_mm' A_mm' D_mm'
         for a in range(3):
             for b_ in range(3):
                 Gm = g.dV * (mom[b_].conj().T @ grads[a][idx])   # <(x-R)_b phi_m|d_a psi_n>

@@ -96,3 +96,16 @@ def test_off_diagonal_components_are_symmetric_to_discretisation_accuracy():
     scale = max(abs(sig[a, b]) for a, b in off)
     print({"offdiag": [sig[a, b] for a, b in off], "asym": asym})
     assert scale > 1e-7 and asym < 1e-5 * np.max(np.abs(sig))
+
+
+def test_blocks_sum_to_the_whole():
+    # with the prefactor D fixed, the stress is additive over blocks of states (spins,
+    # k-points, or a split of the states), the delta term included
+    ns, Ls, atoms, X, f = _system(K_POINT, n=24, L=8.0)
+    g = o.Grid(ns, Ls, K_POINT)
+    ham = o.Hamiltonian(g, np.zeros(g.Nd), atoms)
+    D = o.occupation_matrices(ham, X, f, 0.6)
+    whole = o.hubbard_stress(ham, atoms, X, f, 0.6, D)
+    parts = o.hubbard_stress(ham, atoms, X[:, :2], f[:2], 0.6, D) + \
+        o.hubbard_stress(ham, atoms, X[:, 2:], f[2:], 0.6, D)
+    np.testing.assert_allclose(parts, whole, atol=1e-13 * np.max(np.abs(whole)))
