@@ -203,6 +203,18 @@ int hub_occupation(hub_t h, int spin, const void* X, int ncol, int ld, const dou
 int hub_hubbard_forces(hub_t h, int spin, const void* X, int ncol, int ld, const double* f_host,
                        double kweight, double* F_host, void* work);
 
+/* Hubbard stress tensor of one (spin, k) block (Sec. II.A.4: sigma = (1/|Omega|) dE_U/dF,
+ * the derivative carried by the FD gradient of the orbitals), Ha/bohr^3:
+ *   sigma_ab = (1/|Omega|) sum_J [ -delta_ab sum_mm' M_m'm Dblk_mm'
+ *              - 2 Re sum_mm' M_m'm kweight sum_n f_n conj(<phi_m'|x_n>) <(x - R_T)_b phi_m|d_a x_n> ]
+ * with M = (U/2)(I - 2D) from the D last set for `spin`, Dblk = kweight sum_n f_n <x_n|phi_m'>
+ * <phi_m|x_n> this block's own occupation, and the moment (x - R_T)_b about each periodic
+ * image's centre.  Blocks of all spins and k-points add up to the stress of E_U.
+ * sigma_host: host double [9], row-major (a, b), overwritten.  work: as for
+ * hub_hubbard_forces.  Synchronises.  Errors: HUB_EINVAL, HUB_ECUDA. */
+int hub_hubbard_stress(hub_t h, int spin, const void* X, int ncol, int ld, const double* f_host,
+                       double kweight, double* sigma_host, void* work);
+
 /* k-step Lanczos from the device vector v0 [Nd] (handle element type): returns the
  * smallest Ritz value and the largest Ritz value plus |beta_k| (the CheFSI bound
  * estimate).  1 <= steps <= 64.  Synchronises. */

@@ -57,6 +57,7 @@ _SIGS = {
     "hub_rayleigh_ritz": [_P, _I, _P, _I, _I, _PD, _P],
     "hub_occupation": [_P, _I, _P, _I, _I, _PD, _D, _PD, _PD, _PD],
     "hub_hubbard_forces": [_P, _I, _P, _I, _I, _PD, _D, _PD, _P],
+    "hub_hubbard_stress": [_P, _I, _P, _I, _I, _PD, _D, _PD, _P],
     "hub_gram": [_P, _P, _I, _P, _I, _I, _D, _P],
     "hub_gram_noalloc": [_P, _I, _P, _I, C.c_longlong, _I, _I, _D, _P, _P],
     "hub_lanczos_bound": [_P, _I, _I, _P, _PD, _PD],
@@ -286,6 +287,15 @@ class Hub:
         self._check(self.lib.hub_hubbard_forces(self.h, spin, _tptr(X), ncol, ld, _dptr(f), kweight,
                                                 _dptr(F), _tptr(work)), "hub_hubbard_forces")
         return F[:self.natoms]
+
+    def hubbard_stress(self, spin: int, X, f, kweight: float = 1.0, work=None) -> np.ndarray:
+        """Hubbard stress (3, 3), Ha/bohr^3, of one (spin, k) block with the D last set for `spin`."""
+        ncol, ld = X.shape
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        sig = np.zeros(9)
+        self._check(self.lib.hub_hubbard_stress(self.h, spin, _tptr(X), ncol, ld, _dptr(f), kweight,
+                                                _dptr(sig), _tptr(work)), "hub_hubbard_stress")
+        return sig.reshape(3, 3)
 
     def lanczos_bound(self, spin: int, steps: int, v0):
         lo, up = C.c_double(), C.c_double()

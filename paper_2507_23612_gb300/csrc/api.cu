@@ -508,6 +508,68 @@ int hub_hubbard_forces(hub_t h, int spin, const void* X, int ncol, int ld, const
     return HUB_OK;
 }
 
+int hub_hubbard_stress(hub_t h, int spin, const void* X, int ncol, int ld, const double* f_host,
+                       double kweight, double* sigma_host, void* work) {
+    int rc = check_block(h, spin, X, ncol, ld);
+    if (rc) return rc;
+    if (!sigma_host) return fail(h, HUB_EINVAL, "NULL stress output");
+    if (ncol > 0 && !f_host) return fail(h, HUB_EINVAL, "NULL occupations");
+    std::fill(sigma_host, sigma_host + 9, 0.0);
+    const Table& t = h->proj;
+    if (t.nhub == 0 || ncol == 0) return HUB_OK;
+    auto fact = [](int k) { double r = 1.0; for (int i = 2; i <= k; ++i) r *= i; return r; };
+    double w[3][kMaxHalf];
+    for (int ax = 0; ax < 3; ++ax)
+        for (int p = 1; p <= h->n0; ++p)
+            w[ax][p - 1] = ((p % 2) ? 1.0 : -1.0) * fact(h->n0) * fact(h->n0) /
+                           (h->h[ax] * p * fact(h->n0 - p) * fact(h->n0 + p));
+    void* G = work;
+    if (!G) {
+        if ((rc = ensure(h, &h->d_work, &h->work_bytes, (size_t)ld * ncol * elem_bytes(h)))) return rc;
+        G = h->d_work;
+    }
+    // C = <phi|x> stays in d_C for the whole call (the moment gathers write their own rows)
+    if ((rc = launch_gather(h, X, ncol, ld, spin, false))) return rc;
+    const int cw = h->cplx ? 2 : 1;
+    const size_t nC = (size_t)t.nproj * ncol * cw;
+    const size_t need = (ncol + (size_t)t.nhub * 50 + 3 * nC + 9 * (size_t)t.nhub) * sizeof(double);
+    if ((rc = ensure(h, &h->d_aux, &h->aux_bytes, std::max(need, h->aux_bytes)))) return rc;
+    double* f_dev = (double*)h->d_aux;
+    double* Dblk = f_dev + ncol;
+    double* Gm = Dblk + (size_t)t.nhub * 50;
+    double* out = Gm + 3 * nC;                       // [a][hsite * 3 + b]
+    HUB_CUDA_TRY(h, cudaMemsetAsync(Gm, 0, 3 * nC * sizeof(double), h->stream));
+    HUB_CUDA_TRY(h, cudaMemcpyAsync(f_dev, f_host, ncol * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if ((rc = launch_occupation(h, ncol, f_dev, kweight, Dblk))) return rc;
+    for (int a = 0; a < 3; ++a) {
+        if ((rc = launch_fd_gradient(h, X, ld, ncol, a, w[a], G))) return rc;
+        if ((rc = launch_moment_gather(h, G, ld, ncol, Gm, Gm + nC, Gm + 2 * nC))) return rc;
+        for (int b = 0; b < 3; ++b)
+            if ((rc = launch_hub_force(h, spin, ncol, f_dev, kweight, Gm + b * nC, b,
+                                       out + (size_t)a * t.nhub * 3))) return rc;
+    }
+    std::vector<double> o((size_t)9 * t.nhub), D((size_t)t.nhub * 50);
+    HUB_CUDA_TRY(h, cudaMemcpyAsync(o.data(), out, o.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    HUB_CUDA_TRY(h, cudaMemcpyAsync(D.data(), Dblk, D.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if ((rc = check_flags(h))) return rc;
+    const std::vector<double>& M = t.h_M[spin];
+    const double omega = h->dV * (double)h->Nd;
+    for (int J = 0; J < t.nhub; ++J) {
+        // sum_mm' M_m'm Dblk_mm' (real part); M row m', column m
+        double tr = 0.0;
+        if (!M.empty())
+            for (int m = 0; m < 5; ++m)
+                for (int mp = 0; mp < 5; ++mp) {
+                    const size_t qm = (size_t)J * 25 + mp * 5 + m, qd = (size_t)J * 25 + m * 5 + mp;
+                    tr += M[qm * cw] * D[2 * qd] - (cw == 2 ? M[qm * cw + 1] * D[2 * qd + 1] : 0.0);
+                }
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                sigma_host[a * 3 + b] += ((a == b ? -tr : 0.0) + o[(size_t)a * t.nhub * 3 + J * 3 + b]) / omega;
+    }
+    return HUB_OK;
+}
+
 int hub_projector_stats(hub_t h, long long* function_points, long long* site_points) {
     if (!h) return HUB_EINVAL;
     if (function_points) *function_points = h->proj.nvals;

@@ -224,6 +224,10 @@ int launch_occupation(hub_t h, int ncol, const double* f_dev, double kweight, do
 int launch_hub_force(hub_t h, int spin, int ncol, const double* f_dev, double kweight,
                      const void* C0, int axis, double* F_dev);
 
+// Moment integrals of the stress: Gm_b = dV <(x - R_image)_b phi_m | G> for the Hubbard rows
+// (layout of d_C: [nproj x ncol] doubles, x2 complex; other rows untouched), b = x, y, z
+int launch_moment_gather(hub_t h, const void* G, int ld, int ncol, double* Gm0, double* Gm1, double* Gm2);
+
 // stencil.cu: G = d_axis X by the FD gradient of Sec. II.B (weights w[p-1] include 1/h),
 // Bloch factor exp(i k_a L_a) per wrap (complex only); X, G share ld
 int launch_fd_gradient(hub_t h, const void* X, int ld, int ncol, int axis, const double* w,

@@ -645,6 +645,78 @@ __global__ void k_hub_force(int ncol, const SiteDev* __restrict__ sites, const i
     }
 }
 
+// ---------------------------------------------------------------------------- stress moments
+// Moment integrals of the Hubbard stress (Sec. II.A.4) for one gradient block G = d_a X:
+//   Gm_b[(proj_off + m) * ncol + n] = dV sum_points conj(mom_bm(g)) G[g, n],   b = x, y, z,
+//   mom_bm(g) = sum_T phi_m(x_g - R - T) (x_g - R - T)_b exp(i k.T),
+// the moment about each periodic image's own centre.  The image sum is evaluated again here
+// (the tables hold only its total).  One CTA per (Hubbard atom, column); threads stride over
+// the atom's table points; a block reduction of the 15 (complex) sums.
+template <typename T, bool CPLX>
+__global__ void __launch_bounds__(256)
+k_moment_gather(const T* __restrict__ G, int ld, int ncol, const SiteDev* __restrict__ sites,
+                const int* __restrict__ hub_sites, const int* __restrict__ idx, int n1, int n2,
+                double h1, double h2, double h3, double L1, double L2, double L3, double k1, double k2,
+                double k3, double dV, double* __restrict__ Gm0, double* __restrict__ Gm1,
+                double* __restrict__ Gm2) {
+    constexpr int CW = CPLX ? 2 : 1;
+    const SiteDev S = sites[hub_sites[blockIdx.x]];
+    const int n = blockIdx.y;
+    double acc[3][5][CW];
+    for (int b = 0; b < 3; ++b)
+        for (int m = 0; m < 5; ++m)
+            for (int c = 0; c < CW; ++c) acc[b][m][c] = 0.0;
+    for (int row = S.pt_off + threadIdx.x; row < S.pt_off + S.npts; row += blockDim.x) {
+        const int g = idx[row];
+        const int i1 = g % n1, i2 = (g / n1) % n2, i3 = g / (n1 * n2);
+        const double x = i1 * h1, y = i2 * h2, z = i3 * h3;
+        const T gv = G[(long)n * ld + g];
+        double gr, gi = 0.0;
+        if constexpr (CPLX) { gr = gv.x; gi = gv.y; } else { gr = (double)gv; }
+        for (int t1 = S.tlo[0]; t1 <= S.thi[0]; ++t1)
+            for (int t2 = S.tlo[1]; t2 <= S.thi[1]; ++t2)
+                for (int t3 = S.tlo[2]; t3 <= S.thi[2]; ++t3) {
+                    const double T1 = t1 * L1, T2 = t2 * L2, T3 = t3 * L3;
+                    const double d[3] = {x - S.R[0] - T1, y - S.R[1] - T2, z - S.R[2] - T3};
+                    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (r2 >= S.rc * S.rc) continue;
+                    double c = 1.0, sn = 0.0;
+                    if (CPLX) sincos(k1 * T1 + k2 * T2 + k3 * T3, &sn, &c);
+                    double ylm[5];
+                    solid_harmonics(2, d[0], d[1], d[2], ylm);
+                    const double rad = S.N[0] * exp(-r2 / (2.0 * S.rs[0] * S.rs[0]));
+                    // conj(phi_m d_b e^{i k.T}) * g, accumulated per (b, m)
+                    const double pr = c * gr + sn * gi, pi = c * gi - sn * gr;
+#pragma unroll
+                    for (int m = 0; m < 5; ++m) {
+                        const double v = rad * ylm[m];
+#pragma unroll
+                        for (int b = 0; b < 3; ++b) {
+                            acc[b][m][0] += v * d[b] * pr;
+                            if constexpr (CPLX) acc[b][m][CW - 1] += v * d[b] * pi;
+                        }
+                    }
+                }
+    }
+    __shared__ double red[8][3 * 5 * CW];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int b = 0; b < 3; ++b)
+        for (int m = 0; m < 5; ++m)
+            for (int c = 0; c < CW; ++c) {
+                double v = acc[b][m][c];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                if (lane == 0) red[wid][(b * 5 + m) * CW + c] = v;
+            }
+    __syncthreads();
+    if (threadIdx.x < 3 * 5 * CW) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
+        const int b = threadIdx.x / (5 * CW), m = (threadIdx.x / CW) % 5, c = threadIdx.x % CW;
+        double* out = b == 0 ? Gm0 : (b == 1 ? Gm1 : Gm2);
+        out[((size_t)(S.proj_off + m) * ncol + n) * CW + c] = dV * v;
+    }
+}
+
 __global__ void k_sum_serial(const double* __restrict__ x, int n, double* __restrict__ out) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         double s = 0.0;
@@ -989,8 +1061,9 @@ int build_tables(hub_t h, int natoms, const double* pos, const int* kb_nchan, co
             for (int m = 0; m < 5; ++m) M[(size_t)(i * 25 + m * 5 + m) * (h->cplx ? 2 : 1)] = 0.5 * t.h_U[i];
         HUB_CUDA_TRY(h, cudaMemcpyAsync(t.d_M[s], M.data(), M.size() * sizeof(double),
                                         cudaMemcpyHostToDevice, h->stream));
+        HUB_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        t.h_M[s] = M;                  // host copy of the coefficients in use
     }
-    HUB_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     free_table(h->proj);
     h->proj = std::move(t);
     h->mem_gen++;
@@ -1117,6 +1190,27 @@ int launch_occupation(hub_t h, int ncol, const double* f_dev, double kweight, do
     HUB_CUDA_TRY(h, cudaGetLastError());
     ProfScope ps2(h, HUB_K_OCCUPATION);
     k_sum_serial<<<1, 32, 0, h->stream>>>(eu, t.nhub, h->d_scal);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    return HUB_OK;
+}
+
+int launch_moment_gather(hub_t h, const void* G, int ld, int ncol, double* Gm0, double* Gm1, double* Gm2) {
+    Table& t = h->proj;
+    if (t.nhub == 0 || ncol == 0) return HUB_OK;
+    if (ncol > 65535) return fail(h, HUB_EINVAL, "at most 65535 columns per moment gather");
+    const double kp[3] = {h->cplx ? h->kpt[0] : 0.0, h->cplx ? h->kpt[1] : 0.0, h->cplx ? h->kpt[2] : 0.0};
+    const dim3 grid((unsigned)t.nhub, (unsigned)ncol);
+    ProfScope ps(h, HUB_K_FORCE);
+#define HUB_MOMENT_ARGS ld, ncol, t.d_sites, t.d_hub_sites, t.d_idx, h->n1, h->n2, h->h[0], h->h[1], h->h[2], \
+        h->L[0], h->L[1], h->L[2], kp[0], kp[1], kp[2], h->dV, Gm0, Gm1, Gm2
+    if (h->esize == 8) {
+        if (h->cplx) k_moment_gather<double2, true><<<grid, 256, 0, h->stream>>>((const double2*)G, HUB_MOMENT_ARGS);
+        else k_moment_gather<double, false><<<grid, 256, 0, h->stream>>>((const double*)G, HUB_MOMENT_ARGS);
+    } else {
+        if (h->cplx) k_moment_gather<float2, true><<<grid, 256, 0, h->stream>>>((const float2*)G, HUB_MOMENT_ARGS);
+        else k_moment_gather<float, false><<<grid, 256, 0, h->stream>>>((const float*)G, HUB_MOMENT_ARGS);
+    }
+#undef HUB_MOMENT_ARGS
     HUB_CUDA_TRY(h, cudaGetLastError());
     return HUB_OK;
 }

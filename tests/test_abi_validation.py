@@ -107,3 +107,8 @@ def test_scf_structs_match_the_header(lib):
             names = decl.split(None, 1)[1]
             fields += [n.strip() for n in names.split(",")]
         assert [f for f, _ in struct._fields_] == fields, name
+
+
+def test_hubbard_stress_rejects_a_null_handle(lib):
+    sig = (C.c_double * 9)()
+    assert lib.hub_hubbard_stress(None, 0, None, 0, 0, None, 1.0, sig, None) == EINVAL
