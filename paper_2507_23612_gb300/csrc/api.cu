@@ -65,6 +65,16 @@ void fd_laplacian_weights(int n0, double* c0, double* c) {
     *c0 = -2.0 * s;
 }
 
+// first-derivative weights of Sec. II.B per axis, 1/h_a included:
+// w_p = (-1)^{p+1} (n0!)^2 / (h_a p (n0-p)! (n0+p)!)
+static void fd_gradient_weights(hub_t h, double w[3][kMaxHalf]) {
+    auto fact = [](int k) { double r = 1.0; for (int i = 2; i <= k; ++i) r *= i; return r; };
+    for (int ax = 0; ax < 3; ++ax)
+        for (int p = 1; p <= h->n0; ++p)
+            w[ax][p - 1] = ((p % 2) ? 1.0 : -1.0) * fact(h->n0) * fact(h->n0) /
+                           (h->h[ax] * p * fact(h->n0 - p) * fact(h->n0 + p));
+}
+
 int apply_H_internal(hub_t h, int spin, const void* X, int ld, void* Y, int ncol, double alpha,
                      double shift, const void* Yprev, double beta, const double* coef_dev) {
     int rc;
@@ -472,13 +482,8 @@ int hub_hubbard_forces(hub_t h, int spin, const void* X, int ncol, int ld, const
     const Table& t = h->proj;
     std::fill(F_host, F_host + (size_t)t.natoms * 3, 0.0);
     if (t.nhub == 0 || ncol == 0) return HUB_OK;
-    // first-derivative weights of Sec. II.B per axis (1/h_a included)
-    auto fact = [](int k) { double r = 1.0; for (int i = 2; i <= k; ++i) r *= i; return r; };
     double w[3][kMaxHalf];
-    for (int ax = 0; ax < 3; ++ax)
-        for (int p = 1; p <= h->n0; ++p)
-            w[ax][p - 1] = ((p % 2) ? 1.0 : -1.0) * fact(h->n0) * fact(h->n0) /
-                           (h->h[ax] * p * fact(h->n0 - p) * fact(h->n0 + p));
+    fd_gradient_weights(h, w);
     void* G = work;
     if (!G) {
         if ((rc = ensure(h, &h->d_work, &h->work_bytes, (size_t)ld * ncol * elem_bytes(h)))) return rc;
@@ -517,12 +522,8 @@ int hub_hubbard_stress(hub_t h, int spin, const void* X, int ncol, int ld, const
     std::fill(sigma_host, sigma_host + 9, 0.0);
     const Table& t = h->proj;
     if (t.nhub == 0 || ncol == 0) return HUB_OK;
-    auto fact = [](int k) { double r = 1.0; for (int i = 2; i <= k; ++i) r *= i; return r; };
     double w[3][kMaxHalf];
-    for (int ax = 0; ax < 3; ++ax)
-        for (int p = 1; p <= h->n0; ++p)
-            w[ax][p - 1] = ((p % 2) ? 1.0 : -1.0) * fact(h->n0) * fact(h->n0) /
-                           (h->h[ax] * p * fact(h->n0 - p) * fact(h->n0 + p));
+    fd_gradient_weights(h, w);
     void* G = work;
     if (!G) {
         if ((rc = ensure(h, &h->d_work, &h->work_bytes, (size_t)ld * ncol * elem_bytes(h)))) return rc;

@@ -112,3 +112,12 @@ def test_scf_structs_match_the_header(lib):
 def test_hubbard_stress_rejects_a_null_handle(lib):
     sig = (C.c_double * 9)()
     assert lib.hub_hubbard_stress(None, 0, None, 0, 0, None, 1.0, sig, None) == EINVAL
+
+
+def test_extrapolation_rejects_bad_history(lib):
+    D = (C.c_double * 25)()
+    out = (C.c_double * 25)()
+    assert lib.hub_extrapolate_occupations(25, 4, D, D, 0, None, None, out) == EINVAL    # nhist > 3
+    assert lib.hub_extrapolate_occupations(25, 1, None, D, 0, None, None, out) == EINVAL  # no history array
+    assert lib.hub_extrapolate_occupations(25, 2, D, D, 1, None, None, out) == EINVAL     # no positions
+    assert lib.hub_extrapolate_occupations(25, 0, None, D, 0, None, None, out) == 0       # atomic guess
