@@ -63,6 +63,12 @@ def parse():
     ap.add_argument("--forces", action="store_true",
                     help="time hub_hubbard_forces on the rutile workload (348 orbitals, one spin) "
                          "in --prec and report the FD-gradient kernel against the HBM roofline")
+    ap.add_argument("--stress", action="store_true",
+                    help="time hub_hubbard_stress on the rutile workload (348 orbitals, one spin) in --prec")
+    ap.add_argument("--density-scf", action="store_true",
+                    help="self-consistent density SCF (FD-Poisson Hartree, exchange, Kerker-"
+                         "preconditioned Pulay on rho and D) of the workload in --prec to 1e-5 "
+                         "Ha/atom: iterations, time, CG iterations per SCF iteration")
     ap.add_argument("--scf-compare", action="store_true",
                     help="cold-start SCF to convergence in FP64, FP32 and mixed (BF16 with the "
                          "precision ladder); report time to solution and errors against FP64")
@@ -679,10 +685,90 @@ def run_forces(args):
     return 0
 
 
+def run_stress(args):
+    """Hubbard stress of one (spin, k) block of the rutile workload: three FD gradients,
+    one projector gather, three moment gathers (the orbitals re-evaluated about each image
+    centre for the 24 Hubbard Ti) and nine per-atom reductions per call."""
+    import math
+    import numpy as np
+    import torch
+    import workloads as w
+    from paper_2507_23612_gb300 import Hub
+    wl = w.rutile()
+    dev = torch.device("cuda", 0)
+    hub = Hub(wl.n, wl.L, wl.fd_half_order, prec=PREC[args.prec])
+    hub.set_veff(torch.tensor(wl.veff, device=dev))
+    hub.set_atoms(wl.atoms)
+    hub.set_occupation_matrix(0, wl.D0[0])
+    g = torch.Generator(device=dev).manual_seed(5)
+    X = torch.randn(wl.ncol, wl.Nd, device=dev, dtype=torch.float64, generator=g).to(hub.dtype).contiguous()
+    X /= (X.double().norm(dim=1, keepdim=True) * math.sqrt(wl.dV)).to(X.dtype)
+    f = np.linspace(1.0, 0.0, wl.ncol)
+    work = torch.empty_like(X)
+    sig = hub.hubbard_stress(0, X, f, 1.0, work=work)
+    torch.cuda.synchronize()
+    hub.profile(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sig = hub.hubbard_stress(0, X, f, 1.0, work=work)
+    wall_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    prof = hub.profile_read()
+    hub.profile(0)
+    print(json.dumps({"probe": "hubbard_stress", "prec": args.prec, "grid": list(wl.n),
+                      "orbitals": wl.ncol, "hubbard_atoms": hub.nhub, "ms_per_call": wall_ms,
+                      "kernels": {k: v for k, v in prof.items() if v[1]},
+                      "sigma_Ha_per_bohr3": sig.tolist()}))
+    hub.close()
+    return 0
+
+
+def run_density_scf(args):
+    """Cold-start self-consistent density SCF of the workload (uniform starting density,
+    atomic-guess D) in --prec, to |dE|/atom < 1e-5 Ha twice, max|dD| < 1e-4 and
+    int|rho_out - rho_in| / N_e < 1e-4."""
+    import torch
+    from paper_2507_23612_gb300 import Hub, scf_params
+    dev = torch.device("cuda", 0)
+    wl = make_workload(args.workload)
+    hub = Hub(wl.n, wl.L, wl.fd_half_order, prec=PREC[args.prec])
+    hub.set_veff(torch.tensor(wl.veff, device=dev))
+    hub.set_atoms(wl.atoms)
+    Xs = [torch.tensor(wl.orbitals(s), device=dev).to(hub.dtype).contiguous() for s in range(wl.nspin)]
+    v0s = [torch.tensor(wl.lanczos_start(s), device=dev).to(hub.dtype).contiguous() for s in range(wl.nspin)]
+    p = scf_params(nspin=wl.nspin, ncol=wl.ncol, ld=wl.Nd, degree=wl.degree, max_iter=200,
+                   first_passes=3, lanczos_steps=10, pulay_history=7, natoms=len(wl.atoms),
+                   pulay_beta=0.3, kT=wl.kT if wl.kT > 0 else 0.005, n_elec=wl.n_elec,
+                   tol_e_atom=1e-5, tol_D=1e-4, ladder=1 if args.prec == "mixed" else 0, ladder_tol=1e-4,
+                   density=1, kerker_kappa=0.5, tol_rho=1e-4, cg_tol=1e-10)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hub.scf_begin(p, Xs, v0s, wl.D0)
+    hist = []
+    while True:
+        r = hub.scf_iterate()
+        hist.append({"E": r["E"], "dE": r["dE"], "dD": r["dD"], "drho": r["drho"], "cg_iters": r["cg_iters"]})
+        if r["converged"] or r["iter"] >= p.max_iter:
+            break
+    torch.cuda.synchronize()
+    tts = time.perf_counter() - t0
+    print(json.dumps({"density_scf": {"workload": args.workload, "prec": args.prec,
+                                      "time_to_solution_s": tts, "iterations": r["iter"],
+                                      "converged": bool(r["converged"]), "E_Ha": r["E"],
+                                      "E_H_Ha": r["E_H"], "E_x_Ha": r["E_x"], "E_U_Ha": r["E_U"],
+                                      "cg_iters_per_iteration": [h["cg_iters"] for h in hist],
+                                      "drho": [h["drho"] for h in hist]}}))
+    hub.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.forces:
         return run_forces(args)
+    if args.stress:
+        return run_stress(args)
+    if args.density_scf:
+        return run_density_scf(args)
     if args.probe_apply:
         return probe_apply(args)
     if args.probe_alu:
