@@ -291,6 +291,13 @@ int hub_scf_run(hub_t h, hub_scf_result* res);
 /* Results of the last iteration: eig/occ host [nspin*ncol] (may be NULL),
  * D_out host [nspin*nhub*25] (may be NULL). */
 int hub_scf_get(hub_t h, double* eig, double* occ, double* D_out);
+/* Hubbard forces (and optionally the Hubbard stress) of the SCF's last iteration: the sum
+ * over spin channels of hub_hubbard_forces / hub_hubbard_stress of the SCF's orbitals and
+ * occupations (times 2 for one spin-unpolarized channel), with D = the last iteration's
+ * D_out (the occupation of those orbitals), which becomes the handle's occupation matrix.
+ * F_host host [natoms * 3]; sigma_host NULL or host [9].  Synchronises. */
+int hub_scf_forces(hub_t h, double* F_host, double* sigma_host);
+
 /* Self-consistent density SCF: the output density of the last iteration, summed over the
  * spin channels, into rho_dev (device double [Nd]).  HUB_EINVAL when the SCF is not in
  * density mode.  Synchronises. */

@@ -66,6 +66,7 @@ _SIGS = {
     "hub_scf_run": [_P, C.POINTER(scf_result)],
     "hub_scf_get": [_P, _PD, _PD, _PD],
     "hub_scf_density": [_P, _P],
+    "hub_scf_forces": [_P, _PD, _PD],
     "hub_extrapolate_occupations": [_I, _I, _PD, _PD, _I, _PD, _PD, _PD],
     "hub_density": [_P, _P, _I, _I, _PD, _D, _P],
     "hub_hartree": [_P, _P, _P, _D, _I, _PI, _PD],
@@ -375,6 +376,14 @@ class Hub:
         return (eig.reshape(p.nspin, p.ncol), occ.reshape(p.nspin, p.ncol),
                 D[:p.nspin * self.nhub * 25].reshape(p.nspin, self.nhub, 5, 5))
 
+
+    def scf_forces(self, stress: bool = False):
+        """Hubbard forces (natoms, 3) of the SCF's last iteration, and its stress (3, 3) when asked."""
+        F = np.zeros((max(self.natoms, 1), 3))
+        sig = np.zeros(9) if stress else None
+        self._check(self.lib.hub_scf_forces(self.h, _dptr(F), None if sig is None else _dptr(sig)),
+                    "hub_scf_forces")
+        return (F[:self.natoms], sig.reshape(3, 3)) if stress else F[:self.natoms]
 
     def scf_density(self, rho):
         """Output density of the last density-SCF iteration (summed over spins) into rho."""

@@ -914,6 +914,31 @@ int hub_scf_begin(hub_t h, const hub_scf_params* p, void* const* X, const void* 
     return HUB_OK;
 }
 
+int hub_scf_forces(hub_t h, double* F_host, double* sigma_host) {
+    if (!h || !h->scf) return fail(h, HUB_EINVAL, "hub_scf_begin has not been called");
+    if (!F_host) return fail(h, HUB_EINVAL, "NULL force output");
+    ScfState& st = *h->scf;
+    if (st.iter == 0) return fail(h, HUB_EINVAL, "no SCF iteration has run");
+    const hub_scf_params& p = st.p;
+    const int nh = h->proj.nhub, na = h->proj.natoms;
+    const double deg = p.nspin == 1 ? 2.0 : 1.0;
+    std::fill(F_host, F_host + (size_t)na * 3, 0.0);
+    if (sigma_host) std::fill(sigma_host, sigma_host + 9, 0.0);
+    std::vector<double> F((size_t)std::max(na, 1) * 3), sig(9);
+    int rc;
+    for (int s = 0; s < p.nspin; ++s) {
+        if ((rc = hub_set_occupation_matrix(h, s, st.D_out.data() + (size_t)s * nh * 25, nullptr))) return rc;
+        const double* f = st.occ.data() + (size_t)s * p.ncol;
+        if ((rc = hub_hubbard_forces(h, s, st.X[s], p.ncol, p.ld, f, deg, F.data(), nullptr))) return rc;
+        for (size_t q = 0; q < (size_t)na * 3; ++q) F_host[q] += F[q];
+        if (sigma_host) {
+            if ((rc = hub_hubbard_stress(h, s, st.X[s], p.ncol, p.ld, f, deg, sig.data(), nullptr))) return rc;
+            for (int q = 0; q < 9; ++q) sigma_host[q] += sig[q];
+        }
+    }
+    return HUB_OK;
+}
+
 int hub_scf_density(hub_t h, double* rho_dev) {
     if (!h || !h->scf) return fail(h, HUB_EINVAL, "hub_scf_begin has not been called");
     ScfState& st = *h->scf;

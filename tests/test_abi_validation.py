@@ -121,3 +121,8 @@ def test_extrapolation_rejects_bad_history(lib):
     assert lib.hub_extrapolate_occupations(25, 1, None, D, 0, None, None, out) == EINVAL  # no history array
     assert lib.hub_extrapolate_occupations(25, 2, D, D, 1, None, None, out) == EINVAL     # no positions
     assert lib.hub_extrapolate_occupations(25, 0, None, D, 0, None, None, out) == 0       # atomic guess
+
+
+def test_scf_forces_rejects_a_null_handle(lib):
+    F = (C.c_double * 3)()
+    assert lib.hub_scf_forces(None, F, None) == EINVAL

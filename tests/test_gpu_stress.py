@@ -71,3 +71,31 @@ def test_stress_blocks_add_up():
     parts = hb.hubbard_stress(0, Xd[:20].contiguous(), f[:20], 1.0) + \
         hb.hubbard_stress(0, Xd[20:].contiguous(), f[20:], 1.0)
     assert rel(parts, whole) < 1e-12
+
+
+def test_scf_forces_and_stress_of_the_converged_state():
+    # hub_scf_forces sums the channels of the SCF's last iteration with D_out; the oracle
+    # evaluates the same sums from the downloaded orbitals, occupations and D_out
+    from paper_2507_23612_gb300 import scf_params
+    wl = w.small_test_system(n=(16, 14, 18), natoms=2, ncol=14, hub_rc=3.0, kb_rc=2.0, nspin=2)
+    hb = make_hub(wl, HUB_F64)
+    p = scf_params(nspin=2, ncol=wl.ncol, ld=wl.Nd, degree=12, max_iter=80, first_passes=4,
+                   lanczos_steps=10, pulay_history=7, natoms=len(wl.atoms), pulay_beta=0.3,
+                   kT=0.01, n_elec=16.0, tol_e_atom=1e-8, tol_D=1e-6)
+    Xs = [to_dev(wl.orbitals(s), torch.float64) for s in range(2)]
+    vs = [to_dev(wl.lanczos_start(s), torch.float64) for s in range(2)]
+    hb.scf_begin(p, Xs, vs, wl.D0)
+    res = hb.scf_run()
+    assert res["converged"] == 1
+    eig, occ, D = hb.scf_get()
+    F, sig = hb.scf_forces(stress=True)
+    F_ref = np.zeros((len(wl.atoms), 3))
+    sig_ref = np.zeros((3, 3))
+    hub_atoms = [i for i, a in enumerate(wl.atoms) if a.hub_l >= 0]
+    for s in range(2):
+        X = Xs[s].cpu().numpy().T
+        H = oracle_ham(wl, D=D[s])
+        F_ref[hub_atoms] += o.hubbard_forces(H, X, occ[s], 1.0)
+        sig_ref += o.hubbard_stress(H, wl.atoms, X, occ[s], 1.0)
+    assert rel(F, F_ref) < 1e-10
+    assert rel(sig, sig_ref) < 1e-10
