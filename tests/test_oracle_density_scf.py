@@ -163,3 +163,35 @@ def test_model_b_scf_spin_polarized():
     assert r["converged"]
     assert max(abs(a - b) for a, b in zip(r["hist_E"], r["hist_direct"])) < 1e-10
     assert abs(wl.dV * (np.sum(r["rho"][0]) + np.sum(r["rho"][1])) - 6.0) < 1e-10
+
+
+def _basis_case():
+    g = hb.Grid((20, 18, 22), (6.0, 5.4, 6.6))
+    atoms = [w.Atom("Ti", np.array([1.0, 2.0, 3.0])), w.Atom("O", np.array([4.5, 1.2, 0.4]))]
+    return g, ds.density_basis_atoms(atoms)
+
+
+def test_density_in_the_basis_is_recovered_exactly():
+    g, basis = _basis_case()
+    c = np.array([[0.7, -0.2, 1.3], [0.1, 0.9, 0.4]])
+    rho = ds.expand_density(g, basis, c)
+    np.testing.assert_allclose(ds.fit_density_coefficients(g, basis, rho), c, atol=1e-9)
+
+
+def test_fit_is_the_orthogonal_projection():
+    g, basis = _basis_case()
+    rng = np.random.default_rng(8)
+    rho = rng.uniform(0.0, 1.0, g.Nd)
+    c = ds.fit_density_coefficients(g, basis, rho)
+    B = ds.density_basis_matrix(g, basis)
+    resid = rho - B @ c.ravel()
+    # the residual is orthogonal to every basis function, so any other coefficients fit worse
+    assert np.max(np.abs(g.dV * (B.T @ resid))) < 1e-10 * np.max(np.abs(g.dV * (B.T @ rho)))
+    worse = rho - B @ (c.ravel() + 1e-3 * rng.standard_normal(c.size))
+    assert np.sum(worse ** 2) > np.sum(resid ** 2)
+
+
+def test_expanded_density_carries_the_electron_count():
+    g, basis = _basis_case()
+    rho = ds.expand_density(g, basis, np.array([[0.7, 0.2, 1.3], [0.1, 0.9, 0.4]]), n_elec=12.0)
+    assert abs(g.dV * np.sum(rho) - 12.0) < 1e-12
