@@ -187,6 +187,22 @@ int hub_gram_noalloc(const void* A, int ncol_a, const void* B, int ncol_b, long 
 int hub_occupation(hub_t h, int spin, const void* X, int ncol, int ld, const double* f_host,
                    double kweight, double* D_re_out, double* D_im_out, double* EU_out);
 
+/* Number of projector rows of the handle's tables (KB-type rows and Hubbard rows, atom by
+ * atom in the order of hub_set_atoms_projectors; per atom its KB channels, then its Hubbard
+ * shell; m = -l..l within a channel). */
+int hub_num_projectors(hub_t h, int* nproj);
+
+/* Projector inner products of a block (Sec. II.B: all integrals of an atom computed
+ * together): C_host[p * ncol + n] = dV <proj_p|x_n> for every row p of the tables
+ * (complex handles: (re, im) pairs).  X device [ld x ncol], handle element type; C_host host
+ * double [nproj * ncol] (x2 complex).  Needs hub_set_atoms_projectors only.  Synchronises. */
+int hub_project(hub_t h, const void* X, int ncol, int ld, double* C_host);
+
+/* The adjoint: Y[g, n] += alpha * sum_p proj_p(g) W[p, n] for a host coefficient matrix
+ * W_host double [nproj * ncol] (x2 complex), rounded to the handle's working type.
+ * Y device [ld x ncol].  Asynchronous (the coefficients are copied before return). */
+int hub_expand(hub_t h, const double* W_host, int ncol, void* Y, int ld, double alpha);
+
 /* Hubbard atomic forces of one (spin, k) block (Sec. II.A.3, final force equation, with
  * the derivative carried by the FD gradient of the orbitals of Sec. II.B):
  *   F_J,a = Re sum_mm' U_J (2 D_J,m'm - delta_mm') kweight sum_n f_n
@@ -297,6 +313,11 @@ int hub_scf_get(hub_t h, double* eig, double* occ, double* D_out);
  * D_out (the occupation of those orbitals), which becomes the handle's occupation matrix.
  * F_host host [natoms * 3]; sigma_host NULL or host [9].  Synchronises. */
 int hub_scf_forces(hub_t h, double* F_host, double* sigma_host);
+
+/* Self-consistent density SCF: replace the starting density (uniform by default) before the
+ * first iteration; rho_dev device double [Nd], the total density (split evenly between two
+ * spin channels).  HUB_EINVAL outside density mode or after the first iteration. */
+int hub_scf_set_density(hub_t h, const double* rho_dev);
 
 /* Self-consistent density SCF: the output density of the last iteration, summed over the
  * spin channels, into rho_dev (device double [Nd]).  HUB_EINVAL when the SCF is not in

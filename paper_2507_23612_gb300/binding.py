@@ -66,6 +66,10 @@ _SIGS = {
     "hub_scf_run": [_P, C.POINTER(scf_result)],
     "hub_scf_get": [_P, _PD, _PD, _PD],
     "hub_scf_density": [_P, _P],
+    "hub_scf_set_density": [_P, _P],
+    "hub_num_projectors": [_P, _PI],
+    "hub_project": [_P, _P, _I, _I, _PD],
+    "hub_expand": [_P, _PD, _I, _P, _I, _D],
     "hub_scf_forces": [_P, _PD, _PD],
     "hub_extrapolate_occupations": [_I, _I, _PD, _PD, _I, _PD, _PD, _PD],
     "hub_density": [_P, _P, _I, _I, _PD, _D, _P],
@@ -384,6 +388,38 @@ class Hub:
         self._check(self.lib.hub_scf_forces(self.h, _dptr(F), None if sig is None else _dptr(sig)),
                     "hub_scf_forces")
         return (F[:self.natoms], sig.reshape(3, 3)) if stress else F[:self.natoms]
+
+    def scf_set_density(self, rho):
+        """Starting density of a density-mode SCF (before its first iteration)."""
+        self._check(self.lib.hub_scf_set_density(self.h, _tptr(rho)), "hub_scf_set_density")
+
+    def num_projectors(self) -> int:
+        n = C.c_int()
+        self._check(self.lib.hub_num_projectors(self.h, C.byref(n)), "hub_num_projectors")
+        return n.value
+
+    def project(self, X) -> np.ndarray:
+        """C[p, n] = dV <proj_p|x_n> for every projector row (complex on complex handles)."""
+        ncol, ld = X.shape
+        npj = self.num_projectors()
+        cw = 2 if self.complex else 1
+        out = np.zeros(max(npj * ncol * cw, 1))
+        self._check(self.lib.hub_project(self.h, _tptr(X), ncol, ld, _dptr(out)), "hub_project")
+        out = out[:npj * ncol * cw]
+        if cw == 2:
+            return (out[0::2] + 1j * out[1::2]).reshape(npj, ncol)
+        return out.reshape(npj, ncol)
+
+    def expand(self, W, Y, alpha: float = 1.0):
+        """Y[g, n] += alpha sum_p proj_p(g) W[p, n] (W host, [nproj, ncol])."""
+        ncol, ld = Y.shape
+        W = np.asarray(W)
+        if self.complex:
+            Wf = np.empty(W.size * 2)
+            Wf[0::2], Wf[1::2] = np.real(W).ravel(), np.imag(W).ravel()
+        else:
+            Wf = np.ascontiguousarray(np.real(W), dtype=np.float64).ravel()
+        self._check(self.lib.hub_expand(self.h, _dptr(Wf), ncol, _tptr(Y), ld, float(alpha)), "hub_expand")
 
     def scf_density(self, rho):
         """Output density of the last density-SCF iteration (summed over spins) into rho."""

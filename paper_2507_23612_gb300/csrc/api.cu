@@ -473,6 +473,51 @@ int hub_occupation(hub_t h, int spin, const void* X, int ncol, int ld, const dou
     return HUB_OK;
 }
 
+int hub_num_projectors(hub_t h, int* nproj) {
+    if (!h || !nproj) return HUB_EINVAL;
+    *nproj = h->proj.nproj;
+    return HUB_OK;
+}
+
+static int check_tables(hub_t h, const void* X, int ncol, int ld) {
+    if (!h) return HUB_EINVAL;
+    if (ncol < 0) return fail(h, HUB_EINVAL, "ncol must be >= 0");
+    if (ncol > 0 && !X) return fail(h, HUB_EINVAL, "NULL block");
+    if ((long)ld < h->Nd) return fail(h, HUB_EINVAL, "ld must be >= n1*n2*n3");
+    if (!h->atoms_set) return fail(h, HUB_EINVAL, "hub_set_atoms_projectors has not been called");
+    return HUB_OK;
+}
+
+int hub_project(hub_t h, const void* X, int ncol, int ld, double* C_host) {
+    int rc = check_tables(h, X, ncol, ld);
+    if (rc) return rc;
+    const int cw = h->cplx ? 2 : 1;
+    const size_t n = (size_t)h->proj.nproj * ncol * cw;
+    if (n == 0) return HUB_OK;
+    if (!C_host) return fail(h, HUB_EINVAL, "NULL output");
+    if ((rc = launch_gather(h, X, ncol, ld, 0, false))) return rc;
+    HUB_CUDA_TRY(h, cudaMemcpyAsync(C_host, h->d_C, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return check_flags(h);
+}
+
+int hub_expand(hub_t h, const double* W_host, int ncol, void* Y, int ld, double alpha) {
+    int rc = check_tables(h, Y, ncol, ld);
+    if (rc) return rc;
+    const int cw = h->cplx ? 2 : 1;
+    const size_t n = (size_t)h->proj.nproj * ncol * cw;
+    if (n == 0) return HUB_OK;
+    if (!W_host) return fail(h, HUB_EINVAL, "NULL coefficients");
+    if ((rc = ensure(h, &h->d_W, &h->W_bytes, std::max(n * h->esize, h->W_bytes)))) return rc;
+    if (h->esize == 8) {
+        HUB_CUDA_TRY(h, cudaMemcpyAsync(h->d_W, W_host, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    } else {
+        std::vector<float> wf(W_host, W_host + n);
+        HUB_CUDA_TRY(h, cudaMemcpyAsync(h->d_W, wf.data(), n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        HUB_CUDA_TRY(h, cudaStreamSynchronize(h->stream));     // wf goes out of scope
+    }
+    return launch_scatter(h, Y, ncol, ld, alpha);
+}
+
 int hub_hubbard_forces(hub_t h, int spin, const void* X, int ncol, int ld, const double* f_host,
                        double kweight, double* F_host, void* work) {
     int rc = check_block(h, spin, X, ncol, ld);
@@ -936,6 +981,22 @@ int hub_scf_forces(hub_t h, double* F_host, double* sigma_host) {
             for (int q = 0; q < 9; ++q) sigma_host[q] += sig[q];
         }
     }
+    return HUB_OK;
+}
+
+int hub_scf_set_density(hub_t h, const double* rho_dev) {
+    if (!h || !h->scf) return fail(h, HUB_EINVAL, "hub_scf_begin has not been called");
+    ScfState& st = *h->scf;
+    if (!st.density) return fail(h, HUB_EINVAL, "the SCF is not in density mode");
+    if (st.iter != 0) return fail(h, HUB_EINVAL, "the starting density is set before the first iteration");
+    if (!rho_dev) return fail(h, HUB_EINVAL, "NULL density");
+    const double c = 1.0 / st.p.nspin;
+    for (int s = 0; s < st.p.nspin; ++s) {
+        const double* v[1] = {rho_dev};
+        int rc = density_lincomb(h, st.rho_in[s], 1, v, &c, nullptr, 0.0);
+        if (rc) return rc;
+    }
+    HUB_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return HUB_OK;
 }
 

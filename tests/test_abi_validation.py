@@ -126,3 +126,11 @@ def test_extrapolation_rejects_bad_history(lib):
 def test_scf_forces_rejects_a_null_handle(lib):
     F = (C.c_double * 3)()
     assert lib.hub_scf_forces(None, F, None) == EINVAL
+
+
+def test_projector_entry_points_reject_a_null_handle(lib):
+    n = C.c_int()
+    assert lib.hub_num_projectors(None, C.byref(n)) == EINVAL
+    assert lib.hub_project(None, None, 0, 0, None) == EINVAL
+    assert lib.hub_expand(None, None, 0, None, 0, 1.0) == EINVAL
+    assert lib.hub_scf_set_density(None, None) == EINVAL

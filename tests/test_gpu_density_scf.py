@@ -122,3 +122,55 @@ def test_density_scf_reaches_the_oracle_fixed_point(nspin):
     np.testing.assert_allclose(D, ref["D"], atol=1e-5)
     np.testing.assert_allclose(eig[:, :5], np.array(ref["eig"])[:, :5], atol=1e-6)
     assert wl.dV * np.sum(np.abs(rho.cpu().numpy() - sum(ref["rho"]))) < 1e-4
+
+
+@pytest.mark.parametrize("prec,cplx", [(HUB_F64, False), (HUB_F64, True), (HUB_F32, False)])
+def test_project_and_expand_match_the_oracle_tables(prec, cplx):
+    wl = w.small_test_system(n=(20, 24, 28), ncol=9, natoms=3,
+                             kpt=(0.21, -0.13, 0.34) if cplx else (0.0, 0.0, 0.0))
+    g = o.Grid(wl.n, wl.L, wl.kpts[0])
+    # the oracle's rows in the library's order: per atom its KB channels, then its Hubbard shell
+    cols = []
+    for a in wl.atoms:
+        if len(a.kb_l):
+            idx, vals = o.atom_function_table(g, a.pos, list(zip(a.kb_l, a.kb_rs)), a.kb_rc)
+            B = np.zeros((wl.Nd, vals.shape[1]), dtype=vals.dtype)
+            B[idx] = vals
+            cols.append(B)
+        if a.hub_l >= 0:
+            idx, vals = o.atom_function_table(g, a.pos, [(a.hub_l, a.hub_rs)], a.hub_rc)
+            B = np.zeros((wl.Nd, vals.shape[1]), dtype=vals.dtype)
+            B[idx] = vals
+            cols.append(B)
+    P = np.concatenate(cols, axis=1)
+    X = wl.orbitals(complex_=cplx)
+    if prec == HUB_F32:
+        X = X.astype(np.complex64 if cplx else np.float32).astype(np.complex128 if cplx else np.float64)
+    hb = make_hub(wl, prec)
+    assert hb.num_projectors() == P.shape[1]
+    C = hb.project(to_dev(X, hb.dtype))
+    C_ref = g.dV * (P.conj().T @ X.T)
+    assert rel(C, C_ref) < (1e-12 if prec == HUB_F64 else 1e-5)
+    rng = np.random.default_rng(9)
+    W = rng.standard_normal(C_ref.shape) + (1j * rng.standard_normal(C_ref.shape) if cplx else 0)
+    Y = to_dev(np.zeros_like(X), hb.dtype)
+    hb.expand(W, Y, 0.5)
+    Y_ref = 0.5 * (P @ W).T
+    assert rel(Y.cpu().numpy(), Y_ref) < (1e-12 if prec == HUB_F64 else 1e-5)
+
+
+def test_density_scf_from_a_given_starting_density():
+    # the uniform start written explicitly gives the same run as the default start
+    wl = w.small_test_system(n=(10, 10, 12), ncol=8, natoms=2, seed=11, nspin=1)
+    runs = []
+    for explicit in (False, True):
+        hb = make_hub(wl, HUB_F64)
+        p = scf_params(nspin=1, ncol=wl.ncol, ld=wl.Nd, degree=12, max_iter=80, first_passes=3,
+                       lanczos_steps=10, pulay_history=7, natoms=len(wl.atoms), pulay_beta=0.3,
+                       kT=0.01, n_elec=6.0, tol_e_atom=1e-8, tol_D=1e-6, density=1, tol_rho=1e-6)
+        hb.scf_begin(p, [to_dev(wl.orbitals(), torch.float64)], [to_dev(wl.lanczos_start(), torch.float64)], wl.D0)
+        if explicit:
+            hb.scf_set_density(_dev64(np.full(wl.Nd, 6.0 / (wl.Nd * wl.dV))))
+        runs.append(hb.scf_run())
+    assert runs[0]["iter"] == runs[1]["iter"]
+    assert abs(runs[0]["E"] - runs[1]["E"]) < 1e-12
