@@ -5,9 +5,13 @@ Hubbard atom and updates and mixes D every iteration until it is self-consistent
 SiLU multilayer perceptron (hub_mlp_*: forward, backward and Adam in the library's own
 kernels) maps descriptors of each Hubbard atom's neighbourhood (hub_descriptors) to the 15
 unique entries of its 5x5 D per spin, and is trained on SCF solutions that the library
-itself computes on displaced cells.  The SCF started from the predicted D converges to its
-own fixed point: the model only saves iterations, and the plain SCF remains the fallback
-and the arbiter of its error.  (The paper has no learned component.)
+itself computes on displaced cells.  For the self-consistent density SCF a second model per
+species maps every atom's descriptors to the coefficients of its s-type Gaussian density
+basis (DensityBasis: the least-squares fit of a converged density, by the library's
+projector products), whose expansion is the SCF's starting density.  The SCF started from
+the predicted guess converges to its own fixed point: the models only save iterations, and
+the plain SCF remains the fallback and the arbiter of their error.  (The paper has no
+learned component.)
 
 This module is argument marshalling and orchestration: descriptors, training, inference and
 the SCF all run in the library's kernels.
@@ -44,17 +48,22 @@ def unpack_occupations(Y, nspin: int) -> np.ndarray:
     return D
 
 
-def hubbard_descriptors(atoms, L, device):
-    """Descriptors (device float [nhub, N_IN]) of the Hubbard atoms, in the order in which
-    the library numbers them (atoms with hub_l >= 0, in input order)."""
+def atom_descriptors(atoms, L, centres, device):
+    """Descriptors (device float [len(centres), N_IN]) of the given atoms' neighbourhoods."""
     import torch
     pos = np.asarray([a.pos for a in atoms], dtype=np.float64)
     sp = np.asarray([SPECIES[a.species] for a in atoms], dtype=np.int32)
-    centres = np.asarray([i for i, a in enumerate(atoms) if a.hub_l >= 0], dtype=np.int32)
+    centres = np.asarray(centres, dtype=np.int32)
     out = torch.empty((len(centres), N_IN), dtype=torch.float32, device=device)
     descriptors(pos, sp, np.asarray(L, dtype=np.float64), centres, out, nspecies=len(SPECIES),
                 rc=RC, nrad=NRAD, eta=ETA)
     return out
+
+
+def hubbard_descriptors(atoms, L, device):
+    """Descriptors (device float [nhub, N_IN]) of the Hubbard atoms, in the order in which
+    the library numbers them (atoms with hub_l >= 0, in input order)."""
+    return atom_descriptors(atoms, L, [i for i, a in enumerate(atoms) if a.hub_l >= 0], device)
 
 
 def scf_solve(wl, prec: int = HUB_F64, D0=None, tol_e_atom: float = 1e-5, tol_D: float = 1e-4,
@@ -160,3 +169,156 @@ class OccupationModel:
 def _ptr(t):
     import ctypes
     return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------------------ density
+DENSITY_WIDTHS = (0.5, 1.0, 2.0)     # bohr: s-type Gaussians per atom
+DENSITY_RC_FACTOR = 3.0              # cutoff = factor * the widest Gaussian
+
+
+class DensityBasis:
+    """Atom-centred s-type Gaussian basis of the electron density on one grid and geometry,
+    held as the projector tables of a separate library handle (three l = 0 channels per
+    atom).  fit: least-squares coefficients of a density (normal equations with the basis
+    Gram matrix; both sides from hub_project); expand: the density of given coefficients
+    (hub_expand), scaled to carry n_elec electrons."""
+
+    def __init__(self, wl, atoms=None, device=None):
+        import torch
+        from types import SimpleNamespace
+        self.dev = device or torch.device("cuda", 0)
+        self.atoms = wl.atoms if atoms is None else atoms
+        K = len(DENSITY_WIDTHS)
+        rc = DENSITY_RC_FACTOR * max(DENSITY_WIDTHS)
+        basis = [SimpleNamespace(pos=np.asarray(a.pos, dtype=np.float64), kb_l=(0,) * K,
+                                 kb_rs=DENSITY_WIDTHS, kb_gamma=(0.0,) * K, kb_rc=rc, hub_l=-1,
+                                 hub_rs=1.0, hub_rc=0.0, hub_U=0.0) for a in self.atoms]
+        self.K = K
+        self.Nd, self.dV = wl.Nd, wl.dV
+        self.hub = Hub(wl.n, wl.L, wl.fd_half_order, prec=HUB_F64)
+        self.hub.set_atoms(basis)
+        nb = self.hub.num_projectors()
+        if nb != K * len(self.atoms):
+            raise RuntimeError("density basis tables do not have K functions per atom")
+        eye = torch.zeros((nb, self.Nd), dtype=torch.float64, device=self.dev)
+        self.hub.expand(np.eye(nb), eye)                 # the basis functions, one per column
+        self.G = self.hub.project(eye)                   # <g_i|g_j>
+        del eye
+
+    def fit(self, rho) -> np.ndarray:
+        """Coefficients (natoms, K) of a device density [Nd]."""
+        b = self.hub.project(rho.reshape(1, -1))[:, 0]
+        return np.linalg.solve(self.G, b).reshape(len(self.atoms), self.K)
+
+    def expand(self, coef, n_elec: float):
+        """Device density [Nd] of the coefficients, scaled to integrate to n_elec."""
+        import torch
+        rho = torch.zeros((1, self.Nd), dtype=torch.float64, device=self.dev)
+        self.hub.expand(np.asarray(coef, dtype=np.float64).reshape(-1, 1), rho)
+        total = float(rho.sum()) * self.dV
+        return (rho[0] * (n_elec / total)).contiguous()
+
+    def close(self):
+        self.hub.close()
+
+
+def density_scf_solve(wl, prec: int = HUB_F64, D0=None, rho0=None, tol_e_atom: float = 1e-5,
+                      tol_D: float = 1e-4, tol_rho: float = 1e-4, max_iter: int = 200, device=None):
+    """Self-consistent density SCF of a workload (uniform starting density unless rho0, a
+    device double [Nd] total density, is given).  Returns iterations, energies, D, the output
+    density (device) and the wall time."""
+    import torch
+    dev = device or torch.device("cuda", 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hub = Hub(wl.n, wl.L, wl.fd_half_order, prec=prec)
+    try:
+        hub.set_veff(torch.tensor(wl.veff, device=dev))
+        hub.set_atoms(wl.atoms)
+        Xs = [torch.tensor(wl.orbitals(s), device=dev).to(hub.dtype).contiguous() for s in range(wl.nspin)]
+        v0s = [torch.tensor(wl.lanczos_start(s), device=dev).to(hub.dtype).contiguous()
+               for s in range(wl.nspin)]
+        p = scf_params(nspin=wl.nspin, ncol=wl.ncol, ld=wl.Nd, degree=wl.degree, max_iter=max_iter,
+                       first_passes=3, lanczos_steps=10, pulay_history=7, natoms=len(wl.atoms),
+                       pulay_beta=0.3, kT=wl.kT if wl.kT > 0 else 0.005, n_elec=wl.n_elec,
+                       tol_e_atom=tol_e_atom, tol_D=tol_D, ladder=1 if prec == HUB_MIXED_BF16 else 0,
+                       ladder_tol=1e-4, density=1, kerker_kappa=0.5, tol_rho=tol_rho, cg_tol=1e-10)
+        hub.scf_begin(p, Xs, v0s, wl.D0 if D0 is None else D0)
+        if rho0 is not None:
+            hub.scf_set_density(rho0)
+        res = hub.scf_run()
+        eig, occ, D = hub.scf_get()
+        rho = torch.empty(wl.Nd, dtype=torch.float64, device=dev)
+        hub.scf_density(rho)
+        torch.cuda.synchronize()
+        return {"iterations": res["iter"], "converged": bool(res["converged"]), "E": res["E"],
+                "E_U": res["E_U"], "D": D, "rho": rho, "seconds": time.perf_counter() - t0}
+    finally:
+        hub.close()
+
+
+class DensityModel:
+    """One MLP per species from an atom's descriptors to its K density coefficients."""
+
+    def __init__(self, hidden: int = 256, layers: int = 3, fp16: bool = True, seed: int = 0):
+        K = len(DENSITY_WIDTHS)
+        self.K = K
+        self.mlp = {sp: MLP(N_IN, hidden, layers, K, fp16=fp16, seed=seed + i)
+                    for i, sp in enumerate(SPECIES)}
+        self._X = {sp: [] for sp in SPECIES}
+        self._T = {sp: [] for sp in SPECIES}
+
+    def add_solution(self, atoms, L, coef):
+        """Descriptors of every atom and its fitted coefficients (natoms, K)."""
+        import torch
+        X = atom_descriptors(atoms, L, range(len(atoms)), torch.device("cuda", 0)).cpu().numpy()
+        coef = np.asarray(coef, dtype=np.float32)
+        for sp in SPECIES:
+            sel = [i for i, a in enumerate(atoms) if a.species == sp]
+            if sel:
+                self._X[sp].append(X[sel])
+                self._T[sp].append(coef[sel])
+
+    def fit(self, steps: int = 1500, lr: float = 2e-3, lr_final: float = 2e-5, batch: int = 256, seed: int = 0):
+        """Adam with a cosine decay per species model; returns the last loss of each."""
+        import torch
+        dev = torch.device("cuda", 0)
+        out = {}
+        for sp, mlp in self.mlp.items():
+            if not self._X[sp]:
+                continue
+            Xh, Th = np.concatenate(self._X[sp]), np.concatenate(self._T[sp])
+            perm = np.random.Generator(np.random.PCG64(seed)).permutation(Xh.shape[0])
+            X = torch.tensor(Xh[perm], device=dev).contiguous()
+            T = torch.tensor(Th[perm], device=dev).contiguous()
+            mlp.fit_normalization(X, T)
+            b = min(batch, X.shape[0])
+            nb = max(1, X.shape[0] // b)
+            loss = None
+            for it in range(steps):
+                j = it % nb
+                xb, tb = X[j * b:(j + 1) * b], T[j * b:(j + 1) * b]
+                lr_t = lr_final + 0.5 * (lr - lr_final) * (1.0 + np.cos(np.pi * it / max(steps - 1, 1)))
+                if it == steps - 1:
+                    loss = mlp.train_step(xb, tb, lr_t)
+                else:
+                    mlp._check(mlp.lib.hub_mlp_train_step(mlp.m, _ptr(xb), _ptr(tb), xb.shape[0],
+                                                          float(lr_t), None), "train_step")
+            out[sp] = loss
+        return out
+
+    def predict(self, atoms, L) -> np.ndarray:
+        """Predicted coefficients (natoms, K)."""
+        import torch
+        dev = torch.device("cuda", 0)
+        X = atom_descriptors(atoms, L, range(len(atoms)), dev)
+        coef = np.zeros((len(atoms), self.K))
+        for sp, mlp in self.mlp.items():
+            sel = [i for i, a in enumerate(atoms) if a.species == sp]
+            if not sel:
+                continue
+            Y = torch.empty((len(sel), self.K), dtype=torch.float32, device=dev)
+            mlp.forward(X[sel].contiguous(), Y)
+            coef[sel] = Y.cpu().numpy()
+        return coef
+
