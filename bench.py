@@ -69,6 +69,9 @@ def parse():
                     help="self-consistent density SCF (FD-Poisson Hartree, exchange, Kerker-"
                          "preconditioned Pulay on rho and D) of the workload in --prec to 1e-5 "
                          "Ha/atom: iterations, time, CG iterations per SCF iteration")
+    ap.add_argument("--md-compare", type=int, default=0, metavar="STEPS",
+                    help="SCF at STEPS steps of a seeded rutile 2x2x3 trajectory in --prec, starting D "
+                         "atomic vs second-order extrapolated, previous orbitals reused: iterations per step")
     ap.add_argument("--scf-compare", action="store_true",
                     help="cold-start SCF to convergence in FP64, FP32 and mixed (BF16 with the "
                          "precision ladder); report time to solution and errors against FP64")
@@ -761,8 +764,26 @@ def run_density_scf(args):
     return 0
 
 
+def run_md_compare(args):
+    """Iterations per MD step with the atomic and the extrapolated starting D."""
+    import workloads as w
+    from paper_2507_23612_gb300.warmstart import trajectory_scf
+    steps = w.rutile_trajectory((2, 2, 3), nsteps=args.md_compare, amplitude=0.1, period=12.0)
+    out = {}
+    for start in ("atomic", "extrapolated"):
+        res = trajectory_scf(steps, PREC[args.prec], start=start)
+        out[start] = {"iterations": [r["iterations"] for r in res],
+                      "seconds": [round(r["seconds"], 3) for r in res],
+                      "E": [r["E"] for r in res], "alpha_beta": [r["alpha_beta"] for r in res]}
+    print(json.dumps({"md_compare": out, "prec": args.prec, "steps": args.md_compare,
+                      "trajectory": "rutile 2x2x3, sinusoidal displacements (0.1 bohr, period 12 steps)"}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.md_compare:
+        return run_md_compare(args)
     if args.forces:
         return run_forces(args)
     if args.stress:

@@ -22,7 +22,7 @@ import time
 
 import numpy as np
 
-from .binding import HUB_F64, HUB_MIXED_BF16, MLP, Hub, descriptors, scf_params
+from .binding import HUB_F64, HUB_MIXED_BF16, MLP, Hub, descriptors, extrapolate_occupations, scf_params
 
 SPECIES = {"Ti": 0, "O": 1}
 NRAD = 16
@@ -321,4 +321,32 @@ class DensityModel:
             mlp.forward(X[sel].contiguous(), Y)
             coef[sel] = Y.cpu().numpy()
         return coef
+
+
+# ------------------------------------------------------------------------------ MD steps
+def trajectory_scf(steps, prec: int = HUB_F64, start: str = "extrapolated", reuse_orbitals: bool = True,
+                   tol_e_atom: float = 1e-5, tol_D: float = 1e-4):
+    """SCF at every step of a trajectory (a list of workloads on one grid).  The starting D of
+    a step is the atomic guess (start="atomic") or the second-order extrapolation of the
+    previous steps' converged D (start="extrapolated", hub_extrapolate_occupations with
+    coefficients fitted to the positions; Sec. II.B).  With reuse_orbitals the previous
+    step's converged orbitals start the next SCF.  Returns per step: iterations, E, the
+    extrapolation coefficients and the wall time."""
+    D_hist, R_hist, X, out = [], [], None, []
+    for wl in steps:
+        R = np.array([a.pos for a in wl.atoms])
+        coef = (0.0, 0.0)
+        if start == "extrapolated" and D_hist:
+            h = min(3, len(D_hist))
+            D0, coef = extrapolate_occupations(D_hist[-h:], wl.D0, R_hist[-h:] + [R])
+        else:
+            D0 = wl.D0
+        r = scf_solve(wl, prec, D0=D0, tol_e_atom=tol_e_atom, tol_D=tol_D,
+                      X0=X if (reuse_orbitals and X is not None) else None, keep_orbitals=True)
+        X = r["X"]
+        D_hist.append(r["D"])
+        R_hist.append(R)
+        out.append({"iterations": r["iterations"], "converged": r["converged"], "E": r["E"],
+                    "alpha_beta": coef, "seconds": r["seconds"]})
+    return out
 

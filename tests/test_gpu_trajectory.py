@@ -1,0 +1,33 @@
+"""SCF along a seeded MD trajectory (Sec. II.B, last paragraph): starting D from the atomic
+guess or from the second-order extrapolation of the previous steps, the previous orbitals
+reused.  Both reach the same fixed point at every step; the iteration counts are reported.
+
+Marked gpu_pending: this code has not run on a GPU yet; the marker moves to gpu after its
+first GPU run."""
+import pytest
+
+import workloads as w
+
+pytestmark = pytest.mark.gpu_pending
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2507_23612_gb300 import HUB_F32  # noqa: E402
+from paper_2507_23612_gb300.warmstart import trajectory_scf  # noqa: E402
+
+
+def test_extrapolated_and_atomic_starts_reach_the_same_fixed_points():
+    steps = w.rutile_trajectory((1, 1, 2), nsteps=5, amplitude=0.1, period=12.0)
+    atomic = trajectory_scf(steps, HUB_F32, start="atomic", tol_e_atom=1e-6)
+    extra = trajectory_scf(steps, HUB_F32, start="extrapolated", tol_e_atom=1e-6)
+    print({"atomic": [s["iterations"] for s in atomic], "extrapolated": [s["iterations"] for s in extra],
+           "alpha_beta": [s["alpha_beta"] for s in extra]})
+    nat = len(steps[0].atoms)
+    for a, e in zip(atomic, extra):
+        assert a["converged"] and e["converged"]
+        assert abs(a["E"] - e["E"]) / nat < 1e-5
+    # from the fourth step on the fit sees two position steps of a sinusoid of period 12:
+    # alpha = 2 cos(2 pi / 12), beta = -1
+    al, be = extra[3]["alpha_beta"]
+    assert abs(al - 3 ** 0.5) < 1e-6 and abs(be + 1.0) < 1e-6

@@ -72,3 +72,14 @@ def test_library_extrapolation_matches_the_oracle(lib, nhist):
     D_next, (al2, be2) = extrapolate_occupations(D_hist, Da, R)
     assert abs(al2 - al) < 1e-12 and abs(be2 - be) < 1e-12
     np.testing.assert_allclose(D_next, ref, atol=1e-13)
+
+
+def test_seeded_md_trajectory_is_a_sinusoid():
+    # every coordinate follows a sinusoid of period 12 steps, so the two-step fit recovers
+    # its recurrence x(t+1) = 2 cos(2 pi / 12) x(t) - x(t-1) about the rest position
+    import workloads as w
+    steps = w.rutile_trajectory((1, 1, 2), nsteps=5)
+    R = [np.array([a.pos for a in s.atoms]) for s in steps]
+    al, be = o.alfe_coefficients(R[:4])
+    assert abs(al - 2 * np.cos(2 * np.pi / 12)) < 1e-9 and abs(be + 1.0) < 1e-9
+    assert all(s.n == steps[0].n and s.ncol == steps[0].ncol for s in steps)

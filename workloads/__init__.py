@@ -8,6 +8,7 @@ exactly the same inputs without sharing any computation.
 """
 from .synthetic import (  # noqa: F401
     HARTREE_EV, BOHR_PER_ANGSTROM, Atom, Workload,
-    tiny, rutile, rutile_snapshot, anatase_cell, rutile_cell, snapshot_batch, small_test_system,
+    tiny, rutile, rutile_snapshot, rutile_trajectory, anatase_cell, rutile_cell, snapshot_batch,
+    small_test_system,
     gaussian_potential, random_orbitals, displaced, scaled_grid_for,
 )

@@ -284,6 +284,31 @@ def rutile_snapshot(reps=(2, 2, 3), sigma: float = 0.1, seed: int = 0, h_target:
                     seed_orbitals=70_000 + seed, seed_lanczos=80_000 + seed)
 
 
+def rutile_trajectory(reps=(1, 1, 2), nsteps: int = 6, amplitude: float = 0.1, period: float = 12.0,
+                      seed: int = 0, **kw) -> list:
+    """A smooth seeded trajectory of a rutile-shaped supercell: atom i at step t sits at
+    R_i + a_i sin(2 pi t / period + phi_i), a_i ~ N(0, amplitude) per component and phi_i
+    uniform, one Workload per step on the same grid (the local potential follows the atoms;
+    the orbital and Lanczos seeds stay fixed).  Keyword arguments go to rutile_snapshot."""
+    base = rutile_snapshot(reps, 0.0, seed, **kw)
+    g = _rng(90_000 + seed)
+    R0 = np.array([a.pos for a in base.atoms])
+    amp = amplitude * g.standard_normal(R0.shape)
+    phase = g.uniform(0.0, 2 * np.pi, (len(R0), 1))
+    out = []
+    for t in range(nsteps):
+        R = R0 + amp * np.sin(2 * np.pi * t / period + phase)
+        atoms = [Atom(a.species, R[i].copy(), kb_l=a.kb_l, kb_rs=a.kb_rs, kb_gamma=a.kb_gamma,
+                      kb_rc=a.kb_rc, hub_l=a.hub_l, hub_rs=a.hub_rs, hub_rc=a.hub_rc, hub_U=a.hub_U)
+                 for i, a in enumerate(base.atoms)]
+        veff = _tio2_potential(base.n, base.L, atoms)
+        out.append(Workload(f"{base.name}-md{t}", base.n, base.L, veff, atoms, ncol=base.ncol,
+                            degree=base.degree, nspin=base.nspin, n_elec=base.n_elec, kT=base.kT,
+                            D0=base.D0.copy(), seed_orbitals=base.seed_orbitals,
+                            seed_lanczos=base.seed_lanczos))
+    return out
+
+
 def small_test_system(n=(20, 24, 28), L=None, ncol=37, natoms=3, nspin=1, seed=7,
                       kpt=(0.0, 0.0, 0.0), hub_rc=4.0, kb_rc=2.5) -> Workload:
     """A ragged, anisotropic grid with a few atoms: sizes that span several kernel tiles
