@@ -292,6 +292,7 @@ int hub_set_bf16_terms(hub_t h, int terms) {
 }
 
 int hub_apply_H(hub_t h, int spin, const void* X, void* Y, int ncol, int ld) {
+    hub::NvtxRange nvtx_("hub_apply_H");
     int rc = check_block(h, spin, X, ncol, ld);
     if (rc) return rc;
     if (ncol > 0 && !Y) return fail(h, HUB_EINVAL, "NULL output");
@@ -301,6 +302,7 @@ int hub_apply_H(hub_t h, int spin, const void* X, void* Y, int ncol, int ld) {
 
 int hub_chefsi_filter(hub_t h, int spin, void* X, int ncol, int ld, int degree, double a, double b,
                       double a_low, void* work) {
+    hub::NvtxRange nvtx_("hub_chefsi_filter");
     int rc = check_block(h, spin, X, ncol, ld);
     if (rc) return rc;
     if (degree < 1) return fail(h, HUB_EINVAL, "degree must be >= 1");
@@ -407,6 +409,7 @@ static int rr_two_spins(hub_t h, void* const* X, int n, int ld, double* const* e
 }  // namespace hub
 
 int hub_rayleigh_ritz(hub_t h, int spin, void* X, int ncol, int ld, double* eig_host, void* work) {
+    hub::NvtxRange nvtx_("hub_rayleigh_ritz");
     int rc = check_block(h, spin, X, ncol, ld);
     if (rc) return rc;
     if (h->cplx) return fail(h, HUB_EINVAL, "Rayleigh-Ritz supports real orbitals only");
@@ -442,6 +445,7 @@ int hub_gram(hub_t h, const void* A, int ncol_a, const void* B, int ncol_b, int 
 
 int hub_occupation(hub_t h, int spin, const void* X, int ncol, int ld, const double* f_host,
                    double kweight, double* D_re_out, double* D_im_out, double* EU_out) {
+    hub::NvtxRange nvtx_("hub_occupation");
     int rc = check_block(h, spin, X, ncol, ld);
     if (rc) return rc;
     const int nh = h->proj.nhub;
@@ -520,6 +524,7 @@ int hub_expand(hub_t h, const double* W_host, int ncol, void* Y, int ld, double 
 
 int hub_hubbard_forces(hub_t h, int spin, const void* X, int ncol, int ld, const double* f_host,
                        double kweight, double* F_host, void* work) {
+    hub::NvtxRange nvtx_("hub_hubbard_forces");
     int rc = check_block(h, spin, X, ncol, ld);
     if (rc) return rc;
     if (!F_host) return fail(h, HUB_EINVAL, "NULL force output");
@@ -560,6 +565,7 @@ int hub_hubbard_forces(hub_t h, int spin, const void* X, int ncol, int ld, const
 
 int hub_hubbard_stress(hub_t h, int spin, const void* X, int ncol, int ld, const double* f_host,
                        double kweight, double* sigma_host, void* work) {
+    hub::NvtxRange nvtx_("hub_hubbard_stress");
     int rc = check_block(h, spin, X, ncol, ld);
     if (rc) return rc;
     if (!sigma_host) return fail(h, HUB_EINVAL, "NULL stress output");
@@ -1019,6 +1025,7 @@ int hub_scf_density(hub_t h, double* rho_dev) {
 }
 
 int hub_scf_iterate(hub_t h, hub_scf_result* res) {
+    hub::NvtxRange nvtx_("hub_scf_iterate");
     if (!h || !h->scf) return fail(h, HUB_EINVAL, "hub_scf_begin has not been called");
     ScfState& st = *h->scf;
     const hub_scf_params& p = st.p;

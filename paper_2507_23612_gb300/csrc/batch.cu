@@ -270,6 +270,7 @@ int hub_autotune(hub_t h, int spin, const void* X, int ncol, int ld, int* varian
 int hub_batch_filter(int nsys, const hub_t* sys, const int* spin, void* const* X, const int* ncol,
                      const int* ld, int degree, const double* a, const double* b, const double* a_low,
                      void* cuda_stream) {
+    hub::NvtxRange nvtx_("hub_batch_filter");
     if (nsys < 1 || !sys || !spin || !X || !ncol || !ld || !a || !b || !a_low || degree < 1) return HUB_EINVAL;
     int dev = -1;
     BATCH_TRY(cudaGetDevice(&dev));

@@ -429,6 +429,7 @@ int hub_density(hub_t h, const void* X, int ncol, int ld, const double* f_host, 
 
 int hub_hartree(hub_t h, const double* rho_dev, double* V_dev, double tol, int max_iter,
                 int* iters_out, double* EH_out) {
+    hub::NvtxRange nvtx_("hub_hartree");
     if (!h) return HUB_EINVAL;
     if (!rho_dev || !V_dev) return fail(h, HUB_EINVAL, "NULL density or potential");
     if (!(tol > 0.0) || max_iter < 1) return fail(h, HUB_EINVAL, "tol must be > 0 and max_iter >= 1");
@@ -493,6 +494,7 @@ int hub_lda_exchange(hub_t h, int nchan, const double* rho0, const double* rho1,
 
 int hub_kerker(hub_t h, const double* r_dev, double* z_dev, double kappa, double tol, int max_iter,
                int* iters_out) {
+    hub::NvtxRange nvtx_("hub_kerker");
     if (!h) return HUB_EINVAL;
     if (!r_dev || !z_dev) return fail(h, HUB_EINVAL, "NULL residual or output");
     if (!(kappa >= 0.0) || !(tol > 0.0) || max_iter < 1) return fail(h, HUB_EINVAL, "bad kappa, tol or max_iter");

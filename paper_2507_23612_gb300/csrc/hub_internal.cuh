@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -178,6 +179,15 @@ struct ProfScope {
     }
 };
 int ensure(hub_t h, void** p, size_t* have, size_t need);
+
+// An NVTX range around one ABI call (visible to Nsight tools; without a tool attached the
+// calls return at once)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // flags
 enum { FLAG_NOTSPD = 0, FLAG_NONFINITE = 1, FLAG_TIMEOUT = 2, FLAG_NOCONV = 3 };
