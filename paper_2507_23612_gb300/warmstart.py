@@ -350,3 +350,25 @@ def trajectory_scf(steps, prec: int = HUB_F64, start: str = "extrapolated", reus
                     "alpha_beta": coef, "seconds": r["seconds"]})
     return out
 
+
+
+# ------------------------------------------------------------------------------ checkpoint
+def save_scf_checkpoint(path, Xs, D, meta=None):
+    """Orbital blocks (one [ncol, Nd] tensor or array per spin), the occupation matrices and
+    a small metadata dict (iteration, energy, seeds) in one .npz file."""
+    arrays = {f"X{s}": (x.detach().cpu().numpy() if hasattr(x, "detach") else np.asarray(x))
+              for s, x in enumerate(Xs)}
+    np.savez(path, D=np.asarray(D, dtype=np.float64), nspin=len(Xs),
+             meta=np.array(repr(dict(meta or {}))), **arrays)
+
+
+def load_scf_checkpoint(path, device=None, dtype=None):
+    """(Xs as device tensors, D, meta) of save_scf_checkpoint; with device None the blocks
+    stay numpy arrays."""
+    import ast
+    z = np.load(path, allow_pickle=False)
+    Xs = [z[f"X{s}"] for s in range(int(z["nspin"]))]
+    if device is not None:
+        import torch
+        Xs = [torch.tensor(x, device=device, dtype=dtype).contiguous() for x in Xs]
+    return Xs, z["D"], ast.literal_eval(str(z["meta"]))

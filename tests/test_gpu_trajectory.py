@@ -31,3 +31,17 @@ def test_extrapolated_and_atomic_starts_reach_the_same_fixed_points():
     # alpha = 2 cos(2 pi / 12), beta = -1
     al, be = extra[3]["alpha_beta"]
     assert abs(al - 3 ** 0.5) < 1e-6 and abs(be + 1.0) < 1e-6
+
+
+def test_resume_from_a_checkpoint_reaches_the_same_fixed_point(tmp_path):
+    from paper_2507_23612_gb300.warmstart import load_scf_checkpoint, save_scf_checkpoint, scf_solve
+    wl = w.rutile_snapshot((1, 1, 2), 0.1, seed=5)
+    full = scf_solve(wl, HUB_F32, tol_e_atom=1e-6)
+    part = scf_solve(wl, HUB_F32, tol_e_atom=1e-6, max_iter=4, keep_orbitals=True)
+    assert not part["converged"]
+    save_scf_checkpoint(tmp_path / "scf.npz", part["X"], part["D"], {"iter": part["iterations"]})
+    Xs, D, meta = load_scf_checkpoint(tmp_path / "scf.npz", device="cuda", dtype=torch.float32)
+    resumed = scf_solve(wl, HUB_F32, D0=D, X0=Xs, tol_e_atom=1e-6)
+    print({"full": full["iterations"], "resumed": meta["iter"] + resumed["iterations"]})
+    assert full["converged"] and resumed["converged"]
+    assert abs(full["E"] - resumed["E"]) / len(wl.atoms) < 1e-6

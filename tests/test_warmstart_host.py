@@ -34,3 +34,14 @@ def test_rutile_snapshots_are_seeded_and_displaced():
     assert all(x.kb_gamma == gam[x.species] for x in a.atoms)
     big = w.rutile_snapshot((3, 3, 4))
     assert big.n == (132, 132, 112) and big.ncol == 1044 and len(big.atoms) == 216
+
+
+def test_scf_checkpoint_roundtrip(tmp_path):
+    from paper_2507_23612_gb300.warmstart import load_scf_checkpoint, save_scf_checkpoint
+    rng = np.random.default_rng(0)
+    Xs = [rng.standard_normal((4, 30)) for _ in range(2)]
+    D = rng.standard_normal((2, 3, 5, 5))
+    save_scf_checkpoint(tmp_path / "c.npz", Xs, D, {"iter": 7, "E": -1.25, "seed": 3})
+    X2, D2, meta = load_scf_checkpoint(tmp_path / "c.npz")
+    assert len(X2) == 2 and all(np.array_equal(a, b) for a, b in zip(Xs, X2))
+    assert np.array_equal(D, D2) and meta == {"iter": 7, "E": -1.25, "seed": 3}
