@@ -690,3 +690,26 @@ def extrapolate_occupations(D_hist, D_atomic, alpha: float, beta: float):
     if len(d) >= 3:
         out += beta * (d[-2] - d[-3])
     return Da + out
+
+
+def cutoff_for_threshold(l: int, rs: float, tau: float) -> float:
+    """The radius beyond which the radial function N r^l exp(-r^2 / (2 rs^2)) stays below the
+    value threshold tau (Sec. II.B: the radial orbitals are truncated where their value falls
+    below a threshold).  The function rises to its maximum at r = rs sqrt(l) and decreases
+    after it, so the answer is the root of N r^l exp(-r^2/(2 rs^2)) = tau beyond the
+    maximum, found by bisection; 0 when tau exceeds the maximum."""
+    N = radial_norm(l, rs)
+    f = lambda r: N * r ** l * np.exp(-r * r / (2.0 * rs * rs))      # noqa: E731
+    r_max = rs * sqrt(l)
+    if f(r_max) <= tau:
+        return 0.0
+    lo, hi = r_max, r_max + rs
+    while f(hi) > tau:
+        hi += rs
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if f(mid) > tau:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
