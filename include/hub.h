@@ -187,6 +187,13 @@ int hub_gram_noalloc(const void* A, int ncol_a, const void* B, int ncol_b, long 
 int hub_occupation(hub_t h, int spin, const void* X, int ncol, int ld, const double* f_host,
                    double kweight, double* D_re_out, double* D_im_out, double* EU_out);
 
+/* Cutoff radius of the value-threshold truncation (Sec. II.B: a radial orbital is cut where
+ * its value falls below a threshold): for R(r) = N r^l exp(-r^2 / (2 rs^2)) (N normalising
+ * int R^2 r^2 dr to 1) the radius beyond which R < tau, i.e. the root beyond the maximum at
+ * r = rs sqrt(l); 0 when tau exceeds the maximum.  Host arithmetic, no handle.
+ * Errors: HUB_EINVAL (l outside 0..2, rs <= 0, tau <= 0, NULL output). */
+int hub_cutoff_radius(int l, double rs, double tau, double* rc_out);
+
 /* Number of projector rows of the handle's tables (KB-type rows and Hubbard rows, atom by
  * atom in the order of hub_set_atoms_projectors; per atom its KB channels, then its Hubbard
  * shell; m = -l..l within a channel). */

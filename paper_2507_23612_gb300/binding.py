@@ -72,6 +72,7 @@ _SIGS = {
     "hub_expand": [_P, _PD, _I, _P, _I, _D],
     "hub_scf_forces": [_P, _PD, _PD],
     "hub_extrapolate_occupations": [_I, _I, _PD, _PD, _I, _PD, _PD, _PD],
+    "hub_cutoff_radius": [_I, _D, _D, _PD],
     "hub_density": [_P, _P, _I, _I, _PD, _D, _P],
     "hub_hartree": [_P, _P, _P, _D, _I, _PI, _PD],
     "hub_lda_exchange": [_P, _I, _P, _P, _P, _P, _PD],
@@ -453,6 +454,16 @@ class Hub:
         self._check(self.lib.hub_kerker(self.h, _tptr(r), _tptr(z), kappa, tol, max_iter, C.byref(it)),
                     "hub_kerker")
         return it.value
+
+
+def cutoff_radius(l: int, rs: float, tau: float) -> float:
+    """Radius beyond which N r^l exp(-r^2/(2 rs^2)) stays below tau (hub_cutoff_radius)."""
+    lib = load_library()
+    rc = C.c_double()
+    rc_ = lib.hub_cutoff_radius(int(l), float(rs), float(tau), C.byref(rc))
+    if rc_:
+        raise HubError(rc_, "hub_cutoff_radius: bad arguments")
+    return rc.value
 
 
 def extrapolate_occupations(D_hist, D_atomic, R_hist):

@@ -309,3 +309,21 @@ extern "C" int hub_extrapolate_occupations(int n, int nhist, const double* D_his
     }
     return HUB_OK;
 }
+
+// ---------------------------------------------------------------------------- truncation
+extern "C" int hub_cutoff_radius(int l, double rs, double tau, double* rc_out) {
+    if (l < 0 || l > 2 || !(rs > 0.0) || !(tau > 0.0) || !rc_out) return HUB_EINVAL;
+    const double N = std::sqrt(2.0 / (std::tgamma(l + 1.5) * std::pow(rs, 2 * l + 3)));
+    auto R = [&](double r) { return N * std::pow(r, l) * std::exp(-r * r / (2.0 * rs * rs)); };
+    const double rmax = rs * std::sqrt((double)l);       // R rises to here, falls after
+    if (R(rmax) <= tau) { *rc_out = 0.0; return HUB_OK; }
+    double lo = rmax, hi = rmax + rs;
+    for (int k = 0; k < 10000 && R(hi) > tau; ++k) hi += rs;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (R(mid) > tau) lo = mid; else hi = mid;
+    }
+    *rc_out = 0.5 * (lo + hi);
+    return HUB_OK;
+}
+

@@ -3,6 +3,7 @@ convergence of E_U with the threshold (the paper's truncation study, on a small 
 cell): the cutoff radius of an s function in closed form, the defining equation for l > 0,
 the library's host implementation against the oracle, and E_U(tau) approaching its
 converged value as tau decreases."""
+import ctypes as C
 from math import log, sqrt
 
 import numpy as np
@@ -30,6 +31,21 @@ def test_cutoff_solves_the_threshold_equation_beyond_the_maximum(l, rs, tau):
 
 def test_threshold_above_the_maximum_gives_no_support():
     assert o.cutoff_for_threshold(2, 1.0, 10.0) == 0.0
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2507_23612_gb300 import build as b
+    b.build()
+    from paper_2507_23612_gb300 import binding
+    return binding.load_library()
+
+
+@pytest.mark.parametrize("l,rs,tau", [(0, 0.8, 1e-3), (1, 0.8, 1e-2), (2, 1.0, 5e-3), (2, 1.0, 1e-8), (2, 1.0, 10.0)])
+def test_library_cutoff_matches_the_oracle(lib, l, rs, tau):
+    rc = C.c_double()
+    assert lib.hub_cutoff_radius(l, C.c_double(rs), C.c_double(tau), C.byref(rc)) == 0
+    assert abs(rc.value - o.cutoff_for_threshold(l, rs, tau)) < 1e-10
 
 
 def test_hubbard_energy_converges_with_the_threshold():
