@@ -280,9 +280,9 @@ DENSITY_WIDTHS = (0.5, 1.0, 2.0)     # bohr: s-type Gaussians per atom
 def density_basis_atoms(atoms, widths=DENSITY_WIDTHS, rc_factor: float = 3.0):
     """The density basis as atoms whose only functions are s-type Gaussians
     N exp(-r^2 / (2 rs^2)) with the given widths, cut off at rc_factor * max(widths), summed
-    over periodic images like every atom-centred function.  Reading: the survey asks for
-    per-atom Gaussian density coefficients without fixing the basis; three widths resolve the
-    core, the bond and the tail of a TiO2 atom's density."""
+    over periodic images like every atom-centred function.  Reading: the paper has no learned
+    component, so nothing fixes this basis of the warm start's density targets; three widths
+    resolve the core, the bond and the tail of a TiO2 atom's density."""
     from workloads import Atom
     rc = rc_factor * max(widths)
     return [Atom(a.species, np.asarray(a.pos, dtype=np.float64), kb_l=(0,) * len(widths),
