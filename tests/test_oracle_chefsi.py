@@ -138,3 +138,13 @@ def test_scf_chefsi_matches_dense_scf():
     np.testing.assert_allclose(r1["D"], r2["D"], atol=1e-7)
     # a fixed point: D_out(D_in) = D_in
     assert np.max(np.abs(r1["D"] - r1["D_in"])) < 1e-8
+
+
+def test_fermi_entropy_closed_forms():
+    # S = -sum f ln f + (1 - f) ln(1 - f): ln 2 per half-filled state, 0 for f in {0, 1}, and
+    # the derivative dS/df = ln((1 - f) / f) (the Fermi-Dirac stationarity condition)
+    assert abs(o.fermi_entropy([0.5, 0.5, 0.5]) - 3 * np.log(2.0)) < 1e-14
+    assert abs(o.fermi_entropy([0.0, 1.0, 1.0, 0.0])) < 1e-12
+    f, eps = 0.3, 1e-6
+    d = (o.fermi_entropy([f + eps]) - o.fermi_entropy([f - eps])) / (2 * eps)
+    assert abs(d - np.log((1 - f) / f)) < 1e-8
