@@ -71,7 +71,8 @@ def parse():
                          "Ha/atom: iterations, time, CG iterations per SCF iteration")
     ap.add_argument("--md-compare", type=int, default=0, metavar="STEPS",
                     help="SCF at STEPS steps of a seeded rutile 2x2x3 trajectory in --prec, starting D "
-                         "atomic vs second-order extrapolated, previous orbitals reused: iterations per step")
+                         "atomic vs second-order extrapolated vs the occupation model (trained on "
+                         "--warm-train displaced cells), previous orbitals reused: iterations per step")
     ap.add_argument("--scf-compare", action="store_true",
                     help="cold-start SCF to convergence in FP64, FP32 and mixed (BF16 with the "
                          "precision ladder); report time to solution and errors against FP64")
@@ -768,10 +769,17 @@ def run_md_compare(args):
     """Iterations per MD step with the atomic and the extrapolated starting D."""
     import workloads as w
     from paper_2507_23612_gb300.warmstart import trajectory_scf
+    from paper_2507_23612_gb300.warmstart import OccupationModel, scf_solve
     steps = w.rutile_trajectory((2, 2, 3), nsteps=args.md_compare, amplitude=0.1, period=12.0)
+    # the occupation model, trained on SCF solutions of displaced cells off the trajectory
+    model = OccupationModel(nspin=steps[0].nspin, seed=0)
+    for i in range(args.warm_train):
+        snap = w.rutile_snapshot((2, 2, 3), 0.1, seed=500 + i)
+        model.add_solution(snap.atoms, snap.L, scf_solve(snap, PREC[args.prec])["D"])
+    model.fit(steps=1500)
     out = {}
-    for start in ("atomic", "extrapolated"):
-        res = trajectory_scf(steps, PREC[args.prec], start=start)
+    for start in ("atomic", "extrapolated", "mlp"):
+        res = trajectory_scf(steps, PREC[args.prec], start=start, model=model)
         out[start] = {"iterations": [r["iterations"] for r in res],
                       "seconds": [round(r["seconds"], 3) for r in res],
                       "E": [r["E"] for r in res], "alpha_beta": [r["alpha_beta"] for r in res]}

@@ -325,13 +325,16 @@ class DensityModel:
 
 # ------------------------------------------------------------------------------ MD steps
 def trajectory_scf(steps, prec: int = HUB_F64, start: str = "extrapolated", reuse_orbitals: bool = True,
-                   tol_e_atom: float = 1e-5, tol_D: float = 1e-4):
+                   tol_e_atom: float = 1e-5, tol_D: float = 1e-4, model=None):
     """SCF at every step of a trajectory (a list of workloads on one grid).  The starting D of
-    a step is the atomic guess (start="atomic") or the second-order extrapolation of the
+    a step is the atomic guess (start="atomic"), the second-order extrapolation of the
     previous steps' converged D (start="extrapolated", hub_extrapolate_occupations with
-    coefficients fitted to the positions; Sec. II.B).  With reuse_orbitals the previous
-    step's converged orbitals start the next SCF.  Returns per step: iterations, E, the
+    coefficients fitted to the positions; Sec. II.B), or the prediction of a trained
+    OccupationModel (start="mlp", model=...).  With reuse_orbitals the previous step's
+    converged orbitals start the next SCF.  Returns per step: iterations, E, the
     extrapolation coefficients and the wall time."""
+    if start not in ("atomic", "extrapolated", "mlp") or (start == "mlp" and model is None):
+        raise ValueError("start must be atomic, extrapolated or mlp (with a model)")
     D_hist, R_hist, X, out = [], [], None, []
     for wl in steps:
         R = np.array([a.pos for a in wl.atoms])
@@ -339,6 +342,8 @@ def trajectory_scf(steps, prec: int = HUB_F64, start: str = "extrapolated", reus
         if start == "extrapolated" and D_hist:
             h = min(3, len(D_hist))
             D0, coef = extrapolate_occupations(D_hist[-h:], wl.D0, R_hist[-h:] + [R])
+        elif start == "mlp":
+            D0 = model.predict(wl.atoms, wl.L)
         else:
             D0 = wl.D0
         r = scf_solve(wl, prec, D0=D0, tol_e_atom=tol_e_atom, tol_D=tol_D,
