@@ -112,6 +112,10 @@ def batch_filter(hubs, spins, Xs, degree: int, a, b, a_low, stream=None):
     import torch
     lib = load_library()
     n = len(hubs)
+    if len(Xs) != n:
+        raise ValueError("batch_filter: one block per system")
+    for hb, x in zip(hubs, Xs):
+        hb._blk(x, "batch_filter X")
     st = stream if stream is not None else torch.cuda.current_stream()
     hs = (C.c_void_p * n)(*[hb.h.value for hb in hubs])
     xs = (C.c_void_p * n)(*[x.data_ptr() for x in Xs])
@@ -194,6 +198,23 @@ class Hub:
             msg = self.lib.hub_last_error(self.h)
             raise HubError(rc, f"{what}: {msg.decode() if msg else ''}")
 
+    def _blk(self, X, what):
+        """A block argument: a contiguous CUDA tensor [ncol, ld] of the handle's element type
+        with ld >= Nd (a wrong element size would make the kernels read past the tensor)."""
+        if X.dtype != self.dtype:
+            raise ValueError(f"{what}: expected {self.dtype}, got {X.dtype}")
+        if X.dim() != 2 or (X.shape[0] > 0 and X.shape[1] < self.Nd):
+            raise ValueError(f"{what}: expected a [ncol, ld >= {self.Nd}] block, got {tuple(X.shape)}")
+        return X.shape
+
+    def _vec(self, t, dtype, what, n=None):
+        """A vector argument: a contiguous CUDA tensor of dtype with at least n (default Nd)
+        elements."""
+        if t.dtype != dtype:
+            raise ValueError(f"{what}: expected {dtype}, got {t.dtype}")
+        if t.numel() < (self.Nd if n is None else n):
+            raise ValueError(f"{what}: expected at least {self.Nd if n is None else n} elements")
+
     @property
     def dtype(self):
         import torch
@@ -217,6 +238,8 @@ class Hub:
         self._check(self.lib.hub_set_bf16_terms(self.h, int(terms)), "hub_set_bf16_terms")
 
     def set_veff(self, veff):
+        import torch
+        self._vec(veff, torch.float64, "set_veff")
         self._check(self.lib.hub_set_veff(self.h, _tptr(veff)), "hub_set_veff")
 
     def set_atoms(self, atoms):
@@ -251,16 +274,21 @@ class Hub:
 
     # ------------------------------------------------------------------ hot path
     def apply_H(self, spin: int, X, Y):
-        ncol, ld = X.shape
+        ncol, ld = self._blk(X, "apply_H X")
+        self._blk(Y, "apply_H Y")
         self._check(self.lib.hub_apply_H(self.h, spin, _tptr(X), _tptr(Y), ncol, ld), "hub_apply_H")
 
     def chefsi_filter(self, spin: int, X, degree: int, a: float, b: float, a_low: float, work=None):
-        ncol, ld = X.shape
+        ncol, ld = self._blk(X, "chefsi_filter X")
+        if work is not None:
+            self._vec(work, self.dtype, "chefsi_filter work", ld * ncol)
         self._check(self.lib.hub_chefsi_filter(self.h, spin, _tptr(X), ncol, ld, degree, a, b, a_low,
                                                _tptr(work)), "hub_chefsi_filter")
 
     def rayleigh_ritz(self, spin: int, X, work=None) -> np.ndarray:
-        ncol, ld = X.shape
+        ncol, ld = self._blk(X, "rayleigh_ritz X")
+        if work is not None:
+            self._vec(work, self.dtype, "rayleigh_ritz work", ld * ncol)
         eig = np.zeros(ncol)
         self._check(self.lib.hub_rayleigh_ritz(self.h, spin, _tptr(X), ncol, ld, _dptr(eig),
                                                _tptr(work)), "hub_rayleigh_ritz")
@@ -276,7 +304,7 @@ class Hub:
                     "hub_gram")
 
     def occupation(self, spin: int, X, f, kweight: float = 1.0):
-        ncol, ld = X.shape
+        ncol, ld = self._blk(X, "occupation X")
         f = np.ascontiguousarray(f, dtype=np.float64)
         Dr = np.zeros((max(self.nhub, 1), 5, 5))
         Di = np.zeros_like(Dr)
@@ -287,7 +315,9 @@ class Hub:
 
     def hubbard_forces(self, spin: int, X, f, kweight: float = 1.0, work=None) -> np.ndarray:
         """Hubbard forces (natoms, 3) of one (spin, k) block with the D last set for `spin`."""
-        ncol, ld = X.shape
+        ncol, ld = self._blk(X, "hubbard_forces X")
+        if work is not None:
+            self._vec(work, self.dtype, "hubbard_forces work", ld * ncol)
         f = np.ascontiguousarray(f, dtype=np.float64)
         F = np.zeros((max(self.natoms, 1), 3))
         self._check(self.lib.hub_hubbard_forces(self.h, spin, _tptr(X), ncol, ld, _dptr(f), kweight,
@@ -296,7 +326,9 @@ class Hub:
 
     def hubbard_stress(self, spin: int, X, f, kweight: float = 1.0, work=None) -> np.ndarray:
         """Hubbard stress (3, 3), Ha/bohr^3, of one (spin, k) block with the D last set for `spin`."""
-        ncol, ld = X.shape
+        ncol, ld = self._blk(X, "hubbard_stress X")
+        if work is not None:
+            self._vec(work, self.dtype, "hubbard_stress work", ld * ncol)
         f = np.ascontiguousarray(f, dtype=np.float64)
         sig = np.zeros(9)
         self._check(self.lib.hub_hubbard_stress(self.h, spin, _tptr(X), ncol, ld, _dptr(f), kweight,
@@ -304,13 +336,14 @@ class Hub:
         return sig.reshape(3, 3)
 
     def lanczos_bound(self, spin: int, steps: int, v0):
+        self._vec(v0, self.dtype, "lanczos_bound v0")
         lo, up = C.c_double(), C.c_double()
         self._check(self.lib.hub_lanczos_bound(self.h, spin, steps, _tptr(v0), C.byref(lo), C.byref(up)),
                     "hub_lanczos_bound")
         return lo.value, up.value
 
     def autotune(self, spin: int, X) -> int:
-        ncol, ld = X.shape
+        ncol, ld = self._blk(X, "autotune X")
         v = C.c_int()
         self._check(self.lib.hub_autotune(self.h, spin, _tptr(X), ncol, ld, C.byref(v)), "hub_autotune")
         return v.value
@@ -350,6 +383,10 @@ class Hub:
 
     # ------------------------------------------------------------------ SCF driver
     def scf_begin(self, params: scf_params, Xs, v0s, D0):
+        for x in Xs:
+            self._blk(x, "scf_begin X")
+        for v in v0s:
+            self._vec(v, self.dtype, "scf_begin v0")
         self._scf_keep = (list(Xs), list(v0s))
         xa = (C.c_void_p * len(Xs))(*[t.data_ptr() for t in Xs])
         va = (C.c_void_p * len(v0s))(*[t.data_ptr() for t in v0s])
@@ -392,6 +429,8 @@ class Hub:
 
     def scf_set_density(self, rho):
         """Starting density of a density-mode SCF (before its first iteration)."""
+        import torch
+        self._vec(rho, torch.float64, "scf_set_density rho")
         self._check(self.lib.hub_scf_set_density(self.h, _tptr(rho)), "hub_scf_set_density")
 
     def num_projectors(self) -> int:
@@ -401,7 +440,7 @@ class Hub:
 
     def project(self, X) -> np.ndarray:
         """C[p, n] = dV <proj_p|x_n> for every projector row (complex on complex handles)."""
-        ncol, ld = X.shape
+        ncol, ld = self._blk(X, "project X")
         npj = self.num_projectors()
         cw = 2 if self.complex else 1
         out = np.zeros(max(npj * ncol * cw, 1))
@@ -413,7 +452,7 @@ class Hub:
 
     def expand(self, W, Y, alpha: float = 1.0):
         """Y[g, n] += alpha sum_p proj_p(g) W[p, n] (W host, [nproj, ncol])."""
-        ncol, ld = Y.shape
+        ncol, ld = self._blk(Y, "expand Y")
         W = np.asarray(W)
         if self.complex:
             Wf = np.empty(W.size * 2)
@@ -424,24 +463,34 @@ class Hub:
 
     def scf_density(self, rho):
         """Output density of the last density-SCF iteration (summed over spins) into rho."""
+        import torch
+        self._vec(rho, torch.float64, "scf_density rho")
         self._check(self.lib.hub_scf_density(self.h, _tptr(rho)), "hub_scf_density")
 
     # ------------------------------------------------------------------ density SCF steps
     def density(self, X, f, scale, rho):
         """rho += scale * sum_n f_n |x_n|^2 (rho: device double [Nd])."""
-        ncol, ld = X.shape
+        import torch
+        ncol, ld = self._blk(X, "density X")
+        self._vec(rho, torch.float64, "density rho")
         f = np.ascontiguousarray(f, dtype=np.float64)
         self._check(self.lib.hub_density(self.h, _tptr(X), ncol, ld, _dptr(f), float(scale), _tptr(rho)),
                     "hub_density")
 
     def hartree(self, rho, V, tol=1e-10, max_iter=20000):
         """V (warm start in, solution out) and (CG iterations, E_H)."""
+        import torch
+        self._vec(rho, torch.float64, "hartree rho")
+        self._vec(V, torch.float64, "hartree V")
         it, eh = C.c_int(), C.c_double()
         self._check(self.lib.hub_hartree(self.h, _tptr(rho), _tptr(V), tol, max_iter, C.byref(it),
                                          C.byref(eh)), "hub_hartree")
         return it.value, eh.value
 
     def lda_exchange(self, rhos, vxs) -> float:
+        import torch
+        for t in list(rhos) + list(vxs):
+            self._vec(t, torch.float64, "lda_exchange")
         ex = C.c_double()
         two = len(rhos) == 2
         self._check(self.lib.hub_lda_exchange(self.h, len(rhos), _tptr(rhos[0]), _tptr(rhos[1]) if two else None,
@@ -450,6 +499,9 @@ class Hub:
         return ex.value
 
     def kerker(self, r, z, kappa, tol=1e-10, max_iter=20000) -> int:
+        import torch
+        self._vec(r, torch.float64, "kerker r")
+        self._vec(z, torch.float64, "kerker z")
         it = C.c_int()
         self._check(self.lib.hub_kerker(self.h, _tptr(r), _tptr(z), kappa, tol, max_iter, C.byref(it)),
                     "hub_kerker")

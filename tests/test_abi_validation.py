@@ -134,3 +134,27 @@ def test_projector_entry_points_reject_a_null_handle(lib):
     assert lib.hub_project(None, None, 0, 0, None) == EINVAL
     assert lib.hub_expand(None, None, 0, None, 0, 1.0) == EINVAL
     assert lib.hub_scf_set_density(None, None) == EINVAL
+
+
+def test_binding_rejects_blocks_of_the_wrong_type_before_any_call():
+    # the checks run on the host before the library is called, so a handle-less object
+    # with the handle's type fields is enough (no GPU)
+    torch = pytest.importorskip("torch")
+    from paper_2507_23612_gb300.binding import Hub, HUB_F64, HUB_F32
+    hb = Hub.__new__(Hub)
+    hb.n, hb.Nd, hb.complex = (4, 4, 4), 64, False
+    hb.prec = HUB_F64
+    with pytest.raises(ValueError):
+        hb._blk(torch.zeros((3, 64), dtype=torch.float32), "X")          # float block, FP64 handle
+    with pytest.raises(ValueError):
+        hb._blk(torch.zeros((3, 60), dtype=torch.float64), "X")          # ld < Nd
+    assert hb._blk(torch.zeros((3, 70), dtype=torch.float64), "X") == (3, 70)
+    assert hb._blk(torch.zeros((0, 64), dtype=torch.float64), "X") == (0, 64)
+    hb.prec = HUB_F32
+    hb.complex = True
+    with pytest.raises(ValueError):
+        hb._blk(torch.zeros((3, 64), dtype=torch.float64), "X")          # same size, not complex
+    hb._blk(torch.zeros((3, 64), dtype=torch.complex64), "X")
+    with pytest.raises(ValueError):
+        hb._vec(torch.zeros(63, dtype=torch.float64), torch.float64, "v")  # too short
+    hb.h = None                                                         # nothing to release
