@@ -296,8 +296,10 @@ class Hub:
 
     def gram(self, A, B, alpha: float, G):
         """G (device double [ncol_a, ncol_b]) = alpha * A B^T for row-stored blocks."""
-        na, ld = A.shape
-        nb, ldb = B.shape
+        import torch
+        na, ld = self._blk(A, "gram A")
+        nb, ldb = self._blk(B, "gram B")
+        self._vec(G, torch.float64, "gram G", na * nb)
         if ld != ldb:
             raise ValueError("A and B need the same leading dimension")
         self._check(self.lib.hub_gram(self.h, _tptr(A), na, _tptr(B), nb, ld, float(alpha), _tptr(G)),
