@@ -713,3 +713,81 @@ def cutoff_for_threshold(l: int, rs: float, tau: float) -> float:
         else:
             hi = mid
     return 0.5 * (lo + hi)
+
+
+def scf_model_a_kpoints(n, L, kpts, kweights, veff, atoms, D0, X0s, n_elec: float, kT: float,
+                        degree: int, lanczos_v0s, n0: int = 6, lanczos_steps: int = 10,
+                        max_iter: int = 60, first_passes: int = 3, tol_e_atom: float = 1e-5,
+                        tol_D: float = 1e-4, hist: int = 7, beta: float = 0.3,
+                        eig_solver: str = "chefsi"):
+    """The fixed-V_eff SCF of scf_model_a with Brillouin-zone sampling: the occupation
+    matrices are the weighted average over the k-points of Eq. (orbital_occup_ext),
+    D = sum_k w_k D_k (sum w_k = 1), one Fermi level for all (spin, k) channels, and the
+    Hamiltonian of every k-point carries the same D (complex Hermitian in general; its real
+    and imaginary parts are mixed as one real vector).  A k-set with the Gamma point (real
+    orbitals there) must be closed under k -> -k, which makes D real (D_-k = conj(D_k)).
+    X0s[s][k], lanczos_v0s[s][k]: starting blocks (Nd, ncol) and Lanczos vectors per channel.
+    Energy: E = sum w f lam - sum_I Re sum M_in o D_out^T + E_U(D_out) - kT S, with the spin
+    degeneracy of one channel for both spins when nspin = 1."""
+    nspin, nk = len(X0s), len(kpts)
+    grids = [Grid(n, L, k, n0) for k in kpts]
+    hams = [[Hamiltonian(grids[k], veff, atoms) for k in range(nk)] for _ in range(nspin)]
+    U = np.array([h[2] for h in hams[0][0].hub])
+    deg = 2.0 if nspin == 1 else 1.0
+    D_in = np.asarray(D0, dtype=np.complex128).copy()
+    Xs = [[np.asarray(X0s[s][k]).astype(np.complex128 if grids[k].is_complex else np.float64)
+           for k in range(nk)] for s in range(nspin)]
+    ncol = Xs[0][0].shape[1]
+    bounds = [[None] * nk for _ in range(nspin)]
+    mixer = Pulay(hist, beta)
+    E_prev, small = None, 0
+    for it in range(1, max_iter + 1):
+        lams = [[None] * nk for _ in range(nspin)]
+        if not all(g.is_complex for g in grids) and np.max(np.abs(D_in.imag)) > 1e-10:
+            raise ValueError("a real (Gamma) k-point needs a real D: use a k-set closed under k -> -k")
+        for s in range(nspin):
+            for k in range(nk):
+                ham = hams[s][k]
+                ham.set_occupation(D_in[s] if ham.grid.is_complex else np.real(D_in[s]))
+                if eig_solver == "dense":
+                    w, V = np.linalg.eigh(ham.dense())
+                    lams[s][k] = w[:ncol]
+                    Xs[s][k] = V[:, :ncol] / np.sqrt(ham.grid.dV)
+                    continue
+                for _ in range(first_passes if it == 1 else 1):
+                    if bounds[s][k] is None:
+                        lo, up = lanczos_bounds(ham, lanczos_v0s[s][k], lanczos_steps)
+                        bounds[s][k] = [lo, lo + 0.1 * (up - lo), up]
+                    a_low, a, b = bounds[s][k]
+                    Y = chebyshev_filter(ham, Xs[s][k], degree, a, b, a_low)
+                    lam, Xs[s][k] = rayleigh_ritz(ham, Y)
+                    bounds[s][k] = [lam[0], lam[-1], b]
+                lams[s][k] = lam
+        flat = [lams[s][k] for s in range(nspin) for k in range(nk)]
+        wts = [kweights[k] for s in range(nspin) for k in range(nk)]
+        fl, mu = fermi_dirac(flat, wts, kT, n_elec, deg)
+        f = [[fl[s * nk + k] for k in range(nk)] for s in range(nspin)]
+        D_out = np.zeros_like(D_in)
+        for s in range(nspin):
+            for k in range(nk):
+                D_out[s] += occupation_matrices(hams[s][k], Xs[s][k], f[s][k], kweights[k])
+        e_band = sum(deg * kweights[k] * float(np.dot(f[s][k], lams[s][k]))
+                     for s in range(nspin) for k in range(nk))
+        e_dc = sum(deg * float(np.real(np.sum(0.5 * U[I] * (np.eye(5) - 2.0 * D_in[s, I]) * D_out[s, I].T)))
+                   for s in range(nspin) for I in range(len(U)))
+        e_u = deg * hubbard_energy(D_out, U)
+        ent = sum(deg * kweights[k] * fermi_entropy(f[s][k]) for s in range(nspin) for k in range(nk)) if kT > 0 else 0.0
+        E = e_band - e_dc + e_u - kT * ent
+        dD = float(np.max(np.abs(D_out - D_in)))
+        small = small + 1 if (E_prev is not None and abs(E - E_prev) / len(atoms) < tol_e_atom) else 0
+        E_prev = E
+        res = dict(E=E, E_U=e_u, D=D_out, eig=lams, f=f, mu=mu, iterations=it, converged=False)
+        if small >= 2 and dD < tol_D:
+            res["converged"] = True
+            return res
+        x_in = np.concatenate([D_in.real.ravel(), D_in.imag.ravel()])
+        x_out = np.concatenate([D_out.real.ravel(), D_out.imag.ravel()])
+        x = mixer.mix(x_in, x_out)
+        half = x.size // 2
+        D_in = (x[:half] + 1j * x[half:]).reshape(D_in.shape)
+    return res
