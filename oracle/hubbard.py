@@ -384,20 +384,27 @@ def rayleigh_ritz(ham: Hamiltonian, X):
 def fermi_dirac(eigs, weights, kT: float, n_elec: float, degeneracy: float):
     """Occupations f in [0, 1] of every (channel, state): Fermi-Dirac with one chemical
     potential mu, found by bisection so that sum_channels w * degeneracy * sum_n f = n_elec.
-    (Reading: the paper does not state its smearing.)  kT = 0 gives the step function with
-    the lowest n_elec / degeneracy states filled (ties not split).
+    (Reading: the paper does not state its smearing.)  kT = 0 gives the step function: the
+    lowest states, each holding w * degeneracy electrons of its channel, are filled until
+    n_elec is reached (ties not split).
     eigs: list of 1-D arrays (one per channel), weights: list of channel weights."""
     if kT <= 0.0:
         allv = np.concatenate([np.asarray(e) for e in eigs])
-        nfill = int(round(n_elec / degeneracy / (weights[0] if len(set(weights)) == 1 else 1.0)))
+        allw = np.concatenate([np.full(len(e), w) for e, w in zip(eigs, weights)])
         order = np.argsort(allv, kind="stable")
         f_all = np.zeros_like(allv)
-        f_all[order[:nfill]] = 1.0
+        left, mu = n_elec, float(allv[order[0]])
+        for i in order:
+            if left <= 1e-12:
+                break
+            f_all[i] = 1.0
+            left -= allw[i] * degeneracy
+            mu = float(allv[i])
         out, o = [], 0
         for e in eigs:
             out.append(f_all[o:o + len(e)])
             o += len(e)
-        return out, float(allv[order[nfill - 1]])
+        return out, mu
 
     def count(mu):
         return sum(w * degeneracy * np.sum(0.5 * (1.0 - np.tanh((np.asarray(e) - mu) / (2 * kT))))
