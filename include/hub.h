@@ -187,6 +187,14 @@ int hub_gram_noalloc(const void* A, int ncol_a, const void* B, int ncol_b, long 
 int hub_occupation(hub_t h, int spin, const void* X, int ncol, int ld, const double* f_host,
                    double kweight, double* D_re_out, double* D_im_out, double* EU_out);
 
+/* Fermi-Dirac occupations with one chemical potential over weighted states: f_i in [0, 1]
+ * with sum_i w_i * degeneracy * f_i = n_elec, f_i = 1 / (1 + exp((eig_i - mu) / kT)), mu by
+ * bisection; kT = 0 fills the lowest states (by weight) with f = 1 (ties not split).  w_i is
+ * the k-point weight of state i (1 for one k-point).  Host arithmetic, no handle.
+ * Errors: HUB_EINVAL (n < 1, NULL arrays, kT < 0, n_elec outside the states' capacity). */
+int hub_fermi_dirac(int n, const double* eig, const double* w, double kT, double n_elec,
+                    double degeneracy, double* f_out, double* mu_out);
+
 /* Cutoff radius of the value-threshold truncation (Sec. II.B: a radial orbital is cut where
  * its value falls below a threshold): for R(r) = N r^l exp(-r^2 / (2 rs^2)) (N normalising
  * int R^2 r^2 dr to 1) the radius beyond which R < tau, i.e. the root beyond the maximum at

@@ -73,6 +73,7 @@ _SIGS = {
     "hub_scf_forces": [_P, _PD, _PD],
     "hub_extrapolate_occupations": [_I, _I, _PD, _PD, _I, _PD, _PD, _PD],
     "hub_cutoff_radius": [_I, _D, _D, _PD],
+    "hub_fermi_dirac": [_I, _PD, _PD, _D, _D, _D, _PD, _PD],
     "hub_density": [_P, _P, _I, _I, _PD, _D, _P],
     "hub_hartree": [_P, _P, _P, _D, _I, _PI, _PD],
     "hub_lda_exchange": [_P, _I, _P, _P, _P, _P, _PD],
@@ -508,6 +509,20 @@ class Hub:
         self._check(self.lib.hub_kerker(self.h, _tptr(r), _tptr(z), kappa, tol, max_iter, C.byref(it)),
                     "hub_kerker")
         return it.value
+
+
+def fermi_dirac(eig, weights, kT: float, n_elec: float, degeneracy: float):
+    """(f, mu) for the states eig with k-point weights (hub_fermi_dirac)."""
+    lib = load_library()
+    e = np.ascontiguousarray(eig, dtype=np.float64).ravel()
+    wv = np.ascontiguousarray(np.broadcast_to(np.asarray(weights, dtype=np.float64), e.shape)).ravel()
+    f = np.zeros_like(e)
+    mu = C.c_double()
+    rc = lib.hub_fermi_dirac(e.size, _dptr(e), _dptr(wv), float(kT), float(n_elec), float(degeneracy),
+                             _dptr(f), C.byref(mu))
+    if rc:
+        raise HubError(rc, "hub_fermi_dirac: bad arguments")
+    return f, mu.value
 
 
 def cutoff_radius(l: int, rs: float, tau: float) -> float:

@@ -1,6 +1,7 @@
 // Small device helpers: potential conversion, block copies, deterministic dot products and
 // the Lanczos bound estimator used to place the Chebyshev filter interval (CheFSI, Sec. II.B).
 #include <algorithm>
+#include <vector>
 #include <cmath>
 
 #include "hub_internal.cuh"
@@ -324,6 +325,48 @@ extern "C" int hub_cutoff_radius(int l, double rs, double tau, double* rc_out) {
         if (R(mid) > tau) lo = mid; else hi = mid;
     }
     *rc_out = 0.5 * (lo + hi);
+    return HUB_OK;
+}
+
+// ---------------------------------------------------------------------------- Fermi level
+extern "C" int hub_fermi_dirac(int n, const double* eig, const double* w, double kT, double n_elec,
+                               double degeneracy, double* f_out, double* mu_out) {
+    if (n < 1 || !eig || !w || !f_out || !(kT >= 0.0) || !(degeneracy > 0.0)) return HUB_EINVAL;
+    double cap = 0.0;
+    for (int i = 0; i < n; ++i) cap += w[i] * degeneracy;
+    if (!(n_elec >= 0.0) || n_elec > cap * (1.0 + 1e-12)) return HUB_EINVAL;
+    if (kT == 0.0) {
+        // lowest states first until n_elec is reached
+        std::vector<int> ord(n);
+        for (int i = 0; i < n; ++i) ord[i] = i;
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return eig[a] < eig[b]; });
+        double left = n_elec, mu = eig[ord[0]];
+        for (int i = 0; i < n; ++i) f_out[i] = 0.0;
+        for (int j = 0; j < n && left > 1e-12; ++j) {
+            f_out[ord[j]] = 1.0;
+            left -= w[ord[j]] * degeneracy;
+            mu = eig[ord[j]];
+        }
+        if (mu_out) *mu_out = mu;
+        return HUB_OK;
+    }
+    auto count = [&](double m) {
+        double c = 0.0;
+        for (int i = 0; i < n; ++i) c += w[i] * degeneracy * 0.5 * (1.0 - std::tanh((eig[i] - m) / (2.0 * kT)));
+        return c;
+    };
+    double lo = eig[0], hi = eig[0];
+    for (int i = 1; i < n; ++i) { lo = std::min(lo, eig[i]); hi = std::max(hi, eig[i]); }
+    lo -= 50.0 * kT;
+    hi += 50.0 * kT;
+    for (int it = 0; it < 200; ++it) {
+        const double m = 0.5 * (lo + hi);
+        if (count(m) < n_elec) lo = m; else hi = m;
+        if (hi - lo < 1e-15) break;
+    }
+    const double mu = 0.5 * (lo + hi);
+    for (int i = 0; i < n; ++i) f_out[i] = 0.5 * (1.0 - std::tanh((eig[i] - mu) / (2.0 * kT)));
+    if (mu_out) *mu_out = mu;
     return HUB_OK;
 }
 

@@ -66,3 +66,31 @@ def test_gamma_with_an_unpaired_bloch_point_is_rejected():
     wl = _case()
     with pytest.raises(ValueError):
         _run(wl, [(0.0, 0.0, 0.0), K], [0.5, 0.5], "chefsi", first_passes=1)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2507_23612_gb300 import build as b
+    b.build()
+    from paper_2507_23612_gb300 import binding
+    return binding.load_library()
+
+
+@pytest.mark.parametrize("kT", [0.01, 0.0])
+def test_library_fermi_level_matches_the_oracle(lib, kT):
+    from paper_2507_23612_gb300.binding import fermi_dirac
+    rng = np.random.default_rng(3)
+    eigs = [np.sort(rng.uniform(-1.0, 1.0, 9)) for _ in range(3)]
+    wts = [0.25, 0.25, 0.5]
+    f_ref, mu_ref = o.fermi_dirac(eigs, wts, kT, 7.0, 2.0)
+    f, mu = fermi_dirac(np.concatenate(eigs), np.repeat(wts, 9), kT, 7.0, 2.0)
+    np.testing.assert_allclose(f, np.concatenate(f_ref), atol=1e-12)
+    if kT > 0:
+        assert abs(mu - mu_ref) < 1e-12
+        assert abs(2.0 * np.sum(np.repeat(wts, 9) * f) - 7.0) < 1e-10
+
+
+def test_library_fermi_level_rejects_too_many_electrons(lib):
+    from paper_2507_23612_gb300.binding import HubError, fermi_dirac
+    with pytest.raises(HubError):
+        fermi_dirac([0.0, 1.0], [1.0, 1.0], 0.01, 5.0, 2.0)
