@@ -48,19 +48,23 @@ def _entropy(f):
 class KpointSCF:
     """The workload's cell on one handle per k-point (complex orbitals where k != 0)."""
 
-    def __init__(self, wl, kpts, kweights, prec: int = HUB_F64, device=None):
-        import torch
+    def __init__(self, wl, kpts, kweights, prec: int = HUB_F64, device=None, hub_factory=None):
+        """hub_factory(k) -> a handle with the potential and atoms set (default: a library
+        Hub on `device`); any object with the Hub methods the driver calls will do."""
         if abs(sum(kweights) - 1.0) > 1e-12 or len(kweights) != len(kpts):
             raise ValueError("one weight per k-point, summing to one")
         self.wl, self.kpts, self.kw = wl, [tuple(map(float, k)) for k in kpts], list(map(float, kweights))
-        self.dev = device or torch.device("cuda", 0)
         self.real_k = [not any(k) for k in self.kpts]
-        self.hubs = []
-        for k in self.kpts:
-            hb = Hub(wl.n, wl.L, wl.fd_half_order, kpt=k, complex_=any(k), prec=prec)
-            hb.set_veff(torch.tensor(wl.veff, dtype=torch.float64, device=self.dev))
-            hb.set_atoms(wl.atoms)
-            self.hubs.append(hb)
+        if hub_factory is None:
+            import torch
+            dev = device or torch.device("cuda", 0)
+
+            def hub_factory(k):
+                hb = Hub(wl.n, wl.L, wl.fd_half_order, kpt=k, complex_=any(k), prec=prec)
+                hb.set_veff(torch.tensor(wl.veff, dtype=torch.float64, device=dev))
+                hb.set_atoms(wl.atoms)
+                return hb
+        self.hubs = [hub_factory(k) for k in self.kpts]
         self.U = np.array([a.hub_U for a in wl.atoms if a.hub_l >= 0])
 
     def close(self):
