@@ -325,14 +325,17 @@ class DensityModel:
 
 # ------------------------------------------------------------------------------ MD steps
 def trajectory_scf(steps, prec: int = HUB_F64, start: str = "extrapolated", reuse_orbitals: bool = True,
-                   tol_e_atom: float = 1e-5, tol_D: float = 1e-4, model=None):
+                   tol_e_atom: float = 1e-5, tol_D: float = 1e-4, model=None, solve=None):
     """SCF at every step of a trajectory (a list of workloads on one grid).  The starting D of
     a step is the atomic guess (start="atomic"), the second-order extrapolation of the
     previous steps' converged D (start="extrapolated", hub_extrapolate_occupations with
     coefficients fitted to the positions; Sec. II.B), or the prediction of a trained
     OccupationModel (start="mlp", model=...).  With reuse_orbitals the previous step's
-    converged orbitals start the next SCF.  Returns per step: iterations, E, the
-    extrapolation coefficients and the wall time."""
+    converged orbitals start the next SCF.  solve(wl, prec, D0=..., X0=..., tol_e_atom=...,
+    tol_D=...) runs one SCF (default scf_solve, the library's SCF driver) and returns its
+    iterations, convergence, E, D, orbitals X and wall time.  Returns per step: iterations,
+    E, the starting D, the extrapolation coefficients and the wall time."""
+    solve = solve or (lambda wl, prec, **kw: scf_solve(wl, prec, keep_orbitals=True, **kw))
     if start not in ("atomic", "extrapolated", "mlp") or (start == "mlp" and model is None):
         raise ValueError("start must be atomic, extrapolated or mlp (with a model)")
     D_hist, R_hist, X, out = [], [], None, []
@@ -346,13 +349,13 @@ def trajectory_scf(steps, prec: int = HUB_F64, start: str = "extrapolated", reus
             D0 = model.predict(wl.atoms, wl.L)
         else:
             D0 = wl.D0
-        r = scf_solve(wl, prec, D0=D0, tol_e_atom=tol_e_atom, tol_D=tol_D,
-                      X0=X if (reuse_orbitals and X is not None) else None, keep_orbitals=True)
+        r = solve(wl, prec, D0=D0, tol_e_atom=tol_e_atom, tol_D=tol_D,
+                  X0=X if (reuse_orbitals and X is not None) else None)
         X = r["X"]
         D_hist.append(r["D"])
         R_hist.append(R)
         out.append({"iterations": r["iterations"], "converged": r["converged"], "E": r["E"],
-                    "alpha_beta": coef, "seconds": r["seconds"]})
+                    "D0": np.asarray(D0), "D": r["D"], "alpha_beta": coef, "seconds": r["seconds"]})
     return out
 
 

@@ -83,3 +83,35 @@ def test_seeded_md_trajectory_is_a_sinusoid():
     al, be = o.alfe_coefficients(R[:4])
     assert abs(al - 2 * np.cos(2 * np.pi / 12)) < 1e-9 and abs(be + 1.0) < 1e-9
     assert all(s.n == steps[0].n and s.ncol == steps[0].ncol for s in steps)
+
+
+def test_trajectory_driver_orchestration_on_the_cpu(lib):
+    # the MD driver with the oracle's SCF in place of the library's: each step starts from
+    # the extrapolation of the previous converged D (checked against the oracle's formula)
+    # and from the previous orbitals, and reaches the same fixed point as the atomic start
+    import workloads as w
+    from paper_2507_23612_gb300.warmstart import trajectory_scf
+    steps = w.rutile_trajectory((1, 1, 1), nsteps=4, amplitude=0.1, period=12.0, h_target=0.55,
+                                occ_per_atom=2.0, nspin=1)
+
+    def solve(wl, prec, D0=None, X0=None, tol_e_atom=1e-5, tol_D=1e-4):
+        X = wl.orbitals(0).T if X0 is None else X0[0]
+        r = o.scf_model_a((wl.n, wl.L, (0, 0, 0), wl.fd_half_order), wl.veff, wl.atoms, D0, [X],
+                          n_elec=wl.n_elec, kT=0.01, degree=10, lanczos_v0s=[wl.lanczos_start(0)],
+                          tol_e_atom=tol_e_atom, tol_D=tol_D, max_iter=80)
+        return {"iterations": r["iterations"], "converged": r["converged"], "E": r["E"], "D": r["D"],
+                "X": r["X"], "seconds": 0.0}
+    atomic = trajectory_scf(steps, start="atomic", solve=solve, tol_e_atom=1e-7, tol_D=1e-6)
+    extra = trajectory_scf(steps, start="extrapolated", solve=solve, tol_e_atom=1e-7, tol_D=1e-6)
+    nat = len(steps[0].atoms)
+    for t, (a, e) in enumerate(zip(atomic, extra)):
+        assert a["converged"] and e["converged"]
+        assert abs(a["E"] - e["E"]) / nat < 1e-5
+        np.testing.assert_array_equal(a["D0"], steps[t].D0)
+        if t >= 1:
+            h = min(3, t)
+            R = [np.array([x.pos for x in s.atoms]) for s in steps[t - h:t + 1]]
+            al, be = o.alfe_coefficients(R)
+            ref = o.extrapolate_occupations([extra[j]["D"] for j in range(t - h, t)], steps[t].D0, al, be)
+            np.testing.assert_allclose(e["D0"], ref, atol=1e-12)
+    print({"atomic": [a["iterations"] for a in atomic], "extrapolated": [e["iterations"] for e in extra]})
