@@ -183,7 +183,10 @@ class DensityBasis:
     Gram matrix; both sides from hub_project); expand: the density of given coefficients
     (hub_expand), scaled to carry n_elec electrons."""
 
-    def __init__(self, wl, atoms=None, device=None):
+    def __init__(self, wl, atoms=None, device=None, hub_factory=None):
+        """hub_factory(basis_atoms) -> a handle whose tables hold the basis (default: an FP64
+        library Hub on the workload's grid); any object with num_projectors / project /
+        expand will do."""
         import torch
         from types import SimpleNamespace
         self.dev = device or torch.device("cuda", 0)
@@ -195,8 +198,12 @@ class DensityBasis:
                                  hub_rs=1.0, hub_rc=0.0, hub_U=0.0) for a in self.atoms]
         self.K = K
         self.Nd, self.dV = wl.Nd, wl.dV
-        self.hub = Hub(wl.n, wl.L, wl.fd_half_order, prec=HUB_F64)
-        self.hub.set_atoms(basis)
+        if hub_factory is None:
+            def hub_factory(atoms_):
+                hb = Hub(wl.n, wl.L, wl.fd_half_order, prec=HUB_F64)
+                hb.set_atoms(atoms_)
+                return hb
+        self.hub = hub_factory(basis)
         nb = self.hub.num_projectors()
         if nb != K * len(self.atoms):
             raise RuntimeError("density basis tables do not have K functions per atom")

@@ -195,3 +195,40 @@ def test_expanded_density_carries_the_electron_count():
     g, basis = _basis_case()
     rho = ds.expand_density(g, basis, np.array([[0.7, 0.2, 1.3], [0.1, 0.9, 0.4]]), n_elec=12.0)
     assert abs(g.dV * np.sum(rho) - 12.0) < 1e-12
+
+
+def test_density_basis_driver_on_the_cpu():
+    # the warm start's DensityBasis with the library handle replaced by the oracle's basis
+    # matrix: its Gram matrix (expand the unit vectors, project them), fit and scaled
+    # expansion reproduce the oracle's fit and expansion
+    torch = pytest.importorskip("torch")
+    from paper_2507_23612_gb300.warmstart import DensityBasis
+
+    wl = w.rutile_snapshot((1, 1, 1), 0.1, seed=2, h_target=0.5, nspin=1)
+    g = hb.Grid(wl.n, wl.L)
+
+    class BasisHandle:
+        def __init__(self, atoms_):
+            self.B = ds.density_basis_matrix(g, atoms_)
+
+        def num_projectors(self):
+            return self.B.shape[1]
+
+        def project(self, X):
+            return g.dV * (self.B.T @ X.cpu().numpy().T)
+
+        def expand(self, W, Y, alpha=1.0):
+            Y += torch.tensor((alpha * (self.B @ np.asarray(W))).T, dtype=Y.dtype)
+
+        def close(self):
+            pass
+
+    basis = DensityBasis(wl, device=torch.device("cpu"), hub_factory=BasisHandle)
+    rng = np.random.default_rng(6)
+    rho = rng.uniform(0.0, 1.0, wl.Nd)
+    c = basis.fit(torch.tensor(rho))
+    c_ref = ds.fit_density_coefficients(g, ds.density_basis_atoms(wl.atoms), rho)
+    np.testing.assert_allclose(c, c_ref, rtol=1e-9, atol=1e-12)
+    rho0 = basis.expand(c, wl.n_elec).numpy()
+    ref = ds.expand_density(g, ds.density_basis_atoms(wl.atoms), c_ref, n_elec=wl.n_elec)
+    np.testing.assert_allclose(rho0, ref, rtol=1e-9, atol=1e-12)
