@@ -154,7 +154,7 @@ using namespace hub;
 extern "C" {
 
 int hub_version(char* buf, int len) {
-    const char* s = "hub 0.1 (sm_103a; real-space DFT+U CheFSI)";
+    const char* s = "hub 0.2 (sm_103a; real-space DFT+U CheFSI, forces, stress, density SCF)";
     if (!buf || len <= 0) return HUB_EINVAL;
     std::strncpy(buf, s, (size_t)len - 1);
     buf[len - 1] = 0;
