@@ -83,3 +83,21 @@ def test_gamma_with_an_unpaired_bloch_point_is_rejected(built):
     v0 = [[wl.lanczos_start(), wl.lanczos_start(complex_=True)]]
     with pytest.raises(ValueError):
         scf.run(X0, v0, wl.D0, n_elec=6.0, kT=0.01, degree=12, max_iter=3, first_passes=1)
+
+
+def test_driver_spin_polarized_pair(built):
+    from paper_2507_23612_gb300.kpoint_scf import KpointSCF
+    wl = w.small_test_system(n=(8, 8, 10), ncol=8, natoms=2, seed=11, nspin=2)
+    kpts, kw = [K, tuple(-np.asarray(K))], [0.5, 0.5]
+    X0 = [[wl.orbitals(spin=s, complex_=True) for _ in range(2)] for s in range(2)]
+    v0 = [[wl.lanczos_start(spin=s, complex_=True) for _ in range(2)] for s in range(2)]
+    for s in range(2):
+        X0[s][1], v0[s][1] = np.conj(X0[s][0]), np.conj(v0[s][0])
+    kwargs = dict(n_elec=6.0, kT=0.01, degree=12, max_iter=80, tol_e_atom=1e-9, tol_D=1e-7)
+    ref = o.scf_model_a_kpoints(wl.n, wl.L, kpts, kw, wl.veff, wl.atoms, wl.D0,
+                                [[x.T for x in X0[s]] for s in range(2)], lanczos_v0s=v0, **kwargs)
+    scf = KpointSCF(wl, kpts, kw, hub_factory=lambda k: OracleHandle(wl, k))
+    res = scf.run([[x.copy() for x in X0[s]] for s in range(2)], v0, wl.D0, **kwargs)
+    assert ref["converged"] and res["converged"]
+    assert abs(res["E"] - ref["E"]) < 1e-9 * abs(ref["E"])
+    np.testing.assert_allclose(res["D"], ref["D"], atol=1e-7)
