@@ -73,6 +73,9 @@ def parse():
                     help="SCF at STEPS steps of a seeded rutile 2x2x3 trajectory in --prec, starting D "
                          "atomic vs second-order extrapolated vs the occupation model (trained on "
                          "--warm-train displaced cells), previous orbitals reused: iterations per step")
+    ap.add_argument("--kpoint-scf", action="store_true",
+                    help="SCF of the rutile 2x2x3 cell with a k, -k pair (k = pi/L_x (1/2, 0, 0), "
+                         "weights 1/2) over one handle per k-point in --prec: iterations and time")
     ap.add_argument("--scf-compare", action="store_true",
                     help="cold-start SCF to convergence in FP64, FP32 and mixed (BF16 with the "
                          "precision ladder); report time to solution and errors against FP64")
@@ -788,8 +791,46 @@ def run_md_compare(args):
     return 0
 
 
+def run_kpoint_scf(args):
+    """Brillouin-zone sampling: the SCF of the rutile cell over a time-reversal pair of
+    Bloch vectors (complex orbitals, real D), to 1e-5 Ha/atom."""
+    import math
+    import numpy as np
+    import torch
+    import workloads as w
+    from paper_2507_23612_gb300.kpoint_scf import KpointSCF
+    wl = w.rutile()
+    kx = 0.5 * math.pi / wl.L[0]
+    kpts = [(kx, 0.0, 0.0), (-kx, 0.0, 0.0)]
+    scf = KpointSCF(wl, kpts, [0.5, 0.5], PREC[args.prec])
+    try:
+        dev = torch.device("cuda", 0)
+        X0 = [[torch.tensor(wl.orbitals(s, complex_=True), device=dev).to(scf.hubs[0].dtype).contiguous()
+               for _ in kpts] for s in range(wl.nspin)]
+        v0 = [[torch.tensor(wl.lanczos_start(s, complex_=True), device=dev).to(scf.hubs[0].dtype).contiguous()
+               for _ in kpts] for s in range(wl.nspin)]
+        for s in range(wl.nspin):                 # -k starts from the conjugate of +k
+            X0[s][1] = X0[s][0].conj().resolve_conj().contiguous()
+            v0[s][1] = v0[s][0].conj().resolve_conj().contiguous()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = scf.run(X0, v0, wl.D0, n_elec=wl.n_elec, kT=wl.kT if wl.kT > 0 else 0.005, degree=wl.degree,
+                      max_iter=200, tol_e_atom=1e-5, tol_D=1e-4)
+        torch.cuda.synchronize()
+        tts = time.perf_counter() - t0
+    finally:
+        scf.close()
+    print(json.dumps({"kpoint_scf": {"prec": args.prec, "kpoints": kpts, "weights": [0.5, 0.5],
+                                     "iterations": res["iterations"], "converged": res["converged"],
+                                     "time_to_solution_s": tts, "E_Ha": res["E"], "E_U_Ha": res["E_U"],
+                                     "max_imag_D": float(np.max(np.abs(np.imag(res["D"]))))}}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.kpoint_scf:
+        return run_kpoint_scf(args)
     if args.md_compare:
         return run_md_compare(args)
     if args.forces:
