@@ -292,7 +292,9 @@ typedef struct {
      * density block (Sec. II.B: preconditioned Pulay whose coefficients also mix D); energy
      *   E = sum f eig - sum_s int rho_out^s (V_H + v_x^s)[rho_in] + E_H[rho_out] + E_x[rho_out]
      *       - sum_I Tr(M_in D_out) + E_U(D_out) - kT S;
-     * converged when, in addition, int |rho_out - rho_in| / n_elec < tol_rho. */
+     * converged when, in addition, int |rho_out - rho_in| / n_elec < tol_rho.  From the first
+     * density-mode iteration on, the handle's H uses the SCF's V_eff^s of each spin (also in
+     * hub_apply_H and the filter) until hub_set_veff is called again. */
     int density;
     double kerker_kappa;  /* bohr^-1 (0.5 when 0) */
     double tol_rho;       /* (1e-4 when 0) */
