@@ -1,0 +1,40 @@
+"""Host arithmetic of the benchmark's roofline figures (no GPU): the algorithmic work per
+launch and the fractions of the peaks, checked by hand for one stencil, gather and scatter
+launch in each form."""
+from types import SimpleNamespace
+
+import pytest
+
+import bench
+
+
+def _wl(Nd=1_000_000, ncol=100):
+    return SimpleNamespace(Nd=Nd, ncol=ncol)
+
+
+def test_fp64_stencil_roofline_counts_59_flop_per_point_orbital():
+    # 10 launches of 20 ms in total: 2 ms per launch; 59 * 1e8 flop / 2e-3 s = 2.95 TFLOP/s
+    r = bench.kernel_roofline("stencil", (20.0, 10), _wl(), "f64", 0)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(59 * 1e8 / 2e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / (152 * 2 * 2 * 2.07 / 1e3))
+
+
+def test_fp64_gather_counts_two_flop_per_function_point_and_column():
+    r = bench.kernel_roofline("gather", (4.0, 2), _wl(), "f64", 5_000_000)
+    assert r["achieved"] == pytest.approx(2.0 * 5e6 * 100 / 2e-3 / 1e12)
+
+
+@pytest.mark.parametrize("name,bytes_per", [("stencil", 12.0), ("gather", 4.0), ("scatter", 8.0)])
+def test_float_kernels_count_their_block_bytes_against_hbm(name, bytes_per):
+    r = bench.kernel_roofline(name, (6.0, 3), _wl(), "f32", 0)
+    peak, _ = bench.hbm_peak()
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(bytes_per * 1e8 / 2e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / peak)
+    assert r["traffic"] is None or r["traffic"] > 0
+
+
+def test_whole_job_rate_counts_every_rank():
+    # 4 ranks, 3 steps of 2e9 units each, 6 s on the slowest rank
+    assert bench.whole_job_rate(2e9, 3, 4, 6.0) == pytest.approx(4e9)
