@@ -38,3 +38,24 @@ def test_float_kernels_count_their_block_bytes_against_hbm(name, bytes_per):
 def test_whole_job_rate_counts_every_rank():
     # 4 ranks, 3 steps of 2e9 units each, 6 s on the slowest rank
     assert bench.whole_job_rate(2e9, 3, 4, 6.0) == pytest.approx(4e9)
+
+
+def test_clock_sampler_reads_the_median_clock_and_the_active_reasons(tmp_path):
+    path = tmp_path / "clocks.csv"
+    path.write_text("\n".join([
+        "0, 2070, 2070, 640.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 700.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+    ]) + "\n")
+
+    class DoneProcess:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+    s = bench.ClockSampler(0)
+    s.proc, s.path = DoneProcess(), str(path)
+    out = s.stop()
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
