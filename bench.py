@@ -771,7 +771,7 @@ def run_density_scf(args):
 def run_md_compare(args):
     """Iterations per MD step with the atomic and the extrapolated starting D."""
     import workloads as w
-    from paper_2507_23612_gb300.warmstart import trajectory_scf
+    from paper_2507_23612_gb300.md import trajectory_scf
     from paper_2507_23612_gb300.warmstart import OccupationModel, scf_solve
     steps = w.rutile_trajectory((2, 2, 3), nsteps=args.md_compare, amplitude=0.1, period=12.0)
     # the occupation model, trained on SCF solutions of displaced cells off the trajectory

@@ -14,7 +14,7 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 from paper_2507_23612_gb300 import HUB_F32  # noqa: E402
-from paper_2507_23612_gb300.warmstart import trajectory_scf  # noqa: E402
+from paper_2507_23612_gb300.md import trajectory_scf  # noqa: E402
 
 
 def test_extrapolated_and_atomic_starts_reach_the_same_fixed_points():
@@ -34,7 +34,8 @@ def test_extrapolated_and_atomic_starts_reach_the_same_fixed_points():
 
 
 def test_resume_from_a_checkpoint_reaches_the_same_fixed_point(tmp_path):
-    from paper_2507_23612_gb300.warmstart import load_scf_checkpoint, save_scf_checkpoint, scf_solve
+    from paper_2507_23612_gb300.md import load_scf_checkpoint, save_scf_checkpoint
+    from paper_2507_23612_gb300.warmstart import scf_solve
     wl = w.rutile_snapshot((1, 1, 2), 0.1, seed=5)
     full = scf_solve(wl, HUB_F32, tol_e_atom=1e-6)
     part = scf_solve(wl, HUB_F32, tol_e_atom=1e-6, max_iter=4, keep_orbitals=True)

@@ -90,7 +90,7 @@ def test_trajectory_driver_orchestration_on_the_cpu(lib):
     # the extrapolation of the previous converged D (checked against the oracle's formula)
     # and from the previous orbitals, and reaches the same fixed point as the atomic start
     import workloads as w
-    from paper_2507_23612_gb300.warmstart import trajectory_scf
+    from paper_2507_23612_gb300.md import trajectory_scf
     steps = w.rutile_trajectory((1, 1, 1), nsteps=4, amplitude=0.1, period=12.0, h_target=0.55,
                                 occ_per_atom=2.0, nspin=1)
 

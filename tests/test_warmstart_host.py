@@ -37,7 +37,7 @@ def test_rutile_snapshots_are_seeded_and_displaced():
 
 
 def test_scf_checkpoint_roundtrip(tmp_path):
-    from paper_2507_23612_gb300.warmstart import load_scf_checkpoint, save_scf_checkpoint
+    from paper_2507_23612_gb300.md import load_scf_checkpoint, save_scf_checkpoint
     rng = np.random.default_rng(0)
     Xs = [rng.standard_normal((4, 30)) for _ in range(2)]
     D = rng.standard_normal((2, 3, 5, 5))
