@@ -2,7 +2,10 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#if __has_include(<nvtx3/nvToolsExt.h>)
 #include <nvtx3/nvToolsExt.h>
+#define HUB_HAVE_NVTX 1
+#endif
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -181,10 +184,14 @@ struct ProfScope {
 int ensure(hub_t h, void** p, size_t* have, size_t need);
 
 // An NVTX range around one ABI call (visible to Nsight tools; without a tool attached the
-// calls return at once)
+// calls return at once; compiled out where the toolkit has no NVTX headers)
 struct NvtxRange {
+#ifdef HUB_HAVE_NVTX
     explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
     ~NvtxRange() { nvtxRangePop(); }
+#else
+    explicit NvtxRange(const char*) {}   // toolkits without the NVTX headers: no ranges
+#endif
     NvtxRange(const NvtxRange&) = delete;
     NvtxRange& operator=(const NvtxRange&) = delete;
 };
