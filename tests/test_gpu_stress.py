@@ -99,3 +99,22 @@ def test_scf_forces_and_stress_of_the_converged_state():
         sig_ref += o.hubbard_stress(H, wl.atoms, X, occ[s], 1.0)
     assert rel(F, F_ref) < 1e-10
     assert rel(sig, sig_ref) < 1e-10
+
+
+def test_full_size_rutile_forces_on_sampled_orbitals():
+    # the benchmarked rutile 2x2x3 grid (88x88x84, 24 Hubbard Ti): forces of a few orbitals
+    # against the oracle on the same orbitals (FP64)
+    wl = w.rutile()
+    cols = 6
+    X = w.random_orbitals(wl.Nd, cols, 321).T                  # (Nd, cols)
+    X = X / np.sqrt(wl.dV * np.sum(X * X, axis=0))
+    f = np.linspace(1.0, 0.3, cols)
+    H = oracle_ham(wl, D=wl.D0[0])
+    ref_hub = o.hubbard_forces(H, X, f, 1.0)
+    hub_atoms = [i for i, a in enumerate(wl.atoms) if a.hub_l >= 0]
+    ref = np.zeros((len(wl.atoms), 3))
+    ref[hub_atoms] = ref_hub
+    hb = make_hub(wl, HUB_F64)
+    hb.set_occupation_matrix(0, wl.D0[0])
+    F = hb.hubbard_forces(0, to_dev(X.T, hb.dtype), f, 1.0)
+    assert rel(F, ref) < 1e-10
