@@ -174,3 +174,21 @@ def test_density_scf_from_a_given_starting_density():
         runs.append(hb.scf_run())
     assert runs[0]["iter"] == runs[1]["iter"]
     assert abs(runs[0]["E"] - runs[1]["E"]) < 1e-12
+
+
+def test_full_size_poisson_and_kerker_on_the_rutile_grid():
+    # the benchmarked 88x88x84 grid: V_H and the Kerker image of a seeded density against the
+    # oracle's exact Fourier solutions
+    wl = w.rutile()
+    g = o.Grid(wl.n, wl.L)
+    rng = np.random.default_rng(12)
+    rho = rng.uniform(0.0, 0.2, wl.Nd)
+    hb = make_hub(wl, HUB_F64)
+    V = torch.zeros(wl.Nd, dtype=torch.float64, device=DEV)
+    it, eh = hb.hartree(_dev64(rho), V, tol=1e-12)
+    print("Poisson CG iterations", it)
+    assert rel(V.cpu().numpy(), ds.hartree_potential(rho, g)) < 1e-9
+    z = torch.empty(wl.Nd, dtype=torch.float64, device=DEV)
+    it = hb.kerker(_dev64(rho - rho.mean()), z, 0.5, tol=1e-12)
+    print("Kerker CG iterations", it)
+    assert rel(z.cpu().numpy(), ds.kerker(rho - rho.mean(), g, 0.5)) < 1e-9
