@@ -3,8 +3,7 @@ with the CPU oracle: the density of a block, the FD Poisson solve of the Hartree
 local-density exchange, the Kerker preconditioner, and the SCF's fixed point (energy,
 eigenvalues, D, density) for one and two spin channels.
 
-Marked gpu_pending: this code has not run on a GPU yet; the marker moves to gpu after its
-first GPU run.  Tolerances: density and exchange are elementwise FP64 sums (1e-13
+Tolerances: density and exchange are elementwise FP64 sums (1e-13
 relative); the CG solves stop at a 1e-12 relative residual, so V_H and the Kerker output
 agree with the oracle's exact Fourier solution to 1e-9 relative; the SCF fixed points agree
 to the SCF's own tolerances (the two sides mix with different Pulay solvers, so their
@@ -17,7 +16,7 @@ from oracle import hubbard as o
 from oracle import density_scf as ds
 from hubtest import make_hub, to_dev, rel
 
-pytestmark = pytest.mark.gpu_pending
+pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)

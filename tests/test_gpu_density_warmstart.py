@@ -1,10 +1,7 @@
 """Density warm start of the self-consistent density SCF, end to end on the GPU: the density
 basis fit through the library's projector products against the oracle's fit, and a
 per-species model trained on converged densities of displaced cells, whose predicted
-starting density leads the SCF to the cold start's fixed point.
-
-Marked gpu_pending: this code has not run on a GPU yet; the marker moves to gpu after its
-first GPU run."""
+starting density leads the SCF to the cold start's fixed point."""
 import numpy as np
 import pytest
 
@@ -12,7 +9,7 @@ import workloads as w
 from oracle import hubbard as o
 from oracle import density_scf as ds
 
-pytestmark = pytest.mark.gpu_pending
+pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)

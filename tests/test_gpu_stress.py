@@ -2,8 +2,7 @@
 real and Bloch orbitals, FP64 and float handles, a cell small enough that periodic images
 of one atom overlap, and the sum over blocks.
 
-Marked gpu_pending: this code has not run on a GPU yet; the marker moves to gpu after its
-first GPU run.  Tolerance: FP64 1e-10 relative (norm of the difference over the norm of the
+Tolerance: FP64 1e-10 relative (norm of the difference over the norm of the
 oracle's tensor); float handles 1e-4 (float gradient and products)."""
 import numpy as np
 import pytest
@@ -12,7 +11,7 @@ import workloads as w
 from oracle import hubbard as o
 from hubtest import make_hub, oracle_ham, to_dev, rel
 
-pytestmark = pytest.mark.gpu_pending
+pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)

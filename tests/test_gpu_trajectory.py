@@ -1,14 +1,11 @@
 """SCF along a seeded MD trajectory (Sec. II.B, last paragraph): starting D from the atomic
 guess or from the second-order extrapolation of the previous steps, the previous orbitals
-reused.  Both reach the same fixed point at every step; the iteration counts are reported.
-
-Marked gpu_pending: this code has not run on a GPU yet; the marker moves to gpu after its
-first GPU run."""
+reused.  Both reach the same fixed point at every step; the iteration counts are reported."""
 import pytest
 
 import workloads as w
 
-pytestmark = pytest.mark.gpu_pending
+pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
