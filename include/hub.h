@@ -57,8 +57,9 @@ typedef enum {
 typedef enum {
     HUB_F64 = 0,          /* every step in double */
     HUB_F32 = 1,          /* filter and Rayleigh-Ritz products in float; dense steps double */
-    HUB_MIXED_BF16 = 2    /* float filter, BF16 tensor-core X^T H X and X Q with float
-                             accumulation; Gram, Cholesky, eigensolve, D and E_U double */
+    HUB_MIXED_BF16 = 2    /* float filter; X^T X (always the hi/lo BF16 split), X^T H X and
+                             X Q as BF16 tensor-core products with float accumulation;
+                             Cholesky, eigensolve, D and E_U double */
 } hub_prec;
 
 /* Create a handle for one grid, one Bloch wavevector and one precision.
@@ -139,20 +140,24 @@ int hub_chefsi_filter(hub_t h, int spin, void* X, int ncol, int ld, int degree,
 /* Cholesky Rayleigh-Ritz in place (CheFSI, Sec. II.B):
  *   S = <X|X> = L L^H;  H^ = L^-1 <X|H|X> L^-H;  H^ = V diag(eig) V^H;  X <- X L^-H V.
  * eig_host: host double [ncol], ascending.  work: device scratch >= ld*ncol elements or
- * NULL (handle-owned).  Real orbitals only (ncomplex = 0).
+ * NULL (handle-owned).  Real orbitals (Gamma point) and complex Bloch orbitals (ncomplex =
+ * 1: S and H^ are Hermitian, L is complex lower triangular with a real diagonal and the
+ * eigensolver is a complex Jacobi).  HUB_MIXED_BF16 handles take the block products of a
+ * complex block in float on CUDA cores (the BF16 tensor-core products are real only).
  * Errors: HUB_ENOTSPD (X rank-deficient), HUB_ENOCONV (Jacobi sweep limit),
  * HUB_ETIMEOUT, HUB_EINVAL. */
 int hub_rayleigh_ritz(hub_t h, int spin, void* X, int ncol, int ld, double* eig_host,
                       void* work);
 
-/* Block product of Rayleigh-Ritz (CheFSI, Sec. II.B): G = alpha * A^T B for two real
- * column blocks A [ld x ncol_a] and B [ld x ncol_b] (device, handle element type), summed
- * over the Nd grid rows; with alpha = dV this is the overlap <A|B> (the Gram matrix
- * S = <X|X>, or <X|HX> with B = H X).  G_dev: device double, row-major
- * [ncol_a x ncol_b], overwritten.  When A == B and ncol_a == ncol_b only the upper tiles
- * are computed and mirrored.  On HUB_MIXED_BF16 handles the product runs on the BF16
+/* Block product of Rayleigh-Ritz (CheFSI, Sec. II.B): G = alpha * A^H B for two column
+ * blocks A [ld x ncol_a] and B [ld x ncol_b] (device, handle element type), summed over the
+ * Nd grid rows; with alpha = dV this is the overlap <A|B> (the Gram matrix S = <X|X>, or
+ * <X|HX> with B = H X).  G_dev: device, row-major [ncol_a x ncol_b], overwritten: double
+ * on a real handle, complex double (interleaved re/im, 2 * ncol_a * ncol_b doubles) on a
+ * complex one.  When A == B and ncol_a == ncol_b only the upper tiles are computed and
+ * mirrored (conjugated).  On real HUB_MIXED_BF16 handles the product runs on the BF16
  * tensor cores (see hub_set_bf16_terms) with float accumulation.  Uses handle-owned
- * split-K scratch (allocated on first use).  Real orbitals only.  Errors: HUB_EINVAL. */
+ * split-K scratch (allocated on first use).  Errors: HUB_EINVAL. */
 int hub_gram(hub_t h, const void* A, int ncol_a, const void* B, int ncol_b, int ld,
              double alpha, double* G_dev);
 
@@ -330,6 +335,40 @@ int hub_scf_get(hub_t h, double* eig, double* occ, double* D_out);
  * D_out (the occupation of those orbitals), which becomes the handle's occupation matrix.
  * F_host host [natoms * 3]; sigma_host NULL or host [9].  Synchronises. */
 int hub_scf_forces(hub_t h, double* F_host, double* sigma_host);
+
+/* SCF with Brillouin-zone sampling over one handle per k-point (Eq. orbital_occup_ext:
+ * D = sum_k w_k D_k; Sec. II.B: D updated and Pulay-mixed every iteration).  The handles
+ * share the grid, the atoms, V_eff and the precision; each carries its own Bloch vector
+ * (real handles for Gamma).  One Fermi level spans every (spin, k) state, each weighted
+ * by w_k; every k-point's Hamiltonian carries the same D, complex Hermitian in general
+ * (its real and imaginary parts are Pulay-mixed as one real vector); a real handle needs
+ * a real D, so a k-set holding Gamma must be closed under k -> -k.  Per iteration and
+ * channel: filter + Rayleigh-Ritz (first_passes in the first iteration; bounds as for
+ * hub_scf_iterate), then D_out, the energy
+ *   E = sum_{s,k,n} deg w_k f eig - sum Re Tr(M_in D_out) + E_U(D_out) - kT S,
+ *   M_in = (U/2)(I - 2 D_in), deg = 2 for one spin channel, else 1,
+ * and the convergence test of hub_scf_iterate (natoms, tol_e_atom, tol_D).
+ * hubs[nk]: the handles (not owned; they must outlive the object); kweights[nk] >= 0,
+ * summing to 1 (within 1e-12); p: as for hub_scf_begin (density must be 0; ladder
+ * unused); X[nspin*nk] and v0[nspin*nk] device blocks / Lanczos vectors of each channel,
+ * index s*nk + k, in the element type of handle k (updated in place); D0_re host
+ * [nspin*nhub*25], D0_im NULL (zero) or host of the same shape.
+ * Errors: HUB_EINVAL (bad arguments, handles that disagree). */
+typedef struct hub_kscf* hub_kscf_t;
+int hub_kscf_create(hub_kscf_t* out, int nk, hub_t const* hubs, const double* kweights,
+                    const hub_scf_params* p, void* const* X, const void* const* v0,
+                    const double* D0_re, const double* D0_im);
+/* One iteration; fills *res (E, E_band, E_U, dE, dD, mu, iter, converged).  Synchronises.
+ * Errors: a handle's status (its message in hub_kscf_last_error); HUB_EINVAL when a real
+ * handle would get a D with an imaginary part above 1e-10. */
+int hub_kscf_iterate(hub_kscf_t s, hub_scf_result* res);
+/* Iterations until converged or max_iter (then HUB_ENOCONV). */
+int hub_kscf_run(hub_kscf_t s, hub_scf_result* res);
+/* Last iteration: eig, occ host [nspin*nk*ncol] (channel s*nk + k), D_re, D_im host
+ * [nspin*nhub*25] (D_out); any may be NULL. */
+int hub_kscf_get(hub_kscf_t s, double* eig, double* occ, double* D_re, double* D_im);
+const char* hub_kscf_last_error(hub_kscf_t s);
+int hub_kscf_destroy(hub_kscf_t s);
 
 /* Self-consistent density SCF: replace the starting density (uniform by default) before the
  * first iteration; rho_dev device double [Nd], the total density (split evenly between two

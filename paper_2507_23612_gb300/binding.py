@@ -71,6 +71,13 @@ _SIGS = {
     "hub_project": [_P, _P, _I, _I, _PD],
     "hub_expand": [_P, _PD, _I, _P, _I, _D],
     "hub_scf_forces": [_P, _PD, _PD],
+    "hub_kscf_create": [C.POINTER(C.c_void_p), _I, C.POINTER(C.c_void_p), _PD, C.POINTER(scf_params),
+                        C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), _PD, _PD],
+    "hub_kscf_iterate": [_P, C.POINTER(scf_result)],
+    "hub_kscf_run": [_P, C.POINTER(scf_result)],
+    "hub_kscf_get": [_P, _PD, _PD, _PD, _PD],
+    "hub_kscf_last_error": [_P],
+    "hub_kscf_destroy": [_P],
     "hub_extrapolate_occupations": [_I, _I, _PD, _PD, _I, _PD, _PD, _PD],
     "hub_cutoff_radius": [_I, _D, _D, _PD],
     "hub_fermi_dirac": [_I, _PD, _PD, _D, _D, _D, _PD, _PD],
@@ -144,7 +151,7 @@ def load_library(path: str | None = None) -> C.CDLL:
     for name, args in _SIGS.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = C.c_char_p if name in ("hub_last_error", "hub_mlp_last_error") else C.c_int
+        fn.restype = C.c_char_p if name in ("hub_last_error", "hub_mlp_last_error", "hub_kscf_last_error") else C.c_int
     if path is None:
         _LIB = lib
     return lib
@@ -296,11 +303,12 @@ class Hub:
         return eig
 
     def gram(self, A, B, alpha: float, G):
-        """G (device double [ncol_a, ncol_b]) = alpha * A B^T for row-stored blocks."""
+        """G (device [ncol_a, ncol_b], float64; complex128 on a complex handle) =
+        alpha * conj(A) B^T for row-stored blocks."""
         import torch
         na, ld = self._blk(A, "gram A")
         nb, ldb = self._blk(B, "gram B")
-        self._vec(G, torch.float64, "gram G", na * nb)
+        self._vec(G, torch.complex128 if self.complex else torch.float64, "gram G", na * nb)
         if ld != ldb:
             raise ValueError("A and B need the same leading dimension")
         self._check(self.lib.hub_gram(self.h, _tptr(A), na, _tptr(B), nb, ld, float(alpha), _tptr(G)),

@@ -332,17 +332,22 @@ int hub_chefsi_filter(hub_t h, int spin, void* X, int ncol, int ld, int degree, 
 
 namespace hub {
 // Rayleigh-Ritz in two halves around the subspace eigensolve, so that the SCF can solve the
-// two spin channels' eigenproblems in one launch.  ws: 6 n^2 + n doubles (S, Hs, Linv, T, Vs,
-// Q, eig); HX: a block like X.
+// two spin channels' eigenproblems in one launch.  ws: 6 n x n matrices + n doubles (S, Hs,
+// Linv, T, Vs, Q, eig; each matrix n^2 doubles, or n^2 double2 on a complex handle); HX: a
+// block like X.  Complex (Bloch) blocks: S = dV X^H X = L L^H, Hs = dV X^H HX, H^ = L^-1 Hs
+// L^-H (Hermitian), H^ = V diag(eig) V^H, X <- X L^-H V.
+static size_t rr_mat(hub_t h, int n) { return (size_t)n * n * (h->cplx ? 2 : 1); }
+static size_t rr_ws_doubles(hub_t h, int n) { return 6 * rr_mat(h, n) + n; }
+
 static int rr_prepare(hub_t h, int spin, void* X, int n, int ld, void* HX, double* ws) {
-    const size_t nn = (size_t)n * n;
+    const size_t nn = rr_mat(h, n);
     double* S = ws;
     double* Hs = S + nn;
     double* Linv = Hs + nn;
     double* T = Linv + nn;
     int rc;
     if ((rc = apply_H_internal(h, spin, X, ld, HX, n, 1.0, 0.0, nullptr, 0.0))) return rc;
-    const bool tensor = (h->prec == HUB_MIXED_BF16) && h->bf16_terms > 0;
+    const bool tensor = (h->prec == HUB_MIXED_BF16) && h->bf16_terms > 0 && !h->cplx;
     if (tensor) {
         // the Gram matrix feeds the Cholesky factor: always the hi/lo split (about 16
         // significand bits)
@@ -365,14 +370,14 @@ static int rr_prepare(hub_t h, int spin, void* X, int n, int ld, void* HX, doubl
 }
 
 static int rr_finish(hub_t h, void* X, int n, int ld, void* HX, double* ws, double* eig_host) {
-    const size_t nn = (size_t)n * n;
+    const size_t nn = rr_mat(h, n);
     double* Linv = ws + 2 * nn;
     double* Vs = ws + 4 * nn;
     double* Q = ws + 5 * nn;
     double* eig = ws + 6 * nn;
     int rc;
     if ((rc = dense_gemm(h, true, false, n, n, n, 1.0, Linv, n, Vs, n, 0.0, Q, n))) return rc;
-    if ((h->prec == HUB_MIXED_BF16) && h->bf16_terms > 0) {
+    if ((h->prec == HUB_MIXED_BF16) && h->bf16_terms > 0 && !h->cplx) {
         if ((rc = launch_rotate_bf16(h, X, ld, Q, n, n, HX, ld))) return rc;
     } else {
         if ((rc = launch_rotate(h, X, ld, Q, n, n, HX, ld))) return rc;
@@ -388,7 +393,7 @@ static int rr_finish(hub_t h, void* X, int n, int ld, void* HX, double* ws, doub
 // Rayleigh-Ritz of both spin channels (blocks X[0], X[1] of the same shape): the two
 // subspace eigenproblems are solved in one cooperative launch, half the SMs each.
 static int rr_two_spins(hub_t h, void* const* X, int n, int ld, double* const* eig_host) {
-    const size_t nn = (size_t)n * n, wsz = 6 * nn + n;
+    const size_t nn = rr_mat(h, n), wsz = rr_ws_doubles(h, n);
     const size_t blk = (size_t)ld * n * elem_bytes(h);
     int rc;
     if ((rc = ensure(h, &h->d_work, &h->work_bytes, std::max(2 * blk, h->work_bytes)))) return rc;
@@ -412,7 +417,6 @@ int hub_rayleigh_ritz(hub_t h, int spin, void* X, int ncol, int ld, double* eig_
     hub::NvtxRange nvtx_("hub_rayleigh_ritz");
     int rc = check_block(h, spin, X, ncol, ld);
     if (rc) return rc;
-    if (h->cplx) return fail(h, HUB_EINVAL, "Rayleigh-Ritz supports real orbitals only");
     if (ncol > 0 && !eig_host) return fail(h, HUB_EINVAL, "NULL eigenvalue output");
     if (ncol == 0) return HUB_OK;
     const int n = ncol;
@@ -421,8 +425,8 @@ int hub_rayleigh_ritz(hub_t h, int spin, void* X, int ncol, int ld, double* eig_
         if ((rc = ensure(h, &h->d_work, &h->work_bytes, (size_t)ld * ncol * elem_bytes(h)))) return rc;
         HX = h->d_work;
     }
-    const size_t nn = (size_t)n * n;
-    if ((rc = ensure(h, &h->d_small, &h->small_bytes, (6 * nn + n) * sizeof(double)))) return rc;
+    const size_t nn = rr_mat(h, n);
+    if ((rc = ensure(h, &h->d_small, &h->small_bytes, rr_ws_doubles(h, n) * sizeof(double)))) return rc;
     double* ws = (double*)h->d_small;
     if ((rc = rr_prepare(h, spin, X, n, ld, HX, ws))) return rc;
     if ((rc = dense_jacobi_eigh(h, ws + nn, ws + 4 * nn, ws + 6 * nn, n))) return rc;
@@ -432,13 +436,12 @@ int hub_rayleigh_ritz(hub_t h, int spin, void* X, int ncol, int ld, double* eig_
 int hub_gram(hub_t h, const void* A, int ncol_a, const void* B, int ncol_b, int ld, double alpha,
              double* G_dev) {
     if (!h) return HUB_EINVAL;
-    if (h->cplx) return fail(h, HUB_EINVAL, "hub_gram supports real orbitals only");
     if (ncol_a < 0 || ncol_b < 0) return fail(h, HUB_EINVAL, "negative column count");
     if ((long)ld < h->Nd) return fail(h, HUB_EINVAL, "ld must be >= n1*n2*n3");
     if (ncol_a == 0 || ncol_b == 0) return HUB_OK;
     if (!A || !B || !G_dev) return fail(h, HUB_EINVAL, "NULL pointer");
     const bool sym = (A == B) && (ncol_a == ncol_b);
-    if (h->prec == HUB_MIXED_BF16 && h->bf16_terms > 0)
+    if (h->prec == HUB_MIXED_BF16 && h->bf16_terms > 0 && !h->cplx)
         return launch_gram_bf16(h, A, ld, B, ld, ncol_a, ncol_b, alpha, sym, G_dev);
     return launch_gram(h, A, ld, B, ld, ncol_a, ncol_b, alpha, sym, G_dev);
 }
@@ -669,7 +672,10 @@ static void fermi_dirac(const std::vector<double>& e, double kT, double nel, dou
     for (size_t i = 0; i < n; ++i) f[i] = 0.5 * (1.0 - std::tanh((e[i] - mu) / (2.0 * kT)));
 }
 
-static double fd_entropy(const std::vector<double>& f) {
+}  // extern "C"
+
+namespace hub {
+double fd_entropy(const std::vector<double>& f) {
     double s = 0.0;
     for (double x : f) {
         const double a = std::min(std::max(x, 1e-300), 1.0 - 1e-16);
@@ -681,7 +687,7 @@ static double fd_entropy(const std::vector<double>& f) {
 
 // Pulay / DIIS coefficients: minimise |sum c_i r_i| subject to sum c_i = 1, from the k x k
 // Gram matrix A (row-major) of the residuals.  false when the bordered system is singular.
-static bool pulay_solve(const std::vector<double>& G, int k, std::vector<double>& coef) {
+bool pulay_solve(const std::vector<double>& G, int k, std::vector<double>& coef) {
     coef.assign(k, 0.0);
     if (k < 2) return false;
     const int m = k + 1;
@@ -717,6 +723,10 @@ static bool pulay_solve(const std::vector<double>& G, int k, std::vector<double>
     for (int i = 0; i < k; ++i) coef[i] = x[i];
     return true;
 }
+
+}  // namespace hub
+
+extern "C" {
 
 // pushes (xin, xout - xin) into the D history (at most pulay_history entries)
 static void pulay_push(ScfState& st, const std::vector<double>& xin, const std::vector<double>& xout) {

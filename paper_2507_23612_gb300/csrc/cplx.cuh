@@ -65,6 +65,26 @@ __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc) {
     return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
 }
 
+// conj(a); real part; modulus; a - b; a / r for real r; a real value in T
+__device__ __forceinline__ double cconj(double a) { return a; }
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double re_of(double a) { return a; }
+__device__ __forceinline__ double re_of(double2 a) { return a.x; }
+__device__ __forceinline__ double cabs_of(double a) { return fabs(a); }
+__device__ __forceinline__ double cabs_of(double2 a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ double csub(double a, double b) { return a - b; }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double divr(double a, double r) { return a / r; }
+__device__ __forceinline__ double2 divr(double2 a, double r) { return make_double2(a.x / r, a.y / r); }
+template <typename T> __device__ __forceinline__ T from_real(double v);
+template <> __device__ __forceinline__ double from_real<double>(double v) { return v; }
+template <> __device__ __forceinline__ double2 from_real<double2>(double v) { return make_double2(v, 0.0); }
+// shuffle-down of a real or complex value
+__device__ __forceinline__ double shfl_down(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double2 shfl_down(double2 v, int o) {
+    return make_double2(__shfl_down_sync(0xffffffffu, v.x, o), __shfl_down_sync(0xffffffffu, v.y, o));
+}
+
 __device__ __forceinline__ bool finite_val(double a) { return isfinite(a); }
 __device__ __forceinline__ bool finite_val(float a) { return isfinite(a); }
 __device__ __forceinline__ bool finite_val(double2 a) { return isfinite(a.x) && isfinite(a.y); }

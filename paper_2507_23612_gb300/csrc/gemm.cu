@@ -1,9 +1,12 @@
 // Rayleigh-Ritz block products (CheFSI, Sec. II.B) on CUDA cores:
-//   Gram / projected Hamiltonian  G = alpha * A^T B   (A, B tall: Nd x m, Nd x n)
+//   Gram / projected Hamiltonian  G = alpha * A^H B   (A, B tall: Nd x m, Nd x n)
 //   rotation                      Y = X Q             (X tall: Nd x k, Q small k x n)
-// The tall dimension is split over CTAs (split-K); every CTA writes a double partial tile
-// and a second kernel sums the partials in a fixed order (deterministic).
+// Real blocks (Gamma point) and complex blocks (Bloch orbitals, interleaved re/im; G and Q
+// then complex double2) share the kernels.  The tall dimension is split over CTAs (split-K);
+// every CTA writes a double partial tile and a second kernel sums the partials in a fixed
+// order (deterministic).
 #include <mutex>
+#include <type_traits>
 
 #include "hub_internal.cuh"
 #include "cplx.cuh"
@@ -14,13 +17,27 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16;
 
-// partial[z][i][j] = sum_{k in chunk z} A[k, i] B[k, j] over TB x TB tiles; (TB/4)^2
+// the double type a working-type element accumulates into across splits
+template <typename T> struct Wide { using type = double; };
+template <> struct Wide<float2> { using type = double2; };
+template <> struct Wide<double2> { using type = double2; };
+__device__ __forceinline__ double widen(float a) { return (double)a; }
+__device__ __forceinline__ double widen(double a) { return a; }
+__device__ __forceinline__ double2 widen(float2 a) { return make_double2(a.x, a.y); }
+__device__ __forceinline__ double2 widen(double2 a) { return a; }
+// a double (complex) coefficient in the working type
+template <typename T> __device__ __forceinline__ T narrow(double a) { return (T)a; }
+template <typename T> __device__ __forceinline__ T narrow(double2 a);
+template <> __device__ __forceinline__ float2 narrow<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+template <> __device__ __forceinline__ double2 narrow<double2>(double2 a) { return a; }
+
+// partial[z][i][j] = sum_{k in chunk z} conj(A[k, i]) B[k, j] over TB x TB tiles; (TB/4)^2
 // threads, 4 x 4 outputs each.  Smaller tiles waste less on the ragged edge and on the
 // diagonal tiles of a symmetric product.
 template <typename T, int TB>
 __global__ void __launch_bounds__((TB / 4) * (TB / 4))
 k_gram_partial(const T* __restrict__ A, int lda, const T* __restrict__ B, int ldb, long K, int m,
-               int n, long chunk, int tn, int sym, double* __restrict__ part) {
+               int n, long chunk, int tn, int sym, typename Wide<T>::type* __restrict__ part) {
     constexpr int TT = TB / 4, NTH = TT * TT;
     __shared__ T As[BK][TB + 1];
     __shared__ T Bs[BK][TB + 1];
@@ -30,19 +47,20 @@ k_gram_partial(const T* __restrict__ A, int lda, const T* __restrict__ B, int ld
     const long k0 = (long)blockIdx.y * chunk;
     const long k1 = min(K, k0 + chunk);
     const int tx = threadIdx.x % TT, ty = threadIdx.x / TT;
+    const T zero = zero_of(T());
     T acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+        for (int b = 0; b < 4; ++b) acc[a][b] = zero;
     for (long kb = k0; kb < k1; kb += BK) {
         // TB columns x 16 rows of each operand; k is the contiguous index
         for (int e = threadIdx.x; e < BK * TB; e += NTH) {
             const int kk = e % BK, ii = e / BK;
             const long k = kb + kk;
             const int i = i0 + ii, j = j0 + ii;
-            As[kk][ii] = (k < k1 && i < m) ? A[(size_t)i * lda + k] : (T)0;
-            Bs[kk][ii] = (k < k1 && j < n) ? B[(size_t)j * ldb + k] : (T)0;
+            As[kk][ii] = (k < k1 && i < m) ? A[(size_t)i * lda + k] : zero;
+            Bs[kk][ii] = (k < k1 && j < n) ? B[(size_t)j * ldb + k] : zero;
         }
         __syncthreads();
 #pragma unroll
@@ -53,55 +71,59 @@ k_gram_partial(const T* __restrict__ A, int lda, const T* __restrict__ B, int ld
 #pragma unroll
             for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+                for (int c = 0; c < 4; ++c) acc[r][c] = cfma_conj(a[r], b[c], acc[r][c]);
         }
         __syncthreads();
     }
-    double* P = part + (size_t)blockIdx.y * m * n;
+    typename Wide<T>::type* P = part + (size_t)blockIdx.y * m * n;
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int i = i0 + ty + TT * r, j = j0 + tx + TT * c;
-            if (i < m && j < n) P[(size_t)i * n + j] = (double)acc[r][c];
+            if (i < m && j < n) P[(size_t)i * n + j] = widen(acc[r][c]);
         }
 }
 
-__global__ void k_gram_reduce(const double* __restrict__ part, int splits, int m, int n, double alpha,
-                              int sym, int tb, double* __restrict__ G) {
+// G = alpha * sum of the partials; a symmetric (Hermitian) product mirrors the lower blocks
+template <typename PT>
+__global__ void k_gram_reduce(const PT* __restrict__ part, int splits, int m, int n, double alpha,
+                              int sym, int tb, PT* __restrict__ G) {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long)m * n) return;
     int i = (int)(t / n), j = (int)(t % n);
-    if (sym && (i / tb) > (j / tb)) {   // lower blocks were not computed: mirror
+    const bool mirror = sym && (i / tb) > (j / tb);
+    if (mirror) {                        // lower blocks were not computed
         const int tmp = i; i = j; j = tmp;
     }
-    double s = 0.0;
-    for (int z = 0; z < splits; ++z) s += part[(size_t)z * m * n + (size_t)i * n + j];
-    G[t] = alpha * s;
+    PT s = zero_of(PT());
+    for (int z = 0; z < splits; ++z) s = add(s, part[(size_t)z * m * n + (size_t)i * n + j]);
+    G[t] = mulr(alpha, mirror ? cconj(s) : s);
 }
 
-// Y[r, j] = sum_kk X[r, kk] Q[kk, j]; Q row-major double [k x n]
+// Y[r, j] = sum_kk X[r, kk] Q[kk, j]; Q row-major double (complex: double2) [k x n]
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_rotate(const T* __restrict__ X, int ldx, const double* __restrict__ Q, int k, int n, long K,
+k_rotate(const T* __restrict__ X, int ldx, const typename Wide<T>::type* __restrict__ Q, int k, int n, long K,
          T* __restrict__ Y, int ldy) {
     __shared__ T Xs[BK][BM + 1];
     __shared__ T Qs[BK][BN + 1];
     const long r0 = (long)blockIdx.x * BM;
     const int j0 = blockIdx.y * BN;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const T zero = zero_of(T());
     T acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+        for (int b = 0; b < 4; ++b) acc[a][b] = zero;
     for (int kb = 0; kb < k; kb += BK) {
         for (int e = threadIdx.x; e < BK * BM; e += 256) {
             const int rr = e % BM, kk = e / BM;
             const long r = r0 + rr;
-            Xs[kk][rr] = (r < K && kb + kk < k) ? X[(size_t)(kb + kk) * ldx + r] : (T)0;
+            Xs[kk][rr] = (r < K && kb + kk < k) ? X[(size_t)(kb + kk) * ldx + r] : zero;
             const int jj = e % BN, kq = e / BN;
-            Qs[kq][jj] = (kb + kq < k && j0 + jj < n) ? (T)Q[(size_t)(kb + kq) * n + j0 + jj] : (T)0;
+            Qs[kq][jj] = (kb + kq < k && j0 + jj < n) ? narrow<T>(Q[(size_t)(kb + kq) * n + j0 + jj]) : zero;
         }
         __syncthreads();
 #pragma unroll
@@ -112,7 +134,7 @@ k_rotate(const T* __restrict__ X, int ldx, const double* __restrict__ Q, int k, 
 #pragma unroll
             for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+                for (int c = 0; c < 4; ++c) acc[r][c] = cfma(a[r], b[c], acc[r][c]);
         }
         __syncthreads();
     }
@@ -131,6 +153,7 @@ k_rotate(const T* __restrict__ X, int ldx, const double* __restrict__ Q, int k, 
 template <typename T, int TB>
 int gram_tiles(hub_t h, const void* A, int lda, const void* B, int ldb, int m, int n, double alpha,
                bool sym, double* G) {
+    using PT = typename Wide<T>::type;
     const int tm = (m + TB - 1) / TB, tn = (n + TB - 1) / TB;
     const long ntiles = sym ? (long)tm * (tm + 1) / 2 : (long)tm * tn;
     const long K = h->Nd;
@@ -141,9 +164,9 @@ int gram_tiles(hub_t h, const void* A, int lda, const void* B, int ldb, int m, i
     if (chunk < 4 * BK) chunk = 4 * BK;
     splits = (int)((K + chunk - 1) / chunk);
     int rc;
-    if ((rc = ensure(h, &h->d_gpart, &h->gpart_bytes, (size_t)splits * m * n * sizeof(double))))
+    if ((rc = ensure(h, &h->d_gpart, &h->gpart_bytes, (size_t)splits * m * n * sizeof(PT))))
         return rc;
-    double* part = (double*)h->d_gpart;
+    PT* part = (PT*)h->d_gpart;
     dim3 grid((unsigned)(tm * tn), splits);
     { ProfScope ps(h, HUB_K_GRAM);
     k_gram_partial<T, TB><<<grid, (TB / 4) * (TB / 4), 0, h->stream>>>((const T*)A, lda, (const T*)B, ldb, K, m, n,
@@ -151,8 +174,8 @@ int gram_tiles(hub_t h, const void* A, int lda, const void* B, int ldb, int m, i
     HUB_CUDA_TRY(h, cudaGetLastError());
     const long tot = (long)m * n;
     { ProfScope ps(h, HUB_K_GRAM_REDUCE);
-    k_gram_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(part, splits, m, n, alpha,
-                                                                        sym ? 1 : 0, TB, G); }
+    k_gram_reduce<PT><<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(part, splits, m, n, alpha,
+                                                                            sym ? 1 : 0, TB, (PT*)G); }
     HUB_CUDA_TRY(h, cudaGetLastError());
     return HUB_OK;
 }
@@ -170,18 +193,25 @@ int gram_t(hub_t h, const void* A, int lda, const void* B, int ldb, int m, int n
 
 int launch_gram(hub_t h, const void* A, int lda, const void* B, int ldb, int m, int n,
                 double alpha, bool sym, double* G) {
-    if (h->cplx) return fail(h, HUB_EINVAL, "Rayleigh-Ritz supports real orbitals only");
     if (m == 0 || n == 0) return HUB_OK;
+    if (h->cplx) {
+        if (h->esize == 8) return gram_t<double2>(h, A, lda, B, ldb, m, n, alpha, sym, G);
+        return gram_t<float2>(h, A, lda, B, ldb, m, n, alpha, sym, G);
+    }
     if (h->esize == 8) return gram_t<double>(h, A, lda, B, ldb, m, n, alpha, sym, G);
     return gram_t<float>(h, A, lda, B, ldb, m, n, alpha, sym, G);
 }
 
 int launch_rotate(hub_t h, const void* X, int ldx, const double* Q, int k, int n, void* Y, int ldy) {
-    if (h->cplx) return fail(h, HUB_EINVAL, "Rayleigh-Ritz supports real orbitals only");
     if (n == 0) return HUB_OK;
     dim3 grid((unsigned)((h->Nd + BM - 1) / BM), (n + BN - 1) / BN);
     ProfScope ps(h, HUB_K_ROTATE);
-    if (h->esize == 8)
+    const double2* Qz = (const double2*)Q;
+    if (h->cplx && h->esize == 8)
+        k_rotate<double2><<<grid, 256, 0, h->stream>>>((const double2*)X, ldx, Qz, k, n, h->Nd, (double2*)Y, ldy);
+    else if (h->cplx)
+        k_rotate<float2><<<grid, 256, 0, h->stream>>>((const float2*)X, ldx, Qz, k, n, h->Nd, (float2*)Y, ldy);
+    else if (h->esize == 8)
         k_rotate<double><<<grid, 256, 0, h->stream>>>((const double*)X, ldx, Q, k, n, h->Nd, (double*)Y, ldy);
     else
         k_rotate<float><<<grid, 256, 0, h->stream>>>((const float*)X, ldx, Q, k, n, h->Nd, (float*)Y, ldy);
@@ -248,8 +278,8 @@ int gram_noalloc_t(const void* A, int lda, const void* B, int ldb, long K, int m
                                                     sym ? 1 : 0, part);
     if (cudaGetLastError() != cudaSuccess) return HUB_ECUDA;
     const long tot = (long)m * n;
-    k_gram_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(part, (int)splits, m, n, alpha,
-                                                                     sym ? 1 : 0, BM, G);
+    k_gram_reduce<double><<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(part, (int)splits, m, n, alpha,
+                                                                             sym ? 1 : 0, BM, G);
     if (cudaGetLastError() != cudaSuccess) return HUB_ECUDA;
     return HUB_OK;
 }

@@ -277,6 +277,10 @@ int dense_symmetrize(hub_t h, double* A, int n);
 
 // api.cu: centred second-derivative weights of order 2 n0 (c0 and c_1..c_n0)
 void fd_laplacian_weights(int n0, double* c0, double* c);
+// api.cu: Fermi-Dirac entropy -sum f ln f + (1 - f) ln(1 - f) of occupations f; Pulay / DIIS
+// coefficients from the k x k Gram matrix of the residuals (false: bordered system singular)
+double fd_entropy(const std::vector<double>& f);
+bool pulay_solve(const std::vector<double>& G, int k, std::vector<double>& coef);
 
 // density.cu: reductions and vector algebra of the density SCF on [Nd] double vectors
 int density_sum(hub_t h, const double* x, double* out_host);

@@ -34,3 +34,19 @@ def to_dev(X_cols, dtype):
 
 def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+def rel_elem(a, b):
+    """Element-by-element error: max over elements of |a - b| divided by the RMS magnitude
+    of the reference row the element belongs to (one orbital of a [ncol, Nd] block, one row
+    of a matrix; a vector is one row).  A single wrong element stands out against its own
+    orbital's scale instead of being averaged into a whole-block norm."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    if b.ndim == 1:
+        a, b = a[None, :], b[None, :]
+    a = a.reshape(-1, a.shape[-1]) if a.ndim > 2 else a
+    b = b.reshape(-1, b.shape[-1]) if b.ndim > 2 else b
+    rms = np.sqrt(np.mean(np.abs(b) ** 2, axis=1))
+    scale = np.maximum(rms, 1e-300 + 1e-30 * float(np.max(rms)))
+    return float(np.max(np.max(np.abs(a - b), axis=1) / scale))

@@ -158,3 +158,24 @@ def test_binding_rejects_blocks_of_the_wrong_type_before_any_call():
     with pytest.raises(ValueError):
         hb._vec(torch.zeros(63, dtype=torch.float64), torch.float64, "v")  # too short
     hb.h = None                                                         # nothing to release
+
+
+def test_kpoint_scf_rejects_bad_arguments(lib):
+    from paper_2507_23612_gb300.binding import scf_params, scf_result
+    obj = C.c_void_p()
+    p = scf_params(nspin=1, ncol=4, ld=512, degree=8, max_iter=5, first_passes=1, lanczos_steps=10,
+                   pulay_history=7, natoms=1, pulay_beta=0.3, kT=0.01, n_elec=2.0, tol_e_atom=1e-5, tol_D=1e-4)
+    w = (C.c_double * 1)(1.0)
+    hs = (C.c_void_p * 1)(None)
+    xs = (C.c_void_p * 1)(None)
+    assert lib.hub_kscf_create(None, 1, hs, w, C.byref(p), xs, xs, None, None) == EINVAL
+    assert lib.hub_kscf_create(C.byref(obj), 0, hs, w, C.byref(p), xs, xs, None, None) == EINVAL
+    assert lib.hub_kscf_create(C.byref(obj), 1, hs, w, C.byref(p), xs, xs, None, None) == EINVAL   # NULL handle
+    assert lib.hub_kscf_create(C.byref(obj), 1, None, w, C.byref(p), xs, xs, None, None) == EINVAL
+    assert not obj.value
+    r = scf_result()
+    assert lib.hub_kscf_iterate(None, C.byref(r)) == EINVAL
+    assert lib.hub_kscf_run(None, C.byref(r)) == EINVAL
+    assert lib.hub_kscf_get(None, None, None, None, None) == EINVAL
+    assert lib.hub_kscf_destroy(None) == 0
+    assert lib.hub_kscf_last_error(None)

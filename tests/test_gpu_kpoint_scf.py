@@ -1,10 +1,10 @@
 """The SCF with Brillouin-zone sampling over one library handle per k-point against the
 oracle's k-point SCF: the Gamma point alone, a pair k, -k (real D), and one Bloch point
 (complex Hermitian D).  Both sides start from the same orbitals, Lanczos vectors and D0 and
-must reach the same fixed point.
-
-Marked gpu_pending: this code has not run on a GPU yet; the marker moves to gpu after its
-first GPU run."""
+must reach the same fixed point.  The whole driver (Fermi level over the k-weighted states,
+the Brillouin-zone average of D, the energy terms and Pulay) runs in the library
+(hub_kscf_*); the Python class only marshals handles and arrays.  Tolerances: E to 1e-9
+relative and D to 1e-6 (the SCF tolerances tol_e_atom = 1e-8 and tol_D = 1e-6)."""
 import numpy as np
 import pytest
 
@@ -12,7 +12,7 @@ import workloads as w
 from oracle import hubbard as o
 from hubtest import to_dev
 
-pytestmark = pytest.mark.gpu_pending
+pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
