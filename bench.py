@@ -33,9 +33,12 @@ DTYPE_NAME = {"f64": "f64", "f32": "f32", "mixed": "f32+bf16"}
 # FP64 pipe of one GB300: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (max SM clock)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 # algorithmic work per point-orbital of one stencil pass (12th order, symmetric pairing):
-# 18 adds + 18 FMAs for the 36 neighbours, 1 FMA for alpha*V + centre, 1 multiply, 1 FMA
-# for beta*Yprev  -> 18 + 36 + 2 + 1 + 2 = 59 flop; bytes: read Y, read Yprev, write Yout
-STENCIL_FLOP = 59.0
+# 3 axes x 6 pairs x (add + FMA) + centre + V_eff + the recurrence's axpby = 44 flop (the
+# count the roofline fraction uses).  Counting every FMA as two flops instead (18 adds and
+# 18 FMAs for the 36 neighbours, the centre and V_eff FMAs, one multiply, one FMA for
+# beta * Yprev) gives 59; both are reported.
+STENCIL_FLOP = 44.0
+STENCIL_FLOP_FMA2 = 59.0
 
 
 def parse():
@@ -52,8 +55,8 @@ def parse():
                     help="warm workload: FP64 iterations timed for the extrapolated cold FP64 time")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--scf-tts", action="store_true",
-                    help="also run one cold-start SCF to convergence and report its time")
+    ap.add_argument("--no-scf-tts", action="store_true",
+                    help="skip the cold-start SCF time to solution (FP64 and mixed) of the default run")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--probe-alu", action="store_true",
                     help="measure the FP64 and FP32 FMA throughput of the GPU (roofline denominators)")
@@ -188,11 +191,26 @@ def cpu_oracle_sample(workload: str, seconds: float, cols: int = 2):
 
 # ------------------------------------------------------------------------------ hub arm
 # DRAM bytes per point-orbital of one launch (dram__bytes_read.sum + dram__bytes_write.sum of
-# full-size launches of the 348-orbital rutile block, ncu; profiles/hot_kernels_f32_rutile_dram.md;
-# the mixed form runs the float kernels).
-# Valid for the kernels as they stand; a changed kernel reports null until captured again.
-TRAFFIC_B_PER_PTORB = {"f32": {"stencil": 12.53, "gather": 11.73, "scatter": 8.32},
-                       "f64": {"stencil": 25.29, "gather": 95.70, "scatter": 51.01}}
+# an ncu capture), each valid only for the kernel source the capture ran on: an entry holds
+# the bytes, the source file and the first 16 hex digits of its sha256 at capture time.  A
+# kernel whose source has changed since reports traffic null until it is captured again.
+TRAFFIC_CAPTURES = {}
+
+
+def _source_sha16(rel_path):
+    import hashlib
+    p = os.path.join(ROOT, "paper_2507_23612_gb300", "csrc", rel_path)
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16] if os.path.exists(p) else None
+
+
+def captured_traffic(family, kernel):
+    """Bytes per point-orbital of the capture of (family, kernel), or None when there is no
+    capture or the kernel's source changed since it was taken."""
+    cap = TRAFFIC_CAPTURES.get((family, kernel))
+    if not cap:
+        return None
+    b, src, sha = cap
+    return b if _source_sha16(src) == sha else None
 
 
 def hbm_peak():
@@ -205,7 +223,7 @@ def hbm_peak():
 def kernel_roofline(name, t_n, wl, prec, function_points):
     """Roofline of one hot kernel from its summed event time and launch count (every timed
     launch processes the whole ncol-column block).  Algorithmic work per launch:
-      stencil  FP64: 59 flop per point-orbital against the FP64 pipe; float: 12 B per
+      stencil  FP64: 44 flop per point-orbital against the FP64 pipe; float: 12 B per
                point-orbital (read Y and Yprev, write Yout) against HBM
       gather   FP64: 2 flop per function-point and column against the FP64 pipe; float: one
                read of the block (4 B per point-orbital) against HBM
@@ -217,18 +235,22 @@ def kernel_roofline(name, t_n, wl, prec, function_points):
         flops = (STENCIL_FLOP * pts_orb) if name == "stencil" else 2.0 * function_points * wl.ncol
         achieved = flops / per_launch_s / 1e12
         peak = FP64_PEAK_GFLOPS / 1e3
-        traffic = TRAFFIC_B_PER_PTORB["f64"].get(name)
-        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic * pts_orb if traffic else None, "traffic_unit": "DRAM bytes per launch",
-                "kernel": name,
-                "peak_source": "FP64 pipe: 152 SM x 2 FMA/clk x 2.07 GHz (nominal; bench.py --probe-alu measured 1.253)"}
+        traffic = captured_traffic("f64", name)
+        out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+               "traffic": traffic * pts_orb if traffic else None, "traffic_unit": "DRAM bytes per launch",
+               "kernel": name, "ms_per_launch": t_ms / n,
+               "peak_source": "FP64 pipe: 152 SM x 2 FMA/clk x 2.07 GHz (nominal; bench.py --probe-alu measured 1.253)"}
+        if name == "stencil":
+            out["flop_per_point_orbital"] = STENCIL_FLOP
+            out["frac_fma_as_two_flops"] = STENCIL_FLOP_FMA2 * pts_orb / per_launch_s / 1e12 / peak
+        return out
     per_pt = {"stencil": 12.0, "gather": 4.0, "scatter": 8.0}[name]
     gbs = per_pt * pts_orb / per_launch_s / 1e9
     peak, src = hbm_peak()
-    traffic = TRAFFIC_B_PER_PTORB["f32"].get(name)
+    traffic = captured_traffic("f32", name)
     return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
             "traffic": traffic * pts_orb if traffic else None, "traffic_unit": "DRAM bytes per launch",
-            "kernel": name, "peak_source": src}
+            "kernel": name, "ms_per_launch": t_ms / n, "peak_source": src}
 
 
 # ------------------------------------------------------------------------------ ranks
@@ -287,7 +309,6 @@ def run_hub(args, rank, world, local_rank):
     sampler = ClockSampler(local_rank)
     sampler.start()
     hub.profile(-1)
-    hub.profile(1)
     n0 = hub.launch_count()
     print(f"library launches before the timed region: {n0}", file=sys.stderr)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -301,12 +322,24 @@ def run_hub(args, rank, world, local_rank):
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
     launches = hub.launch_count() - n0
-    hub.profile(0)
-    prof = hub.profile_read()
     clocks = sampler.stop()
     ms = max_over_ranks(ms, dev)
     ptorb_step = nspin * (wl.degree + 1) * wl.Nd * wl.ncol
     value = whole_job_rate(ptorb_step, args.steps, world, ms / 1e3) / 1e9
+
+    # per-kernel breakdown: the same number of SCF iterations again, with a CUDA event pair
+    # around every library launch on the library's stream (kept out of the headline loop)
+    hub.profile(1)
+    ep0, ep1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ep0.record(stream)
+    for _ in range(args.steps):
+        hub.scf_iterate()
+    ep1.record(stream)
+    torch.cuda.synchronize()
+    ms_prof = ep0.elapsed_time(ep1)
+    hub.profile(0)
+    prof = hub.profile_read()
+    hub.profile(-1)
 
     # e2e: the same step through the public API with the orbitals on the host (pinned):
     # every step copies the blocks host->device, iterates, and copies the blocks, the
@@ -333,30 +366,89 @@ def run_hub(args, rank, world, local_rank):
         e2e = {"value": whole_job_rate(ptorb_step, args.steps, world, t_e2e) / 1e9, "unit": "Gpt·orb/s",
                "h2d_bytes_per_step": bx,
                "d2h_bytes_per_step": bx + 8 * (eig.size + occ.size + D.size)}
-
-    tts = None
-    if args.scf_tts:
-        Xs2 = [torch.tensor(x, device=dev).to(dt).contiguous() for x in X0]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        hub.scf_begin(p, Xs2, v0s, wl.D0)
-        res = hub.scf_run()
-        torch.cuda.synchronize()
-        tts = {"seconds": time.perf_counter() - t0, "iterations": res["iter"],
-               "converged": bool(res["converged"]), "E_Ha": res["E"], "E_U_Ha": res["E_U"],
-               "criterion": "|dE|/atom < 1e-5 Ha twice and max|dD| < 1e-4"}
+    fpts = hub.projector_stats()["function_points"]
+    hub.close()
+    del Xs
+    torch.cuda.empty_cache()
 
     # rooflines of the three hot kernels, and the dominant kernel's
-    fpts = hub.projector_stats()["function_points"]
     rooflines = {k: kernel_roofline(k, prof[k], wl, args.prec, fpts) for k in ("stencil", "gather", "scatter")
                  if k in prof}
     dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 0))
     roof = rooflines.get(dom[0])
-    breakdown = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / ms, 4)}
+    breakdown = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / ms_prof, 4)}
                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+
+    # the metric's second half: cold-start SCF time to solution at 1e-5 Ha/atom, FP64 and the
+    # mixed form (BF16 tensor-core products with the precision ladder), on fresh handles, and
+    # the float kernels' rooflines from two profiled iterations of the converged mixed SCF
+    tts = None
+    if not args.no_scf_tts and args.workload == "rutile" and world == 1:
+        tts = scf_time_to_solution(wl, X0, dev)
     return {"value": value, "ms": ms, "launches": launches, "e2e": e2e, "tts": tts,
             "roofline": roof, "rooflines": rooflines, "kernels": breakdown, "clocks": clocks, "last": last,
-            "wl": wl}
+            "wl": wl, "profiled_ms": ms_prof}
+
+
+def scf_solve_timed(wl, X0, dev, prec, profile_after=0):
+    """Cold-start SCF of the workload in one precision form on a fresh handle, timed from
+    handle creation to convergence; optionally profile_after more iterations with per-kernel
+    events.  Returns the result, the per-kernel profile and the projector function points."""
+    import numpy as np
+    import torch
+    from paper_2507_23612_gb300 import Hub, scf_params
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hub = Hub(wl.n, wl.L, wl.fd_half_order, prec=PREC[prec])
+    hub.set_veff(torch.tensor(wl.veff, device=dev))
+    hub.set_atoms(wl.atoms)
+    Xs = [torch.tensor(x, device=dev).to(hub.dtype).contiguous() for x in X0]
+    v0s = [torch.tensor(wl.lanczos_start(s), device=dev).to(hub.dtype).contiguous() for s in range(wl.nspin)]
+    p = scf_params(nspin=wl.nspin, ncol=wl.ncol, ld=wl.Nd, degree=wl.degree, max_iter=200,
+                   first_passes=3, lanczos_steps=10, pulay_history=7, natoms=len(wl.atoms),
+                   pulay_beta=0.3, kT=wl.kT if wl.kT > 0 else 0.005, n_elec=wl.n_elec,
+                   tol_e_atom=1e-5, tol_D=1e-4, ladder=1 if prec == "mixed" else 0, ladder_tol=1e-4)
+    hub.scf_begin(p, Xs, v0s, wl.D0)
+    res = hub.scf_run()
+    torch.cuda.synchronize()
+    seconds = time.perf_counter() - t0
+    eig, occ, D = hub.scf_get()
+    prof, fpts = None, None
+    if profile_after:
+        hub.profile(-1)
+        hub.profile(1)
+        for _ in range(profile_after):
+            hub.scf_iterate()
+        torch.cuda.synchronize()
+        hub.profile(0)
+        prof = hub.profile_read()
+        fpts = hub.projector_stats()["function_points"]
+    hub.close()
+    del Xs
+    torch.cuda.empty_cache()
+    return {"seconds": seconds, "iterations": res["iter"], "converged": bool(res["converged"]),
+            "E": res["E"], "E_U": res["E_U"], "band": float(np.sum(occ * eig)), "D": D}, prof, fpts
+
+
+def scf_time_to_solution(wl, X0, dev):
+    import numpy as np
+    nat = len(wl.atoms)
+    f64, _, _ = scf_solve_timed(wl, X0, dev, "f64")
+    mixed, prof, fpts = scf_solve_timed(wl, X0, dev, "mixed", profile_after=2)
+    out = {"criterion": "|dE|/atom < 1e-5 Ha twice and max|dD| < 1e-4; wall clock from handle creation",
+           "f64": {"seconds": round(f64["seconds"], 3), "iterations": f64["iterations"],
+                   "converged": f64["converged"], "E_Ha": f64["E"], "E_U_Ha": f64["E_U"]},
+           "mixed": {"seconds": round(mixed["seconds"], 3), "iterations": mixed["iterations"],
+                     "converged": mixed["converged"], "E_Ha": mixed["E"], "E_U_Ha": mixed["E_U"],
+                     "error_vs_f64": {"E_Ha_per_atom": abs(mixed["E"] - f64["E"]) / nat,
+                                      "E_U_Ha_per_atom": abs(mixed["E_U"] - f64["E_U"]) / nat,
+                                      "band_Ha_per_atom": abs(mixed["band"] - f64["band"]) / nat,
+                                      "max_abs_dD": float(np.max(np.abs(mixed["D"] - f64["D"])))}},
+           "speedup_mixed_vs_f64": round(f64["seconds"] / mixed["seconds"], 2)}
+    if prof:
+        out["mixed_rooflines"] = {k: kernel_roofline(k, prof[k], wl, "mixed", fpts)
+                                  for k in ("stencil", "gather", "scatter") if k in prof}
+    return out
 
 
 def scf_compare(args):
@@ -369,28 +461,7 @@ def scf_compare(args):
     X0 = [wl.orbitals(s) for s in range(wl.nspin)]
     out = {}
     for form in ("f64", "f32", "mixed"):
-        hub = Hub(wl.n, wl.L, wl.fd_half_order, prec=PREC[form])
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        hub.set_veff(torch.tensor(wl.veff, device=dev))
-        hub.set_atoms(wl.atoms)
-        Xs = [torch.tensor(x, device=dev).to(hub.dtype).contiguous() for x in X0]
-        v0s = [torch.tensor(wl.lanczos_start(s), device=dev).to(hub.dtype).contiguous()
-               for s in range(wl.nspin)]
-        p = scf_params(nspin=wl.nspin, ncol=wl.ncol, ld=wl.Nd, degree=wl.degree, max_iter=200,
-                       first_passes=3, lanczos_steps=10, pulay_history=7, natoms=len(wl.atoms),
-                       pulay_beta=0.3, kT=wl.kT if wl.kT > 0 else 0.005, n_elec=wl.n_elec,
-                       tol_e_atom=1e-5, tol_D=1e-4, ladder=1 if form == "mixed" else 0, ladder_tol=1e-4)
-        hub.scf_begin(p, Xs, v0s, wl.D0)
-        res = hub.scf_run()
-        torch.cuda.synchronize()
-        tts = time.perf_counter() - t0
-        eig, occ, D = hub.scf_get()
-        out[form] = {"seconds": tts, "iterations": res["iter"], "converged": bool(res["converged"]),
-                     "E": res["E"], "E_U": res["E_U"], "band": float(np.sum(occ * eig)), "D": D}
-        hub.close()
-        del Xs
-        torch.cuda.empty_cache()
+        out[form], _, _ = scf_solve_timed(wl, X0, dev, form)
     nat = len(wl.atoms)
     ref = out["f64"]
     table = {}
@@ -909,6 +980,7 @@ def main():
             "gpu_launches": r["launches"], "clocks": r["clocks"],
             "kernels": r["kernels"],
         }
+        line["kernels_profiled_ms"] = r["profiled_ms"]
         if r["tts"]:
             line["scf_time_to_solution"] = r["tts"]
         print(json.dumps(line))

@@ -175,7 +175,10 @@ int hub_gram(hub_t h, const void* A, int ncol_a, const void* B, int ncol_b, int 
  * with leading dimension ld >= nrows; G_dev: device double, row-major
  * [ncol_a x ncol_b], overwritten; cuda_stream: the stream to run on (NULL = default).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current: make that first call before any stream capture.  All calls on
+ * with that device current: make that first call before any stream capture.  The address
+ * is kept for the life of the process and belongs to the device's primary context as it
+ * was then: after cudaDeviceReset (or anything else that tears that context down) this
+ * entry point must not be called again in the same process.  All calls on
  * a device share the one array and it keeps the last call's contents; every call writes
  * each partial sum it reads, so nothing needs clearing, but calls that overlap on the GPU
  * (two streams, or two host threads) race on the array and must be serialised.

@@ -81,45 +81,35 @@ __global__ void k_lanczos_axpy(int mode, typename VT<R, CPLX>::T* __restrict__ o
     }
 }
 
-// eigenvalues of the k x k symmetric tridiagonal (alpha, beta) by cyclic Jacobi, one thread;
-// out[0] = min, out[1] = max + |beta_k|
-__global__ void k_tridiag_bounds(const double* __restrict__ alpha, const double* __restrict__ beta, int k,
-                                 double* out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double A[64][64];
-    for (int i = 0; i < k; ++i)
-        for (int j = 0; j < k; ++j) A[i][j] = 0.0;
+// Extreme eigenvalues of the k x k symmetric tridiagonal T (diagonal alpha, off-diagonal
+// beta) on the host, by bisection on the Sturm count: the number of eigenvalues below x is
+// the number of negative pivots of the LDL^T factorisation of T - x I.
+int tridiag_count_below(const double* alpha, const double* beta, int k, double x) {
+    int neg = 0;
+    double q = 1.0;
     for (int i = 0; i < k; ++i) {
-        A[i][i] = alpha[i];
-        if (i + 1 < k) { A[i][i + 1] = beta[i]; A[i + 1][i] = beta[i]; }
+        const double b2 = i > 0 ? beta[i - 1] * beta[i - 1] : 0.0;
+        q = (alpha[i] - x) - (i > 0 ? b2 / q : 0.0);
+        if (q == 0.0) q = -1e-300;       // x on an eigenvalue of a leading block: count it below
+        neg += q < 0.0;
     }
-    for (int sweep = 0; sweep < 100; ++sweep) {
-        double off = 0.0;
-        for (int p = 0; p < k; ++p)
-            for (int q = p + 1; q < k; ++q) off = fmax(off, fabs(A[p][q]));
-        if (off < 1e-300) break;
-        for (int p = 0; p < k; ++p)
-            for (int q = p + 1; q < k; ++q) {
-                if (A[p][q] == 0.0) continue;
-                const double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
-                const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                for (int r = 0; r < k; ++r) {
-                    const double ap = A[r][p], aq = A[r][q];
-                    A[r][p] = c * ap - s * aq;
-                    A[r][q] = s * ap + c * aq;
-                }
-                for (int r = 0; r < k; ++r) {
-                    const double ap = A[p][r], aq = A[q][r];
-                    A[p][r] = c * ap - s * aq;
-                    A[q][r] = s * ap + c * aq;
-                }
-            }
+    return neg;
+}
+
+double tridiag_eigenvalue(const double* alpha, const double* beta, int k, int idx) {
+    // Gershgorin interval, then bisection on count(x) > idx
+    double lo = alpha[0], hi = alpha[0];
+    for (int i = 0; i < k; ++i) {
+        const double r = (i > 0 ? std::fabs(beta[i - 1]) : 0.0) + (i + 1 < k ? std::fabs(beta[i]) : 0.0);
+        lo = std::min(lo, alpha[i] - r);
+        hi = std::max(hi, alpha[i] + r);
     }
-    double lo = A[0][0], hi = A[0][0];
-    for (int i = 1; i < k; ++i) { lo = fmin(lo, A[i][i]); hi = fmax(hi, A[i][i]); }
-    out[0] = lo;
-    out[1] = hi + fabs(beta[k - 1]);
+    for (int it = 0; it < 200 && hi - lo > 4e-16 * std::max(std::fabs(lo), std::fabs(hi)); ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (tridiag_count_below(alpha, beta, k, mid) > idx) hi = mid; else lo = mid;
+    }
+    return 0.5 * (lo + hi);
 }
 
 template <typename R, bool CPLX>
@@ -161,13 +151,12 @@ int lanczos_t(hub_t h, int spin, int steps, const void* v0, double* lo, double* 
         k_lanczos_axpy<R, CPLX><<<nb, 256, 0, h->stream>>>(0, v, w, nullptr, h->Nd, sc, 64 + j, -1); }
         HUB_CUDA_TRY(h, cudaGetLastError());
     }
-    { ProfScope ps(h, HUB_K_LANCZOS); k_tridiag_bounds<<<1, 32, 0, h->stream>>>(sc, sc + 64, steps, sc + 200); }
-    HUB_CUDA_TRY(h, cudaGetLastError());
-    double b[2];
-    HUB_CUDA_TRY(h, cudaMemcpyAsync(b, sc + 200, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    // bounds from the k x k tridiagonal: lowest Ritz value, highest + |beta_k|
+    double ab[128];
+    HUB_CUDA_TRY(h, cudaMemcpyAsync(ab, sc, 128 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     HUB_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    *lo = b[0];
-    *up = b[1];
+    *lo = tridiag_eigenvalue(ab, ab + 64, steps, 0);
+    *up = tridiag_eigenvalue(ab, ab + 64, steps, steps - 1) + std::fabs(ab[64 + steps - 1]);
     return HUB_OK;
 }
 

@@ -12,12 +12,23 @@ def _wl(Nd=1_000_000, ncol=100):
     return SimpleNamespace(Nd=Nd, ncol=ncol)
 
 
-def test_fp64_stencil_roofline_counts_59_flop_per_point_orbital():
-    # 10 launches of 20 ms in total: 2 ms per launch; 59 * 1e8 flop / 2e-3 s = 2.95 TFLOP/s
+def test_fp64_stencil_roofline_counts_44_flop_per_point_orbital():
+    # 10 launches of 20 ms in total: 2 ms per launch; 44 * 1e8 flop / 2e-3 s = 2.2 TFLOP/s
     r = bench.kernel_roofline("stencil", (20.0, 10), _wl(), "f64", 0)
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
-    assert r["achieved"] == pytest.approx(59 * 1e8 / 2e-3 / 1e12)
-    assert r["frac"] == pytest.approx(r["achieved"] / (152 * 2 * 2 * 2.07 / 1e3))
+    assert r["achieved"] == pytest.approx(44 * 1e8 / 2e-3 / 1e12)
+    peak = 152 * 2 * 2 * 2.07 / 1e3
+    assert r["frac"] == pytest.approx(r["achieved"] / peak)
+    # the count with every FMA as two flops, reported beside it
+    assert r["frac_fma_as_two_flops"] == pytest.approx(59 * 1e8 / 2e-3 / 1e12 / peak)
+
+
+def test_traffic_is_null_once_the_kernel_source_changed(monkeypatch):
+    sha = bench._source_sha16("stencil.cu")
+    monkeypatch.setitem(bench.TRAFFIC_CAPTURES, ("f32", "stencil"), (12.5, "stencil.cu", sha))
+    assert bench.kernel_roofline("stencil", (6.0, 3), _wl(), "f32", 0)["traffic"] == pytest.approx(12.5 * 1e8)
+    monkeypatch.setitem(bench.TRAFFIC_CAPTURES, ("f32", "stencil"), (12.5, "stencil.cu", "0" * 16))
+    assert bench.kernel_roofline("stencil", (6.0, 3), _wl(), "f32", 0)["traffic"] is None
 
 
 def test_fp64_gather_counts_two_flop_per_function_point_and_column():

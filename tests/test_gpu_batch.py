@@ -6,7 +6,7 @@ import pytest
 
 import workloads as w
 from oracle import hubbard as o
-from hubtest import make_hub, oracle_ham, to_dev, rel
+from hubtest import make_hub, oracle_ham, to_dev, rel_elem as rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")

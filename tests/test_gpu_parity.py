@@ -2,15 +2,17 @@
 on seeded synthetic inputs: H application, Chebyshev filter, Lanczos bounds, Rayleigh-Ritz,
 occupation matrices and E_U, and one full filter + Rayleigh-Ritz pass of the 24^3 tiny cell.
 
-Tolerance: FP64 results agree with the FP64 oracle to 1e-10 relative (Frobenius norm of the
-difference over the norm of the oracle's result); float results to the float bound stated
-at each test."""
+Comparisons are element by element: the largest elementwise difference over the RMS
+magnitude of the reference row it belongs to (one orbital of a block, one row of a matrix,
+a whole vector of eigenvalues), so one wrong element at a tile edge stands out against its
+own orbital's scale.  Tolerance: FP64 results agree with the FP64 oracle to 1e-10; float
+results to the float bound stated at each test."""
 import numpy as np
 import pytest
 
 import workloads as w
 from oracle import hubbard as o
-from hubtest import make_hub, oracle_ham, to_dev, rel
+from hubtest import make_hub, oracle_ham, to_dev, rel_elem as rel
 
 pytestmark = pytest.mark.gpu
 
