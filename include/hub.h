@@ -436,7 +436,9 @@ int hub_kerker(hub_t h, const double* r_dev, double* z_dev, double kappa, double
 /* Autotuner: times the candidate stencil tile shapes of this handle's kernel family on the
  * block X (device, ncol columns, leading dimension ld; X is only read), for
  * HUB_MIXED_BF16 handles the split-K factor of the tensor-core Gram product, and for real
- * float handles the projector gather form (point-major or 8x8x4 bricks); keeps the fastest
+ * float handles the projector form (point-major, 8x8x4 bricks on CUDA cores, or 8x8x4
+ * bricks as TF32 tensor-core products for the gather or for gather and scatter; gather and
+ * scatter timed together); keeps the fastest
  * for the handle and for every later handle of the same grid shape, precision and ncol
  * (process-wide cache).  variant_out: NULL or the chosen stencil variant.
  * Synchronises.  Errors: HUB_EINVAL. */
@@ -444,8 +446,14 @@ int hub_autotune(hub_t h, int spin, const void* X, int ncol, int ld, int* varian
 /* Tuning of this handle without timing: stencil_variant in 0 .. n_variants-1 (the tile
  * shapes the autotuner chooses from; 0 is the default), gemm_split >= 1 (split-K factor of
  * the tensor-core Gram product, in units of one wave of tiles), gather_form 0 (point-major
- * projector gather) or 1 (8x8x4 brick form; real float handles only).  Pass -1 to keep
- * any of them.  Errors: HUB_EINVAL. */
+ * projector gather and scatter), 1 (8x8x4 brick form on CUDA cores; real float handles
+ * only), 2 (the brick gather as tcgen05 products, D[128 orbitals x functions] = X_b^T Phi_b
+ * in TF32 with both operands split hi + lo and FP32 accumulation, the brick scatter on CUDA
+ * cores) or 3 (gather and scatter both as tcgen05 products; the scatter per brick and 128
+ * orbitals, D[128 points x 128 orbitals] = Phi_b W_b^T).  Forms 2 and 3 need real float
+ * handles whose n1 is a multiple of 4 and blocks that start on 16-byte boundaries with ld a
+ * multiple of 4.  hub_set_atoms_projectors sets form 2 where its tables exist, else 0.
+ * Pass -1 to keep any of them.  Errors: HUB_EINVAL. */
 int hub_set_tuning(hub_t h, int stencil_variant, int gemm_split, int gather_form);
 /* Current tuning of the handle and the number of stencil variants of its kernel family
  * (any pointer may be NULL). */

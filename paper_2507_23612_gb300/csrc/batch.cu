@@ -122,7 +122,8 @@ extern "C" {
 int hub_set_tuning(hub_t h, int stencil_variant, int gemm_split, int gather_form) {
     if (!h) return HUB_EINVAL;
     if (stencil_variant >= hub::stencil_variants(h) || stencil_variant < -1 || gemm_split == 0 || gemm_split < -1 ||
-        gather_form < -1 || gather_form > 1 || (gather_form == 1 && (h->esize != 4 || h->cplx)))
+        gather_form < -1 || gather_form > 3 || (gather_form >= 1 && (h->esize != 4 || h->cplx)) ||
+        (gather_form >= 2 && !h->proj.tc))
         return hub::fail(h, HUB_EINVAL, "bad tuning");
     if (stencil_variant >= 0) h->stencil_variant = stencil_variant;
     if (gemm_split > 0) h->gemm_split = gemm_split;
@@ -149,7 +150,8 @@ int hub_autotune(hub_t h, int spin, const void* X, int ncol, int ld, int* varian
         if (it != g_tuned.end()) {
             h->stencil_variant = it->second.variant;
             h->gemm_split = it->second.split;
-            h->gather_dense = (h->proj.dense && h->esize == 4 && !h->cplx) ? it->second.gather_form : 0;
+            h->gather_dense = (h->proj.dense && h->esize == 4 && !h->cplx &&
+                               (it->second.gather_form < 2 || h->proj.tc)) ? it->second.gather_form : 0;
             if (variant_out) *variant_out = h->stencil_variant;
             return HUB_OK;
         }
@@ -235,16 +237,21 @@ int hub_autotune(hub_t h, int spin, const void* X, int ncol, int ld, int* varian
         if (rc) { h->prof_on = saved_prof; return rc; }
     }
     h->gemm_split = best_split;
-    // projector gather form (real float handles with brick tables): point-major or bricks
+    // projector forms (real float handles with brick tables), gather and scatter timed
+    // together: point-major; bricks on CUDA cores; the tensor-core gather with the CUDA-core
+    // scatter; both on the tensor cores
     int best_form = 0;
     if (h->proj.dense && h->esize == 4 && !h->cplx) {
-        float fms[2] = {1e30f, 1e30f};
-        for (int form = 0; form < 2 && !rc; ++form) {
+        float fms[4] = {1e30f, 1e30f, 1e30f, 1e30f};
+        const int nforms = h->proj.tc ? 4 : 2;
+        for (int form = 0; form < nforms && !rc; ++form) {
             h->gather_dense = form;
             if ((rc = launch_gather(h, X, ncol, ld, spin, true))) break;       // warm-up
+            if ((rc = launch_scatter(h, h->d_work, ncol, ld, 1.0))) break;
             for (int r = 0; r < 3 && !rc; ++r) {
                 HUB_CUDA_TRY(h, cudaEventRecord(e0, h->stream));
                 rc = launch_gather(h, X, ncol, ld, spin, true);
+                if (!rc) rc = launch_scatter(h, h->d_work, ncol, ld, 1.0);
                 HUB_CUDA_TRY(h, cudaEventRecord(e1, h->stream));
                 HUB_CUDA_TRY(h, cudaEventSynchronize(e1));
                 float ms = 0.f;
@@ -253,7 +260,8 @@ int hub_autotune(hub_t h, int spin, const void* X, int ncol, int ld, int* varian
             }
         }
         if (rc) { h->prof_on = saved_prof; return rc; }
-        best_form = fms[1] < fms[0] ? 1 : 0;
+        for (int form = 1; form < nforms; ++form)
+            if (fms[form] < fms[best_form]) best_form = form;
     }
     h->gather_dense = best_form;
     h->prof_on = saved_prof;

@@ -26,6 +26,7 @@
 #include <mutex>
 
 #include "hub_internal.cuh"
+#include "tcgen05.cuh"
 
 namespace hub {
 
@@ -35,78 +36,6 @@ constexpr int TM = 128;                 // rows of A per tile (TMEM lanes)
 constexpr int TN = 128;                 // rows of B per tile (TMEM columns per n-tile)
 constexpr int TKC = 64;                 // K elements per stage (128 bytes of BF16)
 constexpr int TILE_BYTES = TM * TKC * 2;  // 16 KB
-constexpr long kSpinLimit = 1L << 20;   // polls; a poll may itself block briefly
-
-__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(n) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(ok) : "r"(saddr(b)), "r"(parity) : "memory");
-    return ok != 0;
-}
-// bounded wait; false when the limit ran out (or another thread already gave up)
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
-    long it = 0;
-    while (!mbar_try(b, parity)) {
-        if (*abort_flag) return false;
-        if (++it > kSpinLimit) { *abort_flag = 1; return false; }
-    }
-    return true;
-}
-
-// bounded wait that ignores the abort flag (used to drain work already issued)
-__device__ __forceinline__ bool mbar_drain(uint64_t* b, uint32_t parity) {
-    for (long it = 0; it < kSpinLimit; ++it) {
-        if (mbar_try(b, parity)) return true;
-        __nanosleep(64);
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(saddr(dst)), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(saddr(bar)) : "memory");
-}
-
-__device__ __forceinline__ uint64_t smem_desc(const void* p) {
-    // K-major, SWIZZLE_128B: 8-row groups 1024 B apart (SBO), descriptor version 1
-    const uint64_t a = (saddr(p) & 0x3FFFF) >> 4;
-    return a | (1ull << 16) | (64ull << 32) | (1ull << 46) | (2ull << 61);
-}
-__device__ __forceinline__ uint32_t instr_desc_bf16(int M, int N) {
-    // D f32, A bf16, B bf16, both K-major, dense
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
-    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
-                 ::"r"(tmem_d), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar)) : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 struct TcArgs {
     int m, n;              // valid rows of A-side (M) and B-side (N) of the product
     int kchunks_total;     // K / 64 rounded up
@@ -358,6 +287,13 @@ int launch_tc(hub_t h, const CUtensorMap& ahi, const CUtensorMap& alo, const CUt
 }
 
 }  // namespace
+
+int tensor_map_encoder(hub_t h, PFN_cuTensorMapEncodeTiled_v12000* out) {
+    const int rc = get_encoder(h);
+    if (rc) return rc;
+    *out = g_encode;
+    return HUB_OK;
+}
 
 // G[m x n] = alpha * A^T B with BF16 tensor-core products (A, B float, column-major)
 int launch_gram_bf16(hub_t h, const void* A, int lda, const void* B, int ldb, int m, int n, double alpha,

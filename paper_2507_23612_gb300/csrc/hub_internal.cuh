@@ -51,6 +51,16 @@ struct SiteDev {
     int hub_index;        // Hubbard sites: index among Hubbard atoms, else -1
 };
 
+// Brick form of the projector tables (real float): the grid in bricks of 8 x 8 x 4 points
+// (point p = x + 8 row of a brick, row = y + 8 z), at most BRF functions per entry.
+constexpr int BRX = 8, BRY = 8, BRZ = 4, BRP = BRX * BRY * BRZ, BRF = 64;
+// position of point p of a brick inside a function's 256 values: the two 4-point halves of
+// the 32 rows are stored as two planes, [half][row][4], so that a warp reading one half of
+// 32 consecutive rows touches 512 contiguous bytes
+__host__ __device__ __forceinline__ int brick_slot(int p) {
+    return ((p >> 2) & 1) * 128 + (p >> 3) * 4 + (p & 3);
+}
+
 struct Table {
     int nsites = 0, nproj = 0, npts = 0, nvals = 0, nhub = 0, nitems = 0;
     std::vector<SiteDev> h_sites;
@@ -86,6 +96,19 @@ struct Table {
     int* d_frow = nullptr;            // [npart_rows] global projector row (-1: padding)
     int* d_roff = nullptr;            // [nproj + 1] partial rows of each projector row (CSR)
     int* d_rent = nullptr;
+    // tensor-core form of the brick gather (built with the bricks when n1 % 4 == 0): per
+    // entry its values in the 128-byte-swizzled K-major layout of tcgen05 operands, split as
+    // TF32 hi + lo, functions padded to a multiple of 16
+    int tc = 0;                       // 1 when the arrays below are built
+    int2* d_tcent = nullptr;          // per entry: float offset into d_tchi / d_tclo, padded count
+    float* d_tchi = nullptr;
+    float* d_tclo = nullptr;
+    // tensor-core form of the brick scatter: per used brick (brick, float offset, function
+    // slots), the W row of each slot (-1: padding), values point-major per 32-slot chunk
+    int4* d_tcs_brick = nullptr;
+    int* d_tcs_frow = nullptr;
+    float* d_tcs_hi = nullptr;
+    float* d_tcs_lo = nullptr;
 };
 
 // ---------------------------------------------------------------------------- profiling
@@ -240,6 +263,13 @@ int launch_occupation(hub_t h, int ncol, const double* f_dev, double kweight, do
 // launch_gather (a gather of d_axis X)
 int launch_hub_force(hub_t h, int spin, int ncol, const double* f_dev, double kweight,
                      const void* C0, int axis, double* F_dev);
+
+// projectors_tc.cu: tensor-core tables of the brick gather, and the gather itself (the
+// partial rows of d_part, as the SIMT brick gather writes them)
+int build_tc_tables(hub_t h, Table& t);
+int launch_gather_tc(hub_t h, const void* X, int ncol, int ld);
+// Y += alpha Phi W (W of the last launch_gather) in the tensor-core brick form
+int launch_scatter_tc(hub_t h, void* Y, int ncol, int ld, double alpha, const double* alpha_dev);
 
 // Moment integrals of the stress: Gm_b = dV <(x - R_image)_b phi_m | G> for the Hubbard rows
 // (layout of d_C: [nproj x ncol] doubles, x2 complex; other rows untouched), b = x, y, z

@@ -248,25 +248,56 @@ __device__ __forceinline__ void site_transform(const SiteDev& S, const typename 
     }
 }
 
-// brick form: C of each projector row from its float partials over bricks, then W
-__global__ void k_reduce_transform_dense(int nsites, int ncol, double dV, const SiteDev* __restrict__ sites,
-                                         const int* __restrict__ roff, const int* __restrict__ rent,
-                                         const float* __restrict__ part, const double* __restrict__ gamma,
-                                         const double* __restrict__ M, double* __restrict__ C,
-                                         float* __restrict__ W, int want_W) {
+// brick form: C of each projector row from its float partials over bricks.  One CTA per
+// (row, 128 orbitals): warp w sums the row's partial rows w, w + 8, ..., each lane 4 orbitals
+// 32 apart, in compensated float sums (Kahan: the rounding error of every addition is carried
+// in a second float, so the sum keeps close to double accuracy on the FP32 pipe, which GB300
+// runs far faster than its FP64 pipe); the eight warp sums are added in double in a fixed
+// order.
+constexpr int RR_COLS = 128;
+__global__ void __launch_bounds__(256)
+k_reduce_rows_dense(int ncol, double dV, const int* __restrict__ roff, const int* __restrict__ rent,
+                    const float* __restrict__ part, double* __restrict__ C) {
+    __shared__ double red[8][RR_COLS];
+    const int r = blockIdx.x;
+    const int n0 = blockIdx.y * RR_COLS;
+    const int e0 = roff[r], e1 = roff[r + 1];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int e = e0 + w; e < e1; e += 8) {
+        const float* src = part + (size_t)rent[e] * ncol + n0 + lane;
+        float v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = (n0 + lane + 32 * k < ncol) ? src[32 * k] : 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float y = v[k] - c[k];
+            const float t = s[k] + y;
+            c[k] = (t - s[k]) - y;
+            s[k] = t;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) red[w][lane + 32 * k] = (double)s[k] - (double)c[k];
+    __syncthreads();
+    if (threadIdx.x < RR_COLS && n0 + (int)threadIdx.x < ncol) {
+        double sum = 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sum += red[k][threadIdx.x];
+        C[(size_t)r * ncol + n0 + threadIdx.x] = dV * sum;
+    }
+}
+
+__global__ void k_transform_sites(int nsites, int ncol, const SiteDev* __restrict__ sites,
+                                  const double* __restrict__ C, const double* __restrict__ gamma,
+                                  const double* __restrict__ M, float* __restrict__ W) {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long)nsites * ncol) return;
     const int s = (int)(t / ncol), n = (int)(t - (long)s * ncol);
     const SiteDev S = sites[s];
     double c[kMaxProj];
-    for (int p = 0; p < S.nproj; ++p) {
-        const int r = S.proj_off + p;
-        double acc = 0.0;
-        for (int e = roff[r]; e < roff[r + 1]; ++e) acc += (double)part[(size_t)rent[e] * ncol + n];
-        c[p] = dV * acc;
-        C[(size_t)r * ncol + n] = c[p];
-    }
-    if (want_W) site_transform<float, false>(S, c, gamma, M, W, n, ncol);
+    for (int p = 0; p < S.nproj; ++p) c[p] = C[(size_t)(S.proj_off + p) * ncol + n];
+    site_transform<float, false>(S, c, gamma, M, W, n, ncol);
 }
 
 // reduce partials of each site and apply the coefficient transform
@@ -368,16 +399,9 @@ k_scatter(typename VT<R, CPLX>::T* __restrict__ Y, int ld, int ncol, int norder,
 //            summed per function over its bricks by k_reduce_transform_dense)
 //   scatter: Y[g(p), n] += alpha sum_f phi[p, f] W[frow[f], n]
 // with every X and Y element read once per brick and pass, in 16-byte rows.
-constexpr int BRX = 8, BRY = 8, BRZ = 4, BRP = BRX * BRY * BRZ, BRF = 64;
 constexpr int GD_COLS = 32, GD_XS = GD_COLS + 4;     // gather: columns per pass, smem row stride
 constexpr int SD_COLS = 32;                          // scatter: columns per pass
 
-// position of point p = x + 8 row of a brick inside a function's 256 values: the two
-// 4-point halves of the 32 rows are stored as two planes, [half][row][4], so that a warp
-// reading one half of 32 consecutive rows touches 512 contiguous bytes
-__host__ __device__ __forceinline__ int brick_slot(int p) {
-    return ((p >> 2) & 1) * 128 + (p >> 3) * 4 + (p & 3);
-}
 
 __global__ void k_brick_fill(int npts, const int2* __restrict__ rowinfo, const SiteDev* __restrict__ sites,
                              const float* __restrict__ vals, float* __restrict__ phi) {
@@ -746,7 +770,8 @@ void free_table(Table& t) {
     void* ptrs[] = {t.d_sites, t.d_items, t.d_item_first, t.d_idx, t.d_vals, t.d_csr_off,
                     t.d_csr_ent, t.d_order, t.d_gamma, t.d_hub_sites, t.d_U,
                     t.d_M[0], t.d_M[1], t.d_bent, t.d_bfirst, t.d_phi, t.d_frow, t.d_roff,
-                    t.d_rent};
+                    t.d_rent, t.d_tcent, t.d_tchi, t.d_tclo, t.d_tcs_brick, t.d_tcs_frow, t.d_tcs_hi,
+                    t.d_tcs_lo};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     t = Table();
@@ -850,7 +875,7 @@ static int build_bricks(hub_t h, Table& t, const std::vector<std::vector<int>>& 
     t.nbused = (int)bfirst.size() - 1;
     t.npart_rows = prow;
     t.dense = 1;
-    return HUB_OK;
+    return build_tc_tables(h, t);
 }
 
 int build_tables(hub_t h, int natoms, const double* pos, const int* kb_nchan, const int* kb_l,
@@ -1076,21 +1101,29 @@ static int gather_dense(hub_t h, const void* X, int ncol, int ld, int spin, bool
     if ((rc = ensure(h, &h->d_part, &h->part_bytes, (size_t)t.npart_rows * ncol * sizeof(float)))) return rc;
     if ((rc = ensure(h, &h->d_C, &h->C_bytes, (size_t)t.nproj * ncol * sizeof(double)))) return rc;
     if ((rc = ensure(h, &h->d_W, &h->W_bytes, (size_t)t.nproj * ncol * sizeof(float)))) return rc;
-    {
+    if (h->gather_dense >= 2 && t.tc) {
+        if ((rc = launch_gather_tc(h, X, ncol, ld))) return rc;
+    } else {
         ProfScope ps(h, HUB_K_GATHER);
         dim3 g(t.nbent, (ncol + GD_COLS - 1) / GD_COLS);
         k_gather_dense<<<g, 128, 0, h->stream>>>((const float*)X, ld, ncol, h->n1, h->n2, h->n3, t.nbx, t.nby,
                                                  t.d_bent, t.d_phi, (float*)h->d_part);
     }
     HUB_CUDA_TRY(h, cudaGetLastError());
-    const long nthr = (long)t.nsites * ncol;
     {
         ProfScope ps(h, HUB_K_TRANSFORM);
-        k_reduce_transform_dense<<<(unsigned)((nthr + 127) / 128), 128, 0, h->stream>>>(
-            t.nsites, ncol, h->dV, t.d_sites, t.d_roff, t.d_rent, (const float*)h->d_part, t.d_gamma,
-            t.d_M[spin], (double*)h->d_C, (float*)h->d_W, want_W ? 1 : 0);
+        dim3 g(t.nproj, (ncol + RR_COLS - 1) / RR_COLS);
+        k_reduce_rows_dense<<<g, 256, 0, h->stream>>>(ncol, h->dV, t.d_roff, t.d_rent, (const float*)h->d_part,
+                                                      (double*)h->d_C);
     }
     HUB_CUDA_TRY(h, cudaGetLastError());
+    if (want_W) {
+        const long nthr = (long)t.nsites * ncol;
+        ProfScope ps(h, HUB_K_TRANSFORM);
+        k_transform_sites<<<(unsigned)((nthr + 127) / 128), 128, 0, h->stream>>>(
+            t.nsites, ncol, t.d_sites, (const double*)h->d_C, t.d_gamma, t.d_M[spin], (float*)h->d_W);
+        HUB_CUDA_TRY(h, cudaGetLastError());
+    }
     return HUB_OK;
 }
 
@@ -1163,7 +1196,10 @@ static int scatter_t(hub_t h, void* Y, int ncol, int ld, double alpha, const dou
 
 int launch_scatter(hub_t h, void* Y, int ncol, int ld, double alpha, const double* alpha_dev) {
     if (ncol == 0 || h->proj.nsites == 0) return HUB_OK;
-    if (use_dense(h, Y, ld)) return scatter_dense(h, Y, ncol, ld, alpha, alpha_dev);
+    if (use_dense(h, Y, ld)) {
+        if (h->gather_dense == 3 && h->proj.tc) return launch_scatter_tc(h, Y, ncol, ld, alpha, alpha_dev);
+        return scatter_dense(h, Y, ncol, ld, alpha, alpha_dev);
+    }
     if (h->esize == 8) return h->cplx ? scatter_t<double, true>(h, Y, ncol, ld, alpha, alpha_dev)
                                       : scatter_t<double, false>(h, Y, ncol, ld, alpha, alpha_dev);
     return h->cplx ? scatter_t<float, true>(h, Y, ncol, ld, alpha, alpha_dev)
