@@ -49,8 +49,8 @@ def parse():
     ap.add_argument("--impl", default="hub", choices=["hub", "reference"])
     ap.add_argument("--prec", default="f64", choices=list(PREC))
     ap.add_argument("--workload", default="rutile", choices=["rutile", "tiny", "batched", "warm"])
-    ap.add_argument("--warm-train", type=int, default=8,
-                    help="warm workload: SCF solutions of displaced 2x2x3 cells to train on")
+    ap.add_argument("--warm-train", type=int, default=200,
+                    help="warm workload: SCF solutions of displaced 12-atom cells to train on")
     ap.add_argument("--warm-f64-iters", type=int, default=2,
                     help="warm workload: FP64 iterations timed for the extrapolated cold FP64 time")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -63,6 +63,12 @@ def parse():
     ap.add_argument("--probe-apply", type=int, default=0, metavar="NCOL",
                     help="profiling case: four H applications to NCOL random columns of the rutile "
                          "workload in --prec, then exit (no timing)")
+    ap.add_argument("--projector-forms", action="store_true",
+                    help="per-kernel times of a float H application on the rutile block for every "
+                         "projector form and every float stencil tile shape")
+    ap.add_argument("--probe-rr", type=int, default=0, metavar="NCOL",
+                    help="profiling case: one filter and two Rayleigh-Ritz projections of NCOL random "
+                         "columns of the rutile workload in --prec, then exit (no timing)")
     ap.add_argument("--forces", action="store_true",
                     help="time hub_hubbard_forces on the rutile workload (348 orbitals, one spin) "
                          "in --prec and report the FD-gradient kernel against the HBM roofline")
@@ -479,57 +485,68 @@ def scf_compare(args):
 
 
 def run_warm(args):
-    """Warm-started SCF of the 3x3x4 rutile-shaped supercell (216 atoms, 72 Ti, 132x132x112
-    grid, 1044 orbitals per spin, two spins).  The occupation model (descriptors -> 3x256 SiLU
-    MLP with FP16 weights -> 15 D entries per spin) is trained on SCF solutions of displaced
-    2x2x3 cells computed by the library in mixed precision; the 216-atom cell is then solved
-    cold (atomic-guess D) and warm (predicted D), both in the mixed form with the precision
-    ladder, and its cold FP64 time is extrapolated from timed FP64 iterations."""
+    """Warm start of the 3x3x4 rutile-shaped supercell (216 atoms, 72 Ti, 132x132x112 grid,
+    1044 orbitals per spin, two spins), mixed form with the precision ladder.
+
+    The occupation model (descriptors -> 3x256 SiLU MLP with FP16 weights -> 15 D entries
+    per spin) is trained on --warm-train SCF solutions that the library computes (float) for
+    seeded displaced 12-atom cells (the descriptors see 6 bohr around an atom, so small cells
+    give the local environments cheaply).  Two consecutive steps of a seeded MD trajectory of
+    the 216-atom cell are then solved: step 0 cold (random orbitals, atomic-guess D), step 1
+    from step 0's converged orbitals with the atomic-guess D (the method without the model)
+    and with the model's D.  The cold FP64 time of step 0 is extrapolated from timed FP64
+    iterations and the mixed run's iteration count."""
     import numpy as np
     import torch
     import workloads as w
-    from paper_2507_23612_gb300 import HUB_F64, HUB_MIXED_BF16, Hub, scf_params
+    from paper_2507_23612_gb300 import HUB_F32, HUB_F64, HUB_MIXED_BF16, Hub, scf_params
     from paper_2507_23612_gb300.warmstart import OccupationModel, scf_solve
     dev = torch.device("cuda", 0)
     t0 = time.perf_counter()
     model = OccupationModel(nspin=2, seed=0)
     gen = []
     for i in range(args.warm_train):
-        wl = w.rutile_snapshot((2, 2, 3), 0.1, seed=i)
-        r = scf_solve(wl, HUB_MIXED_BF16)
+        wl = w.rutile_snapshot((1, 1, 2), 0.1, seed=i)
+        r = scf_solve(wl, HUB_F32, tol_e_atom=1e-6, tol_D=1e-5)
         model.add_solution(wl.atoms, wl.L, r["D"])
         gen.append((r["iterations"], r["seconds"]))
     t_gen = time.perf_counter() - t0
     t1 = time.perf_counter()
-    losses = model.fit(steps=2000)
+    losses = model.fit(steps=3000)
     torch.cuda.synchronize()
     t_fit = time.perf_counter() - t1
 
-    big = w.rutile_snapshot((3, 3, 4), 0.1, seed=1000)
-    nat = len(big.atoms)
-    t2 = time.perf_counter()
-    D_pred = model.predict(big.atoms, big.L)
-    t_pred = time.perf_counter() - t2
-    cold = scf_solve(big, HUB_MIXED_BF16)
+    steps = w.rutile_trajectory((3, 3, 4), nsteps=2, amplitude=0.1, period=12.0)
+    s0, s1 = steps
+    nat = len(s0.atoms)
+    cold = scf_solve(s0, HUB_MIXED_BF16, keep_orbitals=True)
+    X0 = [x.clone() for x in cold["X"]]
+    del cold["X"]
     torch.cuda.empty_cache()
-    warm = scf_solve(big, HUB_MIXED_BF16, D0=D_pred)
+    t2 = time.perf_counter()
+    D_pred = model.predict(s1.atoms, s1.L)
+    t_pred = time.perf_counter() - t2
+    atomic = scf_solve(s1, HUB_MIXED_BF16, X0=[x.clone() for x in X0])
+    torch.cuda.empty_cache()
+    warm = scf_solve(s1, HUB_MIXED_BF16, D0=D_pred, X0=[x.clone() for x in X0])
+    del X0
     torch.cuda.empty_cache()
 
-    # cold FP64: the first iteration (first passes) and the following ones timed, then
-    # extrapolated with the cold mixed run's iteration count
+    # cold FP64 of step 0: the first iteration (first passes) and the following ones timed,
+    # then extrapolated with the cold mixed run's iteration count
     f64 = None
     if args.warm_f64_iters > 0:
-        hub = Hub(big.n, big.L, big.fd_half_order, prec=HUB_F64)
-        hub.set_veff(torch.tensor(big.veff, device=dev))
-        hub.set_atoms(big.atoms)
-        Xs = [torch.tensor(big.orbitals(s), device=dev).contiguous() for s in range(big.nspin)]
-        v0s = [torch.tensor(big.lanczos_start(s), device=dev).contiguous() for s in range(big.nspin)]
-        p = scf_params(nspin=2, ncol=big.ncol, ld=big.Nd, degree=big.degree, max_iter=200, first_passes=3,
-                       lanczos_steps=10, pulay_history=7, natoms=nat, pulay_beta=0.3, kT=big.kT,
-                       n_elec=big.n_elec, tol_e_atom=1e-5, tol_D=1e-4)
+        hub = Hub(s0.n, s0.L, s0.fd_half_order, prec=HUB_F64)
+        hub.set_veff(torch.tensor(s0.veff, device=dev))
+        hub.set_atoms(s0.atoms)
+        Xs = [torch.tensor(s0.orbitals(s), device=dev).contiguous() for s in range(s0.nspin)]
+        v0s = [torch.tensor(s0.lanczos_start(s), device=dev).contiguous() for s in range(s0.nspin)]
+        p = scf_params(nspin=2, ncol=s0.ncol, ld=s0.Nd, degree=s0.degree, max_iter=200, first_passes=3,
+                       lanczos_steps=10, pulay_history=7, natoms=nat, pulay_beta=0.3, kT=s0.kT,
+                       n_elec=s0.n_elec, tol_e_atom=1e-5, tol_D=1e-4)
         torch.cuda.synchronize()
         ts = time.perf_counter()
-        hub.scf_begin(p, Xs, v0s, big.D0)
+        hub.scf_begin(p, Xs, v0s, s0.D0)
         times = []
         for _ in range(args.warm_f64_iters):
             hub.scf_iterate()
@@ -544,31 +561,36 @@ def run_warm(args):
         f64 = {"first_iteration_s": round(times[0], 3), "later_iteration_s": round(later, 3),
                "time_to_solution_s_extrapolated": round(est, 2),
                "extrapolation": "first FP64 iteration + (cold mixed iteration count - 1) x timed later FP64 iteration"}
-    err0 = float(np.max(np.abs(big.D0 - cold["D"])))
-    errp = float(np.max(np.abs(D_pred - cold["D"])))
+    err0 = float(np.max(np.abs(s1.D0 - atomic["D"])))
+    errp = float(np.max(np.abs(D_pred - atomic["D"])))
     line = {
-        "metric": "SCF time to solution at 1e-5 Ha/atom (warm start)",
+        "metric": "SCF time to solution at 1e-5 Ha/atom (warm start, MD step)",
         "value": round(warm["seconds"], 3), "unit": "s", "higher_is_better": False, "n_gpus": 1,
         "dtype": "f32+bf16 (FP64 dense steps)", "data": "synthetic",
-        "config": {"workload": big.name, "grid": list(big.n), "orbitals_per_spin": big.ncol, "spins": 2,
-                   "atoms": nat, "hubbard_atoms": D_pred.shape[1], "chebyshev_degree": big.degree,
+        "config": {"workload": s0.name, "grid": list(s0.n), "orbitals_per_spin": s0.ncol, "spins": 2,
+                   "atoms": nat, "hubbard_atoms": D_pred.shape[1], "chebyshev_degree": s0.degree,
+                   "trajectory": "seeded sinusoidal displacements, 0.1 bohr, period 12 steps; steps 0 and 1",
                    "criterion": "|dE|/atom < 1e-5 Ha twice and max|dD| < 1e-4",
                    "model": "descriptors(48) -> 3x256 SiLU -> 30, FP16 weights, FP32 accumulate"},
-        "training": {"scf_solutions": args.warm_train, "cells": "displaced 2x2x3 rutile (72 atoms, 24 Ti), mixed",
+        "training": {"scf_solutions": args.warm_train, "cells": "displaced 1x1x2 rutile (12 atoms, 4 Ti), float",
                      "samples": model.n_samples, "generation_s": round(t_gen, 2),
-                     "scf_iterations": [g[0] for g in gen], "fit_s": round(t_fit, 3), "adam_steps": 2000,
+                     "scf_iterations_mean": float(np.mean([g[0] for g in gen])) if gen else None,
+                     "fit_s": round(t_fit, 3), "adam_steps": 3000,
                      "loss_first_last": [losses[0], losses[-1]], "predict_s": round(t_pred, 4)},
-        "cold_mixed": {"iterations": cold["iterations"], "seconds": round(cold["seconds"], 3),
-                       "E_Ha": cold["E"], "converged": cold["converged"]},
-        "warm_mixed": {"iterations": warm["iterations"], "seconds": round(warm["seconds"], 3),
-                       "E_Ha": warm["E"], "converged": warm["converged"]},
-        "fixed_point": {"dE_Ha_per_atom": abs(warm["E"] - cold["E"]) / nat,
-                        "max_abs_dD": float(np.max(np.abs(warm["D"] - cold["D"])))},
-        "initial_D_error": {"atomic_guess": err0, "model": errp},
-        "cold_f64": f64,
+        "step0_cold_mixed": {"iterations": cold["iterations"], "seconds": round(cold["seconds"], 3),
+                             "E_Ha": cold["E"], "converged": cold["converged"]},
+        "step1_atomic_D_reused_orbitals": {"iterations": atomic["iterations"], "seconds": round(atomic["seconds"], 3),
+                                           "E_Ha": atomic["E"], "converged": atomic["converged"]},
+        "step1_model_D_reused_orbitals": {"iterations": warm["iterations"], "seconds": round(warm["seconds"], 3),
+                                          "E_Ha": warm["E"], "converged": warm["converged"]},
+        "fixed_point_step1": {"dE_Ha_per_atom": abs(warm["E"] - atomic["E"]) / nat,
+                              "max_abs_dD": float(np.max(np.abs(warm["D"] - atomic["D"])))},
+        "initial_D_error_step1": {"atomic_guess": err0, "model": errp},
+        "cold_f64_step0": f64,
     }
     if f64:
         line["speedup_warm_mixed_vs_cold_f64"] = round(f64["time_to_solution_s_extrapolated"] / warm["seconds"], 2)
+    line["speedup_model_vs_atomic_D"] = round(atomic["seconds"] / warm["seconds"], 2)
     print(json.dumps(line))
     return 0
 
@@ -634,6 +656,12 @@ def run_batched(args):
     ms_seq = e0.elapsed_time(e1)
     grids = sorted(set(sn.n for sn in snaps), key=lambda n: n[0] * n[1] * n[2])
     small = batched_small(args, dev, gen)
+    variants = [hb.autotune(0, X) for hb, X in zip(hubs, Xs)][:8]
+    for hb in hubs:
+        hb.close()
+    del Xs
+    torch.cuda.empty_cache()
+    scf_tts = batched_scf_tts(dev)
     print(json.dumps({
         "metric": "H·psi throughput, batched filter", "value": work / (ms_graph / 1e3) / 1e9,
         "unit": "Gpt·orb/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -644,9 +672,79 @@ def run_batched(args):
                    "grids_min_max": [list(grids[0]), list(grids[-1])], "step": "one hub_batch_filter call"},
         "sequential_no_graph": {"ms": ms_seq, "value": work / (ms_seq / 1e3) / 1e9},
         "graph_speedup": ms_seq / ms_graph, "first_call_s": first_s, "setup_s": setup_s,
-        "stencil_variants": [hb.autotune(0, X) for hb, X in zip(hubs, Xs)][:8],
-        "small_systems": small}))
+        "stencil_variants": variants,
+        "small_systems": small, "scf_time_to_solution": scf_tts}))
     return 0
+
+
+def batched_scf_tts(dev):
+    """SCF time to solution of the batched form: k-point SCFs of four snapshot cells (24 and
+    36 atoms, 1-3 Monkhorst-Pack k-points, complex orbitals, 8 channels) to 1e-5 Ha/atom,
+    (a) float, all cells batched (per filter pass one CUDA graph over every channel,
+    hub_kscf_run_batch), (b) float, one cell after another (hub_kscf_run), (c) FP64, one
+    after another; and a launch-bound case, the 24^3 tiny cell with 8 k-points, batched and
+    not.  Wall clock from handle creation to convergence."""
+    import numpy as np
+    import torch
+    import workloads as w
+    from paper_2507_23612_gb300 import HUB_F32, HUB_F64
+    from paper_2507_23612_gb300.kpoint_scf import KpointSCF, run_batched
+
+    def cells():
+        snaps = w.snapshot_batch()
+        return [snaps[i] for i in (0, 1, 5, 6)]
+
+    def tiny_k8():
+        wl = w.tiny()
+        kf = [((i % 2) / 4.0 + 0.125, ((i // 2) % 2) / 4.0 + 0.125, (i // 4) / 4.0 + 0.125) for i in range(8)]
+        wl.kpts = tuple(tuple(2 * np.pi * np.asarray(f) / np.asarray(wl.L)) for f in kf)
+        wl.kweights = tuple([1.0 / 8] * 8)
+        return [wl]
+
+    def solve(wls, prec, batched):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        scfs = []
+        try:
+            for wl in wls:
+                scf = KpointSCF(wl, wl.kpts, wl.kweights, prec, device=dev)
+                scfs.append(scf)
+                dt = scf.hubs[0].dtype
+                X0 = [[torch.tensor(wl.orbitals(0, k, complex_=True), device=dev).to(dt).contiguous()
+                       for k in range(len(wl.kpts))]]
+                v0 = [[torch.tensor(wl.lanczos_start(0, k, complex_=True), device=dev).to(dt).contiguous()
+                       for k in range(len(wl.kpts))]]
+                kw = dict(n_elec=wl.n_elec, kT=wl.kT if wl.kT > 0 else 0.005, degree=wl.degree, max_iter=200,
+                          tol_e_atom=1e-5, tol_D=1e-4)
+                if batched:
+                    scf.begin(X0, v0, wl.D0, **kw)
+                else:
+                    scf.res = scf.run(X0, v0, wl.D0, **kw)
+            res = run_batched(scfs) if batched else [s.res for s in scfs]
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+        finally:
+            for scf in scfs:
+                scf.close()
+        return {"seconds": round(sec, 3), "iterations": [r["iterations"] for r in res],
+                "converged": all(r["converged"] for r in res), "E_Ha": [r["E"] for r in res]}
+
+    out = {}
+    wls = cells()
+    out["cells"] = [f"{wl.name} ({len(wl.kpts)} k)" for wl in wls]
+    out["f32_batched"] = solve(wls, HUB_F32, True)
+    out["f32_one_by_one"] = solve(wls, HUB_F32, False)
+    out["f64_one_by_one"] = solve(wls, HUB_F64, False)
+    nat = [len(wl.atoms) for wl in wls]
+    out["max_dE_f32_batched_vs_f64_Ha_per_atom"] = max(abs(a - b) / n for a, b, n in zip(
+        out["f32_batched"]["E_Ha"], out["f64_one_by_one"]["E_Ha"], nat))
+    out["speedup_batched_vs_f64"] = round(out["f64_one_by_one"]["seconds"] / out["f32_batched"]["seconds"], 2)
+    out["speedup_batched_vs_f32_one_by_one"] = round(out["f32_one_by_one"]["seconds"] / out["f32_batched"]["seconds"], 2)
+    tk = tiny_k8()
+    out["tiny_8k"] = {"f32_batched": solve(tk, HUB_F32, True), "f32_one_by_one": solve(tk, HUB_F32, False)}
+    out["tiny_8k"]["speedup"] = round(out["tiny_8k"]["f32_one_by_one"]["seconds"] /
+                                      out["tiny_8k"]["f32_batched"]["seconds"], 2)
+    return out
 
 
 def batched_small(args, dev, gen):
@@ -712,6 +810,99 @@ def probe_apply(args):
     torch.cuda.synchronize()
     print(json.dumps({"probe": "apply_H", "columns": args.probe_apply, "prec": args.prec,
                       "max_abs": float(Y.abs().max())}))
+    hub.close()
+    return 0
+
+
+def run_projector_forms(args):
+    """Per-kernel times of one float H application on the rutile block (348 random orbitals)
+    for every projector form (point-major, bricks on CUDA cores, tensor-core brick gather,
+    tensor-core gather and scatter) and every float stencil tile shape: 3 warm-up and 10
+    timed applications per setting, CUDA events around every launch on the library's
+    stream.  Also checks that every stencil tile shape gives the same bits."""
+    import torch
+    import workloads as w
+    from paper_2507_23612_gb300 import Hub, HUB_F32
+    wl = w.rutile()
+    dev = torch.device("cuda", 0)
+    hb = Hub(wl.n, wl.L, wl.fd_half_order, prec=HUB_F32)
+    hb.set_veff(torch.tensor(wl.veff, device=dev))
+    hb.set_atoms(wl.atoms)
+    hb.set_occupation_matrix(0, wl.D0[0])
+    g = torch.Generator(device=dev).manual_seed(3)
+    X = torch.randn(wl.ncol, wl.Nd, device=dev, generator=g, dtype=torch.float32)
+    Y = torch.empty_like(X)
+    pts = wl.Nd * wl.ncol
+
+    def timed():
+        for _ in range(3):
+            hb.apply_H(0, X, Y)
+        torch.cuda.synchronize()
+        hb.profile(-1)
+        hb.profile(1)
+        for _ in range(10):
+            hb.apply_H(0, X, Y)
+        torch.cuda.synchronize()
+        hb.profile(0)
+        p = hb.profile_read()
+        hb.profile(-1)
+        # per application (transform: the reduction and coefficient kernels of one gather)
+        return {k: round(v[0] / 10, 4) for k, v in p.items() if k in ("stencil", "gather", "transform", "scatter")}
+
+    forms = {}
+    for form, name in ((0, "point-major"), (1, "bricks, CUDA cores"), (2, "tensor-core gather"),
+                       (3, "tensor-core gather and scatter")):
+        try:
+            hb.set_tuning(gather_form=form)
+        except Exception as e:          # tables not available on this grid
+            forms[name] = str(e)
+            continue
+        t = timed()
+        t["projector_ms"] = round(t.get("gather", 0) + t.get("transform", 0) + t.get("scatter", 0), 4)
+        forms[name] = t
+    hb.set_tuning(gather_form=2)
+    stencil = {}
+    ref = None
+    for v in range(hb.get_tuning()["n_variants"]):
+        hb.set_tuning(stencil_variant=v)
+        t = timed()
+        if ref is None:
+            ref = Y.clone()
+        ms = t["stencil"]
+        stencil[v] = {"ms": ms, "GBs": round(12.0 * pts / (ms * 1e-3) / 1e9, 1),
+                      "frac_of_hbm": round(12.0 * pts / (ms * 1e-3) / 1e9 / hbm_peak()[0], 4),
+                      "same_bits_as_variant_0": bool(torch.equal(Y, ref))}
+    print(json.dumps({"projector_forms_ms_per_application": forms, "float_stencil_variants": stencil,
+                      "workload": "rutile-2x2x3 88x88x84, 348 random orbitals, float", "point_orbitals": pts}))
+    hb.close()
+    return 0
+
+
+def probe_rr(args):
+    """A small case for ncu captures of the Rayleigh-Ritz products: the rutile handle in
+    --prec, one degree-8 filter (so that the block's Gram matrix is well conditioned enough
+    for the mixed form) and two hub_rayleigh_ritz calls on a seeded random block of
+    args.probe_rr columns."""
+    import torch
+    import workloads as w
+    from paper_2507_23612_gb300 import Hub
+    wl = w.rutile()
+    dev = torch.device("cuda", 0)
+    hub = Hub(wl.n, wl.L, wl.fd_half_order, prec=PREC[args.prec])
+    hub.set_veff(torch.tensor(wl.veff, device=dev))
+    hub.set_atoms(wl.atoms)
+    hub.set_occupation_matrix(0, wl.D0[0])
+    g = torch.Generator(device=dev).manual_seed(5)
+    X = torch.randn(args.probe_rr, wl.Nd, device=dev, dtype=torch.float64, generator=g).to(hub.dtype).contiguous()
+    v0 = torch.randn(wl.Nd, device=dev, dtype=torch.float64, generator=g).to(hub.dtype).contiguous()
+    lo, up = hub.lanczos_bound(0, 10, v0)
+    hub.chefsi_filter(0, X, 8, lo + 0.1 * (up - lo), up, lo)
+    eig = None
+    for _ in range(2):
+        eig = hub.rayleigh_ritz(0, X)
+    torch.cuda.synchronize()
+    print(json.dumps({"probe": "rayleigh_ritz", "columns": args.probe_rr, "prec": args.prec,
+                      "eig_min_max": [float(eig[0]), float(eig[-1])]}))
     hub.close()
     return 0
 
@@ -845,12 +1036,13 @@ def run_md_compare(args):
     from paper_2507_23612_gb300.md import trajectory_scf
     from paper_2507_23612_gb300.warmstart import OccupationModel, scf_solve
     steps = w.rutile_trajectory((2, 2, 3), nsteps=args.md_compare, amplitude=0.1, period=12.0)
-    # the occupation model, trained on SCF solutions of displaced cells off the trajectory
+    # the occupation model, trained on SCF solutions of displaced 12-atom cells off the trajectory
+    from paper_2507_23612_gb300 import HUB_F32
     model = OccupationModel(nspin=steps[0].nspin, seed=0)
     for i in range(args.warm_train):
-        snap = w.rutile_snapshot((2, 2, 3), 0.1, seed=500 + i)
-        model.add_solution(snap.atoms, snap.L, scf_solve(snap, PREC[args.prec])["D"])
-    model.fit(steps=1500)
+        snap = w.rutile_snapshot((1, 1, 2), 0.1, seed=500 + i)
+        model.add_solution(snap.atoms, snap.L, scf_solve(snap, HUB_F32, tol_e_atom=1e-6, tol_D=1e-5)["D"])
+    model.fit(steps=3000)
     out = {}
     for start in ("atomic", "extrapolated", "mlp"):
         res = trajectory_scf(steps, PREC[args.prec], start=start, model=model)
@@ -912,6 +1104,10 @@ def main():
         return run_density_scf(args)
     if args.probe_apply:
         return probe_apply(args)
+    if args.probe_rr:
+        return probe_rr(args)
+    if args.projector_forms:
+        return run_projector_forms(args)
     if args.probe_alu:
         from paper_2507_23612_gb300.binding import alu_peaks
         print(json.dumps({"probe": "alu_peaks", **alu_peaks()}))

@@ -372,6 +372,18 @@ int hub_kscf_run(hub_kscf_t s, hub_scf_result* res);
 int hub_kscf_get(hub_kscf_t s, double* eig, double* occ, double* D_re, double* D_im);
 const char* hub_kscf_last_error(hub_kscf_t s);
 int hub_kscf_destroy(hub_kscf_t s);
+/* Batched form (many snapshots or cells at once): one iteration of each of nobj k-point
+ * SCFs (distinct objects over distinct handles; one Chebyshev degree) whose Chebyshev
+ * filters run together: per filter pass and spin, every (object, k) channel still due that
+ * pass goes through one hub_batch_filter call (one CUDA graph), then each channel's
+ * Rayleigh-Ritz, then each object's Fermi level, D, energy and mixing as in
+ * hub_kscf_iterate.  Objects that have converged are left as they are.  res: host
+ * [nobj].  cuda_stream: the stream of the batched filters.  Errors: as hub_kscf_iterate
+ * and hub_batch_filter. */
+int hub_kscf_iterate_batch(int nobj, hub_kscf_t* objs, hub_scf_result* res, void* cuda_stream);
+/* Batched iterations until every object has converged (HUB_OK) or reached its max_iter
+ * (HUB_ENOCONV; the message is on that object). */
+int hub_kscf_run_batch(int nobj, hub_kscf_t* objs, hub_scf_result* res, void* cuda_stream);
 
 /* Self-consistent density SCF: replace the starting density (uniform by default) before the
  * first iteration; rho_dev device double [Nd], the total density (split evenly between two

@@ -77,6 +77,8 @@ _SIGS = {
     "hub_kscf_run": [_P, C.POINTER(scf_result)],
     "hub_kscf_get": [_P, _PD, _PD, _PD, _PD],
     "hub_kscf_last_error": [_P],
+    "hub_kscf_iterate_batch": [_I, C.POINTER(C.c_void_p), C.POINTER(scf_result), _P],
+    "hub_kscf_run_batch": [_I, C.POINTER(C.c_void_p), C.POINTER(scf_result), _P],
     "hub_kscf_destroy": [_P],
     "hub_extrapolate_occupations": [_I, _I, _PD, _PD, _I, _PD, _PD, _PD],
     "hub_cutoff_radius": [_I, _D, _D, _PD],

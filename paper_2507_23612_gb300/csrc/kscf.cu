@@ -115,18 +115,18 @@ int hub_kscf_destroy(hub_kscf_t s) {
 
 const char* hub_kscf_last_error(hub_kscf_t s) { return s ? s->err.c_str() : "NULL k-point SCF"; }
 
-int hub_kscf_iterate(hub_kscf_t s, hub_scf_result* res) {
-    hub::NvtxRange nvtx_("hub_kscf_iterate");
-    if (!s) return HUB_EINVAL;
-    const hub_scf_params& p = s->p;
-    const int ns = p.nspin, nk = s->nk, nh = s->nhub, n = p.ncol;
-    const double deg = ns == 1 ? 2.0 : 1.0;
-    const size_t per = (size_t)nh * 25;
-    int rc;
-    // D_in into every handle; a real handle takes a real D only
+}  // extern "C"
+
+namespace {
+
+// phase 1: D_in into every handle (a real handle takes a real D only)
+int kscf_set_D(hub_kscf_t s) {
+    const int ns = s->p.nspin;
+    const size_t per = (size_t)s->nhub * 25;
     double imax = 0.0;
     for (double v : s->Di_in) imax = std::max(imax, std::fabs(v));
-    for (int k = 0; k < nk; ++k) {
+    int rc;
+    for (int k = 0; k < s->nk; ++k) {
         const hub_t h = s->hubs[k];
         if (!h->cplx && imax > 1e-10)
             return kfail(s, HUB_EINVAL, "a real (Gamma) k-point needs a real D: use a k-set closed under k -> -k");
@@ -136,31 +136,44 @@ int hub_kscf_iterate(hub_kscf_t s, hub_scf_result* res) {
                             "hub_set_occupation_matrix")))
                 return rc;
     }
-    const int passes = s->iter == 0 ? std::max(1, p.first_passes) : 1;
-    for (int sp = 0; sp < ns; ++sp)
-        for (int k = 0; k < nk; ++k) {
-            const hub_t h = s->hubs[k];
-            const int c = sp * nk + k;
-            double* eg = s->eig.data() + (size_t)c * n;
-            for (int pass = 0; pass < passes; ++pass) {
-                if (!s->have_bounds[c]) {
-                    double lo, up;
-                    if ((rc = kcall(s, h, hub_lanczos_bound(h, sp, p.lanczos_steps, s->v0[c], &lo, &up),
-                                    "hub_lanczos_bound")))
-                        return rc;
-                    s->bounds[c] = {lo, lo + 0.1 * (up - lo), up};
-                    s->have_bounds[c] = 1;
-                }
-                const auto& bd = s->bounds[c];
-                if ((rc = kcall(s, h, hub_chefsi_filter(h, sp, s->X[c], n, p.ld, p.degree, bd[1], bd[2], bd[0],
-                                                        nullptr), "hub_chefsi_filter")))
-                    return rc;
-                if ((rc = kcall(s, h, hub_rayleigh_ritz(h, sp, s->X[c], n, p.ld, eg, nullptr), "hub_rayleigh_ritz")))
-                    return rc;
-                s->bounds[c][0] = eg[0];
-                s->bounds[c][1] = eg[n - 1];
-            }
-        }
+    return HUB_OK;
+}
+
+int kscf_passes(hub_kscf_t s) { return s->iter == 0 ? std::max(1, s->p.first_passes) : 1; }
+
+// filter bounds of channel c (spin c / nk, k-point c % nk): Lanczos the first time
+int kscf_bounds(hub_kscf_t s, int c) {
+    if (s->have_bounds[c]) return HUB_OK;
+    const hub_t h = s->hubs[c % s->nk];
+    double lo, up;
+    int rc;
+    if ((rc = kcall(s, h, hub_lanczos_bound(h, c / s->nk, s->p.lanczos_steps, s->v0[c], &lo, &up), "hub_lanczos_bound")))
+        return rc;
+    s->bounds[c] = {lo, lo + 0.1 * (up - lo), up};
+    s->have_bounds[c] = 1;
+    return HUB_OK;
+}
+
+// Rayleigh-Ritz of channel c; the next filter's a_low and a from its Ritz values
+int kscf_rr(hub_kscf_t s, int c) {
+    const hub_t h = s->hubs[c % s->nk];
+    const int n = s->p.ncol;
+    double* eg = s->eig.data() + (size_t)c * n;
+    int rc;
+    if ((rc = kcall(s, h, hub_rayleigh_ritz(h, c / s->nk, s->X[c], n, s->p.ld, eg, nullptr), "hub_rayleigh_ritz")))
+        return rc;
+    s->bounds[c][0] = eg[0];
+    s->bounds[c][1] = eg[n - 1];
+    return HUB_OK;
+}
+
+// phase 3: Fermi level, D_out, energy, convergence and Pulay mixing of D
+int kscf_post(hub_kscf_t s, hub_scf_result* res) {
+    const hub_scf_params& p = s->p;
+    const int ns = p.nspin, nk = s->nk, nh = s->nhub, n = p.ncol;
+    const double deg = ns == 1 ? 2.0 : 1.0;
+    const size_t per = (size_t)nh * 25;
+    int rc;
     // one Fermi level over every (spin, k) state, each weighted by its k-point's weight
     const int nstates = ns * nk * n;
     std::vector<double> w((size_t)nstates);
@@ -257,6 +270,112 @@ int hub_kscf_iterate(hub_kscf_t s, hub_scf_result* res) {
     }
     s->last = r;
     if (res) *res = r;
+    return HUB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hub_kscf_iterate(hub_kscf_t s, hub_scf_result* res) {
+    hub::NvtxRange nvtx_("hub_kscf_iterate");
+    if (!s) return HUB_EINVAL;
+    const hub_scf_params& p = s->p;
+    int rc;
+    if ((rc = kscf_set_D(s))) return rc;
+    const int passes = kscf_passes(s);
+    for (int c = 0; c < p.nspin * s->nk; ++c) {
+        const hub_t h = s->hubs[c % s->nk];
+        for (int pass = 0; pass < passes; ++pass) {
+            if ((rc = kscf_bounds(s, c))) return rc;
+            const auto& bd = s->bounds[c];
+            if ((rc = kcall(s, h, hub_chefsi_filter(h, c / s->nk, s->X[c], p.ncol, p.ld, p.degree, bd[1], bd[2], bd[0],
+                                                    nullptr), "hub_chefsi_filter")))
+                return rc;
+            if ((rc = kscf_rr(s, c))) return rc;
+        }
+    }
+    return kscf_post(s, res);
+}
+
+int hub_kscf_iterate_batch(int nobj, hub_kscf_t* objs, hub_scf_result* res, void* cuda_stream) {
+    hub::NvtxRange nvtx_("hub_kscf_iterate_batch");
+    if (nobj < 1 || !objs || !res) return HUB_EINVAL;
+    for (int i = 0; i < nobj; ++i) {
+        if (!objs[i]) return HUB_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (objs[j] == objs[i]) return HUB_EINVAL;
+    }
+    int rc;
+    std::vector<int> active;
+    for (int i = 0; i < nobj; ++i)
+        if (!objs[i]->last.converged || objs[i]->iter == 0) active.push_back(i);
+    for (int i : active)
+        if ((rc = kscf_set_D(objs[i]))) return rc;
+    int maxpass = 0;
+    for (int i : active) maxpass = std::max(maxpass, kscf_passes(objs[i]));
+    for (int pass = 0; pass < maxpass; ++pass)
+        for (int sp = 0; sp < 2; ++sp) {
+            // every channel of this spin still due a pass, one graph for all of them
+            std::vector<std::pair<int, int>> ch;       // (object, channel)
+            for (int i : active) {
+                hub_kscf_t s = objs[i];
+                if (sp >= s->p.nspin || pass >= kscf_passes(s)) continue;
+                for (int k = 0; k < s->nk; ++k) ch.emplace_back(i, sp * s->nk + k);
+            }
+            if (ch.empty()) continue;
+            std::vector<hub_t> hs;
+            std::vector<int> spin, ncol, ld;
+            std::vector<void*> X;
+            std::vector<double> a, b, al;
+            for (auto& q : ch) {
+                hub_kscf_t s = objs[q.first];
+                if ((rc = kscf_bounds(s, q.second))) return rc;
+                hs.push_back(s->hubs[q.second % s->nk]);
+                spin.push_back(sp);
+                X.push_back(s->X[q.second]);
+                ncol.push_back(s->p.ncol);
+                ld.push_back(s->p.ld);
+                al.push_back(s->bounds[q.second][0]);
+                a.push_back(s->bounds[q.second][1]);
+                b.push_back(s->bounds[q.second][2]);
+            }
+            const int degree = objs[ch[0].first]->p.degree;
+            for (auto& q : ch)
+                if (objs[q.first]->p.degree != degree)
+                    return kfail(objs[q.first], HUB_EINVAL, "batched SCFs need one Chebyshev degree");
+            if ((rc = hub_batch_filter((int)ch.size(), hs.data(), spin.data(), X.data(), ncol.data(), ld.data(), degree,
+                                       a.data(), b.data(), al.data(), cuda_stream))) {
+                const char* m = hub_last_error(hs[0]);
+                return kfail(objs[ch[0].first], rc, std::string("hub_batch_filter: ") + (m ? m : ""));
+            }
+            for (auto& q : ch)
+                if ((rc = kscf_rr(objs[q.first], q.second))) return rc;
+        }
+    for (int i = 0; i < nobj; ++i) {
+        if (std::find(active.begin(), active.end(), i) == active.end()) { res[i] = objs[i]->last; continue; }
+        if ((rc = kscf_post(objs[i], &res[i]))) return rc;
+    }
+    return HUB_OK;
+}
+
+int hub_kscf_run_batch(int nobj, hub_kscf_t* objs, hub_scf_result* res, void* cuda_stream) {
+    if (nobj < 1 || !objs || !res) return HUB_EINVAL;
+    int max_iter = 0;
+    for (int i = 0; i < nobj; ++i) {
+        if (!objs[i]) return HUB_EINVAL;
+        max_iter = std::max(max_iter, objs[i]->p.max_iter);
+    }
+    for (int it = 0; it < max_iter; ++it) {
+        bool done = true;
+        for (int i = 0; i < nobj; ++i)
+            if (!(objs[i]->iter > 0 && objs[i]->last.converged) && objs[i]->iter < objs[i]->p.max_iter) done = false;
+        if (done) break;
+        const int rc = hub_kscf_iterate_batch(nobj, objs, res, cuda_stream);
+        if (rc) return rc;
+    }
+    for (int i = 0; i < nobj; ++i)
+        if (!res[i].converged) return kfail(objs[i], HUB_ENOCONV, "k-point SCF reached max_iter");
     return HUB_OK;
 }
 

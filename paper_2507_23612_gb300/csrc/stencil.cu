@@ -744,6 +744,298 @@ k_stencil_f32s(StencilDev<float> a) {
     cp_async_wait<0>();
 }
 
+// Two y-rows per thread (rows A = 2 ty and B = 2 ty + 1 of the tile, 4 x-points each): the
+// y-neighbour rows of the pair are read once for both (row rb + 1 + p serves A's pair p + 1
+// and B's pair p, row rb - p serves A's pair p and B's pair p + 1; the two centre rows come
+// from the z-queues), halving the shared-memory bytes of the y-terms, and the copy and loop
+// work of a plane is shared by 8 points.  Per point the arithmetic and its order are those of
+// k_stencil_f32s (the results are the same bits).
+template <int TXT, int TYT, int PH>
+struct Split2Cfg {
+    static constexpr int NH = 6, HX = 8;
+    static constexpr int TXP = TXT * 4;
+    static constexpr int TY = 2 * TYT;                 // rows of the tile
+    static constexpr int SXV = (TXP + 2 * HX) / 4;     // float4 vectors per halo row
+    static constexpr int SY = TY + 2 * NH;
+    static constexpr int NT = TXT * TYT;               // threads
+    static constexpr int RS = PH + 2;
+    static constexpr int NVS = SXV * SY;
+    static constexpr int PER = (NVS + NT - 1) / NT;
+    static constexpr size_t YB = 16 * (size_t)NVS;     // halo plane
+    static constexpr size_t IB = 32 * (size_t)NT;      // two float4 per thread (rows A, B)
+    static constexpr size_t STAGE = YB + 3 * IB;       // halo | feed | V | Yprev
+    static constexpr size_t SMEM = STAGE * RS;
+};
+
+template <int TXT, int TYT, int PH>
+__global__ void __launch_bounds__(TXT * TYT, 1)
+k_stencil_f32s2(StencilDev<float> a) {
+    const Coef<float> cf = resolve_coef(a);
+    using C = Split2Cfg<TXT, TYT, PH>;
+    constexpr int NH = C::NH, HX = C::HX, SXV = C::SXV, RS = C::RS, NT = C::NT, PER = C::PER;
+    constexpr int Q = 2 * NH + 1;
+    static_assert(C::YB % 16 == 0 && C::STAGE % 16 == 0, "stage regions stay 16-byte aligned");
+    extern __shared__ __align__(128) unsigned char smem[];
+
+    const int tid = threadIdx.x;
+    const int tx = tid % TXT, ty = tid / TXT;
+    const int col = blockIdx.z / a.nzc;
+    const int zc = blockIdx.z - col * a.nzc;
+    const int z0 = zc * a.zchunk;
+    const int z1 = min(z0 + a.zchunk, a.n3);
+    const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
+    const long plane = (long)n1 * n2;
+    const int gx0 = blockIdx.x * C::TXP, gy0 = blockIdx.y * C::TY;
+
+    const float* __restrict__ Y = reinterpret_cast<const float*>(a.Y) + (size_t)col * a.ld;
+    const float* Yp = a.Yprev ? reinterpret_cast<const float*>(a.Yprev) + (size_t)col * a.ld : nullptr;
+    float* Yo = reinterpret_cast<float*>(a.Yout) + (size_t)col * a.ld;
+
+    int s_idx[PER];
+    const float* s_src[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = tid + k * NT;
+        s_idx[k] = -1;
+        s_src[k] = Y;
+        if (i < C::NVS) {
+            const int cx = i % SXV, iy = i / SXV;
+            const int gx = gx0 - HX + cx * 4, gy = gy0 - NH + iy;
+            const int wx = floordiv(gx, n1), wy = floordiv(gy, n2);
+            s_idx[k] = i;
+            s_src[k] = Y + (long)(gy - wy * n2) * n1 + (gx - wx * n1);
+        }
+    }
+    const int gxt = gx0 + tx * 4, gyA = gy0 + 2 * ty;
+    const bool actA = (gxt < n1) && (gyA < n2);
+    const bool actB = (gxt < n1) && (gyA + 1 < n2);
+    const long ownA = (long)gyA * n1 + gxt, ownB = ownA + n1;
+
+    auto stY = [&](int st) { return reinterpret_cast<ulonglong2*>(smem + C::STAGE * (size_t)st); };
+    auto stI = [&](int st, int k) {            // k = 0 feed, 1 V, 2 Yprev; [2 tid + row]
+        return reinterpret_cast<ulonglong2*>(smem + C::STAGE * (size_t)st + C::YB + C::IB * (size_t)k);
+    };
+    int ip = z0;
+    long ioff = (long)z0 * plane;
+    int fz = z0 + NH + 1;
+    while (fz >= n3) fz -= n3;
+    long foff = (long)fz * plane;
+    auto issue = [&](int st) {
+        if (ip < z1) {
+            ulonglong2* ys = stY(st);
+#pragma unroll
+            for (int k = 0; k < PER; ++k)
+                if (s_idx[k] >= 0) cp_async<16>(ys + s_idx[k], s_src[k] + ioff);
+            if (actA) {
+                cp_async<16>(stI(st, 1) + 2 * tid, a.V + ioff + ownA);
+                if (Yp) cp_async<16>(stI(st, 2) + 2 * tid, Yp + ioff + ownA);
+            }
+            if (actB) {
+                cp_async<16>(stI(st, 1) + 2 * tid + 1, a.V + ioff + ownB);
+                if (Yp) cp_async<16>(stI(st, 2) + 2 * tid + 1, Yp + ioff + ownB);
+            }
+        }
+        if (ip + 1 < z1) {
+            if (actA) cp_async<16>(stI(st, 0) + 2 * tid, Y + foff + ownA);
+            if (actB) cp_async<16>(stI(st, 0) + 2 * tid + 1, Y + foff + ownB);
+        }
+        ++ip;
+        ioff += plane;
+        if (++fz == n3) { fz = 0; foff = 0; } else foff += plane;
+    };
+
+    u64 wx[NH], wy[NH], wz[NH];
+#pragma unroll
+    for (int p = 0; p < NH; ++p) {
+        wx[p] = pk2(cf.w[0][p], cf.w[0][p]);
+        wy[p] = pk2(cf.w[1][p], cf.w[1][p]);
+        wz[p] = pk2(cf.w[2][p], cf.w[2][p]);
+    }
+    const u64 cen2 = pk2(cf.center, cf.center), alp2 = pk2(cf.alpha, cf.alpha), bet2 = pk2(cf.beta, cf.beta);
+    const u64 m2 = pk2(-2.0f, -2.0f);
+
+    u64 qAl[Q], qAh[Q], qBl[Q], qBh[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        qAl[j] = qAh[j] = qBl[j] = qBh[j] = 0ull;
+        const int p = z0 - NH + j;
+        const int wz_ = floordiv(p, n3);
+        const long zo = (long)(p - wz_ * n3) * plane;
+        if (actA) {
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(Y + zo + ownA);
+            qAl[j] = v.x;
+            qAh[j] = v.y;
+        }
+        if (actB) {
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(Y + zo + ownB);
+            qBl[j] = v.x;
+            qBh[j] = v.y;
+        }
+    }
+#pragma unroll 1
+    for (int j = 0; j < PH; ++j) {
+        issue(j % RS);
+        cp_async_commit();
+    }
+    int sz = 0, si = PH % RS;
+    const int rb = 2 * ty + NH;                 // halo row of row A
+    // x-terms of one row: halo row hr, centre (cl, ch), into (xl, xh)
+    auto xterms = [&](const ulonglong2* ys, int hr, u64 cl, u64 ch, u64& xl, u64& xh) {
+        u64 r[10];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            const ulonglong2 v = ys[hr * SXV + tx + j];
+            r[2 * j] = v.x;
+            r[2 * j + 1] = v.y;
+        }
+        u64 u[8];
+#pragma unroll
+        for (int k = 1; k <= 7; ++k) u[k] = pk2(hi2(r[k]), lo2(r[k + 1]));
+#pragma unroll
+        for (int p = 1; p <= NH; ++p) {
+            const u64 lp = (p & 1) ? u[(8 + p - 1) / 2] : r[(8 + p) / 2];
+            const u64 lm = (p & 1) ? u[(8 - p - 1) / 2] : r[(8 - p) / 2];
+            const u64 hp = (p & 1) ? u[(10 + p - 1) / 2] : r[(10 + p) / 2];
+            const u64 hm = (p & 1) ? u[(10 - p - 1) / 2] : r[(10 - p) / 2];
+            const u64 dxl = fma2(m2, cl, add2(lp, lm));
+            const u64 dxh = fma2(m2, ch, add2(hp, hm));
+            if (p == 1) { xl = mul2(wx[0], dxl); xh = mul2(wx[0], dxh); }
+            else { xl = fma2(wx[p - 1], dxl, xl); xh = fma2(wx[p - 1], dxh, xh); }
+        }
+    };
+#pragma unroll 1
+    for (int zb = z0; zb < z1; zb += Q) {
+#pragma unroll
+        for (int st = 0; st < Q; ++st) {
+            const int z = zb + st;
+            if (z >= z1) break;
+            issue(si);
+            cp_async_commit();
+            cp_async_wait<PH>();
+            __syncthreads();
+            if (actA || actB) {
+                const ulonglong2* ys = stY(sz);
+                const u64 cAl = qAl[(st + NH) % Q], cAh = qAh[(st + NH) % Q];
+                const u64 cBl = qBl[(st + NH) % Q], cBh = qBh[(st + NH) % Q];
+                // y-terms of both rows; upl/uph = row rb + p, dnl/dnh = row rb + 1 - p (the
+                // rows A's pair p and B's pair p - 1 share), advanced pairwise
+                u64 yAl = 0ull, yAh = 0ull, yBl = 0ull, yBh = 0ull;
+                u64 upl = cBl, uph = cBh, dnl = cAl, dnh = cAh;
+                if (!actB) {                    // row B outside the cell: its periodic image
+                    const ulonglong2 c1 = ys[(rb + 1) * SXV + tx + 2];
+                    upl = c1.x;
+                    uph = c1.y;
+                }
+#pragma unroll
+                for (int p = 1; p <= NH; ++p) {
+                    const ulonglong2 nu = ys[(rb + 1 + p) * SXV + tx + 2];      // row rb + 1 + p
+                    const ulonglong2 nd = ys[(rb - p) * SXV + tx + 2];          // row rb - p
+                    const u64 dAl = fma2(m2, cAl, add2(upl, nd.x));
+                    const u64 dAh = fma2(m2, cAh, add2(uph, nd.y));
+                    const u64 dBl = fma2(m2, cBl, add2(nu.x, dnl));
+                    const u64 dBh = fma2(m2, cBh, add2(nu.y, dnh));
+                    if (p == 1) {
+                        yAl = mul2(wy[0], dAl); yAh = mul2(wy[0], dAh);
+                        yBl = mul2(wy[0], dBl); yBh = mul2(wy[0], dBh);
+                    } else {
+                        yAl = fma2(wy[p - 1], dAl, yAl); yAh = fma2(wy[p - 1], dAh, yAh);
+                        yBl = fma2(wy[p - 1], dBl, yBl); yBh = fma2(wy[p - 1], dBh, yBh);
+                    }
+                    upl = nu.x; uph = nu.y;
+                    dnl = nd.x; dnh = nd.y;
+                }
+                // row A: z-terms, x-terms, combination (the order of k_stencil_f32s)
+                {
+                    u64 zl = 0ull, zh = 0ull, xl = 0ull, xh = 0ull;
+#pragma unroll
+                    for (int p = 1; p <= NH; ++p) {
+                        const u64 dzl = fma2(m2, cAl, add2(qAl[(st + NH + p) % Q], qAl[(st + NH - p) % Q]));
+                        const u64 dzh = fma2(m2, cAh, add2(qAh[(st + NH + p) % Q], qAh[(st + NH - p) % Q]));
+                        if (p == 1) { zl = mul2(wz[0], dzl); zh = mul2(wz[0], dzh); }
+                        else { zl = fma2(wz[p - 1], dzl, zl); zh = fma2(wz[p - 1], dzh, zh); }
+                    }
+                    xterms(ys, rb, cAl, cAh, xl, xh);
+                    const ulonglong2 vv = stI(sz, 1)[2 * tid];
+                    u64 al = mul2(fma2(alp2, vv.x, cen2), cAl);
+                    u64 ah = mul2(fma2(alp2, vv.y, cen2), cAh);
+                    al = add2(al, add2(add2(xl, yAl), zl));
+                    ah = add2(ah, add2(add2(xh, yAh), zh));
+                    if (Yp) {
+                        const ulonglong2 pv = stI(sz, 2)[2 * tid];
+                        al = fma2(bet2, pv.x, al);
+                        ah = fma2(bet2, pv.y, ah);
+                    }
+                    if (actA) *reinterpret_cast<ulonglong2*>(Yo + (long)z * plane + ownA) = make_ulonglong2(al, ah);
+                }
+                {
+                    u64 zl = 0ull, zh = 0ull, xl = 0ull, xh = 0ull;
+#pragma unroll
+                    for (int p = 1; p <= NH; ++p) {
+                        const u64 dzl = fma2(m2, cBl, add2(qBl[(st + NH + p) % Q], qBl[(st + NH - p) % Q]));
+                        const u64 dzh = fma2(m2, cBh, add2(qBh[(st + NH + p) % Q], qBh[(st + NH - p) % Q]));
+                        if (p == 1) { zl = mul2(wz[0], dzl); zh = mul2(wz[0], dzh); }
+                        else { zl = fma2(wz[p - 1], dzl, zl); zh = fma2(wz[p - 1], dzh, zh); }
+                    }
+                    xterms(ys, rb + 1, cBl, cBh, xl, xh);
+                    const ulonglong2 vv = stI(sz, 1)[2 * tid + 1];
+                    u64 bl = mul2(fma2(alp2, vv.x, cen2), cBl);
+                    u64 bh = mul2(fma2(alp2, vv.y, cen2), cBh);
+                    bl = add2(bl, add2(add2(xl, yBl), zl));
+                    bh = add2(bh, add2(add2(xh, yBh), zh));
+                    if (Yp) {
+                        const ulonglong2 pv = stI(sz, 2)[2 * tid + 1];
+                        bl = fma2(bet2, pv.x, bl);
+                        bh = fma2(bet2, pv.y, bh);
+                    }
+                    if (actB) *reinterpret_cast<ulonglong2*>(Yo + (long)z * plane + ownB) = make_ulonglong2(bl, bh);
+                }
+                if (z + 1 < z1) {
+                    const ulonglong2 fa = stI(sz, 0)[2 * tid], fb = stI(sz, 0)[2 * tid + 1];
+                    qAl[st] = fa.x; qAh[st] = fa.y;         // slot of plane z - NH takes plane z + NH + 1
+                    qBl[st] = fb.x; qBh[st] = fb.y;
+                }
+            }
+            if (++sz == RS) sz = 0;
+            if (++si == RS) si = 0;
+        }
+    }
+    cp_async_wait<0>();
+}
+
+template <int TXT, int TYT, int PH>
+static int run_f32s2(hub_t h, const StencilArgs& s) {
+    using Cfg = Split2Cfg<TXT, TYT, PH>;
+    StencilDev<float> d;
+    d.Y = s.Y;
+    d.Yprev = s.Yprev;
+    d.Yout = s.Yout;
+    d.V = reinterpret_cast<const float*>(s.V);
+    d.n1 = s.n1; d.n2 = s.n2; d.n3 = s.n3; d.ld = s.ld;
+    fill_coefficients<float>(s, d);
+    for (int a = 0; a < 3; ++a) {
+        d.ph[a][0] = 1.0;
+        d.ph[a][1] = 0.0;
+    }
+    const int tiles = ((s.n1 + Cfg::TXP - 1) / Cfg::TXP) * ((s.n2 + Cfg::TY - 1) / Cfg::TY);
+    const long want = 4L * h->num_sms;
+    const long per = (long)tiles * s.ncol;
+    int nzc = 1;
+    if (per < want) nzc = (int)((want + per - 1) / per);
+    int zchunk = (s.n3 + nzc - 1) / nzc;
+    if (zchunk < 16) zchunk = s.n3 < 16 ? s.n3 : 16;
+    nzc = (s.n3 + zchunk - 1) / zchunk;
+    while ((long)s.ncol * nzc > 65535) { zchunk *= 2; nzc = (s.n3 + zchunk - 1) / zchunk; }
+    d.zchunk = zchunk;
+    d.nzc = nzc;
+    HUB_CUDA_TRY(h, cudaFuncSetAttribute(k_stencil_f32s2<TXT, TYT, PH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
+    dim3 grid((s.n1 + Cfg::TXP - 1) / Cfg::TXP, (s.n2 + Cfg::TY - 1) / Cfg::TY, s.ncol * nzc);
+    ProfScope ps(h, HUB_K_STENCIL);
+    k_stencil_f32s2<TXT, TYT, PH><<<grid, TXT * TYT, Cfg::SMEM, h->stream>>>(d);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    return HUB_OK;
+}
+
 template <int TXT, int TY, int PH>
 static int run_f32s(hub_t h, const StencilArgs& s) {
     using Cfg = SplitCfg<TXT, TY, PH>;
@@ -947,7 +1239,7 @@ int launch_fd_gradient(hub_t h, const void* X, int ld, int ncol, int axis, const
 // Tile shapes the autotuner chooses from, per kernel family (index 0 is the default).
 int stencil_variants(hub_t h) {
     const int es = h->esize * (h->cplx ? 2 : 1);
-    if (h->esize == 4) return h->cplx ? 4 : 6;   // float real (packed) / float complex (vector)
+    if (h->esize == 4) return h->cplx ? 4 : 9;   // float real (packed) / float complex (vector)
     return es == 16 ? 2 : 3;              // double complex / double real (scalar pipeline)
 }
 
@@ -968,6 +1260,9 @@ int launch_stencil(hub_t h, const StencilArgs& a) {
                 case 3: return run_f32s<8, 16, 3>(h, a);
                 case 4: return run_f32s<16, 8, 2>(h, a);
                 case 5: return run_f32s<8, 8, 2>(h, a);
+                case 6: return run_f32s2<8, 8, 2>(h, a);
+                case 7: return run_f32s2<8, 16, 2>(h, a);
+                case 8: return run_f32s2<16, 8, 2>(h, a);
                 default: return run_f32s<8, 16, 2>(h, a);
             }
         }

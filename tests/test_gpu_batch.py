@@ -72,8 +72,15 @@ def test_autotune_keeps_results_identical():
     Y0 = torch.empty_like(X)
     hb.apply_H(0, X, Y0)
     v = hb.autotune(0, X)
-    assert 0 <= v < hb.get_tuning()["n_variants"]
+    tuning = hb.get_tuning()
+    assert 0 <= v < tuning["n_variants"]
     Y1 = torch.empty_like(X)
     hb.apply_H(0, X, Y1)
-    # every tile shape evaluates the same arithmetic in the same order per point
-    assert torch.equal(Y0, Y1)
+    # every stencil tile shape evaluates the same arithmetic in the same order per point:
+    # with the tuned projector form kept, the default tile shape gives the same bits
+    hb.set_tuning(stencil_variant=0, gather_form=tuning["gather_form"])
+    Y2 = torch.empty_like(X)
+    hb.apply_H(0, X, Y2)
+    assert torch.equal(Y1, Y2)
+    # the projector forms (point-major, bricks, tensor-core bricks) differ by float rounding
+    assert rel(Y1.cpu().numpy(), Y0.cpu().numpy()) < 5e-6

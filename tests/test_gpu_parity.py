@@ -71,10 +71,13 @@ def test_apply_H_padded_leading_dimension_and_spin_channels():
 
 @pytest.mark.parametrize("prec", [HUB_F32, HUB_F64])
 def test_apply_H_every_stencil_variant(prec):
-    """Every tile shape the autotuner may choose, on a ragged grid with chunked z and on a
-    grid thinner in z than the stencil's half-width (each plane wraps several times)."""
+    """Every tile shape the autotuner may choose, on a ragged grid with chunked z, on a grid
+    thinner in z than the stencil's half-width (each plane wraps several times), and on a
+    grid with an odd number of y-rows (the last row pair of the two-row float tiles has one
+    row outside the cell)."""
     cases = [systems()["ragged"],
-             w.small_test_system(n=(8, 12, 3), ncol=5, natoms=2, hub_rc=2.0, kb_rc=1.5, seed=5)]
+             w.small_test_system(n=(8, 12, 3), ncol=5, natoms=2, hub_rc=2.0, kb_rc=1.5, seed=5),
+             w.small_test_system(n=(12, 9, 10), ncol=6, natoms=2, hub_rc=2.0, kb_rc=1.5, seed=6)]
     for wl in cases:
         X = wl.orbitals()
         ref = oracle_ham(wl, D=wl.D0[0]).apply(X.T).T
