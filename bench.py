@@ -8,7 +8,7 @@ channels, 12th-order FD, Chebyshev degree 24, FP64.  One step = one SCF iteratio
 library's public entry point hub_scf_iterate: per spin a degree-24 filter and a Rayleigh-Ritz
 projection (25 H applications), then Fermi level, occupation matrices, E_U and Pulay mixing.
 
-Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec f64|f32|mixed]
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec f64|f32|mixed|mixed16]
         python bench.py --impl reference ...      (the CPU oracle arm)
 Multi-GPU (torchrun, one rank per GPU): each rank runs an independent replica of the
 workload (spin channels / snapshots are independent units): weak scaling, no collective on
@@ -28,8 +28,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-PREC = {"f64": 0, "f32": 1, "mixed": 2}
-DTYPE_NAME = {"f64": "f64", "f32": "f32", "mixed": "f32+bf16"}
+PREC = {"f64": 0, "f32": 1, "mixed": 2, "mixed16": 3}
+DTYPE_NAME = {"f64": "f64", "f32": "f32", "mixed": "f32+bf16", "mixed16": "f32+f16"}
 # FP64 pipe of one GB300: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (max SM clock)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 # algorithmic work per point-orbital of one stencil pass (12th order, symmetric pairing):
@@ -305,7 +305,7 @@ def run_hub(args, rank, world, local_rank):
                    first_passes=3 if args.workload == "rutile" else 1, lanczos_steps=10,
                    pulay_history=7, natoms=len(wl.atoms), pulay_beta=0.3,
                    kT=wl.kT if wl.kT > 0 else 0.005, n_elec=wl.n_elec, tol_e_atom=1e-5, tol_D=1e-4,
-                   ladder=1 if args.prec == "mixed" else 0, ladder_tol=1e-4)
+                   ladder=1 if args.prec in ("mixed", "mixed16") else 0, ladder_tol=1e-4)
     hub.scf_begin(p, Xs, v0s, wl.D0)
     for _ in range(args.warmup):
         hub.scf_iterate()
@@ -413,7 +413,7 @@ def scf_solve_timed(wl, X0, dev, prec, profile_after=0):
     p = scf_params(nspin=wl.nspin, ncol=wl.ncol, ld=wl.Nd, degree=wl.degree, max_iter=200,
                    first_passes=3, lanczos_steps=10, pulay_history=7, natoms=len(wl.atoms),
                    pulay_beta=0.3, kT=wl.kT if wl.kT > 0 else 0.005, n_elec=wl.n_elec,
-                   tol_e_atom=1e-5, tol_D=1e-4, ladder=1 if prec == "mixed" else 0, ladder_tol=1e-4)
+                   tol_e_atom=1e-5, tol_D=1e-4, ladder=1 if prec in ("mixed", "mixed16") else 0, ladder_tol=1e-4)
     hub.scf_begin(p, Xs, v0s, wl.D0)
     res = hub.scf_run()
     torch.cuda.synchronize()
@@ -441,16 +441,23 @@ def scf_time_to_solution(wl, X0, dev):
     nat = len(wl.atoms)
     f64, _, _ = scf_solve_timed(wl, X0, dev, "f64")
     mixed, prof, fpts = scf_solve_timed(wl, X0, dev, "mixed", profile_after=2)
+    mixed16, _, _ = scf_solve_timed(wl, X0, dev, "mixed16")
+
+    def errors(r):
+        return {"E_Ha_per_atom": abs(r["E"] - f64["E"]) / nat, "E_U_Ha_per_atom": abs(r["E_U"] - f64["E_U"]) / nat,
+                "band_Ha_per_atom": abs(r["band"] - f64["band"]) / nat,
+                "max_abs_dD": float(np.max(np.abs(r["D"] - f64["D"])))}
     out = {"criterion": "|dE|/atom < 1e-5 Ha twice and max|dD| < 1e-4; wall clock from handle creation",
            "f64": {"seconds": round(f64["seconds"], 3), "iterations": f64["iterations"],
                    "converged": f64["converged"], "E_Ha": f64["E"], "E_U_Ha": f64["E_U"]},
            "mixed": {"seconds": round(mixed["seconds"], 3), "iterations": mixed["iterations"],
                      "converged": mixed["converged"], "E_Ha": mixed["E"], "E_U_Ha": mixed["E_U"],
-                     "error_vs_f64": {"E_Ha_per_atom": abs(mixed["E"] - f64["E"]) / nat,
-                                      "E_U_Ha_per_atom": abs(mixed["E_U"] - f64["E_U"]) / nat,
-                                      "band_Ha_per_atom": abs(mixed["band"] - f64["band"]) / nat,
-                                      "max_abs_dD": float(np.max(np.abs(mixed["D"] - f64["D"])))}},
-           "speedup_mixed_vs_f64": round(f64["seconds"] / mixed["seconds"], 2)}
+                     "error_vs_f64": errors(mixed)},
+           "mixed_f16": {"seconds": round(mixed16["seconds"], 3), "iterations": mixed16["iterations"],
+                         "converged": mixed16["converged"], "E_Ha": mixed16["E"], "E_U_Ha": mixed16["E_U"],
+                         "error_vs_f64": errors(mixed16)},
+           "speedup_mixed_vs_f64": round(f64["seconds"] / mixed["seconds"], 2),
+           "speedup_mixed_f16_vs_f64": round(f64["seconds"] / mixed16["seconds"], 2)}
     if prof:
         out["mixed_rooflines"] = {k: kernel_roofline(k, prof[k], wl, "mixed", fpts)
                                   for k in ("stencil", "gather", "scatter") if k in prof}
@@ -466,7 +473,7 @@ def scf_compare(args):
     wl = make_workload(args.workload)
     X0 = [wl.orbitals(s) for s in range(wl.nspin)]
     out = {}
-    for form in ("f64", "f32", "mixed"):
+    for form in ("f64", "f32", "mixed", "mixed16"):
         out[form], _, _ = scf_solve_timed(wl, X0, dev, form)
     nat = len(wl.atoms)
     ref = out["f64"]
@@ -1007,7 +1014,7 @@ def run_density_scf(args):
     p = scf_params(nspin=wl.nspin, ncol=wl.ncol, ld=wl.Nd, degree=wl.degree, max_iter=200,
                    first_passes=3, lanczos_steps=10, pulay_history=7, natoms=len(wl.atoms),
                    pulay_beta=0.3, kT=wl.kT if wl.kT > 0 else 0.005, n_elec=wl.n_elec,
-                   tol_e_atom=1e-5, tol_D=1e-4, ladder=1 if args.prec == "mixed" else 0, ladder_tol=1e-4,
+                   tol_e_atom=1e-5, tol_D=1e-4, ladder=1 if args.prec in ("mixed", "mixed16") else 0, ladder_tol=1e-4,
                    density=1, kerker_kappa=0.5, tol_rho=1e-4, cg_tol=1e-10)
     torch.cuda.synchronize()
     t0 = time.perf_counter()

@@ -15,9 +15,10 @@
  *   - Grid: orthogonal cell L_a = n_a h_a; node (i1,i2,i3) at (i1 h1, i2 h2, i3 h3);
  *     grid functions are flattened x-fastest: g = i1 + n1*(i2 + n2*i3); Nd = n1 n2 n3.
  *   - A block of ncol orbitals is column-major: element (g, j) at X[g + j*ld], ld >= Nd.
- *   - Element type of X/Y/work is fixed by the handle: HUB_F64 -> double, HUB_F32 and
- *     HUB_MIXED_BF16 -> float; with ncomplex = 1 it is the interleaved complex of that type
- *     (re, im).  Occupation matrices, eigenvalues and energies are always double.
+ *   - Element type of X/Y/work is fixed by the handle: HUB_F64 -> double, HUB_F32,
+ *     HUB_MIXED_BF16 and HUB_MIXED_F16 -> float; with ncomplex = 1 it is the interleaved
+ *     complex of that type (re, im).  Occupation matrices, eigenvalues and energies are
+ *     always double.
  *   - Inner products carry the quadrature weight dV = h1 h2 h3: <u|v> = dV sum_g u_g^* v_g,
  *     so Rayleigh-Ritz returns orbitals with dV X^H X = I.
  *   - Ownership: array arguments marked "device" are caller-owned device memory (e.g.
@@ -57,9 +58,13 @@ typedef enum {
 typedef enum {
     HUB_F64 = 0,          /* every step in double */
     HUB_F32 = 1,          /* filter and Rayleigh-Ritz products in float; dense steps double */
-    HUB_MIXED_BF16 = 2    /* float filter; X^T X (always the hi/lo BF16 split), X^T H X and
+    HUB_MIXED_BF16 = 2,   /* float filter; X^T X (always the hi/lo BF16 split), X^T H X and
                              X Q as BF16 tensor-core products with float accumulation;
                              Cholesky, eigensolve, D and E_U double */
+    HUB_MIXED_F16 = 3     /* as HUB_MIXED_BF16 with FP16 operands (11 significand bits, 22
+                             with the hi/lo split): each operand block is scaled by a power
+                             of two so that its largest magnitude lies in [2^14, 2^15) (FP16
+                             overflows at 65504), the scale is removed from the FP32 result */
 } hub_prec;
 
 /* Create a handle for one grid, one Bloch wavevector and one precision.
@@ -83,7 +88,7 @@ int hub_destroy(hub_t h);
 const char* hub_last_error(hub_t h);
 
 /* Local effective potential V_eff (Ha) on the grid, device double [Nd]; copied into the
- * handle (and rounded to float for HUB_F32 / HUB_MIXED_BF16). */
+ * handle (and rounded to float for HUB_F32 and the mixed handles). */
 int hub_set_veff(hub_t h, const double* veff_dev);
 
 /* Atoms and their localized functions (Sec. II.A.1 Bloch-mapped orbitals; Sec. II.B: the
@@ -115,10 +120,13 @@ int hub_num_hubbard_atoms(hub_t h, int* nhub);
  * that spin (Eq. DerED; coefficient of phi_m' is sum_m M_m'm <phi_m|psi>). */
 int hub_set_occupation_matrix(hub_t h, int spin, const double* D_re, const double* D_im);
 
-/* HUB_MIXED_BF16 handles: how the Rayleigh-Ritz block products are taken.
- * terms = 1: operands rounded to BF16 (8 significand bits), one tensor-core product;
- * terms = 3: every float operand split as hi + lo (hi = bf16(x), lo = bf16(x - hi)) and
- *            the product taken as hi*hi + hi*lo + lo*hi (about 16 significand bits);
+/* Mixed handles (HUB_MIXED_BF16, HUB_MIXED_F16): how the Rayleigh-Ritz block products
+ * are taken.  t16 is the handle's 16-bit type (BF16: 8 significand bits; FP16: 11, after
+ * the power-of-two scaling of each operand block described at HUB_MIXED_F16).
+ * terms = 1: operands rounded to t16, one tensor-core product;
+ * terms = 3: every float operand split as hi + lo (hi = t16(x), lo = t16(x - hi)) and
+ *            the product taken as hi*hi + hi*lo + lo*hi (about 16 significand bits with
+ *            BF16, 22 with FP16);
  * terms = 0: float products on CUDA cores (24 significand bits).
  * Tensor-core products accumulate in FP32.  Default 3.  Errors: HUB_EINVAL. */
 int hub_set_bf16_terms(hub_t h, int terms);
@@ -142,8 +150,8 @@ int hub_chefsi_filter(hub_t h, int spin, void* X, int ncol, int ld, int degree,
  * eig_host: host double [ncol], ascending.  work: device scratch >= ld*ncol elements or
  * NULL (handle-owned).  Real orbitals (Gamma point) and complex Bloch orbitals (ncomplex =
  * 1: S and H^ are Hermitian, L is complex lower triangular with a real diagonal and the
- * eigensolver is a complex Jacobi).  HUB_MIXED_BF16 handles take the block products of a
- * complex block in float on CUDA cores (the BF16 tensor-core products are real only).
+ * eigensolver is a complex Jacobi).  Mixed handles take the block products of a complex
+ * block in float on CUDA cores (the 16-bit tensor-core products are real only).
  * Errors: HUB_ENOTSPD (X rank-deficient), HUB_ENOCONV (Jacobi sweep limit),
  * HUB_ETIMEOUT, HUB_EINVAL. */
 int hub_rayleigh_ritz(hub_t h, int spin, void* X, int ncol, int ld, double* eig_host,
@@ -155,7 +163,7 @@ int hub_rayleigh_ritz(hub_t h, int spin, void* X, int ncol, int ld, double* eig_
  * <X|HX> with B = H X).  G_dev: device, row-major [ncol_a x ncol_b], overwritten: double
  * on a real handle, complex double (interleaved re/im, 2 * ncol_a * ncol_b doubles) on a
  * complex one.  When A == B and ncol_a == ncol_b only the upper tiles are computed and
- * mirrored (conjugated).  On real HUB_MIXED_BF16 handles the product runs on the BF16
+ * mirrored (conjugated).  On real mixed handles the product runs on the BF16 or FP16
  * tensor cores (see hub_set_bf16_terms) with float accumulation.  Uses handle-owned
  * split-K scratch (allocated on first use).  Errors: HUB_EINVAL. */
 int hub_gram(hub_t h, const void* A, int ncol_a, const void* B, int ncol_b, int ld,
@@ -285,7 +293,7 @@ typedef struct {
     double n_elec;
     double tol_e_atom;    /* Ha/atom */
     double tol_D;
-    int ladder;           /* HUB_MIXED_BF16 only: 1 = one BF16 tensor-core product per
+    int ladder;           /* mixed handles only: 1 = one 16-bit tensor-core product per
                              Rayleigh-Ritz product until |dE|/natoms < ladder_tol, then float
                              products (hub_set_bf16_terms 0) for the remaining iterations;
                              0 = keep the handle's setting */
@@ -447,7 +455,7 @@ int hub_kerker(hub_t h, const double* r_dev, double* z_dev, double kappa, double
 
 /* Autotuner: times the candidate stencil tile shapes of this handle's kernel family on the
  * block X (device, ncol columns, leading dimension ld; X is only read), for
- * HUB_MIXED_BF16 handles the split-K factor of the tensor-core Gram product, and for real
+ * mixed handles the split-K factor of the tensor-core Gram product, and for real
  * float handles the projector form (point-major, 8x8x4 bricks on CUDA cores, or 8x8x4
  * bricks as TF32 tensor-core products for the gather or for gather and scatter; gather and
  * scatter timed together); keeps the fastest

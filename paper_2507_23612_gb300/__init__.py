@@ -8,6 +8,6 @@ library expects.  There is no CPU fallback: if the library cannot be loaded, imp
 binding's entry points raises.
 """
 from .binding import (  # noqa: F401
-    HubError, Hub, load_library, library_path, HUB_F64, HUB_F32, HUB_MIXED_BF16, KERNEL_KINDS,
-    scf_params, STATUS_NAMES, batch_filter, MLP, descriptors,
+    HubError, Hub, load_library, library_path, HUB_F64, HUB_F32, HUB_MIXED_BF16, HUB_MIXED_F16,
+    KERNEL_KINDS, scf_params, STATUS_NAMES, batch_filter, MLP, descriptors,
 )

@@ -6,7 +6,7 @@ import os
 
 import numpy as np
 
-HUB_F64, HUB_F32, HUB_MIXED_BF16 = 0, 1, 2
+HUB_F64, HUB_F32, HUB_MIXED_BF16, HUB_MIXED_F16 = 0, 1, 2, 3
 STATUS_NAMES = {0: "HUB_OK", -1: "HUB_EINVAL", -2: "HUB_ENOMEM", -3: "HUB_ECUDA",
                 -4: "HUB_ENOTSPD", -5: "HUB_ENONFINITE", -6: "HUB_ENOCONV", -7: "HUB_ETIMEOUT"}
 

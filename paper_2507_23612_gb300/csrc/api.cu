@@ -167,7 +167,7 @@ int hub_create_grid(hub_t* out, int n1, int n2, int n3, double L1, double L2, do
     *out = nullptr;
     if (n1 < 1 || n2 < 1 || n3 < 1 || !(L1 > 0) || !(L2 > 0) || !(L3 > 0)) return HUB_EINVAL;
     if (fd_half_order < 1 || fd_half_order > 6) return HUB_EINVAL;
-    if (prec < HUB_F64 || prec > HUB_MIXED_BF16) return HUB_EINVAL;
+    if (prec < HUB_F64 || prec > HUB_MIXED_F16) return HUB_EINVAL;
     if ((long)n1 * n2 * n3 > 2000000000L) return HUB_EINVAL;
     hub_t h = new (std::nothrow) hub_ctx();
     if (!h) return HUB_ENOMEM;
@@ -187,6 +187,7 @@ int hub_create_grid(hub_t* out, int n1, int n2, int n3, double L1, double L2, do
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_flags, 8 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_bar, 4 * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_scal, 4096 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_tcmax, 4 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&h->d_veff, (size_t)h->Nd * h->esize);
     if (e == cudaSuccess) e = cudaMemset(h->d_flags, 0, 8 * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->d_scal, 0, 4096 * sizeof(double));
@@ -204,7 +205,7 @@ int hub_destroy(hub_t h) {
     for (auto& e : h->prof) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     free_table(h->proj);
     void* ptrs[] = {h->d_veff, h->d_work, h->d_work2, h->d_part, h->d_C, h->d_W, h->d_small,
-                    h->d_gpart, h->d_bf16, h->d_aux, h->d_flags, h->d_bar, h->d_scal, h->d_dens,
+                    h->d_gpart, h->d_bf16, h->d_aux, h->d_flags, h->d_bar, h->d_scal, h->d_tcmax, h->d_dens,
                     h->d_veff_spin[0], h->d_veff_spin[1], h->d_rho_ws, h->d_vloc};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -350,7 +351,7 @@ static int rr_prepare(hub_t h, int spin, void* X, int n, int ld, void* HX, doubl
     double* T = Linv + nn;
     int rc;
     if ((rc = apply_H_internal(h, spin, X, ld, HX, n, 1.0, 0.0, nullptr, 0.0))) return rc;
-    const bool tensor = (h->prec == HUB_MIXED_BF16) && h->bf16_terms > 0 && !h->cplx;
+    const bool tensor = tensor_mixed(h);
     if (tensor) {
         // the Gram matrix feeds the Cholesky factor: always the hi/lo split (about 16
         // significand bits)
@@ -380,7 +381,7 @@ static int rr_finish(hub_t h, void* X, int n, int ld, void* HX, double* ws, doub
     double* eig = ws + 6 * nn;
     int rc;
     if ((rc = dense_gemm(h, true, false, n, n, n, 1.0, Linv, n, Vs, n, 0.0, Q, n))) return rc;
-    if ((h->prec == HUB_MIXED_BF16) && h->bf16_terms > 0 && !h->cplx) {
+    if (tensor_mixed(h)) {
         if ((rc = launch_rotate_bf16(h, X, ld, Q, n, n, HX, ld))) return rc;
     } else {
         if ((rc = launch_rotate(h, X, ld, Q, n, n, HX, ld))) return rc;
@@ -444,7 +445,7 @@ int hub_gram(hub_t h, const void* A, int ncol_a, const void* B, int ncol_b, int 
     if (ncol_a == 0 || ncol_b == 0) return HUB_OK;
     if (!A || !B || !G_dev) return fail(h, HUB_EINVAL, "NULL pointer");
     const bool sym = (A == B) && (ncol_a == ncol_b);
-    if (h->prec == HUB_MIXED_BF16 && h->bf16_terms > 0 && !h->cplx)
+    if (tensor_mixed(h))
         return launch_gram_bf16(h, A, ld, B, ld, ncol_a, ncol_b, alpha, sym, G_dev);
     return launch_gram(h, A, ld, B, ld, ncol_a, ncol_b, alpha, sym, G_dev);
 }
@@ -1046,7 +1047,7 @@ int hub_scf_iterate(hub_t h, hub_scf_result* res) {
     const int ns = p.nspin;
     const double deg = ns == 1 ? 2.0 : 1.0;
     int rc;
-    if (p.ladder && h->prec == HUB_MIXED_BF16) h->bf16_terms = st.laddered ? 0 : 1;
+    if (p.ladder && (h->prec == HUB_MIXED_BF16 || h->prec == HUB_MIXED_F16)) h->bf16_terms = st.laddered ? 0 : 1;
     // per spin channel: filter + Rayleigh-Ritz passes; with two channels both are filtered
     // first and their Rayleigh-Ritz projections share one eigensolver launch
     const int passes = st.iter == 0 ? std::max(1, p.first_passes) : 1;
@@ -1125,7 +1126,7 @@ int hub_scf_iterate(hub_t h, hub_scf_result* res) {
     r.converged = (st.small >= 2 && dD < p.tol_D && (!st.density || drho < dens_tol_rho(p))) ? 1 : 0;
     r.E_H = e_h; r.E_x = e_x; r.drho = drho; r.cg_iters = cg_iters;
     r.E = E; r.E_band = e_band; r.E_U = e_u; r.dE = dE; r.dD = dD; r.mu = mu;
-    r.bf16_terms = h->prec == HUB_MIXED_BF16 ? h->bf16_terms : 0;
+    r.bf16_terms = (h->prec == HUB_MIXED_BF16 || h->prec == HUB_MIXED_F16) ? h->bf16_terms : 0;
     r.jacobi_sweeps = h->last_sweeps;
     if (p.ladder && !st.laddered && st.iter > 1 && std::fabs(dE) / std::max(1, p.natoms) < p.ladder_tol) {
         st.laddered = true;

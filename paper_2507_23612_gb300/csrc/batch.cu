@@ -215,7 +215,7 @@ int hub_autotune(hub_t h, int spin, const void* X, int ncol, int ld, int* varian
     h->stencil_variant = best;
     // split factor of the tensor-core Gram product (mixed handles, real float blocks)
     int best_split = h->gemm_split;
-    if (h->prec == HUB_MIXED_BF16 && !h->cplx && ncol >= 16) {
+    if ((h->prec == HUB_MIXED_BF16 || h->prec == HUB_MIXED_F16) && !h->cplx && ncol >= 16) {
         const size_t gb = (size_t)ncol * ncol * sizeof(double);
         if ((rc = ensure(h, &h->d_small, &h->small_bytes, std::max(h->small_bytes, gb)))) { h->prof_on = saved_prof; return rc; }
         float bms = 1e30f;

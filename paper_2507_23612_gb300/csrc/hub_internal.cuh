@@ -134,7 +134,7 @@ struct hub_ctx {
     double kpt[3] = {0, 0, 0};
     int prec = HUB_F64;
     int esize = 8;                // bytes per real component of the working type
-    int bf16_terms = 3;           // HUB_MIXED_BF16: 1 = bf16 x bf16, 3 = hi/lo split products
+    int bf16_terms = 3;           // mixed handles: 1 = one 16-bit product, 3 = hi/lo split products
     int stencil_variant = 0;      // tile shape chosen by the autotuner (stencil_variants)
     int gather_dense = 0;         // real float: gather in the brick form (else point-major)
     int gemm_split = 2;           // tensor-core split-K: CTAs per SM of the Gram products
@@ -171,6 +171,7 @@ struct hub_ctx {
     int* d_flags = nullptr;       // [8] device error flags (0..5), Jacobi sweep count (6)
     unsigned int* d_bar = nullptr;  // [4] grid-barrier state
     double* d_scal = nullptr;     // [256] device scalars (Lanczos, reductions)
+    unsigned* d_tcmax = nullptr;  // [4] max |x| bit patterns of the FP16 operands (scales)
 
     hub::ScfState* scf = nullptr;
 
@@ -288,7 +289,12 @@ int launch_gram(hub_t h, const void* A, int lda, const void* B, int ldb, int m, 
 // Y[K x n] = X[K x k] Q[k x n]; Q double column-major [k x n] (ldq = k)
 int launch_rotate(hub_t h, const void* X, int ldx, const double* Q, int k, int n, void* Y,
                   int ldy);
-// mixed-precision variants (tcgen05 bf16 path)
+// mixed-precision variants (tcgen05 path; 16-bit operand type from h->prec)
+// true when the Rayleigh-Ritz block products of this handle run on the tensor cores: a mixed
+// handle (BF16 or FP16 operands), real blocks, and a product form with 1 or 3 terms
+inline bool tensor_mixed(const hub_ctx* h) {
+    return (h->prec == HUB_MIXED_BF16 || h->prec == HUB_MIXED_F16) && h->bf16_terms > 0 && !h->cplx;
+}
 int launch_gram_bf16(hub_t h, const void* A, int lda, const void* B, int ldb, int m, int n,
                      double alpha, bool sym, double* G);
 int launch_rotate_bf16(hub_t h, const void* X, int ldx, const double* Q, int k, int n,

@@ -22,7 +22,7 @@ import time
 
 import numpy as np
 
-from .binding import HUB_F64, HUB_MIXED_BF16, MLP, Hub, descriptors, scf_params
+from .binding import HUB_F64, HUB_MIXED_BF16, HUB_MIXED_F16, MLP, Hub, descriptors, scf_params
 
 SPECIES = {"Ti": 0, "O": 1}
 NRAD = 16
@@ -88,7 +88,7 @@ def scf_solve(wl, prec: int = HUB_F64, D0=None, tol_e_atom: float = 1e-5, tol_D:
         v0s = [torch.tensor(wl.lanczos_start(s), device=dev).to(hub.dtype).contiguous()
                for s in range(wl.nspin)]
         if ladder is None:
-            ladder = 1 if prec == HUB_MIXED_BF16 else 0
+            ladder = 1 if prec in (HUB_MIXED_BF16, HUB_MIXED_F16) else 0
         p = scf_params(nspin=wl.nspin, ncol=wl.ncol, ld=wl.Nd, degree=wl.degree, max_iter=max_iter,
                        first_passes=first_passes, lanczos_steps=10, pulay_history=7, natoms=len(wl.atoms),
                        pulay_beta=0.3, kT=wl.kT if wl.kT > 0 else 0.005, n_elec=wl.n_elec,
@@ -248,7 +248,7 @@ def density_scf_solve(wl, prec: int = HUB_F64, D0=None, rho0=None, tol_e_atom: f
         p = scf_params(nspin=wl.nspin, ncol=wl.ncol, ld=wl.Nd, degree=wl.degree, max_iter=max_iter,
                        first_passes=3, lanczos_steps=10, pulay_history=7, natoms=len(wl.atoms),
                        pulay_beta=0.3, kT=wl.kT if wl.kT > 0 else 0.005, n_elec=wl.n_elec,
-                       tol_e_atom=tol_e_atom, tol_D=tol_D, ladder=1 if prec == HUB_MIXED_BF16 else 0,
+                       tol_e_atom=tol_e_atom, tol_D=tol_D, ladder=1 if prec in (HUB_MIXED_BF16, HUB_MIXED_F16) else 0,
                        ladder_tol=1e-4, density=1, kerker_kappa=0.5, tol_rho=tol_rho, cg_tol=1e-10)
         hub.scf_begin(p, Xs, v0s, wl.D0 if D0 is None else D0)
         if rho0 is not None:

@@ -25,7 +25,7 @@ def _create(lib, n=(8, 8, 8), L=(2.0, 2.0, 2.0), order=6, prec=0):
 
 @pytest.mark.parametrize("kw", [dict(n=(0, 8, 8)), dict(n=(8, -1, 8)), dict(L=(2.0, 0.0, 2.0)),
                                 dict(L=(float("nan"), 2.0, 2.0)), dict(order=0), dict(order=7),
-                                dict(prec=3), dict(prec=-1), dict(n=(2000, 2000, 1000))])
+                                dict(prec=4), dict(prec=-1), dict(n=(2000, 2000, 1000))])
 def test_create_grid_rejects_bad_arguments(lib, kw):
     rc, h = _create(lib, **kw)
     assert rc == EINVAL and not h.value

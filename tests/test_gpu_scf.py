@@ -51,11 +51,12 @@ def test_scf_spin_polarised_matches_oracle():
     np.testing.assert_allclose(occ, np.array(ref["f"]), atol=1e-8)
 
 
-@pytest.mark.parametrize("prec,ladder", [("f32", 0), ("mixed", 1)])
+@pytest.mark.parametrize("prec,ladder", [("f32", 0), ("mixed", 1), ("mixed16", 1), ("mixed16", 0)])
 def test_reduced_precision_scf_reaches_the_fp64_fixed_point(prec, ladder):
-    """FP32 filter (and BF16 tensor-core products with the precision ladder) reach the
-    oracle's FP64 SCF fixed point within 1e-5 Ha/atom in energy and band energy."""
-    from paper_2507_23612_gb300 import HUB_F32, HUB_MIXED_BF16
+    """FP32 filter (and BF16 or FP16 tensor-core products, with or without the precision
+    ladder) reach the oracle's FP64 SCF fixed point within 1e-5 Ha/atom in energy and band
+    energy."""
+    from paper_2507_23612_gb300 import HUB_F32, HUB_MIXED_BF16, HUB_MIXED_F16
     wl = w.small_test_system(n=(16, 16, 20), natoms=2, ncol=14, hub_rc=3.0, kb_rc=2.0, nspin=2)
     kw = dict(n_elec=16.0, kT=0.01, degree=12, max_iter=80, tol_e_atom=1e-7, tol_D=1e-5,
               first_passes=4, hist=7, beta=0.3, lanczos_steps=10)
@@ -64,7 +65,7 @@ def test_reduced_precision_scf_reaches_the_fp64_fixed_point(prec, ladder):
     ref = o.scf_model_a((wl.n, wl.L, (0, 0, 0), 6), wl.veff, wl.atoms, wl.D0, [x.T for x in X0s],
                         lanczos_v0s=v0s, **kw)
     assert ref["converged"]
-    P = HUB_F32 if prec == "f32" else HUB_MIXED_BF16
+    P = {"f32": HUB_F32, "mixed": HUB_MIXED_BF16, "mixed16": HUB_MIXED_F16}[prec]
     hb = make_hub(wl, P)
     p = scf_params(nspin=2, ncol=wl.ncol, ld=wl.Nd, degree=kw["degree"], max_iter=kw["max_iter"],
                    first_passes=kw["first_passes"], lanczos_steps=10, pulay_history=7,
