@@ -7,9 +7,10 @@
 //
 // are one tcgen05 product D[128 orbitals x NP functions] = X_b^T Phi_b over the K = 256
 // points of the brick (summed per function over its bricks afterwards, as for the SIMT brick
-// gather).  Both operands are split for TF32: hi = the float with its low 13 significand bits
-// cleared, lo = value - hi (exact), and D = hi*hi + (hi*lo + lo*hi) with FP32 accumulation in
-// TMEM, about 21 significant bits (the float path's own accuracy).  The two small correction
+// gather).  Both operands are split for TF32: hi = the float rounded to the 10 TF32
+// significand bits, lo = value - hi (exact) rounded the same way, and D = hi*hi + (hi*lo +
+// lo*hi) with FP32 accumulation in TMEM, about 22 significant bits (the float path's own
+// accuracy) and no rounding bias.  The two small correction
 // products accumulate apart from hi*hi (the tensor core aligns the addends of a sum to the
 // largest, so corrections added to the large accumulator lose their low bits) and the two
 // accumulators are added when the result is read out.
@@ -63,8 +64,15 @@ struct GtcArgs {
     int* flags;
 };
 
+// TF32 split rounded to nearest (ties away from zero in magnitude): hi = x rounded to the 10
+// TF32 significand bits, lo = x - hi (exact in float, |lo| <= 2^-11 |x|) rounded the same
+// way.  Rounding both parts to nearest keeps the split unbiased: with truncation (low bits
+// cleared) hi and lo both lean towards zero and the dropped lo*lo term has the sign of the
+// product, which biased every projector inner product by ~5e-7 of its value towards zero.
+__device__ __forceinline__ uint32_t tf32_round(uint32_t u) { return (u + 0x1000u) & kTf32Hi; }
+__device__ __forceinline__ uint32_t split_hi(uint32_t u) { return tf32_round(u); }
 __device__ __forceinline__ uint32_t split_lo(uint32_t u) {
-    return __float_as_uint(__uint_as_float(u) - __uint_as_float(u & kTf32Hi));
+    return tf32_round(__float_as_uint(__uint_as_float(u) - __uint_as_float(tf32_round(u))));
 }
 
 // the 8 16-byte chunks a converter thread loads for slice q of unit u: chunk j = it * 128 + c
@@ -214,8 +222,8 @@ k_gather_tc(GtcArgs a) {
                     const uint32_t off = (uint32_t)n * 128 + ((uint32_t)(ch ^ (n & 7)) << 4);
                     const uint4 v = make_uint4(__float_as_uint(L.v[it].x), __float_as_uint(L.v[it].y),
                                                __float_as_uint(L.v[it].z), __float_as_uint(L.v[it].w));
-                    *reinterpret_cast<uint4*>(xs + off) = make_uint4(v.x & kTf32Hi, v.y & kTf32Hi, v.z & kTf32Hi,
-                                                                    v.w & kTf32Hi);
+                    *reinterpret_cast<uint4*>(xs + off) = make_uint4(split_hi(v.x), split_hi(v.y), split_hi(v.z),
+                                                                    split_hi(v.w));
                     *reinterpret_cast<uint4*>(xs + GT_XB + off) =
                         make_uint4(split_lo(v.x), split_lo(v.y), split_lo(v.z), split_lo(v.w));
                 }
@@ -288,7 +296,7 @@ __global__ void k_fill_tc(const int4* __restrict__ bent, const int2* __restrict_
         const float v = r < E.y ? phi[(size_t)E.z + (size_t)r * BRP + brick_slot(k)] : 0.f;
         const uint32_t u = __float_as_uint(v);
         const size_t dst = (size_t)T.x + (size_t)q * GT_K * T.y + (size_t)r * GT_K + ((((kk >> 2) ^ (r & 7)) << 2) | (kk & 3));
-        vhi[dst] = __uint_as_float(u & kTf32Hi);
+        vhi[dst] = __uint_as_float(split_hi(u));
         vlo[dst] = __uint_as_float(split_lo(u));
     }
 }
@@ -451,8 +459,8 @@ k_scatter_tc(StcArgs a) {
                         v[q] = (r >= 0 && col < a.ncol) ? __float_as_uint(a.W[(size_t)r * a.ncol + col]) : 0u;
                     }
                     const uint32_t off = (uint32_t)t * 128 + ((uint32_t)(f4 ^ (t & 7)) << 4);
-                    *reinterpret_cast<uint4*>(st + off) = make_uint4(v[0] & kTf32Hi, v[1] & kTf32Hi, v[2] & kTf32Hi,
-                                                                    v[3] & kTf32Hi);
+                    *reinterpret_cast<uint4*>(st + off) = make_uint4(split_hi(v[0]), split_hi(v[1]), split_hi(v[2]),
+                                                                    split_hi(v[3]));
                     *reinterpret_cast<uint4*>(st + ST_BB + off) =
                         make_uint4(split_lo(v[0]), split_lo(v[1]), split_lo(v[2]), split_lo(v[3]));
                 }
@@ -570,7 +578,7 @@ __global__ void k_fill_tcs(const int4* __restrict__ sbrick, const int* __restric
         const size_t dst = (size_t)B.y + ((size_t)(c * 2 + h) * GT_M + row) * ST_KC +
                            ((((kf >> 2) ^ (row & 7)) << 2) | (kf & 3));
         const uint32_t u = __float_as_uint(v);
-        vhi[dst] = __uint_as_float(u & kTf32Hi);
+        vhi[dst] = __uint_as_float(split_hi(u));
         vlo[dst] = __uint_as_float(split_lo(u));
     }
 }
