@@ -14,7 +14,7 @@ import pytest
 import workloads as w
 from oracle import hubbard as o
 from oracle import density_scf as ds
-from hubtest import make_hub, to_dev, rel
+from hubtest import make_hub, to_dev, rel_elem
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -43,7 +43,7 @@ def test_density_of_a_block(prec, cplx):
     hb = make_hub(wl, prec)
     rho = _dev64(np.full(wl.Nd, 0.5))
     hb.density(to_dev(X, hb.dtype), f, 1.4, rho)
-    assert rel(rho.cpu().numpy(), ref) < 1e-13
+    assert rel_elem(rho.cpu().numpy(), ref) < 1e-13
 
 
 @pytest.mark.parametrize("n", [(20, 24, 28), (5, 7, 4), (33, 9, 17)])
@@ -57,7 +57,7 @@ def test_hartree_potential(n):
     V = torch.zeros(wl.Nd, dtype=torch.float64, device=DEV)
     it, eh = hb.hartree(_dev64(rho), V, tol=1e-12)
     print(n, "CG iterations", it)
-    assert rel(V.cpu().numpy(), ref) < 1e-9
+    assert rel_elem(V.cpu().numpy(), ref) < 1e-9
     assert abs(eh - ds.hartree_energy(rho, g)) < 1e-9 * abs(ds.hartree_energy(rho, g))
     # a warm start from the solution converges at once
     it2, _ = hb.hartree(_dev64(rho), V, tol=1e-9)
@@ -76,7 +76,7 @@ def test_lda_exchange(nchan):
     E = hb.lda_exchange([_dev64(r) for r in rhos], vx)
     assert abs(E - E_ref) < 1e-12 * abs(E_ref)
     for s in range(nchan):
-        assert rel(vx[s].cpu().numpy(), v_ref[s]) < 1e-13
+        assert rel_elem(vx[s].cpu().numpy(), v_ref[s]) < 1e-13
 
 
 def test_kerker_preconditioner():
@@ -89,7 +89,7 @@ def test_kerker_preconditioner():
     z = torch.empty(wl.Nd, dtype=torch.float64, device=DEV)
     it = hb.kerker(_dev64(r), z, 0.5, tol=1e-12)
     print("CG iterations", it)
-    assert rel(z.cpu().numpy(), ref) < 1e-9
+    assert rel_elem(z.cpu().numpy(), ref) < 1e-9
 
 
 @pytest.mark.parametrize("nspin", [1, 2])
@@ -149,13 +149,13 @@ def test_project_and_expand_match_the_oracle_tables(prec, cplx):
     assert hb.num_projectors() == P.shape[1]
     C = hb.project(to_dev(X, hb.dtype))
     C_ref = g.dV * (P.conj().T @ X.T)
-    assert rel(C, C_ref) < (1e-12 if prec == HUB_F64 else 1e-5)
+    assert rel_elem(C, C_ref) < (1e-12 if prec == HUB_F64 else 1e-5)
     rng = np.random.default_rng(9)
     W = rng.standard_normal(C_ref.shape) + (1j * rng.standard_normal(C_ref.shape) if cplx else 0)
     Y = to_dev(np.zeros_like(X), hb.dtype)
     hb.expand(W, Y, 0.5)
     Y_ref = 0.5 * (P @ W).T
-    assert rel(Y.cpu().numpy(), Y_ref) < (1e-12 if prec == HUB_F64 else 1e-5)
+    assert rel_elem(Y.cpu().numpy(), Y_ref) < (1e-12 if prec == HUB_F64 else 1e-5)
 
 
 def test_density_scf_from_a_given_starting_density():
@@ -186,9 +186,11 @@ def test_full_size_poisson_and_kerker_on_the_rutile_grid():
     V = torch.zeros(wl.Nd, dtype=torch.float64, device=DEV)
     it, eh = hb.hartree(_dev64(rho), V, tol=1e-13)
     print("Poisson CG iterations", it)
-    # (condition number ~2500 on this grid: a 1e-13 residual bounds the error by ~3e-10)
-    assert rel(V.cpu().numpy(), ds.hartree_potential(rho, g)) < 1e-8
+    # condition number ~2500 on this grid: a 1e-13 relative residual bounds the relative
+    # error by ~2500 x 1e-13 = 2.5e-10; 1e-9 leaves a factor 4 for the max-norm against the RMS
+    err_v = rel_elem(V.cpu().numpy(), ds.hartree_potential(rho, g))
     z = torch.empty(wl.Nd, dtype=torch.float64, device=DEV)
     it = hb.kerker(_dev64(rho - rho.mean()), z, 0.5, tol=1e-13)
-    print("Kerker CG iterations", it)
-    assert rel(z.cpu().numpy(), ds.kerker(rho - rho.mean(), g, 0.5)) < 1e-8
+    err_z = rel_elem(z.cpu().numpy(), ds.kerker(rho - rho.mean(), g, 0.5))
+    print("Kerker CG iterations", it, "V_H elementwise err", err_v, "Kerker elementwise err", err_z)
+    assert err_v < 1e-9 and err_z < 1e-9
