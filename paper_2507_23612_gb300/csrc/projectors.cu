@@ -185,7 +185,7 @@ __device__ __forceinline__ void gather_body(const T* __restrict__ X, int ld, int
         }
 }
 
-template <typename R, bool CPLX, int GW, int PTS>
+template <typename R, bool CPLX, int GW, int PTS, int NC>
 __global__ void __launch_bounds__(GW * 32)
 k_gather(const typename VT<R, CPLX>::T* __restrict__ X, int ld, int ncol,
          const SiteDev* __restrict__ sites, const int* __restrict__ items,
@@ -193,7 +193,6 @@ k_gather(const typename VT<R, CPLX>::T* __restrict__ X, int ld, int ncol,
          typename VT<double, CPLX>::T* __restrict__ part) {
     using T = typename VT<R, CPLX>::T;
     using D = typename VT<double, CPLX>::T;
-    constexpr int NC = 16 / sizeof(T);
     const int it = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int s = items[3 * it], first = items[3 * it + 1], cnt = items[3 * it + 2];
@@ -1151,14 +1150,19 @@ static int gather_t(hub_t h, const void* X, int ncol, int ld, int spin, bool wan
     if ((rc = ensure(h, &h->d_part, &h->part_bytes, (size_t)t.nitems * kMaxProj * ncol * sizeof(D)))) return rc;
     if ((rc = ensure(h, &h->d_C, &h->C_bytes, (size_t)t.nproj * ncol * sizeof(D)))) return rc;
     if ((rc = ensure(h, &h->d_W, &h->W_bytes, (size_t)t.nproj * ncol * sizeof(T)))) return rc;
-    constexpr int NC = 16 / sizeof(T);
+    // columns per warp (the value table is re-read once per column group): 16 bytes of each
+    // point's row, except complex float, which takes four columns (32 bytes) with two points
+    // per lane and iteration (rutile, 348 columns: 4.28 -> 2.66 ms; eight columns 2.58 ms at
+    // 255 registers)
+    constexpr bool C64 = CPLX && sizeof(R) == 4;
+    constexpr int NC = C64 ? 4 : 16 / (int)sizeof(T);
     { ProfScope ps(h, HUB_K_GATHER);
     // one warp per CTA and four points per lane and iteration: the fastest of the shapes
     // measured on the rutile workload (1, 2, 4, 8 warps x 2, 4 points)
-    constexpr int GW = 1, PTS = 4;
+    constexpr int GW = 1, PTS = C64 ? 2 : 4;
     dim3 g1(t.nitems, (ncol + GW * NC - 1) / (GW * NC));
-    k_gather<R, CPLX, GW, PTS><<<g1, GW * 32, 0, h->stream>>>((const T*)X, ld, ncol, t.d_sites, t.d_items,
-                                                            t.d_idx, (const T*)t.d_vals, (D*)h->d_part);
+    k_gather<R, CPLX, GW, PTS, NC><<<g1, GW * 32, 0, h->stream>>>((const T*)X, ld, ncol, t.d_sites, t.d_items,
+                                                                t.d_idx, (const T*)t.d_vals, (D*)h->d_part);
     }
     HUB_CUDA_TRY(h, cudaGetLastError());
     const long nthr = (long)t.nsites * ncol;
