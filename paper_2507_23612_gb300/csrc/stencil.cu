@@ -1002,6 +1002,282 @@ k_stencil_f32s2(StencilDev<float> a) {
     cp_async_wait<0>();
 }
 
+// ---------------------------------------------------------------------------- complex float form
+// Complex float (Bloch orbitals), two consecutive x-points per thread held as two packed
+// (re, im) pairs: the Laplacian's real weights, V and the recurrence act on re and im alike,
+// so every add and FMA is one f32x2 instruction on one complex value, and the x-neighbours of
+// both points are whole pairs (no register moves to form them).  Same split ring as the real
+// float form: a stage holds the halo'd plane z (x/y neighbours, NHC = 6 points = 3 vectors of
+// halo on each side of a row), plus three per-thread interior slots: the queue feed plane
+// z + NH + 1, V (two floats) and Yprev of plane z.  Bloch factors: a halo slot whose copy
+// wrapped across an x or y face is multiplied by exp(i k_a L_a)^wraps by the thread that
+// copied it, after its copy landed and before the plane's barrier (interior tiles have no
+// such slots); a queue plane that wrapped in z takes exp(i k_3 L_3)^wraps when it enters
+// the queue.
+template <int TXT, int TY, int PH>
+struct SplitCCfg {
+    static constexpr int NH = 6, HXV = 3;               // halo: 6 complex = 3 vectors per side
+    static constexpr int TXP = TXT * 2;                 // complex points per tile row
+    static constexpr int SXV = TXT + 2 * HXV;           // 16-byte vectors per halo row
+    static constexpr int SY = TY + 2 * NH;
+    static constexpr int NT = TXT * TY;
+    static constexpr int RS = PH + 2;
+    static constexpr int NVS = SXV * SY;
+    static constexpr int PER = (NVS + NT - 1) / NT;
+    static constexpr size_t YB = 16 * (size_t)NVS;      // halo plane
+    static constexpr size_t IB = 16 * (size_t)NT;       // one vector per thread (feed, Yprev)
+    static constexpr size_t VB = 8 * (size_t)NT;        // two floats per thread (V)
+    static constexpr size_t STAGE = YB + 2 * IB + VB;   // halo | feed | Yprev | V
+    static constexpr size_t SMEM = STAGE * RS;
+};
+
+__device__ __forceinline__ u64 f2u(float2 v) { return pk2(v.x, v.y); }
+__device__ __forceinline__ float2 u2f(u64 v) { return make_float2(lo2(v), hi2(v)); }
+
+template <int TXT, int TY, int PH>
+__global__ void __launch_bounds__(TXT * TY)
+k_stencil_c32s(StencilDev<float> a) {
+    const Coef<float> cf = resolve_coef(a);
+    using C = SplitCCfg<TXT, TY, PH>;
+    constexpr int NH = C::NH, HXV = C::HXV, SXV = C::SXV, RS = C::RS, NT = C::NT, PER = C::PER;
+    constexpr int Q = 2 * NH + 1;
+    static_assert(C::YB % 16 == 0 && C::STAGE % 16 == 0, "stage regions stay 16-byte aligned");
+    extern __shared__ __align__(128) unsigned char smem[];
+
+    const int tid = threadIdx.x;
+    const int tx = tid % TXT, ty = tid / TXT;
+    const int col = blockIdx.z / a.nzc;
+    const int zc = blockIdx.z - col * a.nzc;
+    const int z0 = zc * a.zchunk;
+    const int z1 = min(z0 + a.zchunk, a.n3);
+    const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
+    const long plane = (long)n1 * n2;
+    const int gx0 = blockIdx.x * C::TXP, gy0 = blockIdx.y * TY;
+
+    // element = one complex float (8 bytes)
+    const float2* __restrict__ Y = reinterpret_cast<const float2*>(a.Y) + (size_t)col * a.ld;
+    const float2* Yp = a.Yprev ? reinterpret_cast<const float2*>(a.Yprev) + (size_t)col * a.ld : nullptr;
+    float2* Yo = reinterpret_cast<float2*>(a.Yout) + (size_t)col * a.ld;
+
+    int s_idx[PER];
+    const float2* s_src[PER];
+    float2 s_ph[PER];            // Bloch factor of a slot that wrapped in x or y
+    bool s_wrap[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = tid + k * NT;
+        s_idx[k] = -1;
+        s_src[k] = Y;
+        s_ph[k] = make_float2(1.f, 0.f);
+        s_wrap[k] = false;
+        if (i < C::NVS) {
+            const int cx = i % SXV, iy = i / SXV;
+            const int gx = gx0 + 2 * (cx - HXV), gy = gy0 - NH + iy;
+            const int wx = floordiv(gx, n1), wy = floordiv(gy, n2);
+            s_idx[k] = i;
+            s_src[k] = Y + (long)(gy - wy * n2) * n1 + (gx - wx * n1);
+            if (wx != 0 || wy != 0) {
+                s_wrap[k] = true;
+                s_ph[k] = cmul(phase_pow<float2>(a.ph[0][0], a.ph[0][1], wx), phase_pow<float2>(a.ph[1][0], a.ph[1][1], wy));
+            }
+        }
+    }
+    const bool active = (gx0 + tx * 2 < n1) && (gy0 + ty < n2);
+    const long own = (long)(gy0 + ty) * n1 + (gx0 + tx * 2);
+
+    auto stY = [&](int st) { return reinterpret_cast<ulonglong2*>(smem + C::STAGE * (size_t)st); };
+    auto stI = [&](int st, int k) {            // k = 0 feed, 1 Yprev
+        return reinterpret_cast<ulonglong2*>(smem + C::STAGE * (size_t)st + C::YB + C::IB * (size_t)k);
+    };
+    auto stV = [&](int st) { return reinterpret_cast<float2*>(smem + C::STAGE * (size_t)st + C::YB + 2 * C::IB); };
+    int ip = z0;
+    long ioff = (long)z0 * plane;
+    int fz = z0 + NH + 1;
+    while (fz >= n3) fz -= n3;
+    long foff = (long)fz * plane;
+    const float2* Yown = Y + own;
+    const float* Vown = a.V + own;
+    const float2* Pown = Yp ? Yp + own : nullptr;
+    auto issue = [&](int st) {
+        if (ip < z1) {
+            ulonglong2* ys = stY(st);
+#pragma unroll
+            for (int k = 0; k < PER; ++k)
+                if (s_idx[k] >= 0) cp_async<16>(ys + s_idx[k], s_src[k] + ioff);
+            if (active) {
+                cp_async<8>(stV(st) + tid, Vown + ioff);
+                if (Pown) cp_async<16>(stI(st, 1) + tid, Pown + ioff);
+            }
+        }
+        if (active && ip + 1 < z1) cp_async<16>(stI(st, 0) + tid, Yown + foff);
+        ++ip;
+        ioff += plane;
+        if (++fz == n3) { fz = 0; foff = 0; } else foff += plane;
+    };
+
+    u64 wx[NH], wy[NH], wz[NH];
+#pragma unroll
+    for (int p = 0; p < NH; ++p) {
+        wx[p] = pk2(cf.w[0][p], cf.w[0][p]);
+        wy[p] = pk2(cf.w[1][p], cf.w[1][p]);
+        wz[p] = pk2(cf.w[2][p], cf.w[2][p]);
+    }
+    const u64 cen2 = pk2(cf.center, cf.center), alp2 = pk2(cf.alpha, cf.alpha), bet2 = pk2(cf.beta, cf.beta);
+    const u64 m2 = pk2(-2.0f, -2.0f);
+
+    // z-queues of the two points (planes z0-NH .. z0+NH), Bloch factors of wrapped planes
+    u64 ql[Q], qh[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        ql[j] = 0ull;
+        qh[j] = 0ull;
+        if (active) {
+            const int p = z0 - NH + j;
+            const int wz_ = floordiv(p, n3);
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(Y + (long)(p - wz_ * n3) * plane + own);
+            ql[j] = v.x;
+            qh[j] = v.y;
+            if (wz_ != 0) {
+                const float2 f = phase_pow<float2>(a.ph[2][0], a.ph[2][1], wz_);
+                ql[j] = f2u(cmul(u2f(ql[j]), f));
+                qh[j] = f2u(cmul(u2f(qh[j]), f));
+            }
+        }
+    }
+    // wrap count and Bloch factor of the feed plane consumed next (plane z + NH + 1)
+    int fzc = z0 + NH + 1, fwc = 0;
+    while (fzc >= n3) { fzc -= n3; ++fwc; }
+    float2 fph = phase_pow<float2>(a.ph[2][0], a.ph[2][1], fwc);
+#pragma unroll 1
+    for (int j = 0; j < PH; ++j) {
+        issue(j % RS);
+        cp_async_commit();
+    }
+    int sz = 0, si = PH % RS;
+    const int rbase = (ty + NH) * SXV;
+#pragma unroll 1
+    for (int zb = z0; zb < z1; zb += Q) {
+#pragma unroll
+        for (int st = 0; st < Q; ++st) {
+            const int z = zb + st;
+            if (z >= z1) break;
+            issue(si);
+            cp_async_commit();
+            cp_async_wait<PH>();
+            // this thread's wrapped halo slots of plane z take their Bloch factors
+            {
+                ulonglong2* ys = stY(sz);
+#pragma unroll
+                for (int k = 0; k < PER; ++k)
+                    if (s_wrap[k]) {
+                        ulonglong2 v = ys[s_idx[k]];
+                        v.x = f2u(cmul(u2f(v.x), s_ph[k]));
+                        v.y = f2u(cmul(u2f(v.y), s_ph[k]));
+                        ys[s_idx[k]] = v;
+                    }
+            }
+            __syncthreads();
+            if (active) {
+                const ulonglong2* ys = stY(sz);
+                // the row around the thread's two points: complex x-offsets -6 .. +7
+                u64 r[14];
+#pragma unroll
+                for (int j = 0; j < 7; ++j) {
+                    const ulonglong2 v = ys[rbase + tx + j];
+                    r[2 * j] = v.x;
+                    r[2 * j + 1] = v.y;
+                }
+                const float2 vv = stV(sz)[tid];
+                const u64 cl = ql[(st + NH) % Q], ch = qh[(st + NH) % Q];
+                u64 xl = 0ull, xh = 0ull, yl = 0ull, yh = 0ull, zl = 0ull, zh = 0ull;
+#pragma unroll
+                for (int p = 1; p <= NH; ++p) {
+                    const u64 dzl = fma2(m2, cl, add2(ql[(st + NH + p) % Q], ql[(st + NH - p) % Q]));
+                    const u64 dzh = fma2(m2, ch, add2(qh[(st + NH + p) % Q], qh[(st + NH - p) % Q]));
+                    const u64 dxl = fma2(m2, cl, add2(r[6 + p], r[6 - p]));
+                    const u64 dxh = fma2(m2, ch, add2(r[7 + p], r[7 - p]));
+                    const ulonglong2 up = ys[rbase + p * SXV + tx + HXV];
+                    const ulonglong2 dn = ys[rbase - p * SXV + tx + HXV];
+                    const u64 dyl = fma2(m2, cl, add2(up.x, dn.x));
+                    const u64 dyh = fma2(m2, ch, add2(up.y, dn.y));
+                    if (p == 1) {
+                        zl = mul2(wz[0], dzl); zh = mul2(wz[0], dzh);
+                        xl = mul2(wx[0], dxl); xh = mul2(wx[0], dxh);
+                        yl = mul2(wy[0], dyl); yh = mul2(wy[0], dyh);
+                    } else {
+                        zl = fma2(wz[p - 1], dzl, zl); zh = fma2(wz[p - 1], dzh, zh);
+                        xl = fma2(wx[p - 1], dxl, xl); xh = fma2(wx[p - 1], dxh, xh);
+                        yl = fma2(wy[p - 1], dyl, yl); yh = fma2(wy[p - 1], dyh, yh);
+                    }
+                }
+                u64 al = mul2(fma2(alp2, pk2(vv.x, vv.x), cen2), cl);
+                u64 ah = mul2(fma2(alp2, pk2(vv.y, vv.y), cen2), ch);
+                al = add2(al, add2(add2(xl, yl), zl));
+                ah = add2(ah, add2(add2(xh, yh), zh));
+                if (Yp) {
+                    const ulonglong2 pv = stI(sz, 1)[tid];
+                    al = fma2(bet2, pv.x, al);
+                    ah = fma2(bet2, pv.y, ah);
+                }
+                *reinterpret_cast<ulonglong2*>(Yo + (long)z * plane + own) = make_ulonglong2(al, ah);
+                if (z + 1 < z1) {
+                    const ulonglong2 f = stI(sz, 0)[tid];
+                    // slot of plane z - NH takes plane z + NH + 1 (with its Bloch factor)
+                    if (fwc != 0) {
+                        ql[st] = f2u(cmul(u2f(f.x), fph));
+                        qh[st] = f2u(cmul(u2f(f.y), fph));
+                    } else {
+                        ql[st] = f.x;
+                        qh[st] = f.y;
+                    }
+                }
+            }
+            if (++fzc == n3) {
+                fzc = 0;
+                ++fwc;
+                fph = phase_pow<float2>(a.ph[2][0], a.ph[2][1], fwc);
+            }
+            if (++sz == RS) sz = 0;
+            if (++si == RS) si = 0;
+        }
+    }
+    cp_async_wait<0>();
+}
+
+template <int TXT, int TY, int PH>
+static int run_c32s(hub_t h, const StencilArgs& s) {
+    using Cfg = SplitCCfg<TXT, TY, PH>;
+    StencilDev<float> d;
+    d.Y = s.Y;
+    d.Yprev = s.Yprev;
+    d.Yout = s.Yout;
+    d.V = reinterpret_cast<const float*>(s.V);
+    d.n1 = s.n1; d.n2 = s.n2; d.n3 = s.n3; d.ld = s.ld;
+    fill_coefficients<float>(s, d);
+    for (int a = 0; a < 3; ++a) {
+        d.ph[a][0] = s.phase[a][0];
+        d.ph[a][1] = s.phase[a][1];
+    }
+    const int tiles = ((s.n1 + Cfg::TXP - 1) / Cfg::TXP) * ((s.n2 + TY - 1) / TY);
+    const long want = 8L * h->num_sms;
+    const long per = (long)tiles * s.ncol;
+    int nzc = 1;
+    if (per < want) nzc = (int)((want + per - 1) / per);
+    int zchunk = (s.n3 + nzc - 1) / nzc;
+    if (zchunk < 16) zchunk = s.n3 < 16 ? s.n3 : 16;
+    nzc = (s.n3 + zchunk - 1) / zchunk;
+    while ((long)s.ncol * nzc > 65535) { zchunk *= 2; nzc = (s.n3 + zchunk - 1) / zchunk; }
+    d.zchunk = zchunk;
+    d.nzc = nzc;
+    HUB_CUDA_TRY(h, cudaFuncSetAttribute(k_stencil_c32s<TXT, TY, PH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
+    dim3 grid((s.n1 + Cfg::TXP - 1) / Cfg::TXP, (s.n2 + TY - 1) / TY, s.ncol * nzc);
+    ProfScope ps(h, HUB_K_STENCIL);
+    k_stencil_c32s<TXT, TY, PH><<<grid, TXT * TY, Cfg::SMEM, h->stream>>>(d);
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    return HUB_OK;
+}
+
 template <int TXT, int TYT, int PH>
 static int run_f32s2(hub_t h, const StencilArgs& s) {
     using Cfg = Split2Cfg<TXT, TYT, PH>;
@@ -1239,7 +1515,7 @@ int launch_fd_gradient(hub_t h, const void* X, int ld, int ncol, int axis, const
 // Tile shapes the autotuner chooses from, per kernel family (index 0 is the default).
 int stencil_variants(hub_t h) {
     const int es = h->esize * (h->cplx ? 2 : 1);
-    if (h->esize == 4) return h->cplx ? 4 : 9;   // float real (packed) / float complex (vector)
+    if (h->esize == 4) return h->cplx ? 6 : 9;   // float real (packed) / float complex (packed, vector)
     return es == 16 ? 2 : 3;              // double complex / double real (scalar pipeline)
 }
 
@@ -1266,11 +1542,14 @@ int launch_stencil(hub_t h, const StencilArgs& a) {
                 default: return run_f32s<8, 16, 2>(h, a);
             }
         }
+        // complex: packed-pair split ring, or the vector form
         switch (v) {
-            case 1: return run_vec<float, true, 2, 16, 8, 2>(h, a);
-            case 2: return run_vec<float, true, 2, 8, 16, 2>(h, a);
-            case 3: return run_vec<float, true, 2, 8, 8, 4>(h, a);
-            default: return run_vec<float, true, 2, 16, 16, 2>(h, a);
+            case 1: return run_c32s<8, 8, 2>(h, a);
+            case 2: return run_c32s<16, 8, 2>(h, a);
+            case 3: return run_vec<float, true, 2, 16, 16, 2>(h, a);
+            case 4: return run_vec<float, true, 2, 16, 8, 2>(h, a);
+            case 5: return run_vec<float, true, 2, 8, 16, 2>(h, a);
+            default: return run_c32s<8, 16, 2>(h, a);
         }
     }
     // FP64 is bound by the FP64 pipe: a short ring keeps two CTAs per SM

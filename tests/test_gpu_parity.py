@@ -78,8 +78,14 @@ def test_apply_H_every_stencil_variant(prec):
     cases = [systems()["ragged"],
              w.small_test_system(n=(8, 12, 3), ncol=5, natoms=2, hub_rc=2.0, kb_rc=1.5, seed=5),
              w.small_test_system(n=(12, 9, 10), ncol=6, natoms=2, hub_rc=2.0, kb_rc=1.5, seed=6)]
+    # Bloch (complex) blocks: a ragged grid, and one thinner in z than the half-width with
+    # wraps on every face (the halo and queue planes carry their Bloch factors)
+    cases += [w.small_test_system(n=(12, 10, 14), ncol=6, natoms=3, kpt=(0.21, -0.13, 0.34)),
+              w.small_test_system(n=(8, 12, 3), ncol=5, natoms=2, hub_rc=2.0, kb_rc=1.5, seed=5,
+                                  kpt=(0.31, 0.17, -0.45))]
     for wl in cases:
-        X = wl.orbitals()
+        cplx = bool(np.any(np.asarray(wl.kpts[0]) != 0))
+        X = wl.orbitals(complex_=cplx)
         ref = oracle_ham(wl, D=wl.D0[0]).apply(X.T).T
         hb = make_hub(wl, prec)
         hb.set_occupation_matrix(0, wl.D0[0])
@@ -88,7 +94,7 @@ def test_apply_H_every_stencil_variant(prec):
             hb.set_tuning(v)
             Yd = torch.empty_like(Xd)
             hb.apply_H(0, Xd, Yd)
-            err = rel(Yd.cpu().numpy().astype(np.float64), ref)
+            err = rel(Yd.cpu().numpy().astype(np.complex128 if cplx else np.float64), ref)
             assert err < (5e-6 if prec == HUB_F32 else TOL64), (wl.name, v, err)
         with pytest.raises(HubError):
             hb.set_tuning(hb.get_tuning()["n_variants"])
