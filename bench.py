@@ -200,7 +200,19 @@ def cpu_oracle_sample(workload: str, seconds: float, cols: int = 2):
 # an ncu capture), each valid only for the kernel source the capture ran on: an entry holds
 # the bytes, the source file and the first 16 hex digits of its sha256 at capture time.  A
 # kernel whose source has changed since reports traffic null until it is captured again.
-TRAFFIC_CAPTURES = {}
+# Captured on the rutile 2x2x3 workload (348 orbitals, one launch = 226.4 M point-orbitals)
+# with `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+# --clock-control none -k regex:"k_stencil|k_gather|k_scatter" -s 300 -c 3` (FP64) and `-c 6`
+# (`--prec f32`) around `python bench.py [--prec f32] --steps 1 --warmup 1 --no-scf-tts
+# --no-e2e --no-cpu-baseline`; the float gather is the tensor-core brick gather.
+TRAFFIC_CAPTURES = {
+    ("f64", "stencil"): (25.11, "stencil.cu", "7095f36bbcbc94c0"),
+    ("f64", "gather"): (95.89, "projectors.cu", "6dea3a0515b2605e"),
+    ("f64", "scatter"): (51.09, "projectors.cu", "6dea3a0515b2605e"),
+    ("f32", "stencil"): (12.52, "stencil.cu", "7095f36bbcbc94c0"),
+    ("f32", "gather"): (5.68, "projectors_tc.cu", "0c8e2456bd0c1a25"),
+    ("f32", "scatter"): (8.31, "projectors.cu", "6dea3a0515b2605e"),
+}
 
 
 def _source_sha16(rel_path):
