@@ -20,7 +20,6 @@
 
 #include "hub_internal.cuh"
 #include "cplx.cuh"
-#include "tcgen05.cuh"
 
 namespace hub {
 
@@ -1347,304 +1346,6 @@ static int run_f32s(hub_t h, const StencilArgs& s) {
     return HUB_OK;
 }
 
-// ---------------------------------------------------------------------------- float TMA form
-// Real float, the k_stencil_f32s arithmetic (same bits) with the plane copies issued by one
-// thread as TMA boxes instead of per-thread cp.async copies: no per-thread copy addressing
-// in the z-loop.  The halo'd plane of a tile (TXP = 32 x-points, TY rows) is split into boxes
-// that never cross a cell face, each landing at a 128-byte aligned shared-memory address:
-//   C: the tile's 32 columns over rows -6 .. TYv + 5 (top halo 6 rows, interior TYv rows,
-//      bottom halo 6 rows, each its own box whose y start is wrapped into the cell),
-//   L, R: the 8 columns left of the tile and right of its last valid column, interior rows
-//      only (the star stencil needs no corners), x start wrapped into the cell,
-// plus V, Yprev and the queue feed plane z + NH + 1 (interior boxes).  TYv / Wv are the
-// tile's valid rows / columns; a ragged last y-tile uses boxes TYr = n2 % TY rows high so
-// that its interior box ends where its bottom halo starts.  Usable when n1 and ld are
-// multiples of 4, n1 % TXP is 0 or >= 8, n2 % TY is 0 or >= 6, n2 >= 6 and n1 >= 16.
-// Waits on the stage barriers are bounded: a wait that runs out raises FLAG_TIMEOUT, the
-// CTA stops, its copies in flight land, and it returns.
-constexpr int TF_TXT = 8, TF_TXP = 32, TF_NH = 6;
-
-template <int TY, int PH>
-struct TmaCfg {
-    static constexpr int NT = TF_TXT * TY;
-    static constexpr int RS = PH + 2;
-    static constexpr size_t CB = (size_t)(TY + 2 * TF_NH) * TF_TXP * 4;   // C rows
-    static constexpr size_t LB = (size_t)TY * 8 * 4;                      // L (and R)
-    static constexpr size_t IB = (size_t)TY * TF_TXP * 4;                 // V, Yprev, feed
-    static constexpr size_t OC = 0, OL = CB, OR = CB + LB, OV = CB + 2 * LB, OP = OV + IB, OF = OP + IB;
-    static constexpr size_t STAGE = OF + IB;
-    static constexpr size_t SMEM = STAGE * RS + 128;
-    static_assert(CB % 128 == 0 && LB % 128 == 0 && IB % 128 == 0, "boxes land on 128-byte boundaries");
-};
-
-struct TmaMaps {
-    CUtensorMap c6;     // Y: 32 x 6 (halo rows)
-    CUtensorMap ci;     // Y: 32 x TY (interior rows; also the feed plane)
-    CUtensorMap cir;    // Y: 32 x TYr (interior rows of a ragged last y-tile)
-    CUtensorMap lr;     // Y: 8 x TY
-    CUtensorMap lrr;    // Y: 8 x TYr
-    CUtensorMap p;      // Yprev: 32 x TY
-    CUtensorMap v;      // V: 32 x TY
-};
-
-template <int TY, int PH>
-__global__ void __launch_bounds__(TF_TXT * TY)
-k_stencil_f32t(const __grid_constant__ TmaMaps m, StencilDev<float> a, int tyr, int* flags) {
-    const Coef<float> cf = resolve_coef(a);
-    using C = TmaCfg<TY, PH>;
-    constexpr int NH = TF_NH, RS = C::RS;
-    constexpr int Q = 2 * NH + 1;
-    extern __shared__ __align__(128) unsigned char tsm[];
-    unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tsm) + 127) & ~(uintptr_t)127);
-    __shared__ __align__(8) uint64_t full_bar[RS];
-    __shared__ volatile int abort_flag;
-
-    const int tid = threadIdx.x;
-    const int tx = tid % TF_TXT, ty = tid / TF_TXT;
-    const int col = blockIdx.z / a.nzc;
-    const int zc = blockIdx.z - col * a.nzc;
-    const int z0 = zc * a.zchunk;
-    const int z1 = min(z0 + a.zchunk, a.n3);
-    const int n1 = a.n1, n2 = a.n2, n3 = a.n3;
-    const long plane = (long)n1 * n2;
-    const int gx0 = blockIdx.x * TF_TXP, gy0 = blockIdx.y * TY;
-    const int wv = min(TF_TXP, n1 - gx0);                     // valid columns (multiple of 4)
-    const bool ragged = gy0 + TY > n2;                        // last y-tile, tyr valid rows
-    const int tyv = ragged ? tyr : TY;
-    // box origins (wrapped into the cell; none crosses a face)
-    const int ytop = gy0 >= NH ? gy0 - NH : n2 - NH;
-    const int ybot = gy0 + tyv == n2 ? 0 : gy0 + tyv;
-    const int xl = gx0 >= 8 ? gx0 - 8 : n1 - 8;
-    const int xr = gx0 + wv == n1 ? 0 : gx0 + wv;
-
-    const float* __restrict__ Y = reinterpret_cast<const float*>(a.Y) + (size_t)col * a.ld;
-    float* Yo = reinterpret_cast<float*>(a.Yout) + (size_t)col * a.ld;
-    const bool has_prev = a.Yprev != nullptr;
-
-    if (tid == 0) {
-        abort_flag = 0;
-        for (int s = 0; s < RS; ++s) mbar_init(&full_bar[s], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-
-    const bool active = (tx * 4 < wv) && (gy0 + ty < n2);
-    const long own = (long)(gy0 + ty) * n1 + (gx0 + tx * 4);
-    // shared-memory byte offsets (within a stage) of the thread's five x-neighbour vectors
-    // (chunks tx - 2 .. tx + 2 of its row): L, C or R
-    uint32_t xo[5];
-#pragma unroll
-    for (int j = 0; j < 5; ++j) {
-        const int c = tx - 2 + j;
-        if (c < 0) xo[j] = (uint32_t)(C::OL + (size_t)ty * 32 + (size_t)(c + 2) * 16);
-        else if (4 * c >= wv) xo[j] = (uint32_t)(C::OR + (size_t)ty * 32 + (size_t)(c - wv / 4) * 16);
-        else xo[j] = (uint32_t)(C::OC + (size_t)(NH + ty) * 128 + (size_t)c * 16);
-    }
-
-    // plane copies of group j into stage st: plane ip (< z1) and the feed plane
-    int ip = z0;
-    int fz = z0 + NH + 1;
-    while (fz >= n3) fz -= n3;
-    auto issue = [&](int st) {
-        unsigned char* sb = ring + C::STAGE * (size_t)st;
-        uint32_t bytes = 0;
-        if (ip < z1) bytes += (uint32_t)(2 * 6 * 128 + (ragged ? tyr : TY) * 128 + 2 * 32 * (ragged ? tyr : TY) +
-                                         C::IB * (has_prev ? 2 : 1));
-        if (ip + 1 < z1) bytes += (uint32_t)C::IB;
-        if (bytes) {
-            mbar_expect_tx(&full_bar[st], bytes);
-            if (ip < z1) {
-                tma_load_4d(sb + C::OC, &m.c6, gx0, ytop, ip, col, &full_bar[st]);
-                tma_load_4d(sb + C::OC + (size_t)NH * 128, ragged ? &m.cir : &m.ci, gx0, gy0, ip, col, &full_bar[st]);
-                tma_load_4d(sb + C::OC + (size_t)(NH + tyv) * 128, &m.c6, gx0, ybot, ip, col, &full_bar[st]);
-                tma_load_4d(sb + C::OL, ragged ? &m.lrr : &m.lr, xl, gy0, ip, col, &full_bar[st]);
-                tma_load_4d(sb + C::OR, ragged ? &m.lrr : &m.lr, xr, gy0, ip, col, &full_bar[st]);
-                tma_load_3d(sb + C::OV, &m.v, gx0, gy0, ip, &full_bar[st]);
-                if (has_prev) tma_load_4d(sb + C::OP, &m.p, gx0, gy0, ip, col, &full_bar[st]);
-            }
-            if (ip + 1 < z1) tma_load_4d(sb + C::OF, &m.ci, gx0, gy0, fz, col, &full_bar[st]);
-        } else {
-            mbar_arrive(&full_bar[st]);       // nothing to copy: complete the phase
-        }
-        ++ip;
-        if (++fz == n3) fz = 0;
-    };
-
-    u64 wx[NH], wy[NH], wz[NH];
-#pragma unroll
-    for (int p = 0; p < NH; ++p) {
-        wx[p] = pk2(cf.w[0][p], cf.w[0][p]);
-        wy[p] = pk2(cf.w[1][p], cf.w[1][p]);
-        wz[p] = pk2(cf.w[2][p], cf.w[2][p]);
-    }
-    const u64 cen2 = pk2(cf.center, cf.center), alp2 = pk2(cf.alpha, cf.alpha), bet2 = pk2(cf.beta, cf.beta);
-    const u64 m2 = pk2(-2.0f, -2.0f);
-
-    u64 ql[Q], qh[Q];
-#pragma unroll
-    for (int j = 0; j < Q; ++j) {
-        ql[j] = 0ull;
-        qh[j] = 0ull;
-        if (active) {
-            const int p = z0 - NH + j;
-            const int wz_ = floordiv(p, n3);
-            const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(Y + (long)(p - wz_ * n3) * plane + own);
-            ql[j] = v.x;
-            qh[j] = v.y;
-        }
-    }
-    if (tid == 0)
-        for (int j = 0; j < PH; ++j) issue(j % RS);
-    int sz = 0, si = PH % RS;
-    bool stop = false;
-#pragma unroll 1
-    for (int zb = z0; zb < z1 && !stop; zb += Q) {
-#pragma unroll
-        for (int st = 0; st < Q; ++st) {
-            const int z = zb + st;
-            if (z >= z1) break;
-            if (tid == 0) issue(si);
-            const bool ok = mbar_wait(&full_bar[sz], (uint32_t)(((z - z0) / RS) & 1), &abort_flag);
-            if (__syncthreads_or(!ok)) { stop = true; break; }
-            if (active) {
-                const unsigned char* sb = ring + C::STAGE * (size_t)sz;
-                u64 r[10];
-#pragma unroll
-                for (int j = 0; j < 5; ++j) {
-                    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(sb + xo[j]);
-                    r[2 * j] = v.x;
-                    r[2 * j + 1] = v.y;
-                }
-                u64 u[8];
-#pragma unroll
-                for (int k = 1; k <= 7; ++k) u[k] = pk2(hi2(r[k]), lo2(r[k + 1]));
-                const ulonglong2* crow = reinterpret_cast<const ulonglong2*>(sb + C::OC + (size_t)(NH + ty) * 128) + tx;
-                const ulonglong2 vv = reinterpret_cast<const ulonglong2*>(sb + C::OV + (size_t)ty * 128)[tx];
-                const u64 cl = ql[(st + NH) % Q], ch = qh[(st + NH) % Q];
-                u64 xl = 0ull, xh = 0ull, yl = 0ull, yh = 0ull, zl = 0ull, zh = 0ull;
-#pragma unroll
-                for (int p = 1; p <= NH; ++p) {
-                    const u64 dzl = fma2(m2, cl, add2(ql[(st + NH + p) % Q], ql[(st + NH - p) % Q]));
-                    const u64 dzh = fma2(m2, ch, add2(qh[(st + NH + p) % Q], qh[(st + NH - p) % Q]));
-                    const u64 lp = (p & 1) ? u[(8 + p - 1) / 2] : r[(8 + p) / 2];
-                    const u64 lm = (p & 1) ? u[(8 - p - 1) / 2] : r[(8 - p) / 2];
-                    const u64 hp = (p & 1) ? u[(10 + p - 1) / 2] : r[(10 + p) / 2];
-                    const u64 hm = (p & 1) ? u[(10 - p - 1) / 2] : r[(10 - p) / 2];
-                    const u64 dxl = fma2(m2, cl, add2(lp, lm));
-                    const u64 dxh = fma2(m2, ch, add2(hp, hm));
-                    const ulonglong2 up = crow[p * 8];          // 8 vectors of 16 bytes per C row
-                    const ulonglong2 dn = crow[-p * 8];
-                    const u64 dyl = fma2(m2, cl, add2(up.x, dn.x));
-                    const u64 dyh = fma2(m2, ch, add2(up.y, dn.y));
-                    if (p == 1) {
-                        zl = mul2(wz[0], dzl); zh = mul2(wz[0], dzh);
-                        xl = mul2(wx[0], dxl); xh = mul2(wx[0], dxh);
-                        yl = mul2(wy[0], dyl); yh = mul2(wy[0], dyh);
-                    } else {
-                        zl = fma2(wz[p - 1], dzl, zl); zh = fma2(wz[p - 1], dzh, zh);
-                        xl = fma2(wx[p - 1], dxl, xl); xh = fma2(wx[p - 1], dxh, xh);
-                        yl = fma2(wy[p - 1], dyl, yl); yh = fma2(wy[p - 1], dyh, yh);
-                    }
-                }
-                u64 al = mul2(fma2(alp2, vv.x, cen2), cl);
-                u64 ah = mul2(fma2(alp2, vv.y, cen2), ch);
-                al = add2(al, add2(add2(xl, yl), zl));
-                ah = add2(ah, add2(add2(xh, yh), zh));
-                if (has_prev) {
-                    const ulonglong2 pv = reinterpret_cast<const ulonglong2*>(sb + C::OP + (size_t)ty * 128)[tx];
-                    al = fma2(bet2, pv.x, al);
-                    ah = fma2(bet2, pv.y, ah);
-                }
-                *reinterpret_cast<ulonglong2*>(Yo + (long)z * plane + own) = make_ulonglong2(al, ah);
-                if (z + 1 < z1) {
-                    const ulonglong2 f = reinterpret_cast<const ulonglong2*>(sb + C::OF + (size_t)ty * 128)[tx];
-                    ql[st] = f.x;                 // slot of plane z - NH takes plane z + NH + 1
-                    qh[st] = f.y;
-                }
-            }
-            if (++sz == RS) sz = 0;
-            if (++si == RS) si = 0;
-        }
-    }
-    if (tid == 0) {
-        if (stop) atomicExch(flags + FLAG_TIMEOUT, 1);
-        // every issued group's copies land before the CTA's shared memory goes away
-        const int issued = ip - z0;
-        for (int g = issued > RS ? issued - RS : 0; g < issued; ++g)
-            mbar_drain(&full_bar[g % RS], (uint32_t)((g / RS) & 1));
-    }
-    __syncthreads();
-}
-
-// 2-D .. 4-D float32 tensor map over a grid function (or a block of them), no swizzle
-static int tf_map(hub_t h, PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* mp, const void* base, int rank,
-                  const cuuint64_t* dims, const cuuint64_t* strides, uint32_t bx, uint32_t by) {
-    cuuint32_t box[4] = {bx, by, 1, 1};
-    cuuint32_t es[4] = {1, 1, 1, 1};
-    if (enc(mp, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return fail(h, HUB_ECUDA, "stencil: cuTensorMapEncodeTiled failed");
-    return HUB_OK;
-}
-
-// whether the TMA form applies to this grid (see k_stencil_f32t)
-static bool tma_stencil_ok(int n1, int n2, int ty) {
-    const int rx = n1 % TF_TXP, ry = n2 % ty;
-    return n1 % 4 == 0 && n1 >= 16 && n2 >= TF_NH && (rx == 0 || rx >= 8) && (ry == 0 || ry >= TF_NH);
-}
-
-template <int TY, int PH>
-static int run_f32t(hub_t h, const StencilArgs& s) {
-    using Cfg = TmaCfg<TY, PH>;
-    if (!tma_stencil_ok(s.n1, s.n2, TY) || s.ld % 4 != 0) return run_f32s<8, TY, PH>(h, s);
-    StencilDev<float> d;
-    d.Y = s.Y;
-    d.Yprev = s.Yprev;
-    d.Yout = s.Yout;
-    d.V = reinterpret_cast<const float*>(s.V);
-    d.n1 = s.n1; d.n2 = s.n2; d.n3 = s.n3; d.ld = s.ld;
-    fill_coefficients<float>(s, d);
-    for (int a = 0; a < 3; ++a) {
-        d.ph[a][0] = 1.0;
-        d.ph[a][1] = 0.0;
-    }
-    PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
-    int rc = tensor_map_encoder(h, &enc);
-    if (rc) return rc;
-    const int tyr = s.n2 % TY;
-    const uint32_t tyr_box = tyr ? (uint32_t)tyr : (uint32_t)TY;
-    const cuuint64_t dY[4] = {(cuuint64_t)s.n1, (cuuint64_t)s.n2, (cuuint64_t)s.n3, (cuuint64_t)s.ncol};
-    const cuuint64_t sY[3] = {(cuuint64_t)s.n1 * 4, (cuuint64_t)s.n1 * s.n2 * 4, (cuuint64_t)s.ld * 4};
-    const cuuint64_t dV[3] = {(cuuint64_t)s.n1, (cuuint64_t)s.n2, (cuuint64_t)s.n3};
-    TmaMaps m;
-    if ((rc = tf_map(h, enc, &m.c6, s.Y, 4, dY, sY, TF_TXP, TF_NH))) return rc;
-    if ((rc = tf_map(h, enc, &m.ci, s.Y, 4, dY, sY, TF_TXP, TY))) return rc;
-    if ((rc = tf_map(h, enc, &m.cir, s.Y, 4, dY, sY, TF_TXP, tyr_box))) return rc;
-    if ((rc = tf_map(h, enc, &m.lr, s.Y, 4, dY, sY, 8, TY))) return rc;
-    if ((rc = tf_map(h, enc, &m.lrr, s.Y, 4, dY, sY, 8, tyr_box))) return rc;
-    if ((rc = tf_map(h, enc, &m.p, s.Yprev ? s.Yprev : s.Y, 4, dY, sY, TF_TXP, TY))) return rc;
-    if ((rc = tf_map(h, enc, &m.v, s.V, 3, dV, sY, TF_TXP, TY))) return rc;
-    const int tiles = ((s.n1 + TF_TXP - 1) / TF_TXP) * ((s.n2 + TY - 1) / TY);
-    const long want = 8L * h->num_sms;
-    const long per = (long)tiles * s.ncol;
-    int nzc = 1;
-    if (per < want) nzc = (int)((want + per - 1) / per);
-    int zchunk = (s.n3 + nzc - 1) / nzc;
-    if (zchunk < 16) zchunk = s.n3 < 16 ? s.n3 : 16;
-    nzc = (s.n3 + zchunk - 1) / zchunk;
-    while ((long)s.ncol * nzc > 65535) { zchunk *= 2; nzc = (s.n3 + zchunk - 1) / zchunk; }
-    d.zchunk = zchunk;
-    d.nzc = nzc;
-    HUB_CUDA_TRY(h, cudaFuncSetAttribute(k_stencil_f32t<TY, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Cfg::SMEM));
-    dim3 grid((s.n1 + TF_TXP - 1) / TF_TXP, (s.n2 + TY - 1) / TY, s.ncol * nzc);
-    ProfScope ps(h, HUB_K_STENCIL);
-    k_stencil_f32t<TY, PH><<<grid, TF_TXT * TY, Cfg::SMEM, h->stream>>>(m, d, tyr, h->d_flags);
-    HUB_CUDA_TRY(h, cudaGetLastError());
-    return HUB_OK;
-}
-
 template <typename R, bool CPLX, int VEC, int TXT, int TY, int P>
 static int run_vec(hub_t h, const StencilArgs& s) {
     using Cfg = VecCfg<R, CPLX, VEC, TXT, TY, P>;
@@ -1814,7 +1515,7 @@ int launch_fd_gradient(hub_t h, const void* X, int ld, int ncol, int axis, const
 // Tile shapes the autotuner chooses from, per kernel family (index 0 is the default).
 int stencil_variants(hub_t h) {
     const int es = h->esize * (h->cplx ? 2 : 1);
-    if (h->esize == 4) return h->cplx ? 6 : 11;  // float real (packed) / float complex (packed, vector)
+    if (h->esize == 4) return h->cplx ? 6 : 9;   // float real (packed) / float complex (packed, vector)
     return es == 16 ? 2 : 3;              // double complex / double real (scalar pipeline)
 }
 
@@ -1838,8 +1539,6 @@ int launch_stencil(hub_t h, const StencilArgs& a) {
                 case 6: return run_f32s2<8, 8, 2>(h, a);
                 case 7: return run_f32s2<8, 16, 2>(h, a);
                 case 8: return run_f32s2<16, 8, 2>(h, a);
-                case 9: return run_f32t<16, 2>(h, a);
-                case 10: return run_f32t<8, 2>(h, a);
                 default: return run_f32s<8, 16, 2>(h, a);
             }
         }

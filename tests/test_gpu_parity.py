@@ -78,8 +78,8 @@ def test_apply_H_every_stencil_variant(prec):
     cases = [systems()["ragged"],
              w.small_test_system(n=(8, 12, 3), ncol=5, natoms=2, hub_rc=2.0, kb_rc=1.5, seed=5),
              w.small_test_system(n=(12, 9, 10), ncol=6, natoms=2, hub_rc=2.0, kb_rc=1.5, seed=6),
-             # two x-tiles of the TMA form (the second 8 columns wide) and ragged y-tiles of
-             # 14 and 6 rows, z thinner than the queue
+             # a ragged second x-tile (8 columns), ragged y-tiles of 14 and 6 rows, z thinner
+             # than the queue
              w.small_test_system(n=(40, 30, 12), ncol=5, natoms=2, hub_rc=2.5, kb_rc=1.5, seed=8)]
     # Bloch (complex) blocks: a ragged grid, and one thinner in z than the half-width with
     # wraps on every face (the halo and queue planes carry their Bloch factors)
