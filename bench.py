@@ -425,10 +425,12 @@ def run_hub(args, rank, world, local_rank):
             "wl": wl, "profiled_ms": ms_prof}
 
 
-def scf_solve_timed(wl, X0, dev, prec, profile_after=0):
+def scf_solve_timed(wl, X0, dev, prec, profile_after=0, ladder=None):
     """Cold-start SCF of the workload in one precision form on a fresh handle, timed from
     handle creation to convergence; optionally profile_after more iterations with per-kernel
-    events.  Returns the result, the per-kernel profile and the projector function points."""
+    events.  Returns the result, the per-kernel profile and the projector function points.
+    ladder: the mixed forms' precision ladder (default on for them; 0 = three-term 16-bit
+    products throughout)."""
     import numpy as np
     import torch
     from paper_2507_23612_gb300 import Hub, scf_params
@@ -442,7 +444,9 @@ def scf_solve_timed(wl, X0, dev, prec, profile_after=0):
     p = scf_params(nspin=wl.nspin, ncol=wl.ncol, ld=wl.Nd, degree=wl.degree, max_iter=200,
                    first_passes=3, lanczos_steps=10, pulay_history=7, natoms=len(wl.atoms),
                    pulay_beta=0.3, kT=wl.kT if wl.kT > 0 else 0.005, n_elec=wl.n_elec,
-                   tol_e_atom=1e-5, tol_D=1e-4, ladder=1 if prec in ("mixed", "mixed16") else 0, ladder_tol=1e-4)
+                   tol_e_atom=1e-5, tol_D=1e-4,
+                   ladder=(1 if prec in ("mixed", "mixed16") else 0) if ladder is None else ladder,
+                   ladder_tol=1e-4)
     hub.scf_begin(p, Xs, v0s, wl.D0)
     res = hub.scf_run()
     torch.cuda.synchronize()
