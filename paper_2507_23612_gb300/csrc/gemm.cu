@@ -150,6 +150,98 @@ k_rotate(const T* __restrict__ X, int ldx, const typename Wide<T>::type* __restr
     }
 }
 
+// Real float rotation Y = X Q with 8 x 8 outputs per thread: 128 rows x 64 columns per CTA
+// of 128 threads; 16-deep slices of X (16-byte loads along the rows) and of Q (double,
+// rounded to float) in shared memory.  Requires 16-byte aligned X and Y with ldx, ldy
+// multiples of 4.
+constexpr int R8_BM = 128, R8_BN = 64, R8_BK = 16;
+__global__ void __launch_bounds__(128)
+k_rotate_f32x8(const float* __restrict__ X, int ldx, const double* __restrict__ Q, int k, int n, long K,
+               float* __restrict__ Y, int ldy) {
+    __shared__ __align__(16) float Xs[R8_BK][R8_BM + 4];
+    __shared__ __align__(16) float Qs[R8_BK][R8_BN + 4];
+    const long r0 = (long)blockIdx.x * R8_BM;
+    const int j0 = blockIdx.y * R8_BN;
+    const int t = threadIdx.x, tx = t % 8, ty = t / 8;
+    float acc[8][8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+    // the next k-slice's loads fly while the current one is multiplied
+    float4 xv[4];
+    float qv[8];
+    auto load = [&](int kb) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = t + 128 * q;
+            const int kk = e / 32, rv = e % 32;
+            const long r = r0 + 4 * rv;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (kb + kk < k) {
+                const float* src = X + (size_t)(kb + kk) * ldx;
+                if (r + 3 < K) v = *reinterpret_cast<const float4*>(src + r);
+                else {
+                    if (r < K) v.x = src[r];
+                    if (r + 1 < K) v.y = src[r + 1];
+                    if (r + 2 < K) v.z = src[r + 2];
+                }
+            }
+            xv[q] = v;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = t + 128 * q;
+            const int kq = e / 64, jj = e % 64;
+            qv[q] = (kb + kq < k && j0 + jj < n) ? (float)Q[(size_t)(kb + kq) * n + j0 + jj] : 0.f;
+        }
+    };
+    if (k > 0) load(0);
+    for (int kb = 0; kb < k; kb += R8_BK) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = t + 128 * q;
+            *reinterpret_cast<float4*>(&Xs[e / 32][4 * (e % 32)]) = xv[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int e = t + 128 * q;
+            Qs[e / 64][e % 64] = qv[q];
+        }
+        __syncthreads();
+        if (kb + R8_BK < k) load(kb + R8_BK);
+#pragma unroll
+        for (int kk = 0; kk < R8_BK; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&Xs[kk][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&Xs[kk][ty * 8 + 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Qs[kk][tx * 8]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Qs[kk][tx * 8 + 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+    const long rb = r0 + ty * 8;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int j = j0 + tx * 8 + c;
+        if (j >= n) continue;
+        float* dst = Y + (size_t)j * ldy + rb;
+        if (rb + 7 < K) {
+            *reinterpret_cast<float4*>(dst) = make_float4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
+            *reinterpret_cast<float4*>(dst + 4) = make_float4(acc[4][c], acc[5][c], acc[6][c], acc[7][c]);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+                if (rb + r < K) dst[r] = acc[r][c];
+        }
+    }
+}
+
 template <typename T, int TB>
 int gram_tiles(hub_t h, const void* A, int lda, const void* B, int ldb, int m, int n, double alpha,
                bool sym, double* G) {
@@ -180,6 +272,112 @@ int gram_tiles(hub_t h, const void* A, int lda, const void* B, int ldb, int m, i
     return HUB_OK;
 }
 
+// Real float Gram product with 8 x 8 outputs per thread: 64 x 64 tiles, 64 threads, the
+// 16-deep k-slices of both operands staged in shared memory (each thread copies one column
+// of each tile in 16-byte loads), every k step two 16-byte shared loads per operand for 64
+// FMAs (the 4 x 4 kernel needs one shared load per two FMAs and was bound by them).
+// Requires 16-byte aligned operands with lda, ldb multiples of 4.
+constexpr int G8_TB = 64, G8_BK = 16;
+__global__ void __launch_bounds__(64)
+k_gram_f32x8(const float* __restrict__ A, int lda, const float* __restrict__ B, int ldb, long K, int m, int n,
+             long chunk, int tn, int sym, double* __restrict__ part) {
+    __shared__ __align__(16) float As[G8_BK][G8_TB + 4];
+    __shared__ __align__(16) float Bs[G8_BK][G8_TB + 4];
+    const int bi = blockIdx.x / tn, bj = blockIdx.x % tn;
+    if (sym && bi > bj) return;          // mirrored by the reduction
+    const int i0 = bi * G8_TB, j0 = bj * G8_TB;
+    const long k0 = (long)blockIdx.y * chunk;
+    const long k1 = min(K, k0 + chunk);
+    const int t = threadIdx.x, tx = t % 8, ty = t / 8;
+    float acc[8][8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+    const float* Ac = (i0 + t < m) ? A + (size_t)(i0 + t) * lda : nullptr;   // this thread's columns
+    const float* Bc = (j0 + t < n) ? B + (size_t)(j0 + t) * ldb : nullptr;
+    // the next k-slice's loads fly while the current one is multiplied
+    float av[G8_BK], bv[G8_BK];
+    auto load = [&](long kb) {
+        if (kb + G8_BK <= k1) {
+#pragma unroll
+            for (int q = 0; q < G8_BK / 4; ++q) {
+                const float4 x = Ac ? *reinterpret_cast<const float4*>(Ac + kb + 4 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 y = Bc ? *reinterpret_cast<const float4*>(Bc + kb + 4 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                av[4 * q] = x.x; av[4 * q + 1] = x.y; av[4 * q + 2] = x.z; av[4 * q + 3] = x.w;
+                bv[4 * q] = y.x; bv[4 * q + 1] = y.y; bv[4 * q + 2] = y.z; bv[4 * q + 3] = y.w;
+            }
+        } else {
+#pragma unroll
+            for (int kk = 0; kk < G8_BK; ++kk) {
+                av[kk] = (Ac && kb + kk < k1) ? Ac[kb + kk] : 0.f;
+                bv[kk] = (Bc && kb + kk < k1) ? Bc[kb + kk] : 0.f;
+            }
+        }
+    };
+    if (k0 < k1) load(k0);
+    for (long kb = k0; kb < k1; kb += G8_BK) {
+#pragma unroll
+        for (int kk = 0; kk < G8_BK; ++kk) {
+            As[kk][t] = av[kk];
+            Bs[kk][t] = bv[kk];
+        }
+        __syncthreads();
+        if (kb + G8_BK < k1) load(kb + G8_BK);
+#pragma unroll
+        for (int kk = 0; kk < G8_BK; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][ty * 8 + 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8 + 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+    double* P = part + (size_t)blockIdx.y * m * n;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int i = i0 + ty * 8 + r;
+        if (i >= m) continue;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int j = j0 + tx * 8 + c;
+            if (j < n) P[(size_t)i * n + j] = (double)acc[r][c];
+        }
+    }
+}
+
+int gram_f32x8(hub_t h, const float* A, int lda, const float* B, int ldb, int m, int n, double alpha, bool sym,
+               double* G) {
+    const int tm = (m + G8_TB - 1) / G8_TB, tn = (n + G8_TB - 1) / G8_TB;
+    const long ntiles = sym ? (long)tm * (tm + 1) / 2 : (long)tm * tn;
+    const long K = h->Nd;
+    int splits = (int)((8L * h->num_sms + ntiles - 1) / ntiles);
+    long chunk = (K + splits - 1) / splits;
+    chunk = ((chunk + G8_BK - 1) / G8_BK) * G8_BK;
+    if (chunk < 4 * G8_BK) chunk = 4 * G8_BK;
+    splits = (int)((K + chunk - 1) / chunk);
+    int rc;
+    if ((rc = ensure(h, &h->d_gpart, &h->gpart_bytes, std::max(h->gpart_bytes, (size_t)splits * m * n * sizeof(double)))))
+        return rc;
+    double* part = (double*)h->d_gpart;
+    dim3 grid((unsigned)(tm * tn), splits);
+    { ProfScope ps(h, HUB_K_GRAM);
+    k_gram_f32x8<<<grid, 64, 0, h->stream>>>(A, lda, B, ldb, K, m, n, chunk, tn, sym ? 1 : 0, part); }
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    const long tot = (long)m * n;
+    { ProfScope ps(h, HUB_K_GRAM_REDUCE);
+    k_gram_reduce<double><<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(part, splits, m, n, alpha,
+                                                                                sym ? 1 : 0, G8_TB, G); }
+    HUB_CUDA_TRY(h, cudaGetLastError());
+    return HUB_OK;
+}
+
 // 32 x 32 tiles: on the 348-orbital rutile block the 64-wide tiles computed 42 % more
 // elements than the symmetric product needs (ragged edge, full diagonal tiles), the 32-wide
 // ones 11 %; the FP64 Gram product went from 112 to 81 ms
@@ -199,6 +397,8 @@ int launch_gram(hub_t h, const void* A, int lda, const void* B, int ldb, int m, 
         return gram_t<float2>(h, A, lda, B, ldb, m, n, alpha, sym, G);
     }
     if (h->esize == 8) return gram_t<double>(h, A, lda, B, ldb, m, n, alpha, sym, G);
+    if (lda % 4 == 0 && ldb % 4 == 0 && (uintptr_t)A % 16 == 0 && (uintptr_t)B % 16 == 0)
+        return gram_f32x8(h, (const float*)A, lda, (const float*)B, ldb, m, n, alpha, sym, G);
     return gram_t<float>(h, A, lda, B, ldb, m, n, alpha, sym, G);
 }
 
@@ -213,6 +413,9 @@ int launch_rotate(hub_t h, const void* X, int ldx, const double* Q, int k, int n
         k_rotate<float2><<<grid, 256, 0, h->stream>>>((const float2*)X, ldx, Qz, k, n, h->Nd, (float2*)Y, ldy);
     else if (h->esize == 8)
         k_rotate<double><<<grid, 256, 0, h->stream>>>((const double*)X, ldx, Q, k, n, h->Nd, (double*)Y, ldy);
+    else if (ldx % 4 == 0 && ldy % 4 == 0 && (uintptr_t)X % 16 == 0 && (uintptr_t)Y % 16 == 0)
+        k_rotate_f32x8<<<dim3((unsigned)((h->Nd + R8_BM - 1) / R8_BM), (n + R8_BN - 1) / R8_BN), 128, 0, h->stream>>>(
+            (const float*)X, ldx, Q, k, n, h->Nd, (float*)Y, ldy);
     else
         k_rotate<float><<<grid, 256, 0, h->stream>>>((const float*)X, ldx, Q, k, n, h->Nd, (float*)Y, ldy);
     HUB_CUDA_TRY(h, cudaGetLastError());
