@@ -223,12 +223,12 @@ def cpu_oracle_sample(workload: str, seconds: float, cols: int = 2, procs: int =
 # (`--prec f32`) around `python bench.py [--prec f32] --steps 1 --warmup 1 --no-scf-tts
 # --no-e2e --no-cpu-baseline`; the float gather is the tensor-core brick gather.
 TRAFFIC_CAPTURES = {
-    ("f64", "stencil"): (25.11, "stencil.cu", "7095f36bbcbc94c0"),
-    ("f64", "gather"): (95.89, "projectors.cu", "6dea3a0515b2605e"),
-    ("f64", "scatter"): (51.09, "projectors.cu", "6dea3a0515b2605e"),
+    ("f64", "stencil"): (25.30, "stencil.cu", "7095f36bbcbc94c0"),
+    ("f64", "gather"): (95.83, "projectors.cu", "1fe8b3fc7739462a"),
+    ("f64", "scatter"): (51.07, "projectors.cu", "1fe8b3fc7739462a"),
     ("f32", "stencil"): (12.52, "stencil.cu", "7095f36bbcbc94c0"),
     ("f32", "gather"): (5.68, "projectors_tc.cu", "0c8e2456bd0c1a25"),
-    ("f32", "scatter"): (8.31, "projectors.cu", "6dea3a0515b2605e"),
+    ("f32", "scatter"): (8.32, "projectors.cu", "1fe8b3fc7739462a"),
 }
 
 
