@@ -396,7 +396,7 @@ static int rr_finish(hub_t h, void* X, int n, int ld, void* HX, double* ws, doub
 
 // Rayleigh-Ritz of both spin channels (blocks X[0], X[1] of the same shape): the two
 // subspace eigenproblems are solved in one cooperative launch, half the SMs each.
-static int rr_two_spins(hub_t h, void* const* X, int n, int ld, double* const* eig_host) {
+extern "C++" int rr_two_spins(hub_t h, void* const* X, int n, int ld, double* const* eig_host) {
     const size_t nn = rr_mat(h, n), wsz = rr_ws_doubles(h, n);
     const size_t blk = (size_t)ld * n * elem_bytes(h);
     int rc;

@@ -333,6 +333,10 @@ int launch_axpby_vec(hub_t h, int op, void* w, const void* v, const void* vprev,
 int launch_lanczos(hub_t h, int spin, int steps, const void* v0, double* lo, double* up);
 int launch_copy_block(hub_t h, const void* src, int lds, void* dst, int ldd, int ncol);
 
+// api: Rayleigh-Ritz of both spin channels of one handle (blocks X[0], X[1] of the same
+// shape), the two subspace eigenproblems in one cooperative launch, half the SMs each
+int rr_two_spins(hub_t h, void* const* X, int n, int ld, double* const* eig_host);
+
 // api: apply_H with explicit buffers (used by filter / RR / Lanczos)
 // Y = alpha (H X - shift X) + beta Yprev  (Yprev may alias Y; X, Y, Yprev share ld)
 int apply_H_internal(hub_t h, int spin, const void* X, int ld, void* Y, int ncol, double alpha,

@@ -167,6 +167,22 @@ int kscf_rr(hub_kscf_t s, int c) {
     return HUB_OK;
 }
 
+// Rayleigh-Ritz of the two spin channels of k-point k (one handle): both subspace
+// eigenproblems in one launch
+int kscf_rr_pair(hub_kscf_t s, int k) {
+    const hub_t h = s->hubs[k];
+    const int n = s->p.ncol, c0 = k, c1 = s->nk + k;
+    void* X[2] = {s->X[c0], s->X[c1]};
+    double* eg[2] = {s->eig.data() + (size_t)c0 * n, s->eig.data() + (size_t)c1 * n};
+    int rc;
+    if ((rc = kcall(s, h, hub::rr_two_spins(h, X, n, s->p.ld, eg), "Rayleigh-Ritz of both spins"))) return rc;
+    for (int c : {c0, c1}) {
+        s->bounds[c][0] = s->eig[(size_t)c * n];
+        s->bounds[c][1] = s->eig[(size_t)c * n + n - 1];
+    }
+    return HUB_OK;
+}
+
 // phase 3: Fermi level, D_out, energy, convergence and Pulay mixing of D
 int kscf_post(hub_kscf_t s, hub_scf_result* res) {
     const hub_scf_params& p = s->p;
@@ -284,16 +300,27 @@ int hub_kscf_iterate(hub_kscf_t s, hub_scf_result* res) {
     int rc;
     if ((rc = kscf_set_D(s))) return rc;
     const int passes = kscf_passes(s);
-    for (int c = 0; c < p.nspin * s->nk; ++c) {
+    auto filter = [&](int c) {
         const hub_t h = s->hubs[c % s->nk];
-        for (int pass = 0; pass < passes; ++pass) {
-            if ((rc = kscf_bounds(s, c))) return rc;
-            const auto& bd = s->bounds[c];
-            if ((rc = kcall(s, h, hub_chefsi_filter(h, c / s->nk, s->X[c], p.ncol, p.ld, p.degree, bd[1], bd[2], bd[0],
-                                                    nullptr), "hub_chefsi_filter")))
-                return rc;
-            if ((rc = kscf_rr(s, c))) return rc;
-        }
+        int r;
+        if ((r = kscf_bounds(s, c))) return r;
+        const auto& bd = s->bounds[c];
+        return kcall(s, h, hub_chefsi_filter(h, c / s->nk, s->X[c], p.ncol, p.ld, p.degree, bd[1], bd[2], bd[0],
+                                             nullptr), "hub_chefsi_filter");
+    };
+    if (p.nspin == 2) {
+        // per k-point both spin channels, their Rayleigh-Ritz in one eigensolver launch
+        for (int k = 0; k < s->nk; ++k)
+            for (int pass = 0; pass < passes; ++pass) {
+                if ((rc = filter(k)) || (rc = filter(s->nk + k))) return rc;
+                if ((rc = kscf_rr_pair(s, k))) return rc;
+            }
+    } else {
+        for (int c = 0; c < s->nk; ++c)
+            for (int pass = 0; pass < passes; ++pass) {
+                if ((rc = filter(c))) return rc;
+                if ((rc = kscf_rr(s, c))) return rc;
+            }
     }
     return kscf_post(s, res);
 }
@@ -349,8 +376,17 @@ int hub_kscf_iterate_batch(int nobj, hub_kscf_t* objs, hub_scf_result* res, void
                 const char* m = hub_last_error(hs[0]);
                 return kfail(objs[ch[0].first], rc, std::string("hub_batch_filter: ") + (m ? m : ""));
             }
-            for (auto& q : ch)
-                if ((rc = kscf_rr(objs[q.first], q.second))) return rc;
+            // spin 0 of a two-spin object waits for its spin 1 filter: both Rayleigh-Ritz
+            // projections in one eigensolver launch
+            for (auto& q : ch) {
+                hub_kscf_t s = objs[q.first];
+                if (s->p.nspin == 2 && sp == 0) continue;
+                if (s->p.nspin == 2) {
+                    if ((rc = kscf_rr_pair(s, q.second - s->nk))) return rc;
+                } else if ((rc = kscf_rr(s, q.second))) {
+                    return rc;
+                }
+            }
         }
     for (int i = 0; i < nobj; ++i) {
         if (std::find(active.begin(), active.end(), i) == active.end()) { res[i] = objs[i]->last; continue; }
