@@ -254,6 +254,7 @@ int kscf_post(hub_kscf_t s, hub_scf_result* res) {
     r.iter = s->iter;
     r.converged = (s->small >= 2 && dD < p.tol_D) ? 1 : 0;
     r.E = E; r.E_band = e_band; r.E_U = e_u; r.dE = dE; r.dD = dD; r.mu = mu;
+    for (int k = 0; k < nk; ++k) r.jacobi_sweeps = std::max(r.jacobi_sweeps, s->hubs[k]->last_sweeps);
     if (!r.converged) {
         // Pulay / DIIS on x = [Re D, Im D] with history p.pulay_history and mixing p.pulay_beta
         const size_t nD = s->Dr_in.size();
