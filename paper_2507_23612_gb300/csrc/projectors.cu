@@ -509,8 +509,13 @@ k_scatter_dense(float* __restrict__ Y, int ld, int ncol, int n1, int n2, int n3,
             }
             __syncthreads();
             const float* ph = phi + E.z + row * 4;
+            // the eight column groups start at staggered functions (each sums its functions
+            // in a fixed rotated order), so that the warps do not request the same value
+            // lines at the same time: L1 then serves most of them (rutile: 0.98 -> 0.87 ms)
+            const int fs = (cg * fp) >> 3;
 #pragma unroll 4
-            for (int f = 0; f < fp; ++f) {
+            for (int i = 0; i < fp; ++i) {
+                const int f = i + fs < fp ? i + fs : i + fs - fp;
                 const float4 pa = __ldg(reinterpret_cast<const float4*>(ph + (size_t)f * BRP));
                 const float4 pb = __ldg(reinterpret_cast<const float4*>(ph + (size_t)f * BRP + 128));
                 const float4 w4 = *reinterpret_cast<const float4*>(ws + f * SD_COLS + cg * 4);
