@@ -23,10 +23,11 @@
 // projector values are stored in the same layout when the tables are built (one row per
 // function and slice) and copied with cp.async.bulk.
 //
-// Kernel: persistent CTAs of 192 threads over (entry, orbital tile) units.  Warp 0 issues
+// Kernel: persistent CTAs of 320 threads over (entry, orbital tile) units.  Warp 0 issues
 // the value copies into a two-stage ring, warp 1 issues the MMAs into one of two TMEM
-// accumulators, warps 2-5 load and split the X slices and, once a unit's product is
-// complete, read the accumulator (tcgen05.ld) and write the partial rows.  Every mbarrier
+// accumulators, warps 2-5 load and split the X slices, and warps 6-9, once a unit's product
+// is complete, read its accumulator (tcgen05.ld) and write the partial rows while the next
+// unit is converted and multiplied.  Every mbarrier
 // wait is bounded: after its limit the CTA raises FLAG_TIMEOUT, stops issuing, drains the
 // copies and MMAs it issued, frees its TMEM and returns.
 #include <algorithm>
@@ -47,7 +48,7 @@ constexpr int GT_S = 2;                       // ring stages
 constexpr int GT_XB = GT_M * GT_K * 4;        // 16 KB: one X slice
 constexpr int GT_BB = GT_NP * GT_K * 4;       // 8 KB: one value slice at most
 constexpr int GT_STAGE = 2 * GT_XB + 2 * GT_BB;   // X hi, X lo, values hi, values lo
-constexpr int GT_THREADS = 192;
+constexpr int GT_THREADS = 320;           // producer, MMA, 4 converter and 4 epilogue warps
 constexpr uint32_t GT_TMEM_COLS = 4 * GT_NP;  // two units in flight x (hi*hi, corrections)
 constexpr size_t GT_SMEM = (size_t)GT_S * GT_STAGE + 1024;
 constexpr uint32_t kTf32Hi = 0xFFFFE000u;     // sign, exponent and the 10 TF32 significand bits
@@ -195,14 +196,10 @@ k_gather_tc(GtcArgs a) {
             }
             mma_commit(&done_bar);                      // every MMA issued by this thread
         }
-    } else {
-        // warps 2-5: X slices into the stages (hi and lo), then the unit's partial rows; warp
-        // w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31.  Waits are decided per warp (all
-        // lanes leave together), so the warp-collective TMEM loads stay converged.
+    } else if (warp < 6) {
+        // warps 2-5: X slices into the stages (hi and lo), slice after slice over the units.
+        // Waits are decided per warp (all lanes leave together).
         const int c = threadIdx.x - 64;
-        const int quad = warp & 3;
-        const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
-        const int row = 32 * quad + lane;
         SliceLoad L;
         if (nu > 0) load_slice(a, (int)blockIdx.x / a.ctiles, (int)blockIdx.x % a.ctiles, 0, c, L);
         int i = 0;
@@ -236,7 +233,16 @@ k_gather_tc(GtcArgs a) {
                     load_slice(a, un / a.ctiles, un % a.ctiles, 0, c, L);
                 }
             }
-            if (stop) break;
+        }
+    } else {
+        // warps 6-9: each unit's partial rows from its accumulator while the converters and
+        // the MMAs go on with the next unit; warp w reads TMEM lanes 32 (w % 4) .. + 31
+        const int quad = warp & 3;
+        const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+        const int row = 32 * quad + lane;
+        for (int uu = 0; uu < nu; ++uu) {
+            const int u = (int)blockIdx.x + uu * (int)gridDim.x;
+            const int e = u / a.ctiles, ct = u - e * a.ctiles;
             const int buf = uu & 1;
             const bool ok = mbar_wait(&tfull_bar[buf], (uu >> 1) & 1, &abort_flag);
             if (__any_sync(0xffffffffu, !ok)) break;
