@@ -221,14 +221,14 @@ def cpu_oracle_sample(workload: str, seconds: float, cols: int = 2, procs: int =
 # with `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
 # --clock-control none -k regex:"k_stencil|k_gather|k_scatter" -s 300 -c 3` (FP64) and `-c 6`
 # (`--prec f32`) around `python bench.py [--prec f32] --steps 1 --warmup 1 --no-scf-tts
-# --no-e2e --no-cpu-baseline`; the float gather is the tensor-core brick gather.
+# --no-e2e --no-cpu-baseline`; the float gather and scatter are the tensor-core brick forms.
 TRAFFIC_CAPTURES = {
-    ("f64", "stencil"): (25.30, "stencil.cu", "7095f36bbcbc94c0"),
-    ("f64", "gather"): (95.83, "projectors.cu", "1fe8b3fc7739462a"),
-    ("f64", "scatter"): (51.07, "projectors.cu", "1fe8b3fc7739462a"),
+    ("f64", "stencil"): (25.36, "stencil.cu", "7095f36bbcbc94c0"),
+    ("f64", "gather"): (95.82, "projectors.cu", "fc1a61ec662a13cc"),
+    ("f64", "scatter"): (50.96, "projectors.cu", "fc1a61ec662a13cc"),
     ("f32", "stencil"): (12.52, "stencil.cu", "7095f36bbcbc94c0"),
-    ("f32", "gather"): (5.68, "projectors_tc.cu", "0c8e2456bd0c1a25"),
-    ("f32", "scatter"): (8.32, "projectors.cu", "1fe8b3fc7739462a"),
+    ("f32", "gather"): (5.67, "projectors_tc.cu", "f67850d2e2255137"),
+    ("f32", "scatter"): (10.45, "projectors_tc.cu", "f67850d2e2255137"),
 }
 
 
@@ -903,7 +903,7 @@ def run_projector_forms(args):
         t = timed()
         t["projector_ms"] = round(t.get("gather", 0) + t.get("transform", 0) + t.get("scatter", 0), 4)
         forms[name] = t
-    hb.set_tuning(gather_form=2)
+    hb.set_tuning(gather_form=3)
     stencil = {}
     ref = None
     for v in range(hb.get_tuning()["n_variants"]):

@@ -470,9 +470,10 @@ int hub_autotune(hub_t h, int spin, const void* X, int ncol, int ld, int* varian
  * only), 2 (the brick gather as tcgen05 products, D[128 orbitals x functions] = X_b^T Phi_b
  * in TF32 with both operands split hi + lo and FP32 accumulation, the brick scatter on CUDA
  * cores) or 3 (gather and scatter both as tcgen05 products; the scatter per brick and 128
- * orbitals, D[128 points x 128 orbitals] = Phi_b W_b^T).  Forms 2 and 3 need real float
- * handles whose n1 is a multiple of 4 and blocks that start on 16-byte boundaries with ld a
- * multiple of 4.  hub_set_atoms_projectors sets form 2 where its tables exist, else 0.
+ * orbitals, D[128 points x 128 orbitals] = Phi_b W_b^T, added to Y by TMA reduce-add).
+ * Forms 2 and 3 need real float handles whose n1 is a multiple of 4 and blocks that start
+ * on 16-byte boundaries with ld a multiple of 4.  hub_set_atoms_projectors sets form 3
+ * where its tables exist, else 0.
  * Pass -1 to keep any of them.  Errors: HUB_EINVAL. */
 int hub_set_tuning(hub_t h, int stencil_variant, int gemm_split, int gather_form);
 /* Current tuning of the handle and the number of stencil variants of its kernel family

@@ -249,9 +249,10 @@ int hub_set_atoms_projectors(hub_t h, int natoms, const double* pos, const int* 
     if (rc) return rc;
     h->atoms_set = true;
     h->D_set[0] = h->D_set[1] = false;
-    // real float blocks: the tensor-core brick gather when its tables exist (the fastest form
-    // measured on the rutile workload; hub_autotune and hub_set_tuning can change it)
-    h->gather_dense = h->proj.tc ? 2 : 0;
+    // real float blocks: the tensor-core brick gather and scatter when their tables exist (the
+    // fastest form measured on the rutile workload; hub_autotune and hub_set_tuning can
+    // change it)
+    h->gather_dense = h->proj.tc ? 3 : 0;
     return HUB_OK;
 }
 

@@ -310,42 +310,45 @@ __global__ void k_fill_tc(const int4* __restrict__ bent, const int2* __restrict_
 // ---------------------------------------------------------------------------- scatter
 // Y[g(p), n] += alpha sum_f phi_f(p) W[frow(f), n] per brick: one unit per (brick, 128-orbital
 // tile) holds every entry of the brick (so one unit writes each Y element it touches), its
-// functions concatenated in chunks of 32 (each entry padded to a multiple of 32).  Per chunk:
+// functions concatenated and padded to chunks of 32.  Per chunk:
 // A = the values [128 points x 32 functions] of each half of the brick (table layout, bulk
 // copies), B = W^T [128 orbitals x 32 functions] gathered from W's rows and split hi / lo by
 // four builder warps, and D_half[128 points x 128 orbitals] += A_hi B_hi + A_hi B_lo +
 // A_lo B_hi in TMEM (one accumulator per half; the correction terms ride in it: an error of
-// the projector term far below the float H bound).  Four epilogue warps read D 32 orbitals
-// at a time into a shared tile [32 orbitals][256 points] and add alpha D to Y in runs of 8
-// points (32 bytes: one x-row of the brick per lane), while the MMAs of the next unit run in
-// the other TMEM accumulator.
+// the projector term far below the float H bound).  Four epilogue warps read D 16 orbitals
+// at a time, write alpha D into a shared tile [16 orbitals][256 points] (the layout of a
+// tensor-map box of 8 x 8 x 4 points x 16 orbitals of Y) and one thread adds the tile to Y
+// with a TMA reduce-add (the read-modify-write of Y happens in L2; out-of-grid points and
+// orbitals beyond ncol are clipped by the tensor map), two tiles alternating, while the MMAs
+// of the next unit run in the other TMEM accumulator.
 constexpr int ST_KC = 32;                          // functions per chunk
 constexpr int ST_AB = 2 * GT_M * ST_KC * 4;        // 32 KB: values of both halves for one chunk
 constexpr int ST_BB = GT_M * ST_KC * 4;            // 16 KB: one W^T chunk
 constexpr int ST_STAGE = 2 * ST_AB + 2 * ST_BB;    // values hi, lo; W^T hi, lo
 constexpr int ST_S = 2;
-constexpr int ST_EO = 32;                          // orbitals per epilogue tile
-constexpr int ST_EB = ST_EO * BRP * 4;             // 32 KB epilogue tile
-constexpr size_t ST_SMEM = (size_t)ST_S * ST_STAGE + ST_EB + 1024;
+constexpr int ST_EO = 16;                          // orbitals per epilogue tile
+constexpr int ST_EB = ST_EO * BRP * 4;             // 16 KB epilogue tile
+constexpr size_t ST_SMEM = (size_t)ST_S * ST_STAGE + 2 * ST_EB + 1024;
 constexpr uint32_t ST_TMEM_COLS = 512;             // two units x two halves x 128 orbitals
 constexpr int ST_THREADS = 320;                    // load, MMA, 4 builder and 4 epilogue warps
 
 struct StcArgs {
     float* Y;
     long ld;
-    const int4* sbrick;   // per used brick: brick, float offset of its values, function slots K
+    const int4* sbrick;   // per used brick: brick, float offset of its values, function slots
+                          // K (a multiple of 32), functions (K without the padding)
     const int* sfrow;     // per function slot (value offset / 256): row of W, or -1
     const float* vhi;
     const float* vlo;
     const float* W;       // [nproj x ncol]
     float alpha;
     const double* alpha_dev;
-    int ncol, n1, n2, n3, nbx, nby, nunits, ctiles;
+    int ncol, n1, n2, n3, nbx, nby, nbricks, ctiles;
     int* flags;
 };
 
 __global__ void __launch_bounds__(ST_THREADS, 1)
-k_scatter_tc(StcArgs a) {
+k_scatter_tc(const __grid_constant__ CUtensorMap ymap, StcArgs a) {
     extern __shared__ __align__(1024) unsigned char dsm[];
     unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full_bar[ST_S], lo_bar[ST_S], empty_bar[ST_S], tfull_bar[2], tempty_bar[2],
@@ -355,7 +358,11 @@ k_scatter_tc(StcArgs a) {
     __shared__ int issued_sh;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nu = (a.nunits - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    // units of this CTA: its bricks blockIdx.x, + gridDim.x, ..., each with its orbital tiles
+    // one after another (the brick's values, read from memory for the first tile, come from
+    // L2 for the others)
+    const int nu = (a.nbricks - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x * a.ctiles;
+    auto brick_of = [&](int uu) { return (int)blockIdx.x + (uu / a.ctiles) * (int)gridDim.x; };
     const float alpha = a.alpha_dev ? (float)a.alpha_dev[0] : a.alpha;
 
     if (threadIdx.x == 0) {
@@ -387,8 +394,7 @@ k_scatter_tc(StcArgs a) {
         if (lane == 0) {
             int i = 0;
             for (int uu = 0; uu < nu && !abort_flag; ++uu) {
-                const int u = (int)blockIdx.x + uu * (int)gridDim.x;
-                const int4 B = a.sbrick[u / a.ctiles];
+                const int4 B = a.sbrick[brick_of(uu)];
                 bool stop = false;
                 for (int c = 0; c < B.z / ST_KC; ++c, ++i) {
                     const int s = i % ST_S;
@@ -408,8 +414,7 @@ k_scatter_tc(StcArgs a) {
             const uint32_t idesc = instr_desc_tf32(GT_M, GT_M);
             int i = 0;
             for (int uu = 0; uu < nu && !abort_flag; ++uu) {
-                const int u = (int)blockIdx.x + uu * (int)gridDim.x;
-                const int4 B = a.sbrick[u / a.ctiles];
+                const int4 B = a.sbrick[brick_of(uu)];
                 const int buf = uu & 1;
                 if (uu >= 2 && !mbar_wait(&tempty_bar[buf], ((uu >> 1) - 1) & 1, &abort_flag)) break;
                 tc_fence_after();
@@ -420,6 +425,7 @@ k_scatter_tc(StcArgs a) {
                         !mbar_wait(&lo_bar[s], (i / ST_S) & 1, &abort_flag)) { stop = true; break; }
                     tc_fence_after();
                     unsigned char* st = ring + (size_t)s * ST_STAGE;
+                    const int kval = B.w - c * ST_KC;           // functions of this chunk
                     const uint64_t bh = smem_desc(st + 2 * ST_AB), bl = smem_desc(st + 2 * ST_AB + ST_BB);
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
@@ -427,6 +433,7 @@ k_scatter_tc(StcArgs a) {
                         const uint64_t ah = smem_desc(st + h * (ST_AB / 2)), al = smem_desc(st + ST_AB + h * (ST_AB / 2));
 #pragma unroll
                         for (int kk = 0; kk < ST_KC / 8; ++kk) {
+                            if (kk * 8 >= kval) break;      // padding slots of the last chunk: zeros
                             const uint64_t ko = (uint64_t)(kk * 32) >> 4;
                             mma_tf32(dcol, ah + ko, bh + ko, idesc, (c > 0 || kk > 0) ? 1u : 0u);
                             mma_tf32(dcol, ah + ko, bl + ko, idesc, 1u);
@@ -441,37 +448,56 @@ k_scatter_tc(StcArgs a) {
             mma_commit(&done_bar);
         }
     } else if (warp < 6) {
-        // builders: W^T chunks, split hi / lo
+        // builders: W^T chunks, split hi / lo.  The W values of the next chunk are loaded
+        // (32 independent loads per thread) before the wait for this chunk's stage, so their
+        // latency overlaps the wait and the stores.
         const int t = threadIdx.x - 64;                 // orbital row of the W^T tile
-        int i = 0;
-        bool stop = false;
-        for (int uu = 0; uu < nu && !stop; ++uu) {
-            const int u = (int)blockIdx.x + uu * (int)gridDim.x;
-            const int bi = u / a.ctiles, ct = u - bi * a.ctiles;
+        auto load = [&](int uu, int c, float (&v)[ST_KC]) {
+            const int bi = brick_of(uu), ct = uu % a.ctiles;
             const int4 B = a.sbrick[bi];
             const int col = ct * GT_M + t;
-            const int* frow = a.sfrow + (size_t)B.y / BRP;
-            for (int c = 0; c < B.z / ST_KC; ++c, ++i) {
+            const int4* fr = reinterpret_cast<const int4*>(a.sfrow + (size_t)B.y / BRP + (size_t)c * ST_KC);
+#pragma unroll
+            for (int f4 = 0; f4 < ST_KC / 4; ++f4) {
+                const int4 r = fr[f4];
+                const bool cin = col < a.ncol;
+                v[4 * f4 + 0] = (r.x >= 0 && cin) ? a.W[(size_t)r.x * a.ncol + col] : 0.f;
+                v[4 * f4 + 1] = (r.y >= 0 && cin) ? a.W[(size_t)r.y * a.ncol + col] : 0.f;
+                v[4 * f4 + 2] = (r.z >= 0 && cin) ? a.W[(size_t)r.z * a.ncol + col] : 0.f;
+                v[4 * f4 + 3] = (r.w >= 0 && cin) ? a.W[(size_t)r.w * a.ncol + col] : 0.f;
+            }
+        };
+        auto nchunks = [&](int uu) { return a.sbrick[brick_of(uu)].z / ST_KC; };
+        if (nu > 0) {
+            float cur[ST_KC], nxt[ST_KC];
+            int uu = 0, c = 0, i = 0;
+            load(0, 0, cur);
+            while (true) {
+                int nuu = uu, nc = c + 1;
+                if (nc == nchunks(uu)) { nuu = uu + 1; nc = 0; }
+                const bool more = nuu < nu;
+                if (more) load(nuu, nc, nxt);
                 const int s = i % ST_S;
                 const bool ok = i < ST_S || mbar_wait(&empty_bar[s], ((i / ST_S) - 1) & 1, &abort_flag);
-                if (__any_sync(0xffffffffu, !ok)) { stop = true; break; }
+                if (__any_sync(0xffffffffu, !ok)) break;
                 unsigned char* st = ring + (size_t)s * ST_STAGE + 2 * ST_AB;
-#pragma unroll 2
-                for (int f4 = 0; f4 < ST_KC / 4; ++f4) {
-                    uint32_t v[4];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int r = frow[c * ST_KC + f4 * 4 + q];
-                        v[q] = (r >= 0 && col < a.ncol) ? __float_as_uint(a.W[(size_t)r * a.ncol + col]) : 0u;
-                    }
+                for (int f4 = 0; f4 < ST_KC / 4; ++f4) {
+                    const uint32_t v0 = __float_as_uint(cur[4 * f4]), v1 = __float_as_uint(cur[4 * f4 + 1]);
+                    const uint32_t v2 = __float_as_uint(cur[4 * f4 + 2]), v3 = __float_as_uint(cur[4 * f4 + 3]);
                     const uint32_t off = (uint32_t)t * 128 + ((uint32_t)(f4 ^ (t & 7)) << 4);
-                    *reinterpret_cast<uint4*>(st + off) = make_uint4(split_hi(v[0]), split_hi(v[1]), split_hi(v[2]),
-                                                                    split_hi(v[3]));
+                    *reinterpret_cast<uint4*>(st + off) = make_uint4(split_hi(v0), split_hi(v1), split_hi(v2), split_hi(v3));
                     *reinterpret_cast<uint4*>(st + ST_BB + off) =
-                        make_uint4(split_lo(v[0]), split_lo(v[1]), split_lo(v[2]), split_lo(v[3]));
+                        make_uint4(split_lo(v0), split_lo(v1), split_lo(v2), split_lo(v3));
                 }
                 fence_proxy_async();
                 mbar_arrive(&lo_bar[s]);
+                ++i;
+                if (!more) break;
+#pragma unroll
+                for (int k = 0; k < ST_KC; ++k) cur[k] = nxt[k];
+                uu = nuu;
+                c = nc;
             }
         }
     } else {
@@ -480,10 +506,10 @@ k_scatter_tc(StcArgs a) {
         const int quad = warp & 3;
         const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
         const int prow = 32 * quad + lane;
-        float* tile = reinterpret_cast<float*>(ring + (size_t)ST_S * ST_STAGE);    // [32 orbitals][256 points]
+        float* tiles = reinterpret_cast<float*>(ring + (size_t)ST_S * ST_STAGE);   // 2 x [16 orbitals][256 points]
+        int ep = 0;                                     // tiles written so far
         for (int uu = 0; uu < nu; ++uu) {
-            const int u = (int)blockIdx.x + uu * (int)gridDim.x;
-            const int bi = u / a.ctiles, ct = u - bi * a.ctiles;
+            const int bi = brick_of(uu), ct = uu % a.ctiles;
             const int4 B = a.sbrick[bi];
             const int buf = uu & 1;
             // the four epilogue warps go on or stop together (they share named barrier 1, which
@@ -495,60 +521,30 @@ k_scatter_tc(StcArgs a) {
             if (!all) break;
             tc_fence_after();
             const int bx = B.x % a.nbx, by = (B.x / a.nbx) % a.nby, bz = B.x / (a.nbx * a.nby);
-            for (int o0 = 0; o0 < GT_M; o0 += ST_EO) {
+            for (int o0 = 0; B.z > 0 && o0 < GT_M && ct * GT_M + o0 < a.ncol; o0 += ST_EO, ++ep) {
+                float v0[16], v1[16];
+                tmem_ld16(tmem + lane_base + (uint32_t)(buf * 256 + o0), v0);
+                tmem_ld16(tmem + lane_base + (uint32_t)(buf * 256 + GT_M + o0), v1);
+                float* tile = tiles + (ep & 1) * (ST_EO * BRP);
+                // the tile's previous reduce (two tiles back) has finished reading it
+                if (t == 0) bulk_wait_read<1>();
+                asm volatile("bar.sync 1, 128;" ::: "memory");
 #pragma unroll
-                for (int h = 0; h < 2; ++h)
-#pragma unroll
-                    for (int sub = 0; sub < ST_EO; sub += 16) {
-                        float v[16];
-                        tmem_ld16(tmem + lane_base + (uint32_t)(buf * 256 + h * GT_M + o0 + sub), v);
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) tile[(sub + q) * BRP + h * GT_M + prow] = v[q];
-                    }
+                for (int q = 0; q < 16; ++q) {
+                    tile[q * BRP + prow] = alpha * v0[q];
+                    tile[q * BRP + GT_M + prow] = alpha * v1[q];
+                }
+                fence_proxy_async();
                 asm volatile("bar.sync 1, 128;" ::: "memory");      // the tile is complete
-                // Y update: pair j = (orbital j / 32, x-row j % 32 of the brick), 8 points each;
-                // every load of the thread's pairs is issued before the first store
-                constexpr int NPAIR = ST_EO * 32 / 128;
-                float* yp[NPAIR];
-                float4 y0[NPAIR], y1[NPAIR];
-                uint32_t has = 0, has_hi = 0;
-#pragma unroll
-                for (int k = 0; k < NPAIR; ++k) {
-                    const int j = k * 128 + t;
-                    const int o = j >> 5, r = j & 31;
-                    const int n = ct * GT_M + o0 + o;
-                    const int x = 8 * bx, y = 8 * by + (r & 7), z = 4 * bz + (r >> 3);
-                    yp[k] = a.Y + (size_t)n * a.ld + x + (size_t)a.n1 * (y + (size_t)a.n2 * z);
-                    if (n < a.ncol && y < a.n2 && z < a.n3 && x < a.n1) {
-                        has |= 1u << k;
-                        y0[k] = *reinterpret_cast<const float4*>(yp[k]);
-                        if (x + 4 < a.n1) {
-                            has_hi |= 1u << k;
-                            y1[k] = *reinterpret_cast<const float4*>(yp[k] + 4);
-                        }
-                    }
+                if (t == 0) {
+                    tma_reduce_add_4d(&ymap, tile, 8 * bx, 8 * by, 4 * bz, ct * GT_M + o0);
+                    bulk_commit();
                 }
-#pragma unroll
-                for (int k = 0; k < NPAIR; ++k) {
-                    if (!(has >> k & 1)) continue;
-                    const int j = k * 128 + t;
-                    const float4* tp = reinterpret_cast<const float4*>(tile + (j >> 5) * BRP + 8 * (j & 31));
-                    const float4 d0 = tp[0];
-                    y0[k].x = fmaf(alpha, d0.x, y0[k].x); y0[k].y = fmaf(alpha, d0.y, y0[k].y);
-                    y0[k].z = fmaf(alpha, d0.z, y0[k].z); y0[k].w = fmaf(alpha, d0.w, y0[k].w);
-                    *reinterpret_cast<float4*>(yp[k]) = y0[k];
-                    if (has_hi >> k & 1) {
-                        const float4 d1 = tp[1];
-                        y1[k].x = fmaf(alpha, d1.x, y1[k].x); y1[k].y = fmaf(alpha, d1.y, y1[k].y);
-                        y1[k].z = fmaf(alpha, d1.z, y1[k].z); y1[k].w = fmaf(alpha, d1.w, y1[k].w);
-                        *reinterpret_cast<float4*>(yp[k] + 4) = y1[k];
-                    }
-                }
-                asm volatile("bar.sync 1, 128;" ::: "memory");      // the tile may be refilled
             }
             tc_fence_before();
             mbar_arrive(&tempty_bar[buf]);
         }
+        if (t == 0) bulk_wait_all();
     }
     __syncwarp();
     __syncthreads();
@@ -613,7 +609,9 @@ int build_tc_tables(hub_t h, Table& t) {
         k_fill_tc<<<t.nbent, 256, 0, h->stream>>>(t.d_bent, t.d_tcent, t.d_phi, t.d_tchi, t.d_tclo);
     }
     HUB_CUDA_TRY(h, cudaGetLastError());
-    // scatter tables: per used brick its entries' functions in slots of 32-padded entries
+    // scatter tables: per used brick the functions of its entries one after another in
+    // function slots, the brick's count padded to a multiple of 32 (an entry holds 4 to 14
+    // functions: padding each entry to 32 would more than double the MMA work)
     std::vector<int> bfirst(t.nbused + 1), frow(t.npart_rows);
     HUB_CUDA_TRY(h, cudaMemcpy(bfirst.data(), t.d_bfirst, bfirst.size() * sizeof(int), cudaMemcpyDeviceToHost));
     HUB_CUDA_TRY(h, cudaMemcpy(frow.data(), t.d_frow, frow.size() * sizeof(int), cudaMemcpyDeviceToHost));
@@ -624,14 +622,18 @@ int build_tc_tables(hub_t h, Table& t) {
         int K = 0;
         for (int e = bfirst[bi]; e < bfirst[bi + 1]; ++e) {
             const int4& E = bent[e];
-            const int np = (E.y + ST_KC - 1) / ST_KC * ST_KC;
-            for (int f = 0; f < np; ++f) {
-                sfrow.push_back(f < E.y ? frow[E.w + f] : -1);
-                ssrc.push_back(f < E.y ? E.z + f * BRP : -1);
+            for (int f = 0; f < E.y; ++f) {
+                sfrow.push_back(frow[E.w + f]);
+                ssrc.push_back(E.z + f * BRP);
             }
-            K += np;
+            K += E.y;
         }
-        sbrick[bi] = make_int4(bent[bfirst[bi]].x, (int)soff, K, 0);
+        const int Kreal = K;
+        for (; K % ST_KC != 0; ++K) {
+            sfrow.push_back(-1);
+            ssrc.push_back(-1);
+        }
+        sbrick[bi] = make_int4(bent[bfirst[bi]].x, (int)soff, K, Kreal);
         soff += (size_t)K * BRP;
         if (soff >= (1ull << 31)) return HUB_OK;          // keep the SIMT scatter
     }
@@ -706,12 +708,27 @@ int launch_scatter_tc(hub_t h, void* Y, int ncol, int ld, double alpha, const do
     a.nbx = t.nbx;
     a.nby = t.nby;
     a.ctiles = (ncol + GT_M - 1) / GT_M;
-    a.nunits = t.nbused * a.ctiles;
+    a.nbricks = t.nbused;
     a.flags = h->d_flags;
-    const int grid = std::max(1, std::min(a.nunits, h->num_sms));
+    // Y as a 4-D tensor (x, y, z, orbital) for the reduce-add of 8 x 8 x 4-point, 16-orbital
+    // boxes: strides multiples of 16 bytes (n1 and ld multiples of 4), base 16-byte aligned
+    if ((uintptr_t)Y % 16 != 0 || ld % 4 != 0 || h->n1 % 4 != 0)
+        return fail(h, HUB_EINVAL, "tensor-core scatter: block not 16-byte aligned");
+    PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+    int rc;
+    if ((rc = tensor_map_encoder(h, &enc))) return rc;
+    CUtensorMap ymap;
+    const cuuint64_t dims[4] = {(cuuint64_t)h->n1, (cuuint64_t)h->n2, (cuuint64_t)h->n3, (cuuint64_t)ncol};
+    const cuuint64_t strides[3] = {(cuuint64_t)h->n1 * 4, (cuuint64_t)h->n1 * h->n2 * 4, (cuuint64_t)ld * 4};
+    const cuuint32_t box[4] = {8, 8, 4, (cuuint32_t)ST_EO};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    if (enc(&ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, Y, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return fail(h, HUB_ECUDA, "tensor-core scatter: cuTensorMapEncodeTiled failed");
+    const int grid = std::max(1, std::min(a.nbricks, h->num_sms));
     HUB_CUDA_TRY(h, cudaFuncSetAttribute(k_scatter_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ST_SMEM));
     ProfScope ps(h, HUB_K_SCATTER);
-    k_scatter_tc<<<grid, ST_THREADS, ST_SMEM, h->stream>>>(a);
+    k_scatter_tc<<<grid, ST_THREADS, ST_SMEM, h->stream>>>(ymap, a);
     HUB_CUDA_TRY(h, cudaGetLastError());
     return HUB_OK;
 }
