@@ -96,11 +96,15 @@ struct Table {
     int* d_frow = nullptr;            // [npart_rows] global projector row (-1: padding)
     int* d_roff = nullptr;            // [nproj + 1] partial rows of each projector row (CSR)
     int* d_rent = nullptr;
-    // tensor-core form of the brick gather (built with the bricks when n1 % 4 == 0): per
-    // entry its values in the 128-byte-swizzled K-major layout of tcgen05 operands, split as
-    // TF32 hi + lo, functions padded to a multiple of 16
+    // tensor-core form of the brick gather (built with the bricks when n1 % 4 == 0): the
+    // entries of each brick packed into groups of at most 64 functions, per group its values
+    // in the 128-byte-swizzled K-major layout of tcgen05 operands, split as TF32 hi + lo,
+    // function slots padded to a multiple of 16
     int tc = 0;                       // 1 when the arrays below are built
-    int2* d_tcent = nullptr;          // per entry: float offset into d_tchi / d_tclo, padded count
+    int ntcg = 0;                     // groups
+    int4* d_tcg = nullptr;            // per group: brick, float offset into d_tchi / d_tclo,
+                                      // slots NP, first slot
+    int* d_tcg_row = nullptr;         // per slot: partial row of its function (-1: padding)
     float* d_tchi = nullptr;
     float* d_tclo = nullptr;
     // tensor-core form of the brick scatter: per used brick (brick, float offset, function

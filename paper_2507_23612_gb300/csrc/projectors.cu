@@ -776,7 +776,7 @@ void free_table(Table& t) {
     void* ptrs[] = {t.d_sites, t.d_items, t.d_item_first, t.d_idx, t.d_vals, t.d_csr_off,
                     t.d_csr_ent, t.d_order, t.d_gamma, t.d_hub_sites, t.d_U,
                     t.d_M[0], t.d_M[1], t.d_bent, t.d_bfirst, t.d_phi, t.d_frow, t.d_roff,
-                    t.d_rent, t.d_tcent, t.d_tchi, t.d_tclo, t.d_tcs_brick, t.d_tcs_frow, t.d_tcs_hi,
+                    t.d_rent, t.d_tcg, t.d_tcg_row, t.d_tchi, t.d_tclo, t.d_tcs_brick, t.d_tcs_frow, t.d_tcs_hi,
                     t.d_tcs_lo};
     for (void* p : ptrs)
         if (p) cudaFree(p);

@@ -1,13 +1,16 @@
 // Tensor-core form of the projector gather (Sec. II.B: the inner products of all functions
 // of an atom are computed together), for real float blocks.  The brick tables group, per
 // 8 x 8 x 4 brick of the grid, the functions of the sites that touch it (entries of at most
-// 64).  Per entry and per tile of 128 orbitals the partial inner products
+// 64), and the tensor-core tables pack each brick's entries into groups of at most 64
+// functions (one group per brick on average on the rutile workload, against six entries).
+// Per group and per tile of 128 orbitals the partial inner products
 //
-//   part[prow + f, n] = sum_{p in brick} phi_f(p) X[g(p), n]
+//   part[prow(f), n] = sum_{p in brick} phi_f(p) X[g(p), n]
 //
 // are one tcgen05 product D[128 orbitals x NP functions] = X_b^T Phi_b over the K = 256
 // points of the brick (summed per function over its bricks afterwards, as for the SIMT brick
-// gather).  Both operands are split for TF32: hi = the float rounded to the 10 TF32
+// gather), so that the brick's X is loaded and split once for all the functions of the
+// group.  Both operands are split for TF32: hi = the float rounded to the 10 TF32
 // significand bits, lo = value - hi (exact) rounded the same way, and D = hi*hi + (hi*lo +
 // lo*hi) with FP32 accumulation in TMEM, about 22 significant bits (the float path's own
 // accuracy) and no rounding bias.  The two small correction
@@ -23,7 +26,7 @@
 // projector values are stored in the same layout when the tables are built (one row per
 // function and slice) and copied with cp.async.bulk.
 //
-// Kernel: persistent CTAs of 320 threads over (entry, orbital tile) units.  Warp 0 issues
+// Kernel: persistent CTAs of 320 threads over (group, orbital tile) units.  Warp 0 issues
 // the value copies into a two-stage ring, warp 1 issues the MMAs into one of two TMEM
 // accumulators, warps 2-5 load and split the X slices, and warps 6-9, once a unit's product
 // is complete, read its accumulator (tcgen05.ld) and write the partial rows while the next
@@ -43,7 +46,7 @@ namespace {
 constexpr int GT_M = 128;                     // orbitals per tile (MMA M, TMEM lanes)
 constexpr int GT_K = 32;                      // brick points per slice (128 bytes of FP32)
 constexpr int GT_SLICES = BRP / GT_K;         // 8 slices per brick
-constexpr int GT_NP = BRF;                    // functions per entry at most (MMA N)
+constexpr int GT_NP = BRF;                    // functions per group at most (MMA N)
 constexpr int GT_S = 2;                       // ring stages
 constexpr int GT_XB = GT_M * GT_K * 4;        // 16 KB: one X slice
 constexpr int GT_BB = GT_NP * GT_K * 4;       // 8 KB: one value slice at most
@@ -55,8 +58,8 @@ constexpr uint32_t kTf32Hi = 0xFFFFE000u;     // sign, exponent and the 10 TF32 
 
 struct GtcArgs {
     const float* X;       // block, column-major with leading dimension ld
-    const int4* bent;     // per entry: brick, fp, SIMT value offset, first partial row
-    const int2* tcent;    // per entry: float offset of its tensor-core values, padded count NP
+    const int4* grp;      // per group: brick, float offset of its values, slots NP, first slot
+    const int* grow;      // per slot: partial row of its function (-1: padding)
     const float* vhi;
     const float* vlo;
     float* part;
@@ -83,9 +86,9 @@ struct SliceLoad {
     float4 v[8];
 };
 
-__device__ __forceinline__ void load_slice(const GtcArgs& a, int e, int ct, int q, int c, SliceLoad& L) {
-    const int4 E = a.bent[e];
-    const int bx = E.x % a.nbx, by = (E.x / a.nbx) % a.nby, bz = E.x / (a.nbx * a.nby);
+__device__ __forceinline__ void load_slice(const GtcArgs& a, int g, int ct, int q, int c, SliceLoad& L) {
+    const int brick = a.grp[g].x;
+    const int bx = brick % a.nbx, by = (brick / a.nbx) % a.nby, bz = brick / (a.nbx * a.nby);
     const int z = 4 * bz + (q >> 1);
 #pragma unroll
     for (int it = 0; it < 8; ++it) {
@@ -143,15 +146,15 @@ k_gather_tc(GtcArgs a) {
             int i = 0;
             for (int uu = 0; uu < nu && !abort_flag; ++uu) {
                 const int u = (int)blockIdx.x + uu * (int)gridDim.x;
-                const int2 T = a.tcent[u / a.ctiles];
-                const uint32_t vb = (uint32_t)T.y * GT_K * 4;
+                const int4 G = a.grp[u / a.ctiles];
+                const uint32_t vb = (uint32_t)G.z * GT_K * 4;
                 bool stop = false;
                 for (int q = 0; q < GT_SLICES; ++q, ++i) {
                     const int s = i % GT_S;
                     if (i >= GT_S && !mbar_wait(&empty_bar[s], ((i / GT_S) - 1) & 1, &abort_flag)) { stop = true; break; }
                     unsigned char* st = ring + (size_t)s * GT_STAGE;
                     mbar_expect_tx(&full_bar[s], 2 * vb);
-                    const size_t off = (size_t)T.x + (size_t)q * GT_K * T.y;
+                    const size_t off = (size_t)G.y + (size_t)q * GT_K * G.z;
                     bulk_load(st + 2 * GT_XB, a.vhi + off, vb, &full_bar[s]);
                     bulk_load(st + 2 * GT_XB + GT_BB, a.vlo + off, vb, &full_bar[s]);
                     issued_sh = i + 1;
@@ -164,12 +167,12 @@ k_gather_tc(GtcArgs a) {
             int i = 0;
             for (int uu = 0; uu < nu && !abort_flag; ++uu) {
                 const int u = (int)blockIdx.x + uu * (int)gridDim.x;
-                const int2 T = a.tcent[u / a.ctiles];
+                const int4 G = a.grp[u / a.ctiles];
                 const int buf = uu & 1;
                 // the accumulator's previous unit must have been read out
                 if (uu >= 2 && !mbar_wait(&tempty_bar[buf], ((uu >> 1) - 1) & 1, &abort_flag)) break;
                 tc_fence_after();
-                const uint32_t idesc = instr_desc_tf32(GT_M, T.y);
+                const uint32_t idesc = instr_desc_tf32(GT_M, G.z);
                 const uint32_t dcol = tmem + (uint32_t)(2 * buf * GT_NP);      // hi * hi
                 const uint32_t ccol = dcol + (uint32_t)GT_NP;                  // hi * lo + lo * hi
                 bool stop = false;
@@ -247,18 +250,23 @@ k_gather_tc(GtcArgs a) {
             const bool ok = mbar_wait(&tfull_bar[buf], (uu >> 1) & 1, &abort_flag);
             if (__any_sync(0xffffffffu, !ok)) break;
             tc_fence_after();
-            const int4 E = a.bent[e];
-            const int2 T = a.tcent[e];
+            const int4 G = a.grp[e];
             const int col = ct * GT_M + row;
-            float* out = a.part + (size_t)E.w * a.ncol + col;
-            for (int c0 = 0; c0 < T.y; c0 += 16) {
+            for (int c0 = 0; c0 < G.z; c0 += 16) {
                 float v[16], w[16];
                 tmem_ld16(tmem + lane_base + (uint32_t)(2 * buf * GT_NP + c0), v);
                 tmem_ld16(tmem + lane_base + (uint32_t)(2 * buf * GT_NP + GT_NP + c0), w);
+                const int4* gr = reinterpret_cast<const int4*>(a.grow + G.w + c0);   // 16 slots
+                int r[16];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int4 q4 = gr[k];
+                    r[4 * k] = q4.x; r[4 * k + 1] = q4.y; r[4 * k + 2] = q4.z; r[4 * k + 3] = q4.w;
+                }
                 if (col < a.ncol) {
 #pragma unroll
                     for (int f = 0; f < 16; ++f)
-                        if (c0 + f < E.y) out[(size_t)(c0 + f) * a.ncol] = v[f] + w[f];
+                        if (r[f] >= 0) a.part[(size_t)r[f] * a.ncol + col] = v[f] + w[f];
                 }
             }
             tc_fence_before();
@@ -285,23 +293,24 @@ k_gather_tc(GtcArgs a) {
     }
 }
 
-// tensor-core values of every entry from the SIMT brick values: entry e's block holds, per
-// slice q of 32 points, NP rows of 128 bytes (row f = function f, zero beyond fp), point
-// kk of the slice in 16-byte chunk kk / 4 XOR (f % 8), split TF32 hi + lo
-__global__ void k_fill_tc(const int4* __restrict__ bent, const int2* __restrict__ tcent, const float* __restrict__ phi,
+// tensor-core values of every group from the SIMT brick values: group g's block holds, per
+// slice q of 32 points, NP rows of 128 bytes (row r = function slot r, zero for padding),
+// point kk of the slice in 16-byte chunk kk / 4 XOR (r % 8), split TF32 hi + lo; slot r takes
+// its values from the SIMT brick values at src[first slot + r] (-1: padding)
+__global__ void k_fill_tc(const int4* __restrict__ grp, const int* __restrict__ src, const float* __restrict__ phi,
                           float* __restrict__ vhi, float* __restrict__ vlo) {
-    const int e = blockIdx.x;
-    const int4 E = bent[e];
-    const int2 T = tcent[e];
-    const int n = T.y * BRP;
+    const int4 G = grp[blockIdx.x];
+    const int np = G.z;
+    const int n = np * BRP;
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        const int q = t / (T.y * GT_K);
-        const int r = (t / GT_K) % T.y;
+        const int q = t / (np * GT_K);
+        const int r = (t / GT_K) % np;
         const int kk = t % GT_K;
         const int k = q * GT_K + kk;
-        const float v = r < E.y ? phi[(size_t)E.z + (size_t)r * BRP + brick_slot(k)] : 0.f;
+        const int o = src[G.w + r];
+        const float v = o >= 0 ? phi[(size_t)o + brick_slot(k)] : 0.f;
         const uint32_t u = __float_as_uint(v);
-        const size_t dst = (size_t)T.x + (size_t)q * GT_K * T.y + (size_t)r * GT_K + ((((kk >> 2) ^ (r & 7)) << 2) | (kk & 3));
+        const size_t dst = (size_t)G.y + (size_t)q * GT_K * np + (size_t)r * GT_K + ((((kk >> 2) ^ (r & 7)) << 2) | (kk & 3));
         vhi[dst] = __uint_as_float(split_hi(u));
         vlo[dst] = __uint_as_float(split_lo(u));
     }
@@ -592,29 +601,57 @@ int build_tc_tables(hub_t h, Table& t) {
     if (!t.dense || h->n1 % 4 != 0 || t.nbent == 0) return HUB_OK;
     std::vector<int4> bent(t.nbent);
     HUB_CUDA_TRY(h, cudaMemcpy(bent.data(), t.d_bent, bent.size() * sizeof(int4), cudaMemcpyDeviceToHost));
-    std::vector<int2> tcent(t.nbent);
+    std::vector<int> bfirst(t.nbused + 1), frow(t.npart_rows);
+    HUB_CUDA_TRY(h, cudaMemcpy(bfirst.data(), t.d_bfirst, bfirst.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    HUB_CUDA_TRY(h, cudaMemcpy(frow.data(), t.d_frow, frow.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    // gather groups: the entries of each used brick packed in order into groups of at most
+    // GT_NP functions; per function slot its value offset and its partial row
+    std::vector<int4> grp;
+    std::vector<int> gsrc, grow;
     size_t off = 0;
-    for (int e = 0; e < t.nbent; ++e) {
-        const int np = std::max(16, (bent[e].y + 15) / 16 * 16);
-        tcent[e] = make_int2((int)off, np);
-        off += (size_t)np * BRP;
-        if (off >= (1ull << 31)) return HUB_OK;          // keep the SIMT forms
+    for (int bi = 0; bi < t.nbused; ++bi) {
+        int e = bfirst[bi];
+        while (e < bfirst[bi + 1]) {
+            if (bent[e].y > GT_NP) return HUB_OK;            // keep the SIMT forms
+            const int first = (int)gsrc.size();
+            int nf = 0;
+            for (; e < bfirst[bi + 1] && nf + bent[e].y <= GT_NP; ++e) {
+                for (int f = 0; f < bent[e].y; ++f) {
+                    gsrc.push_back(bent[e].z + f * BRP);
+                    grow.push_back(bent[e].w + f);
+                }
+                nf += bent[e].y;
+            }
+            const int np = std::max(16, (nf + 15) / 16 * 16);
+            for (int f = nf; f < np; ++f) {
+                gsrc.push_back(-1);
+                grow.push_back(-1);
+            }
+            grp.push_back(make_int4(bent[bfirst[bi]].x, (int)off, np, first));
+            off += (size_t)np * BRP;
+            if (off >= (1ull << 31)) return HUB_OK;          // keep the SIMT forms
+        }
     }
-    HUB_CUDA_TRY(h, cudaMalloc((void**)&t.d_tcent, tcent.size() * sizeof(int2)));
-    HUB_CUDA_TRY(h, cudaMemcpy(t.d_tcent, tcent.data(), tcent.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    t.ntcg = (int)grp.size();
+    int* d_gsrc = nullptr;
+    HUB_CUDA_TRY(h, cudaMalloc((void**)&t.d_tcg, grp.size() * sizeof(int4)));
+    HUB_CUDA_TRY(h, cudaMemcpy(t.d_tcg, grp.data(), grp.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    HUB_CUDA_TRY(h, cudaMalloc((void**)&t.d_tcg_row, grow.size() * sizeof(int)));
+    HUB_CUDA_TRY(h, cudaMemcpy(t.d_tcg_row, grow.data(), grow.size() * sizeof(int), cudaMemcpyHostToDevice));
+    HUB_CUDA_TRY(h, cudaMalloc((void**)&d_gsrc, gsrc.size() * sizeof(int)));
+    HUB_CUDA_TRY(h, cudaMemcpy(d_gsrc, gsrc.data(), gsrc.size() * sizeof(int), cudaMemcpyHostToDevice));
     HUB_CUDA_TRY(h, cudaMalloc((void**)&t.d_tchi, off * sizeof(float)));
     HUB_CUDA_TRY(h, cudaMalloc((void**)&t.d_tclo, off * sizeof(float)));
     {
         ProfScope ps(h, HUB_K_TABLE);
-        k_fill_tc<<<t.nbent, 256, 0, h->stream>>>(t.d_bent, t.d_tcent, t.d_phi, t.d_tchi, t.d_tclo);
+        k_fill_tc<<<t.ntcg, 256, 0, h->stream>>>(t.d_tcg, d_gsrc, t.d_phi, t.d_tchi, t.d_tclo);
     }
     HUB_CUDA_TRY(h, cudaGetLastError());
+    HUB_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    cudaFree(d_gsrc);
     // scatter tables: per used brick the functions of its entries one after another in
     // function slots, the brick's count padded to a multiple of 32 (an entry holds 4 to 14
     // functions: padding each entry to 32 would more than double the MMA work)
-    std::vector<int> bfirst(t.nbused + 1), frow(t.npart_rows);
-    HUB_CUDA_TRY(h, cudaMemcpy(bfirst.data(), t.d_bfirst, bfirst.size() * sizeof(int), cudaMemcpyDeviceToHost));
-    HUB_CUDA_TRY(h, cudaMemcpy(frow.data(), t.d_frow, frow.size() * sizeof(int), cudaMemcpyDeviceToHost));
     std::vector<int4> sbrick(t.nbused);
     std::vector<int> sfrow, ssrc;
     size_t soff = 0;
@@ -664,8 +701,8 @@ int launch_gather_tc(hub_t h, const void* X, int ncol, int ld) {
     if (ncol == 0) return HUB_OK;
     GtcArgs a{};
     a.X = (const float*)X;
-    a.bent = t.d_bent;
-    a.tcent = t.d_tcent;
+    a.grp = t.d_tcg;
+    a.grow = t.d_tcg_row;
     a.vhi = t.d_tchi;
     a.vlo = t.d_tclo;
     a.part = (float*)h->d_part;
@@ -677,7 +714,7 @@ int launch_gather_tc(hub_t h, const void* X, int ncol, int ld) {
     a.nbx = t.nbx;
     a.nby = t.nby;
     a.ctiles = (ncol + GT_M - 1) / GT_M;
-    a.nunits = t.nbent * a.ctiles;
+    a.nunits = t.ntcg * a.ctiles;
     a.flags = h->d_flags;
     const int grid = std::max(1, std::min(a.nunits, 2 * h->num_sms));
     HUB_CUDA_TRY(h, cudaFuncSetAttribute(k_gather_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GT_SMEM));
