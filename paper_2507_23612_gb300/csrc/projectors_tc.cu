@@ -21,8 +21,9 @@
 // Operands are K-major in the 128-byte-swizzled layout of tcgen05 (rows of 128 bytes = 32
 // brick points, 8-row groups of 1024 bytes, the 16-byte chunk c of row r stored at chunk
 // c XOR (r % 8)).  An X slice (32 brick points = 4 rows of 8 points of one z-plane, for 128
-// orbitals: one row per orbital) is read from global memory by the converter warps in
-// 16-byte loads (8 lanes per orbital, one slice ahead) and written split into hi and lo; the
+// orbitals: one row per orbital) is copied from global memory by the converter warps with
+// 16-byte cp.async (8 lanes per orbital, six slices in flight) into raw slice buffers, read
+// back by the same threads and written split into hi and lo; the
 // projector values are stored in the same layout when the tables are built (one row per
 // function and slice) and copied with cp.async.bulk.
 //
@@ -53,7 +54,8 @@ constexpr int GT_BB = GT_NP * GT_K * 4;       // 8 KB: one value slice at most
 constexpr int GT_STAGE = 2 * GT_XB + 2 * GT_BB;   // X hi, X lo, values hi, values lo
 constexpr int GT_THREADS = 320;           // producer, MMA, 4 converter and 4 epilogue warps
 constexpr uint32_t GT_TMEM_COLS = 4 * GT_NP;  // two units in flight x (hi*hi, corrections)
-constexpr size_t GT_SMEM = (size_t)GT_S * GT_STAGE + 1024;
+constexpr int GT_D = 6;                       // raw X slices in flight per converter thread
+constexpr size_t GT_SMEM = (size_t)GT_S * GT_STAGE + (size_t)GT_D * GT_XB + 1024;
 constexpr uint32_t kTf32Hi = 0xFFFFE000u;     // sign, exponent and the 10 TF32 significand bits
 
 struct GtcArgs {
@@ -79,14 +81,12 @@ __device__ __forceinline__ uint32_t split_lo(uint32_t u) {
     return tf32_round(__float_as_uint(__uint_as_float(u) - __uint_as_float(tf32_round(u))));
 }
 
-// the 8 16-byte chunks a converter thread loads for slice q of unit u: chunk j = it * 128 + c
-// of the slice is orbital n = j / 8 of the tile, its 4 points x % 4 = 0..3 at x / 4 = j % 2,
-// y-row (j / 2) % 4
-struct SliceLoad {
-    float4 v[8];
-};
-
-__device__ __forceinline__ void load_slice(const GtcArgs& a, int g, int ct, int q, int c, SliceLoad& L) {
+// the 8 16-byte chunks a converter thread copies for slice q of group g and orbital tile ct:
+// chunk j = it * 128 + c of the slice is orbital n = j / 8 of the tile, its 4 points
+// x % 4 = 0..3 at x / 4 = j % 2, y-row (j / 2) % 4; each lands in the thread's own 16-byte
+// slots of a raw slice buffer (chunk it at (it * 128 + c) * 16), zero-filled outside the
+// grid and beyond ncol.  cp.async keeps GT_D slices in flight without holding registers.
+__device__ __forceinline__ void copy_slice(const GtcArgs& a, int g, int ct, int q, int c, unsigned char* raw) {
     const int brick = a.grp[g].x;
     const int bx = brick % a.nbx, by = (brick / a.nbx) % a.nby, bz = brick / (a.nbx * a.nby);
     const int z = 4 * bz + (q >> 1);
@@ -96,13 +96,14 @@ __device__ __forceinline__ void load_slice(const GtcArgs& a, int g, int ct, int 
         const int n = j >> 3, ch = j & 7;
         const int x = 8 * bx + 4 * (ch & 1), y = 8 * by + 4 * (q & 1) + (ch >> 1);
         const int col = ct * GT_M + n;
-        L.v[it] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (x < a.n1 && y < a.n2 && z < a.n3 && col < a.ncol)
-            L.v[it] = __ldg(reinterpret_cast<const float4*>(a.X + (size_t)col * a.ld + x + (size_t)a.n1 * (y + (size_t)a.n2 * z)));
+        const bool in = x < a.n1 && y < a.n2 && z < a.n3 && col < a.ncol;
+        const float* src = in ? a.X + (size_t)col * a.ld + x + (size_t)a.n1 * (y + (size_t)a.n2 * z) : a.X;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr(raw + (size_t)j * 16)), "l"(src),
+                     "r"(in ? 16 : 0) : "memory");
     }
 }
 
-__global__ void __launch_bounds__(GT_THREADS, 2)
+__global__ void __launch_bounds__(GT_THREADS, 1)
 k_gather_tc(GtcArgs a) {
     extern __shared__ __align__(1024) unsigned char dsm[];
     unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm) + 1023) & ~(uintptr_t)1023);
@@ -200,43 +201,44 @@ k_gather_tc(GtcArgs a) {
             mma_commit(&done_bar);                      // every MMA issued by this thread
         }
     } else if (warp < 6) {
-        // warps 2-5: X slices into the stages (hi and lo), slice after slice over the units.
-        // Waits are decided per warp (all lanes leave together).
+        // warps 2-5: X slices into the stages (hi and lo), slice after slice over the units:
+        // slice i's raw copy was issued GT_D - 1 slices earlier into raw buffer i % GT_D; the
+        // thread reads back only its own chunks, so its cp.async wait is the only sync needed.
+        // Waits on the stages are decided per warp (all lanes leave together).
         const int c = threadIdx.x - 64;
-        SliceLoad L;
-        if (nu > 0) load_slice(a, (int)blockIdx.x / a.ctiles, (int)blockIdx.x % a.ctiles, 0, c, L);
-        int i = 0;
-        bool stop = false;
-        for (int uu = 0; uu < nu && !stop; ++uu) {
-            const int u = (int)blockIdx.x + uu * (int)gridDim.x;
-            const int e = u / a.ctiles, ct = u - e * a.ctiles;
-            for (int q = 0; q < GT_SLICES; ++q, ++i) {
-                const int s = i % GT_S;
-                const bool ok = i < GT_S || mbar_wait(&empty_bar[s], ((i / GT_S) - 1) & 1, &abort_flag);
-                if (__any_sync(0xffffffffu, !ok)) { stop = true; break; }
-                unsigned char* xs = ring + (size_t)s * GT_STAGE;
-#pragma unroll
-                for (int it = 0; it < 8; ++it) {
-                    const int j = it * 128 + c;
-                    const int n = j >> 3, ch = j & 7;
-                    const uint32_t off = (uint32_t)n * 128 + ((uint32_t)(ch ^ (n & 7)) << 4);
-                    const uint4 v = make_uint4(__float_as_uint(L.v[it].x), __float_as_uint(L.v[it].y),
-                                               __float_as_uint(L.v[it].z), __float_as_uint(L.v[it].w));
-                    *reinterpret_cast<uint4*>(xs + off) = make_uint4(split_hi(v.x), split_hi(v.y), split_hi(v.z),
-                                                                    split_hi(v.w));
-                    *reinterpret_cast<uint4*>(xs + GT_XB + off) =
-                        make_uint4(split_lo(v.x), split_lo(v.y), split_lo(v.z), split_lo(v.w));
-                }
-                fence_proxy_async();
-                mbar_arrive(&lo_bar[s]);
-                // the next slice's loads fly while this one is multiplied
-                if (q + 1 < GT_SLICES) load_slice(a, e, ct, q + 1, c, L);
-                else if (uu + 1 < nu) {
-                    const int un = u + (int)gridDim.x;
-                    load_slice(a, un / a.ctiles, un % a.ctiles, 0, c, L);
-                }
+        unsigned char* raw = ring + (size_t)GT_S * GT_STAGE;
+        const int nsl = nu * GT_SLICES;
+        auto issue = [&](int i) {
+            if (i < nsl) {
+                const int u = (int)blockIdx.x + (i / GT_SLICES) * (int)gridDim.x;
+                copy_slice(a, u / a.ctiles, u % a.ctiles, i % GT_SLICES, c, raw + (size_t)(i % GT_D) * GT_XB);
             }
+            asm volatile("cp.async.commit_group;" ::: "memory");     // one group per slice, empty or not
+        };
+        for (int i = 0; i < GT_D - 1; ++i) issue(i);
+        for (int i = 0; i < nsl; ++i) {
+            issue(i + GT_D - 1);
+            const int s = i % GT_S;
+            const bool ok = i < GT_S || mbar_wait(&empty_bar[s], ((i / GT_S) - 1) & 1, &abort_flag);
+            if (__any_sync(0xffffffffu, !ok)) break;
+            asm volatile("cp.async.wait_group %0;" ::"n"(GT_D - 1) : "memory");   // slice i has landed
+            const unsigned char* rs = raw + (size_t)(i % GT_D) * GT_XB;
+            unsigned char* xs = ring + (size_t)s * GT_STAGE;
+#pragma unroll
+            for (int it = 0; it < 8; ++it) {
+                const int j = it * 128 + c;
+                const int n = j >> 3, ch = j & 7;
+                const uint32_t off = (uint32_t)n * 128 + ((uint32_t)(ch ^ (n & 7)) << 4);
+                const uint4 v = *reinterpret_cast<const uint4*>(rs + (size_t)j * 16);
+                *reinterpret_cast<uint4*>(xs + off) = make_uint4(split_hi(v.x), split_hi(v.y), split_hi(v.z),
+                                                                split_hi(v.w));
+                *reinterpret_cast<uint4*>(xs + GT_XB + off) =
+                    make_uint4(split_lo(v.x), split_lo(v.y), split_lo(v.z), split_lo(v.w));
+            }
+            fence_proxy_async();
+            mbar_arrive(&lo_bar[s]);
         }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");        // no copy outlives the CTA
     } else {
         // warps 6-9: each unit's partial rows from its accumulator while the converters and
         // the MMAs go on with the next unit; warp w reads TMEM lanes 32 (w % 4) .. + 31
@@ -716,7 +718,7 @@ int launch_gather_tc(hub_t h, const void* X, int ncol, int ld) {
     a.ctiles = (ncol + GT_M - 1) / GT_M;
     a.nunits = t.ntcg * a.ctiles;
     a.flags = h->d_flags;
-    const int grid = std::max(1, std::min(a.nunits, 2 * h->num_sms));
+    const int grid = std::max(1, std::min(a.nunits, h->num_sms));
     HUB_CUDA_TRY(h, cudaFuncSetAttribute(k_gather_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GT_SMEM));
     ProfScope ps(h, HUB_K_GATHER);
     k_gather_tc<<<grid, GT_THREADS, GT_SMEM, h->stream>>>(a);
