@@ -227,8 +227,8 @@ TRAFFIC_CAPTURES = {
     ("f64", "gather"): (95.82, "projectors.cu", "fc1a61ec662a13cc"),
     ("f64", "scatter"): (50.96, "projectors.cu", "fc1a61ec662a13cc"),
     ("f32", "stencil"): (12.52, "stencil.cu", "7095f36bbcbc94c0"),
-    ("f32", "gather"): (5.76, "projectors_tc.cu", "846a2ab76d1ad794"),
-    ("f32", "scatter"): (10.42, "projectors_tc.cu", "846a2ab76d1ad794"),
+    ("f32", "gather"): (5.71, "projectors_tc.cu", "c1f826507f2e5e4b"),
+    ("f32", "scatter"): (10.42, "projectors_tc.cu", "c1f826507f2e5e4b"),
 }
 
 

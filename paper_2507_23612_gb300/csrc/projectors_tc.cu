@@ -22,13 +22,13 @@
 // brick points, 8-row groups of 1024 bytes, the 16-byte chunk c of row r stored at chunk
 // c XOR (r % 8)).  An X slice (32 brick points = 4 rows of 8 points of one z-plane, for 128
 // orbitals: one row per orbital) is copied from global memory by the converter warps with
-// 16-byte cp.async (8 lanes per orbital, six slices in flight) into raw slice buffers, read
+// 16-byte cp.async (8 lanes per orbital, four slices in flight) into raw slice buffers, read
 // back by the same threads and written split into hi and lo; the
 // projector values are stored in the same layout when the tables are built (one row per
 // function and slice) and copied with cp.async.bulk.
 //
 // Kernel: persistent CTAs of 320 threads over (group, orbital tile) units.  Warp 0 issues
-// the value copies into a two-stage ring, warp 1 issues the MMAs into one of two TMEM
+// the value copies into a three-stage ring, warp 1 issues the MMAs into one of two TMEM
 // accumulators, warps 2-5 load and split the X slices, and warps 6-9, once a unit's product
 // is complete, read its accumulator (tcgen05.ld) and write the partial rows while the next
 // unit is converted and multiplied.  Every mbarrier
@@ -48,13 +48,13 @@ constexpr int GT_M = 128;                     // orbitals per tile (MMA M, TMEM 
 constexpr int GT_K = 32;                      // brick points per slice (128 bytes of FP32)
 constexpr int GT_SLICES = BRP / GT_K;         // 8 slices per brick
 constexpr int GT_NP = BRF;                    // functions per group at most (MMA N)
-constexpr int GT_S = 2;                       // ring stages
+constexpr int GT_S = 3;                       // ring stages (values and split X)
 constexpr int GT_XB = GT_M * GT_K * 4;        // 16 KB: one X slice
 constexpr int GT_BB = GT_NP * GT_K * 4;       // 8 KB: one value slice at most
 constexpr int GT_STAGE = 2 * GT_XB + 2 * GT_BB;   // X hi, X lo, values hi, values lo
 constexpr int GT_THREADS = 320;           // producer, MMA, 4 converter and 4 epilogue warps
 constexpr uint32_t GT_TMEM_COLS = 4 * GT_NP;  // two units in flight x (hi*hi, corrections)
-constexpr int GT_D = 6;                       // raw X slices in flight per converter thread
+constexpr int GT_D = 4;                       // raw X slices in flight per converter thread
 constexpr size_t GT_SMEM = (size_t)GT_S * GT_STAGE + (size_t)GT_D * GT_XB + 1024;
 constexpr uint32_t kTf32Hi = 0xFFFFE000u;     // sign, exponent and the 10 TF32 significand bits
 
