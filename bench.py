@@ -224,8 +224,8 @@ def cpu_oracle_sample(workload: str, seconds: float, cols: int = 2, procs: int =
 # --no-e2e --no-cpu-baseline`; the float gather and scatter are the tensor-core brick forms.
 TRAFFIC_CAPTURES = {
     ("f64", "stencil"): (25.36, "stencil.cu", "7095f36bbcbc94c0"),
-    ("f64", "gather"): (95.82, "projectors.cu", "fc1a61ec662a13cc"),
-    ("f64", "scatter"): (50.96, "projectors.cu", "fc1a61ec662a13cc"),
+    ("f64", "gather"): (95.82, "projectors.cu", "4b61aaf339edd58a"),
+    ("f64", "scatter"): (50.96, "projectors.cu", "4b61aaf339edd58a"),
     ("f32", "stencil"): (12.52, "stencil.cu", "7095f36bbcbc94c0"),
     ("f32", "gather"): (5.71, "projectors_tc.cu", "c1f826507f2e5e4b"),
     ("f32", "scatter"): (10.42, "projectors_tc.cu", "c1f826507f2e5e4b"),
